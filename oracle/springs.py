@@ -1,0 +1,216 @@
+"""Virtual-spring collision response (Sec. II-C, Eq. 5, Sec. III-A.3).
+
+Test infrastructure only (see the package docstring).
+
+Each non-fixed boundary vertex v carries at most one spring (v, v_c) with
+energy k |v - v_c|^2 (Eq. 5).  Per iteration, after detection:
+
+* v inside an obstacle sphere: an obstacle spring to the closest point of the
+  sphere grown by eps, v_c = c_j + (r_j + eps) u, u = (x_v - c_j)/|x_v - c_j|
+  (u = -n(v) when x_v = c_j); with several spheres the nearest surface
+  (smallest |x_v - c_j| - r_j, then lowest j) wins.  The obstacle takes
+  precedence over self-collision.
+* else v in a self pair: a self spring.  The correspondence is found by
+  searching from x_v along -n(v) (Sec. II-C): the ray hits the boundary faces
+  f not containing v whose outward normal points along the ray
+  ((-n(v)) . n_f > 0, "exit" faces); the hit with the smallest t > 0 and
+  inclusive barycentrics wins (ties: lower face id), using the Moller-Trumbore
+  ray-triangle test (Moller and Trumbore 1997).  With no hit, the closest
+  point over boundary faces not containing v is used.  The stored record is
+  (face f, barycentrics beta1, beta2) and v_c = b + eps n_f, b the hit point
+  and n_f the unit face normal.
+* else an existing spring is released or kept by the paper's release
+  condition (v outside the obstacle and its normal distance to the contact
+  surface above eps), read as: obstacle spring released iff
+  |x_v - c_j| - r_j > eps; self spring released iff n_f . (x_v - b) > eps,
+  with b and n_f re-evaluated from the stored (f, beta) at the current
+  positions.  A kept spring is re-targeted from its stored record.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+KIND_SELF = 0
+KIND_OBSTACLE = 1
+
+
+@dataclass
+class SpringState:
+    """Per-query-vertex spring records (query = sorted non-fixed surface verts)."""
+
+    active: np.ndarray   # (n_q,) bool
+    kind: np.ndarray     # (n_q,) int8: 0 self, 1 obstacle
+    face: np.ndarray     # (n_q,) int64: boundary face id, or sphere id
+    bary: np.ndarray     # (n_q, 2) float64
+    target: np.ndarray   # (n_q, 3) float64
+
+    @staticmethod
+    def empty(n_q: int) -> "SpringState":
+        return SpringState(np.zeros(n_q, bool), np.zeros(n_q, np.int8), np.full(n_q, -1, np.int64),
+                           np.zeros((n_q, 2)), np.zeros((n_q, 3)))
+
+    def copy(self) -> "SpringState":
+        return SpringState(self.active.copy(), self.kind.copy(), self.face.copy(),
+                           self.bary.copy(), self.target.copy())
+
+
+def _ray_triangle(o, d, q0, q1, q2):
+    """Moller-Trumbore: (hit, t, beta1, beta2) of the ray o + t d against the
+    triangle q0 q1 q2, barycentrics inclusive, t > 0."""
+    e1 = q1 - q0
+    e2 = q2 - q0
+    pv = np.cross(d, e2)
+    det = float(np.dot(e1, pv))
+    if det == 0.0:
+        return False, 0.0, 0.0, 0.0
+    inv = 1.0 / det
+    tv = o - q0
+    b1 = float(np.dot(tv, pv)) * inv
+    qv = np.cross(tv, e1)
+    b2 = float(np.dot(d, qv)) * inv
+    t = float(np.dot(e2, qv)) * inv
+    hit = (b1 >= 0.0) and (b2 >= 0.0) and (b1 + b2 <= 1.0) and (t > 0.0)
+    return hit, t, b1, b2
+
+
+def _closest_on_segment(p, a, b):
+    ab = b - a
+    den = float(np.dot(ab, ab))
+    s = 0.0 if den == 0.0 else min(1.0, max(0.0, float(np.dot(p - a, ab)) / den))
+    return a + s * ab, s
+
+
+def closest_point_triangle(p, q0, q1, q2):
+    """Closest point of triangle q0 q1 q2 to p and its barycentrics (b1, b2)
+    (weights of q1 and q2): the plane projection when it falls inside,
+    otherwise the nearest of the three edge projections."""
+    e1 = q1 - q0
+    e2 = q2 - q0
+    n = np.cross(e1, e2)
+    nn = float(np.dot(n, n))
+    if nn > 0.0:
+        x = p - (float(np.dot(p - q0, n)) / nn) * n
+        # barycentrics of x by the 2x2 normal equations
+        d11, d12, d22 = float(np.dot(e1, e1)), float(np.dot(e1, e2)), float(np.dot(e2, e2))
+        r = x - q0
+        r1, r2 = float(np.dot(r, e1)), float(np.dot(r, e2))
+        den = d11 * d22 - d12 * d12
+        b1 = (d22 * r1 - d12 * r2) / den
+        b2 = (d11 * r2 - d12 * r1) / den
+        if b1 >= 0.0 and b2 >= 0.0 and b1 + b2 <= 1.0:
+            return x, b1, b2
+    best = None
+    for (a, b, wa) in ((q0, q1, 0), (q1, q2, 1), (q2, q0, 2)):
+        c, s = _closest_on_segment(p, a, b)
+        dd = float(np.dot(p - c, p - c))
+        if wa == 0:
+            bb = (s, 0.0)
+        elif wa == 1:
+            bb = (1.0 - s, s)
+        else:
+            bb = (0.0, 1.0 - s)
+        if best is None or dd < best[0]:
+            best = (dd, c, bb)
+    return best[1], best[2][0], best[2][1]
+
+
+def _face_point(X, face_verts, b1, b2):
+    q0, q1, q2 = X[face_verts[0]], X[face_verts[1]], X[face_verts[2]]
+    return (1.0 - b1 - b2) * q0 + b1 * q1 + b2 * q2
+
+
+def _face_unit_normal(X, face_verts):
+    q0, q1, q2 = X[face_verts[0]], X[face_verts[1]], X[face_verts[2]]
+    n = np.cross(q1 - q0, q2 - q0)
+    return n / np.linalg.norm(n)
+
+
+def ray_cast_target(X, v, nrm_v, faces, fnormals):
+    """Self-collision correspondence of vertex v: (face id, b1, b2)."""
+    d = -nrm_v
+    o = X[v]
+    cand = np.nonzero((fnormals @ d > 0.0) & np.all(faces != v, axis=1))[0]
+    best = None
+    for f in cand:
+        hit, t, b1, b2 = _ray_triangle(o, d, X[faces[f, 0]], X[faces[f, 1]], X[faces[f, 2]])
+        if hit and (best is None or t < best[0]):
+            best = (t, int(f), b1, b2)
+    if best is not None:
+        return best[1], best[2], best[3]
+    # no exit face hit: closest point over boundary faces not containing v
+    bestc = None
+    for f in np.nonzero(np.all(faces != v, axis=1))[0]:
+        x, b1, b2 = closest_point_triangle(o, X[faces[f, 0]], X[faces[f, 1]], X[faces[f, 2]])
+        dd = float(np.dot(o - x, o - x))
+        if bestc is None or dd < bestc[0]:
+            bestc = (dd, int(f), b1, b2)
+    return bestc[1], bestc[2], bestc[3]
+
+
+def _sphere_target(x, c, r, eps, nrm_v):
+    u = x - c
+    nu = float(np.linalg.norm(u))
+    u = -nrm_v if nu == 0.0 else u / nu
+    return c + (r + eps) * u
+
+
+def update_springs(X, query, prev: SpringState, self_pairs, sphere_pairs, spheres,
+                   faces, vnormals, eps) -> SpringState:
+    """One spring update (create, re-target or release) for every query vertex."""
+    st = prev.copy()
+    fn = np.cross(X[faces[:, 1]] - X[faces[:, 0]], X[faces[:, 2]] - X[faces[:, 0]])
+    in_self = np.zeros(query.shape[0], bool)
+    pos = {int(v): i for i, v in enumerate(query)}
+    for v, _e in self_pairs:
+        in_self[pos[int(v)]] = True
+    obs_hits = {}
+    for v, j in sphere_pairs:
+        obs_hits.setdefault(pos[int(v)], []).append(int(j))
+    for i, v in enumerate(query):
+        x = X[v]
+        if i in obs_hits:
+            js = obs_hits[i]
+            dists = [float(np.linalg.norm(x - spheres[j, :3])) - float(spheres[j, 3]) for j in js]
+            j = js[int(np.argmin(dists))]
+            st.active[i] = True
+            st.kind[i] = KIND_OBSTACLE
+            st.face[i] = j
+            st.bary[i] = 0.0
+            st.target[i] = _sphere_target(x, spheres[j, :3], float(spheres[j, 3]), eps, vnormals[v])
+        elif in_self[i]:
+            f, b1, b2 = ray_cast_target(X, v, vnormals[v], faces, fn)
+            st.active[i] = True
+            st.kind[i] = KIND_SELF
+            st.face[i] = f
+            st.bary[i] = (b1, b2)
+            b = _face_point(X, faces[f], b1, b2)
+            st.target[i] = b + eps * _face_unit_normal(X, faces[f])
+        elif st.active[i]:
+            if st.kind[i] == KIND_OBSTACLE:
+                j = int(st.face[i])
+                c, r = spheres[j, :3], float(spheres[j, 3])
+                if float(np.linalg.norm(x - c)) - r > eps:
+                    st.active[i] = False
+                else:
+                    st.target[i] = _sphere_target(x, c, r, eps, vnormals[v])
+            else:
+                f = int(st.face[i])
+                b = _face_point(X, faces[f], st.bary[i, 0], st.bary[i, 1])
+                nf = _face_unit_normal(X, faces[f])
+                if float(np.dot(nf, x - b)) > eps:
+                    st.active[i] = False
+                else:
+                    st.target[i] = b + eps * nf
+    st.face[~st.active] = -1
+    st.bary[~st.active] = 0.0
+    st.target[~st.active] = 0.0
+    return st
+
+
+def spring_energy(X, query, st: SpringState, k):
+    """k sum_{v in V_col} |x_v - v_c|^2 (Eq. 5 summed, Eq. 8 second term)."""
+    a = st.active
+    d = X[query[a]] - st.target[a]
+    return float(k * np.sum(d * d))
