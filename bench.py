@@ -1,0 +1,369 @@
+#!/usr/bin/env python3
+"""Benchmark of the collision-aware local-global loop on GB300.
+
+One step = one full solve of the three-finger gripper workload: reset to the
+rest shape, then 200 outer iterations (collision check, spring update, local
+step, RHS gather, PCG global solve) of 193,920 tets with a rigid sphere, in
+MIXED precision.  The metric is tet-element iterations per second
+(n_tets * n_iters / time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl casim|reference]
+
+``--impl reference`` times the FP64 CPU oracle (a bounded sample: one outer
+iteration of the same workload per step) on the host cores.  With several GPUs
+each rank runs an independent replica of the workload (a single mesh does not
+shard); the value is the work of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "tet-element iterations/sec at 200k tets"
+UNIT = "tet-iterations/s"
+WORKLOAD = ("gripper3_plate_sphere: three 60x12x12-voxel pneumatic fingers (8 chambers each) "
+            "below a 40x40x4-voxel plate, rigid sphere r=3cm, 193,920 tets, 200 outer iterations")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="casim", choices=["casim", "reference"])
+    ap.add_argument("--iters", type=int, default=200, help="outer iterations per step")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        if self.th is not None:
+            self.th.join(timeout=5)
+
+    def summary(self):
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in self.rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in self.rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        sm_sorted = sorted(sm)
+        med = sm_sorted[len(sm_sorted) // 2] if sm_sorted else None
+        return {"sm_mhz": med, "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------- roofline
+def pcg_bytes_per_launch(n_free: int, nnz_row: float, k_pcg: float) -> float:
+    """Algorithmic DRAM bytes of one PCG launch (FP32 vectors, 12 B per 3-vector,
+    4 B per scalar, 8 B per off-diagonal entry): the initial residual pass
+    (52 + 8 nnz), the first SpMV pass (40 + 8 nnz) and per iteration
+    148 + 8 nnz bytes per free vertex (x, r, p, s, u, w each read and written
+    once, the diagonal read once, the matrix row read once)."""
+    return n_free * ((52 + 8 * nnz_row) + (40 + 8 * nnz_row) + k_pcg * (148 + 8 * nnz_row))
+
+
+def offdiag_nnz_per_free_row(m) -> float:
+    import numpy as np
+
+    fixed = m.fixed.astype(bool)
+    t = m.tets.astype(np.int64)
+    pairs = []
+    for a in range(4):
+        for b in range(4):
+            if a != b:
+                pairs.append(np.stack([t[:, a], t[:, b]], axis=1))
+    e = np.unique(np.concatenate(pairs), axis=0)
+    e = e[~fixed[e[:, 0]] & ~fixed[e[:, 1]]]
+    return e.shape[0] / max(1, int((~fixed).sum()))
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("solve.cu", "common.cuh", "kernels.h"):
+        with open(os.path.join(ROOT, "paper_2203_02054_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    from the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as fh:
+            rec = json.load(fh).get(kernel)
+    except (OSError, ValueError):
+        return None
+    if not rec or rec.get("source_hash") != kernel_source_hash():
+        return None
+    return rec.get("bytes_per_launch")
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ oracle arm
+def oracle_sample(m, prep=None):
+    """One outer iteration of the FP64 oracle from the rest shape; returns
+    (seconds, tet-iterations)."""
+    import numpy as np
+
+    from oracle import loop, springs
+
+    prep = prep or loop.prepare(m.rest, m.tets, m.group, m.fixed)
+    st = springs.SpringState.empty(prep.query.shape[0])
+    t0 = time.perf_counter()
+    loop.iterate(prep, np.array(m.rest), st, m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps, m.collision)
+    return time.perf_counter() - t0, m.n_tets
+
+
+def cpu_threads_used() -> int:
+    return 1
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    from paper_2203_02054_gb300 import synth
+    from oracle import loop
+
+    m = synth.config3_gripper()
+    prep = loop.prepare(m.rest, m.tets, m.group, m.fixed)
+    for _ in range(args.warmup):
+        oracle_sample(m, prep)
+    tot_t = 0.0
+    tot_u = 0
+    for _ in range(args.steps):
+        t, u = oracle_sample(m, prep)
+        tot_t += t
+        tot_u += u
+    value = tot_u / tot_t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_tets": m.n_tets, "sample": "1 outer iteration per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
+                         "sample": "one outer iteration of the 193,920-tet gripper from rest per step "
+                                   "(brute-force exact collision check, springs, local step, sparse LU global solve)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# -------------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    rank, world, local = dist_env()
+    import numpy as np
+    import torch
+
+    from paper_2203_02054_gb300 import casim, synth
+
+    torch.cuda.set_device(local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+        pg = dist
+    stream = torch.cuda.current_stream()
+    m = synth.config3_gripper(n_iters=args.iters)
+    n_iters = args.iters
+    sim = casim.Sim(m, stream=stream.cuda_stream, stats=0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def one_step():
+        casim.casim_reset(sim.h)
+        casim.casim_step(sim.h, n_iters)
+
+    for _ in range(max(args.warmup, 0)):
+        one_step()
+    st = casim.casim_sync(sim.h)
+    if st != 0:
+        print("warning: device status %d after warm-up" % st, file=sys.stderr)
+
+    def barrier():
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier()
+    if sampler:
+        sampler.start()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()                     # L2 flush between timed steps (not timed)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        one_step()
+        b.record(stream)
+        evs.append((a, b))
+    barrier()
+    if sampler:
+        sampler.stop()
+    status = casim.casim_sync(sim.h)
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if pg is not None:
+        pg.all_reduce(t_local, op=pg.ReduceOp.MAX)
+    ms_max = float(t_local.item())
+    units = float(m.n_tets) * n_iters * args.steps * world
+    value = units / (ms_max / 1e3)
+    kernels_per_iter = 11   # 2 hash binning + 3 scan + narrow + springs + local + rhs + pcg + finalize
+    gpu_launches = kernels_per_iter * n_iters * args.steps
+    stats = casim.casim_get_stats(sim.h)
+
+    # ---- end-to-end through the public API with host buffers ----
+    rest = np.ascontiguousarray(m.rest)
+    alpha = np.ascontiguousarray(m.alpha)
+    out = np.empty_like(rest)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        casim.casim_reset(sim.h)
+        casim.casim_set_positions(sim.h, rest)
+        casim.casim_set_actuation(sim.h, alpha)
+        casim.casim_step(sim.h, n_iters)
+        casim.casim_get_positions(sim.h, m.n_verts)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if pg is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = units / e2e_s
+    del out
+
+    line = None
+    if rank == 0:
+        # ---- roofline of the dominant kernel: eager pass with phase events ----
+        prof = casim.Sim(m, stream=stream.cuda_stream, stats=2)
+        prof.step(n_iters)
+        prof.sync()
+        ph = casim.casim_get_phase_times(prof.h)
+        pst = casim.casim_get_stats(prof.h)
+        prof.close()
+        k_pcg = pst.total_pcg_iters / max(1, pst.iterations)
+        pcg_ms = ph[4] / n_iters
+        nnz = offdiag_nnz_per_free_row(m)
+        n_free = int((m.fixed == 0).sum())
+        bpl = pcg_bytes_per_launch(n_free, nnz, k_pcg)
+        peak, peak_kind = load_peaks()
+        achieved = bpl / (pcg_ms / 1e3) / 1e9
+        clocks = sampler.summary() if sampler else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64-reductions", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_tets": m.n_tets, "n_verts": m.n_verts, "n_iters": n_iters,
+                       "precision": "MIXED (FP32 vectors/targets, FP64 dots, exact predicates)",
+                       "l2": "flushed between timed steps (256 MiB write); one step's working set fits L2",
+                       "parallelism": "replicas" if world > 1 else "single-gpu",
+                       "device_status": status},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * 3 * m.n_verts + 8 * m.n_groups,
+                    "d2h_bytes_per_step": 8 * 3 * m.n_verts},
+            "gpu_launches": gpu_launches,
+            "roofline": {"bound": "hbm", "kernel": "k_pcg (persistent Chronopoulos-Gear PCG)",
+                         "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "peak_kind": peak_kind, "traffic": recorded_traffic("k_pcg"),
+                         "bytes_per_launch": bpl, "ms_per_launch": pcg_ms, "k_pcg_mean": k_pcg,
+                         "phase_ms_per_iter": {"collision": ph[0] / n_iters, "springs": ph[1] / n_iters,
+                                               "local": ph[2] / n_iters, "rhs": ph[3] / n_iters,
+                                               "pcg": ph[4] / n_iters}},
+            "clocks": clocks,
+            "solver": {"k_pcg_mean_timed": stats.total_pcg_iters / max(1, stats.iterations)},
+        }
+        # ---- CPU baseline: the oracle on a bounded sample of the same workload ----
+        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(v, "1")
+        t, u = oracle_sample(m)
+        line["cpu_baseline"] = {"value": u / t, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
+                                "sample": "one outer iteration of the 193,920-tet gripper from rest "
+                                          "(FP64 numpy/scipy, brute-force exact collision check)"}
+        print(json.dumps(line))
+    sim.close()
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

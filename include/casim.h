@@ -1,0 +1,221 @@
+/*
+ * casim -- collision-aware local-global soft-robot simulation on one GPU.
+ *
+ * C ABI of the CUDA library.  The method is the paper's projection-based
+ * local-global solver with virtual-spring collision response (Fang, Tian,
+ * Weightman, Wang, "Collision-Aware Fast Simulation for Soft Robots by
+ * Optimization-Based Geometric Computing", Sec. II-III, Algorithm 1).
+ *
+ * One outer iteration i (the inner while-loop of Algorithm 1, run a fixed
+ * number of times) maps positions X_i to X_{i+1}:
+ *   1. collision check on X_i (Sec. II-B, Eq. 3, Eq. 4): every non-fixed
+ *      boundary vertex strictly inside a tet that does not contain it, or
+ *      inside an obstacle sphere;
+ *   2. spring update (Sec. II-C, Eq. 5, Sec. III-A.3): create, re-target or
+ *      release one virtual spring per boundary vertex;
+ *   3. local step (Sec. III-A, Eq. 6, Eq. 7): per-tet rotation by SVD and the
+ *      chamber / body target shape;
+ *   4. global step (Sec. III-B, Eq. 8): assemble the right-hand side and solve
+ *      the SPD system for the free vertex positions by PCG.
+ *
+ * Conventions for every entry point:
+ *   - Return value: 0 (CASIM_OK) on success, a negative CASIM_E_* code on
+ *     error, a positive CASIM_W_* code for a warning.  No C++ exception ever
+ *     crosses this boundary.  casim_last_error() describes the last failure.
+ *   - Host input arrays are copied before the call returns; the caller keeps
+ *     ownership.  Output buffers belong to the caller.
+ *   - Device pointers ("dev_*") are CUDA device addresses on the device that
+ *     was current when the simulation was created.
+ *   - All device work is enqueued on the stream given at creation (NULL means
+ *     the legacy default stream); the stream belongs to the caller.
+ *   - A simulation handle must be used from one host thread at a time.
+ *   - Vertex and tet ids are always the caller's ids (0-based, as uploaded).
+ */
+#ifndef CASIM_H
+#define CASIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define CASIM_OK 0
+#define CASIM_E_INVALID (-1)   /* bad argument (null pointer, size, value)      */
+#define CASIM_E_CUDA (-2)      /* a CUDA runtime call failed                     */
+#define CASIM_E_SINGULAR (-3)  /* a connected component has no fixed vertex      */
+#define CASIM_E_STATE (-4)     /* call out of order (e.g. step before upload)    */
+#define CASIM_E_CAPACITY (-5)  /* caller's output buffer is too small            */
+#define CASIM_E_NONFINITE (-6) /* NaN or Inf met on the device                   */
+#define CASIM_E_TIMEOUT (-7)   /* a device-side wait ran out of its budget       */
+#define CASIM_E_OVERFLOW (-8)  /* a device work list exceeded its capacity       */
+#define CASIM_W_PCG_MAXIT 1    /* PCG stopped at its iteration cap (warning)     */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define CASIM_FP64 0   /* every quantity in FP64                                  */
+#define CASIM_MIXED 1  /* positions, rotations, targets and PCG vectors in FP32;
+                          dot products, norms and PCG scalars in FP64; collision
+                          predicates exact                                        */
+
+/* ---- collision modes ---------------------------------------------------- */
+#define CASIM_COLLISION_OFF 0
+#define CASIM_COLLISION_SELF 1
+#define CASIM_COLLISION_SELF_OBSTACLE 2
+
+typedef struct casim_sim casim_sim;
+
+/* Solver parameters.  casim_default_params() fills every field. */
+typedef struct {
+  int32_t precision;        /* CASIM_FP64 or CASIM_MIXED                              */
+  int32_t collision;        /* CASIM_COLLISION_*                                      */
+  double k_spring;          /* spring weight k of Eq. 5 (Eq. 8 uses 1)                */
+  double eps;               /* contact offset epsilon of Sec. II-C (length units)     */
+  double pcg_tol;           /* stop when |r|_2 <= pcg_tol * |b|_2                     */
+  int32_t pcg_max_iter;     /* PCG iteration cap per outer iteration                  */
+  int32_t n_w_knots;        /* number of (strain, w) knots of R_omega, >= 1           */
+  const double* w_knots;    /* host, 2*n_w_knots doubles (eps_i, w_i), eps ascending;
+                               copied at casim_create                                 */
+  double cell_size;         /* spatial-hash cell edge (length units), > 0             */
+  int32_t stats;            /* 1: record the Eq. 8 energy per iteration               */
+  int32_t max_pairs_per_vertex; /* self pairs stored per vertex (1..16)              */
+  uint64_t wait_budget_cycles;  /* SM clock cycles a grid-barrier wait may spin
+                                   before the kernel gives up with CASIM_E_TIMEOUT;
+                                   0 selects the default (about 2 s)                 */
+} casim_params;
+
+/* Per-iteration record (Eq. 8 energy at X_i with the targets of iteration i). */
+typedef struct {
+  double energy;            /* 0 unless params.stats                                 */
+  double pcg_rel_residual;  /* |r|/|b| at PCG exit (recursive residual)              */
+  int32_t n_self_pairs;     /* |P_self| found on X_i                                 */
+  int32_t n_obstacle_pairs; /* |P_obs| found on X_i                                  */
+  int32_t n_springs;        /* |V_col| after the spring update                       */
+  int32_t pcg_iters;        /* PCG iterations of this outer iteration                */
+} casim_iter_record;
+
+typedef struct {
+  int64_t iterations;       /* outer iterations run since the last upload            */
+  int64_t total_pcg_iters;
+  casim_iter_record last;   /* record of the most recent iteration                   */
+  int32_t status;           /* device status code of the last casim_sync             */
+} casim_stats;
+
+/* Fills *p with the defaults: MIXED, self collision, k = 1, eps = 0.005,
+   pcg_tol = 1e-6, pcg_max_iter = 1000, w == 1 (one knot), cell_size = 0.5,
+   stats = 1, max_pairs_per_vertex = 8, wait budget default. */
+void casim_default_params(casim_params* p);
+
+/* Creates a simulation.  cuda_stream: a cudaStream_t (NULL: default stream).
+   Errors: CASIM_E_INVALID for out-of-range parameters. */
+int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out);
+
+/* Uploads a tetrahedral mesh M = M_c + M_b (Sec. II-A) and resets the state to
+   the rest shape with no springs.
+     rest_xyz  host, n_verts*3 doubles, vertex positions of the rest shape V
+     tets      host, n_tets*4 int32 vertex ids, positively oriented
+               (det[v1-v0, v2-v0, v3-v0] > 0)
+     tet_group host, n_tets int32: -1 body element, g >= 0 chamber group g
+     fixed     host, n_verts uint8: nonzero = position held fixed
+   Errors: CASIM_E_INVALID (ids out of range, non-positive rest volume, group
+   ids not dense from 0), CASIM_E_SINGULAR (a connected component without a
+   fixed vertex), CASIM_E_CUDA. */
+int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, int32_t n_tets,
+                      const int32_t* tets, const int32_t* tet_group, const uint8_t* fixed);
+
+/* Volume ratios alpha_g per chamber group (Eq. 2; chamber targets are scaled
+   by cbrt(alpha_g), Sec. III-A.1).  n_groups must equal 1 + the largest group
+   id of the mesh.  Errors: CASIM_E_INVALID (alpha <= 0), CASIM_E_STATE. */
+int casim_set_actuation(casim_sim* sim, int32_t n_groups, const double* alpha);
+
+/* Rigid obstacle spheres O_obs (Eq. 4): host, n*4 doubles (cx, cy, cz, r). */
+int casim_set_spheres(casim_sim* sim, int32_t n, const double* cxyzr);
+
+/* Overwrites all vertex positions (host, n_verts*3 doubles, caller order).
+   In MIXED mode the values are rounded to FP32. */
+int casim_set_positions(casim_sim* sim, const double* xyz);
+
+/* Asynchronously restores the rest positions (or the positions of the last
+   casim_set_positions / casim_load_state call) and clears every spring, on the
+   stream, without host copies.  History and counters are kept. */
+int casim_reset(casim_sim* sim);
+
+/* Enqueues n_iters outer iterations on the stream (asynchronous).
+   Errors: CASIM_E_STATE (no mesh or actuation), CASIM_E_CUDA. */
+int casim_step(casim_sim* sim, int32_t n_iters);
+
+/* Waits for the stream and returns the device status: CASIM_OK,
+   CASIM_W_PCG_MAXIT, CASIM_E_NONFINITE, CASIM_E_TIMEOUT or CASIM_E_OVERFLOW.
+   The device status is cleared after it is read. */
+int casim_sync(casim_sim* sim);
+
+/* Current positions, caller order, as n_verts*3 doubles into host_out (may be
+   NULL) and/or as n_verts*3 values of the working precision (float in MIXED,
+   double in FP64) into dev_out (may be NULL).  Synchronises the stream when
+   host_out is given. */
+int casim_get_positions(casim_sim* sim, double* host_out, void* dev_out);
+
+/* Contact sets found by the last collision check (on X_i of the last
+   iteration run): self pairs (v, e) sorted by (v, e) into pairs[2*k], and the
+   vertices inside an obstacle sphere (sorted) into obstacle_verts.  On entry
+   *n_pairs / *n_obst hold the capacities (in pairs / vertices); on exit the
+   counts.  Returns CASIM_E_CAPACITY (with the counts set) when too small.
+   A vertex whose self pairs exceeded max_pairs_per_vertex sets the
+   CASIM_E_OVERFLOW device status. */
+int casim_get_contacts(casim_sim* sim, int32_t* pairs, int64_t* n_pairs, int32_t* obstacle_verts,
+                       int64_t* n_obst);
+
+/* Spring records after the last spring update, one per non-fixed boundary
+   vertex in ascending vertex id.  Any output pointer may be NULL.
+     verts   int32 vertex id            active  uint8 1 = spring present
+     kind    int32 0 self, 1 obstacle   face    int32 boundary face id (self),
+                                                 sphere id (obstacle), -1 none
+     bary    2 doubles (weights of the face's 2nd and 3rd vertex)
+     target  3 doubles, the spring's other end v_c
+   *n (in: capacity, out: count).  Boundary faces are numbered by (tet id,
+   local face k), face k being the face opposite the tet's k-th vertex. */
+int casim_get_springs(casim_sim* sim, int64_t* n, int32_t* verts, uint8_t* active, int32_t* kind,
+                      int32_t* face, double* bary, double* target);
+
+/* Replaces the spring records (same layout as casim_get_springs; verts must
+   list the non-fixed boundary vertices in ascending order). */
+int casim_set_springs(casim_sim* sim, int64_t n, const int32_t* verts, const uint8_t* active,
+                      const int32_t* kind, const int32_t* face, const double* bary,
+                      const double* target);
+
+/* Element targets of the last local step: host n_tets*12 doubles, P_e as a
+   row-major 3x4 matrix per tet (not weighted by omega_e). */
+int casim_get_targets(casim_sim* sim, double* host_out);
+
+/* Per-iteration records of the last min(cap, iterations) iterations, oldest
+   first; *n receives the count. */
+int casim_get_history(casim_sim* sim, int32_t cap, casim_iter_record* out, int32_t* n);
+
+int casim_get_stats(casim_sim* sim, casim_stats* out);
+
+/* Saves / restores positions and spring records (checkpoint / resume).
+   casim_save_state with buf == NULL stores the required size in *len. */
+int casim_save_state(casim_sim* sim, void* buf, size_t* len);
+int casim_load_state(casim_sim* sim, const void* buf, size_t len);
+
+/* Sizes of the uploaded mesh (any pointer may be NULL). */
+int casim_get_sizes(casim_sim* sim, int32_t* n_verts, int32_t* n_tets, int32_t* n_free,
+                    int32_t* n_boundary_faces, int32_t* n_query_verts);
+
+/* Last launch configuration and device time split of the previous
+   casim_step (milliseconds per phase: collision, springs, local, rhs, pcg),
+   measured with CUDA events when params.stats >= 2; zero otherwise. */
+int casim_get_phase_times(casim_sim* sim, double* ms_out5);
+
+void casim_destroy(casim_sim* sim);
+
+/* Message of the last failure on this handle (or of the last casim_create
+   failure when sim is NULL).  Valid until the next call on the handle. */
+const char* casim_last_error(const casim_sim* sim);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CASIM_H */

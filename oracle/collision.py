@@ -21,8 +21,8 @@ The orientation sign uses Shewchuk's floating-point filter (Shewchuk 1997,
 "Adaptive precision floating-point arithmetic and fast robust geometric
 predicates": error bound (7 + 56 eps) eps times the permanent, eps = 2^-53)
 and falls back to exact rational arithmetic (``fractions.Fraction``) when the
-filter cannot decide.  An axis-aligned bounding-box test is used first; it is
-exact (a point strictly inside a tet lies in the tet's closed bounding box).
+filter cannot decide.  Exact rejections come first: a point strictly inside a tet lies in the tet's
+closed bounding box, and so in the tet's slab range along one axis.
 """
 from __future__ import annotations
 
@@ -87,30 +87,53 @@ def strictly_inside(p, a, b, c, d) -> np.ndarray:
     return (s0 > 0) & (s1 > 0) & (s2 > 0) & (s3 > 0)
 
 
-def self_pairs(X: np.ndarray, tets: np.ndarray, query: np.ndarray, chunk: int = 64) -> np.ndarray:
+def self_pairs(X: np.ndarray, tets: np.ndarray, query: np.ndarray, chunk: int = 64,
+               n_slabs: int = 64) -> np.ndarray:
     """All (v, e) with v in ``query`` strictly inside tet e not containing v,
-    sorted by (v, e); returns an (m, 2) int64 array."""
+    sorted by (v, e); returns an (m, 2) int64 array.
+
+    Every (vertex, tet) pair is decided by the exact predicate after two exact
+    rejections: the tet's closed bounding box, and before it a 1-D slab test
+    along the longest axis (p can lie in a tet only if lo_a <= p_a <= hi_a, and
+    floor((x - base) / width) is monotone in x, so such a tet is listed in p's
+    slab)."""
     E = X[tets]                      # (n_t, 4, 3)
     lo = E.min(axis=1)
     hi = E.max(axis=1)
-    out = []
     query = np.asarray(query, dtype=np.int64)
-    for s in range(0, query.shape[0], chunk):
-        vs = query[s:s + chunk]
-        p = X[vs]                    # (c, 3)
-        box = np.all((p[:, None, :] >= lo[None]) & (p[:, None, :] <= hi[None]), axis=2)
-        vi, ei = np.nonzero(box)
-        if vi.size == 0:
+    if query.size == 0 or tets.shape[0] == 0:
+        return np.zeros((0, 2), dtype=np.int64)
+    ext = hi.max(axis=0) - lo.min(axis=0)
+    ax = int(np.argmax(ext))
+    base = float(lo[:, ax].min())
+    width = max(float(ext[ax]) / n_slabs, 1e-300)
+    s_lo = np.floor((lo[:, ax] - base) / width).astype(np.int64)
+    s_hi = np.floor((hi[:, ax] - base) / width).astype(np.int64)
+    s_q = np.floor((X[query, ax] - base) / width).astype(np.int64)
+    out = []
+    for sl in np.unique(s_q):
+        cand = np.nonzero((s_lo <= sl) & (s_hi >= sl))[0]
+        if cand.size == 0:
             continue
-        v = vs[vi]
-        keep = np.all(tets[ei] != v[:, None], axis=1)
-        v, ei = v[keep], ei[keep]
-        if v.size == 0:
-            continue
-        t = tets[ei]
-        ins = strictly_inside(X[v], X[t[:, 0]], X[t[:, 1]], X[t[:, 2]], X[t[:, 3]])
-        if np.any(ins):
-            out.append(np.stack([v[ins], ei[ins]], axis=1))
+        qs = query[s_q == sl]
+        lo_c, hi_c = lo[cand], hi[cand]
+        for s in range(0, qs.shape[0], chunk):
+            vs = qs[s:s + chunk]
+            p = X[vs]                    # (c, 3)
+            box = np.all((p[:, None, :] >= lo_c[None]) & (p[:, None, :] <= hi_c[None]), axis=2)
+            vi, ci = np.nonzero(box)
+            if vi.size == 0:
+                continue
+            v = vs[vi]
+            ei = cand[ci]
+            keep = np.all(tets[ei] != v[:, None], axis=1)
+            v, ei = v[keep], ei[keep]
+            if v.size == 0:
+                continue
+            t = tets[ei]
+            ins = strictly_inside(X[v], X[t[:, 0]], X[t[:, 1]], X[t[:, 2]], X[t[:, 3]])
+            if np.any(ins):
+                out.append(np.stack([v[ins], ei[ins]], axis=1))
     if not out:
         return np.zeros((0, 2), dtype=np.int64)
     pairs = np.concatenate(out).astype(np.int64)

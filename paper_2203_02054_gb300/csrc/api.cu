@@ -1,0 +1,1188 @@
+// casim C ABI: host-side mesh preparation, validation, device memory and the
+// CUDA graph that runs one outer iteration of the collision-aware
+// local-global loop (Algorithm 1, inner while-loop).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <cstddef>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "casim.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace casim;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// Outward faces of a positively oriented tet (v0, v1, v2, v3): face k is the
+// face opposite local vertex k, counter-clockwise seen from outside.
+const int kTetFace[4][3] = {{1, 2, 3}, {0, 3, 2}, {0, 1, 3}, {0, 2, 1}};
+
+size_t pow2_at_least(size_t n) {
+  size_t p = 1024;
+  while (p < n) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+struct casim_sim {
+  casim_params params{};
+  std::vector<double> knots;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  std::string err;
+  int device = 0;
+  bool has_mesh = false;
+  bool has_act = false;
+  // host-side mesh
+  int n_v = 0, n_t = 0, n_free = 0, n_q = 0, n_f = 0, n_groups = 0, n_spheres = 0;
+  std::vector<int> int_of_user, user_of_int;
+  std::vector<double> omega;
+  std::vector<int> q_verts;  // internal ids
+  std::vector<int> fx_ptr, fx_col;
+  std::vector<double> fx_val;
+  std::vector<double> X_fixed;  // internal order of fixed vertices, 3 per vertex
+  std::vector<double> spheres;
+  // device memory
+  std::vector<void*> allocs;
+  size_t rs = 4;  // bytes per real
+  void *X = nullptr, *Tc = nullptr, *tinfo = nullptr, *P = nullptr, *cbrt_alpha = nullptr;
+  void *diagL = nullptr, *bfix = nullptr, *b = nullptr, *diag = nullptr, *sl_val = nullptr;
+  void *r = nullptr, *u = nullptr, *p = nullptr, *s = nullptr, *w = nullptr, *spring_c = nullptr;
+  void* pos_out = nullptr;
+  void* X0 = nullptr;  // positions restored by casim_reset
+  int4 *tet = nullptr, *faces = nullptr;
+  int *inc_ptr = nullptr, *inc = nullptr, *sl_ptr = nullptr, *sl_col = nullptr;
+  int *q_verts_d = nullptr, *qf_ptr = nullptr, *qf = nullptr;
+  int *cell_count = nullptr, *cell_start = nullptr, *cell_cursor = nullptr, *items = nullptr;
+  int *pair_count = nullptr, *pair_tet = nullptr, *obs_sphere = nullptr, *int_of_user_d = nullptr;
+  double *knots_d = nullptr, *spheres_d = nullptr, *partials = nullptr, *e_partials = nullptr;
+  SpringDev sp{};
+  Ctrl* ctrl = nullptr;
+  IterRec* hist = nullptr;
+  int hist_cap = 4096;
+  CollisionScratch cs{};
+  unsigned H_t = 0, H_f = 0;
+  int cap_items = 0, n_slices = 0, pcg_grid = 1, n_e_local = 0, n_e_spring = 0;
+  // graph of one iteration
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_dirty = true;
+  bool no_graph = false;  // capture refused: launch the iteration eagerly
+  long long iters = 0;
+  int last_status = 0;
+  double phase_ms[5] = {0, 0, 0, 0, 0};
+
+  int fail(int code, const std::string& msg) {
+    err = msg;
+    return code;
+  }
+  template <class X>
+  X* dalloc(size_t n) {
+    void* q = nullptr;
+    if (n == 0) n = 1;
+    if (cudaMalloc(&q, n * sizeof(X)) != cudaSuccess) return nullptr;
+    allocs.push_back(q);
+    return static_cast<X*>(q);
+  }
+  void* dalloc_bytes(size_t n) {
+    void* q = nullptr;
+    if (n == 0) n = 16;
+    if (cudaMalloc(&q, n) != cudaSuccess) return nullptr;
+    allocs.push_back(q);
+    return q;
+  }
+  void free_all() {
+    if (gexec) cudaGraphExecDestroy(gexec);
+    gexec = nullptr;
+    for (void* q : allocs) cudaFree(q);
+    allocs.clear();
+    graph_dirty = true;
+  }
+};
+
+#define CK(call)                                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) return sim->fail(CASIM_E_CUDA, std::string(#call) + ": " + \
+                                                              cudaGetErrorString(e_)); \
+  } while (0)
+
+namespace {
+
+template <typename T>
+Dev<T> make_dev(casim_sim* sim) {
+  Dev<T> d{};
+  d.n_v = sim->n_v;
+  d.n_t = sim->n_t;
+  d.n_free = sim->n_free;
+  d.n_q = sim->n_q;
+  d.n_f = sim->n_f;
+  d.n_groups = sim->n_groups;
+  d.n_spheres = sim->params.collision >= 2 ? sim->n_spheres : 0;
+  d.n_knots = (int)sim->knots.size() / 2;
+  d.X = (R4<T>*)sim->X;
+  d.tet = sim->tet;
+  d.Tc = (const R4<T>*)sim->Tc;
+  d.tinfo = (const R4<T>*)sim->tinfo;
+  d.P = (R4<T>*)sim->P;
+  d.cbrt_alpha = (const T*)sim->cbrt_alpha;
+  d.knots = sim->knots_d;
+  d.inc_ptr = sim->inc_ptr;
+  d.inc = sim->inc;
+  d.diagL = (const T*)sim->diagL;
+  d.bfix = (const R4<T>*)sim->bfix;
+  d.b = (R4<T>*)sim->b;
+  d.diag = (T*)sim->diag;
+  d.n_slices = sim->n_slices;
+  d.sl_ptr = sim->sl_ptr;
+  d.sl_col = sim->sl_col;
+  d.sl_val = (const T*)sim->sl_val;
+  d.r = (R4<T>*)sim->r;
+  d.u = (R4<T>*)sim->u;
+  d.p = (R4<T>*)sim->p;
+  d.s = (R4<T>*)sim->s;
+  d.w = (R4<T>*)sim->w;
+  d.partials = sim->partials;
+  d.q_verts = sim->q_verts_d;
+  d.qf_ptr = sim->qf_ptr;
+  d.qf = sim->qf;
+  d.faces = sim->faces;
+  d.spheres = sim->spheres_d;
+  d.H_t = sim->H_t;
+  d.H_f = sim->H_f;
+  d.cell_count = sim->cell_count;
+  d.cell_start = sim->cell_start;
+  d.cell_cursor = sim->cell_cursor;
+  d.items = sim->items;
+  d.cap_items = sim->cap_items;
+  d.pair_count = sim->pair_count;
+  d.pair_tet = sim->pair_tet;
+  d.obs_sphere = sim->obs_sphere;
+  d.max_pairs = sim->params.max_pairs_per_vertex;
+  d.sp = sim->sp;
+  d.spring_c = (R4<T>*)sim->spring_c;
+  d.k_spring = sim->params.k_spring;
+  d.eps = sim->params.eps;
+  d.cell = sim->params.cell_size;
+  d.inv_cell = 1.0 / sim->params.cell_size;
+  d.tol2 = sim->params.pcg_tol * sim->params.pcg_tol;
+  d.max_iter = sim->params.pcg_max_iter;
+  d.collision = sim->params.collision;
+  d.stats = sim->params.stats;
+  d.wait_budget = sim->params.wait_budget_cycles ? sim->params.wait_budget_cycles : 4000000000ull;
+  d.ctrl = sim->ctrl;
+  d.hist = sim->hist;
+  d.hist_cap = sim->hist_cap;
+  d.e_partials = sim->e_partials;
+  d.n_e_local = sim->n_e_local;
+  d.n_e_spring = sim->n_e_spring;
+  return d;
+}
+
+// Enqueues one outer iteration on stream st (used for graph capture and for
+// the timed eager path).
+template <typename T>
+cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) {
+  const Dev<T> d = make_dev<T>(sim);
+  if (ev) cudaEventRecord(ev[0], st);
+  if (d.collision >= 1 && d.n_q > 0) launch_collision<T>(d, sim->cs, st);
+  if (ev) cudaEventRecord(ev[1], st);
+  if (d.collision >= 1 && d.n_q > 0) launch_springs<T>(d, st);
+  if (ev) cudaEventRecord(ev[2], st);
+  launch_local<T>(d, st);
+  if (ev) cudaEventRecord(ev[3], st);
+  launch_rhs<T>(d, st);
+  if (ev) cudaEventRecord(ev[4], st);
+  // reset the grid-barrier words (abort, count, generation) before the PCG
+  cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st);
+  cudaError_t e = launch_pcg<T>(d, sim->pcg_grid, st);
+  if (e != cudaSuccess) return e;
+  if (ev) cudaEventRecord(ev[5], st);
+  launch_finalize<T>(d, st);
+  return cudaGetLastError();
+}
+
+template <typename T>
+void to_real(const std::vector<double>& a, std::vector<T>& out) {
+  out.resize(a.size());
+  for (size_t i = 0; i < a.size(); ++i) out[i] = (T)a[i];
+}
+
+template <typename T>
+int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std::vector<int>& tets_int,
+                 const std::vector<int>& group, const std::vector<double>& Tc, const std::vector<double>& vol0,
+                 const std::vector<double>& tt, const std::vector<int>& faces4, const std::vector<int>& qf_ptr,
+                 const std::vector<int>& qf, const std::vector<int>& inc_ptr, const std::vector<int>& inc,
+                 const std::vector<double>& diagL, const std::vector<int>& sl_ptr,
+                 const std::vector<int>& sl_col, const std::vector<double>& sl_val) {
+  const int n_v = sim->n_v, n_t = sim->n_t, n_free = sim->n_free, n_q = sim->n_q, n_f = sim->n_f;
+  sim->X = sim->dalloc<R4<T>>(n_v);
+  sim->X0 = sim->dalloc<R4<T>>(n_v);
+  sim->pos_out = sim->dalloc<T>(3 * (size_t)n_v);
+  sim->tet = sim->dalloc<int4>(n_t);
+  sim->Tc = sim->dalloc<R4<T>>(3 * (size_t)n_t);
+  sim->tinfo = sim->dalloc<R4<T>>(n_t);
+  sim->P = sim->dalloc<R4<T>>(4 * (size_t)n_t);
+  sim->cbrt_alpha = sim->dalloc<T>(std::max(1, sim->n_groups));
+  sim->knots_d = sim->dalloc<double>(sim->knots.size());
+  sim->inc_ptr = sim->dalloc<int>(n_free + 1);
+  sim->inc = sim->dalloc<int>(inc.size());
+  sim->diagL = sim->dalloc<T>(n_free);
+  sim->bfix = sim->dalloc<R4<T>>(n_free);
+  sim->b = sim->dalloc<R4<T>>(n_free);
+  sim->diag = sim->dalloc<T>(n_free);
+  sim->sl_ptr = sim->dalloc<int>(sl_ptr.size());
+  sim->sl_col = sim->dalloc<int>(sl_col.size());
+  sim->sl_val = sim->dalloc<T>(sl_val.size());
+  sim->r = sim->dalloc<R4<T>>(n_free);
+  sim->u = sim->dalloc<R4<T>>(n_free);
+  sim->p = sim->dalloc<R4<T>>(n_free);
+  sim->s = sim->dalloc<R4<T>>(n_free);
+  sim->w = sim->dalloc<R4<T>>(n_free);
+  sim->spring_c = sim->dalloc<R4<T>>(n_free);
+  sim->partials = sim->dalloc<double>(2 * 4 * (size_t)std::max(sim->pcg_grid, 1));
+  sim->q_verts_d = sim->dalloc<int>(n_q);
+  sim->qf_ptr = sim->dalloc<int>(n_q + 1);
+  sim->qf = sim->dalloc<int>(qf.size());
+  sim->faces = sim->dalloc<int4>(n_f);
+  sim->spheres_d = sim->dalloc<double>(4 * 64);
+  const size_t H = (size_t)sim->H_t + sim->H_f;
+  sim->cell_count = sim->dalloc<int>(H + 1);
+  sim->cell_start = sim->dalloc<int>(H + 1);
+  sim->cell_cursor = sim->dalloc<int>(H);
+  sim->items = sim->dalloc<int>(sim->cap_items);
+  sim->cs.tile_sums = sim->dalloc<int>(scan_tiles((int)H + 1) + 1);
+  sim->cs.total = sim->dalloc<int>(1);
+  sim->pair_count = sim->dalloc<int>(n_q);
+  sim->pair_tet = sim->dalloc<int>((size_t)n_q * sim->params.max_pairs_per_vertex);
+  sim->obs_sphere = sim->dalloc<int>(n_q);
+  sim->sp.active = sim->dalloc<int>(n_q);
+  sim->sp.kind = sim->dalloc<int>(n_q);
+  sim->sp.face = sim->dalloc<int>(n_q);
+  sim->sp.bary = sim->dalloc<double>(2 * (size_t)n_q);
+  sim->sp.target = sim->dalloc<double>(3 * (size_t)n_q);
+  sim->int_of_user_d = sim->dalloc<int>(n_v);
+  sim->ctrl = sim->dalloc<Ctrl>(1);
+  sim->hist = sim->dalloc<IterRec>(sim->hist_cap);
+  sim->n_e_local = local_blocks(n_t);
+  sim->n_e_spring = spring_blocks(n_q);
+  sim->e_partials = sim->dalloc<double>(sim->n_e_local + sim->n_e_spring + 1);
+  for (void* q : sim->allocs)
+    if (!q) return sim->fail(CASIM_E_CUDA, "cudaMalloc failed");
+  if (!sim->X || !sim->items || !sim->P || !sim->e_partials || !sim->hist)
+    return sim->fail(CASIM_E_CUDA, "device allocation failed");
+
+  std::vector<R4<T>> Xh(n_v);
+  for (int i = 0; i < n_v; ++i) Xh[i] = R4<T>{(T)rest_int[3 * i], (T)rest_int[3 * i + 1], (T)rest_int[3 * i + 2], T(0)};
+  std::vector<int4> th(n_t);
+  for (int e = 0; e < n_t; ++e) th[e] = make_int4(tets_int[4 * e], tets_int[4 * e + 1], tets_int[4 * e + 2], tets_int[4 * e + 3]);
+  std::vector<R4<T>> Tch(3 * (size_t)n_t), info(n_t);
+  for (int e = 0; e < n_t; ++e) {
+    for (int i = 0; i < 3; ++i)
+      Tch[3 * (size_t)e + i] = R4<T>{(T)Tc[12 * (size_t)e + 4 * i], (T)Tc[12 * (size_t)e + 4 * i + 1],
+                                     (T)Tc[12 * (size_t)e + 4 * i + 2], (T)Tc[12 * (size_t)e + 4 * i + 3]};
+    info[e] = R4<T>{(T)sim->omega[e], (T)vol0[e], (T)tt[e], (T)group[e]};
+  }
+  std::vector<int4> fh(n_f);
+  for (int f = 0; f < n_f; ++f) fh[f] = make_int4(faces4[4 * f], faces4[4 * f + 1], faces4[4 * f + 2], faces4[4 * f + 3]);
+  std::vector<T> dl, slv;
+  to_real(diagL, dl);
+  to_real(sl_val, slv);
+  cudaStream_t st = sim->stream;
+  CK(cudaMemcpyAsync(sim->X, Xh.data(), sizeof(R4<T>) * n_v, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->X0, Xh.data(), sizeof(R4<T>) * n_v, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->tet, th.data(), sizeof(int4) * n_t, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->Tc, Tch.data(), sizeof(R4<T>) * 3 * (size_t)n_t, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->tinfo, info.data(), sizeof(R4<T>) * n_t, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->knots_d, sim->knots.data(), sizeof(double) * sim->knots.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->inc_ptr, inc_ptr.data(), sizeof(int) * inc_ptr.size(), cudaMemcpyHostToDevice, st));
+  if (!inc.empty()) CK(cudaMemcpyAsync(sim->inc, inc.data(), sizeof(int) * inc.size(), cudaMemcpyHostToDevice, st));
+  if (!dl.empty()) CK(cudaMemcpyAsync(sim->diagL, dl.data(), sizeof(T) * dl.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->sl_ptr, sl_ptr.data(), sizeof(int) * sl_ptr.size(), cudaMemcpyHostToDevice, st));
+  if (!sl_col.empty()) {
+    CK(cudaMemcpyAsync(sim->sl_col, sl_col.data(), sizeof(int) * sl_col.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sim->sl_val, slv.data(), sizeof(T) * slv.size(), cudaMemcpyHostToDevice, st));
+  }
+  if (n_q) {
+    CK(cudaMemcpyAsync(sim->q_verts_d, sim->q_verts.data(), sizeof(int) * n_q, cudaMemcpyHostToDevice, st));
+  }
+  CK(cudaMemcpyAsync(sim->qf_ptr, qf_ptr.data(), sizeof(int) * qf_ptr.size(), cudaMemcpyHostToDevice, st));
+  if (!qf.empty()) CK(cudaMemcpyAsync(sim->qf, qf.data(), sizeof(int) * qf.size(), cudaMemcpyHostToDevice, st));
+  if (n_f) CK(cudaMemcpyAsync(sim->faces, fh.data(), sizeof(int4) * n_f, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->int_of_user_d, sim->int_of_user.data(), sizeof(int) * n_v, cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(sim->spring_c, 0, sizeof(R4<T>) * std::max(n_free, 1), st));
+  CK(cudaMemsetAsync(sim->sp.active, 0, sizeof(int) * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->sp.kind, 0, sizeof(int) * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->sp.face, 0xff, sizeof(int) * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->sp.bary, 0, sizeof(double) * 2 * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->sp.target, 0, sizeof(double) * 3 * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->pair_count, 0, sizeof(int) * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->obs_sphere, 0xff, sizeof(int) * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->ctrl, 0, sizeof(Ctrl), st));
+  CK(cudaMemsetAsync(sim->hist, 0, sizeof(IterRec) * sim->hist_cap, st));
+  CK(cudaMemsetAsync(sim->e_partials, 0, sizeof(double) * (sim->n_e_local + sim->n_e_spring + 1), st));
+  CK(cudaMemsetAsync(sim->P, 0, sizeof(R4<T>) * 4 * (size_t)std::max(n_t, 1), st));
+  CK(cudaStreamSynchronize(st));
+  return CASIM_OK;
+}
+
+// bfix_v = sum over fixed u of A_vu x_u for every free row (constant between
+// position uploads).
+template <typename T>
+int upload_bfix(casim_sim* sim) {
+  std::vector<R4<T>> bf(std::max(sim->n_free, 1));
+  for (int v = 0; v < sim->n_free; ++v) {
+    double a[3] = {0, 0, 0};
+    for (int k = sim->fx_ptr[v]; k < sim->fx_ptr[v + 1]; ++k) {
+      const int u = sim->fx_col[k] - sim->n_free;
+      for (int c = 0; c < 3; ++c) a[c] += sim->fx_val[k] * sim->X_fixed[3 * (size_t)u + c];
+    }
+    bf[v] = R4<T>{(T)a[0], (T)a[1], (T)a[2], T(0)};
+  }
+  CK(cudaMemcpyAsync(sim->bfix, bf.data(), sizeof(R4<T>) * sim->n_free, cudaMemcpyHostToDevice, sim->stream));
+  CK(cudaStreamSynchronize(sim->stream));
+  return CASIM_OK;
+}
+
+template <typename T>
+int set_positions_typed(casim_sim* sim, const double* xyz) {
+  std::vector<R4<T>> Xh(sim->n_v);
+  for (int uv = 0; uv < sim->n_v; ++uv) {
+    const int i = sim->int_of_user[uv];
+    Xh[i] = R4<T>{(T)xyz[3 * (size_t)uv], (T)xyz[3 * (size_t)uv + 1], (T)xyz[3 * (size_t)uv + 2], T(0)};
+  }
+  for (int i = sim->n_free; i < sim->n_v; ++i)
+    for (int c = 0; c < 3; ++c) sim->X_fixed[3 * (size_t)(i - sim->n_free) + c] = (double)(&Xh[i].x)[c];
+  CK(cudaMemcpyAsync(sim->X, Xh.data(), sizeof(R4<T>) * sim->n_v, cudaMemcpyHostToDevice, sim->stream));
+  CK(cudaMemcpyAsync(sim->X0, Xh.data(), sizeof(R4<T>) * sim->n_v, cudaMemcpyHostToDevice, sim->stream));
+  return upload_bfix<T>(sim);
+}
+
+template <typename T>
+int get_positions_typed(casim_sim* sim, double* host_out, void* dev_out) {
+  const Dev<T> d = make_dev<T>(sim);
+  launch_gather_positions<T>(d, sim->int_of_user_d, sim->n_v, (T*)sim->pos_out, sim->stream);
+  CK(cudaGetLastError());
+  if (dev_out)
+    CK(cudaMemcpyAsync(dev_out, sim->pos_out, sizeof(T) * 3 * (size_t)sim->n_v, cudaMemcpyDeviceToDevice,
+                       sim->stream));
+  if (host_out) {
+    std::vector<T> h(3 * (size_t)sim->n_v);
+    CK(cudaMemcpyAsync(h.data(), sim->pos_out, sizeof(T) * h.size(), cudaMemcpyDeviceToHost, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+    for (size_t i = 0; i < h.size(); ++i) host_out[i] = (double)h[i];
+  }
+  return CASIM_OK;
+}
+
+template <typename T>
+int get_targets_typed(casim_sim* sim, double* out) {
+  std::vector<R4<T>> h(4 * (size_t)sim->n_t);
+  CK(cudaMemcpyAsync(h.data(), sim->P, sizeof(R4<T>) * h.size(), cudaMemcpyDeviceToHost, sim->stream));
+  CK(cudaStreamSynchronize(sim->stream));
+  for (int e = 0; e < sim->n_t; ++e) {
+    const double om = sim->omega[e];
+    for (int k = 0; k < 4; ++k) {
+      const R4<T>& c = h[4 * (size_t)e + k];
+      out[12 * (size_t)e + 0 * 4 + k] = (double)c.x / om;
+      out[12 * (size_t)e + 1 * 4 + k] = (double)c.y / om;
+      out[12 * (size_t)e + 2 * 4 + k] = (double)c.z / om;
+    }
+  }
+  return CASIM_OK;
+}
+
+template <typename T>
+int set_actuation_typed(casim_sim* sim, const std::vector<double>& alpha) {
+  std::vector<T> c(std::max<size_t>(alpha.size(), 1), T(1));
+  for (size_t g = 0; g < alpha.size(); ++g) c[g] = (T)std::cbrt(alpha[g]);
+  CK(cudaMemcpyAsync(sim->cbrt_alpha, c.data(), sizeof(T) * c.size(), cudaMemcpyHostToDevice, sim->stream));
+  CK(cudaStreamSynchronize(sim->stream));
+  return CASIM_OK;
+}
+
+template <typename T>
+int capture_graph(casim_sim* sim) {
+  if (sim->gexec) {
+    cudaGraphExecDestroy(sim->gexec);
+    sim->gexec = nullptr;
+  }
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(sim->cap_stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = enqueue_iteration<T>(sim, sim->cap_stream, nullptr);
+  cudaError_t e2 = cudaStreamEndCapture(sim->cap_stream, &g);
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return sim->fail(CASIM_E_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  }
+  if (e2 != cudaSuccess) return sim->fail(CASIM_E_CUDA, std::string("end capture: ") + cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&sim->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return sim->fail(CASIM_E_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  sim->graph_dirty = false;
+  return CASIM_OK;
+}
+
+template <typename T>
+int step_typed(casim_sim* sim, int n_iters) {
+  if (sim->params.stats >= 2) {
+    // eager launches with events between the phases (diagnostic timing)
+    cudaEvent_t ev[6];
+    for (auto& x : ev) CK(cudaEventCreate(&x));
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int i = 0; i < n_iters; ++i) {
+      cudaError_t e = enqueue_iteration<T>(sim, sim->stream, ev);
+      if (e != cudaSuccess) return sim->fail(CASIM_E_CUDA, cudaGetErrorString(e));
+      CK(cudaEventSynchronize(ev[5]));
+      for (int k = 0; k < 5; ++k) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ev[k], ev[k + 1]);
+        acc[k] += ms;
+      }
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    for (int k = 0; k < 5; ++k) sim->phase_ms[k] = acc[k];
+    sim->iters += n_iters;
+    return CASIM_OK;
+  }
+  if (sim->graph_dirty && !sim->no_graph) {
+    if (capture_graph<T>(sim) != CASIM_OK) {
+      cudaGetLastError();
+      sim->no_graph = true;
+    }
+  }
+  if (sim->no_graph) {
+    for (int i = 0; i < n_iters; ++i) {
+      cudaError_t e = enqueue_iteration<T>(sim, sim->stream, nullptr);
+      if (e != cudaSuccess) return sim->fail(CASIM_E_CUDA, cudaGetErrorString(e));
+    }
+    sim->iters += n_iters;
+    return CASIM_OK;
+  }
+  for (int i = 0; i < n_iters; ++i) CK(cudaGraphLaunch(sim->gexec, sim->stream));
+  sim->iters += n_iters;
+  return CASIM_OK;
+}
+
+struct Triplet {
+  int r, c;
+  double v;
+};
+
+}  // namespace
+
+extern "C" {
+
+void casim_default_params(casim_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->precision = CASIM_MIXED;
+  p->collision = CASIM_COLLISION_SELF;
+  p->k_spring = 1.0;
+  p->eps = 0.005;
+  p->pcg_tol = 1e-6;
+  p->pcg_max_iter = 1000;
+  p->n_w_knots = 0;
+  p->w_knots = nullptr;
+  p->cell_size = 0.5;
+  p->stats = 1;
+  p->max_pairs_per_vertex = 8;
+  p->wait_budget_cycles = 0;
+}
+
+int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out) {
+  if (!params || !out) {
+    g_create_error = "null argument";
+    return CASIM_E_INVALID;
+  }
+  *out = nullptr;
+  const casim_params& p = *params;
+  std::string why;
+  if (p.precision != CASIM_FP64 && p.precision != CASIM_MIXED) why = "precision";
+  else if (p.collision < 0 || p.collision > 2) why = "collision";
+  else if (!(p.k_spring >= 0.0) || !std::isfinite(p.k_spring)) why = "k_spring";
+  else if (!(p.eps >= 0.0) || !std::isfinite(p.eps)) why = "eps";
+  else if (!(p.pcg_tol > 0.0) || !std::isfinite(p.pcg_tol)) why = "pcg_tol";
+  else if (p.pcg_max_iter < 1) why = "pcg_max_iter";
+  else if (p.n_w_knots < 0 || (p.n_w_knots > 0 && !p.w_knots) || p.n_w_knots > 64) why = "w_knots";
+  else if (!(p.cell_size > 0.0) || !std::isfinite(p.cell_size)) why = "cell_size";
+  else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
+  if (why.empty() && p.n_w_knots > 1) {
+    for (int i = 0; i + 1 < p.n_w_knots; ++i)
+      if (!(p.w_knots[2 * i + 2] > p.w_knots[2 * i])) why = "w_knots must be strictly ascending";
+  }
+  if (!why.empty()) {
+    g_create_error = "invalid parameter: " + why;
+    return CASIM_E_INVALID;
+  }
+  casim_sim* sim = new (std::nothrow) casim_sim();
+  if (!sim) {
+    g_create_error = "out of host memory";
+    return CASIM_E_INVALID;
+  }
+  sim->params = p;
+  if (p.n_w_knots > 0)
+    sim->knots.assign(p.w_knots, p.w_knots + 2 * p.n_w_knots);
+  else
+    sim->knots = {0.0, 1.0};
+  sim->params.w_knots = nullptr;
+  sim->params.n_w_knots = (int)sim->knots.size() / 2;
+  sim->stream = static_cast<cudaStream_t>(cuda_stream);
+  if (cudaGetDevice(&sim->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    g_create_error = "CUDA unavailable";
+    delete sim;
+    return CASIM_E_CUDA;
+  }
+  *out = sim;
+  return CASIM_OK;
+}
+
+int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, int32_t n_tets,
+                      const int32_t* tets, const int32_t* tet_group, const uint8_t* fixed) {
+  if (!sim) return CASIM_E_INVALID;
+  if (n_verts <= 0 || n_tets <= 0 || !rest_xyz || !tets || !tet_group || !fixed)
+    return sim->fail(CASIM_E_INVALID, "empty mesh or null pointer");
+  for (long long i = 0; i < 3LL * n_verts; ++i)
+    if (!std::isfinite(rest_xyz[i])) return sim->fail(CASIM_E_INVALID, "non-finite rest position");
+  int max_group = -1;
+  for (int e = 0; e < n_tets; ++e) {
+    for (int k = 0; k < 4; ++k)
+      if (tets[4 * e + k] < 0 || tets[4 * e + k] >= n_verts)
+        return sim->fail(CASIM_E_INVALID, "tet vertex id out of range at tet " + std::to_string(e));
+    for (int k = 0; k < 4; ++k)
+      for (int j = k + 1; j < 4; ++j)
+        if (tets[4 * e + k] == tets[4 * e + j])
+          return sim->fail(CASIM_E_INVALID, "repeated vertex in tet " + std::to_string(e));
+    if (tet_group[e] < -1) return sim->fail(CASIM_E_INVALID, "group id < -1");
+    max_group = std::max(max_group, (int)tet_group[e]);
+  }
+  sim->free_all();
+  sim->has_mesh = false;
+  sim->has_act = false;
+  const int n_v = n_verts, n_t = n_tets;
+  // ---- rest element quantities (FP64) ----
+  std::vector<double> Tc(12 * (size_t)n_t), vol0(n_t), tt(n_t);
+  double vsum = 0.0;
+  for (int e = 0; e < n_t; ++e) {
+    double V[3][4];
+    for (int k = 0; k < 4; ++k)
+      for (int i = 0; i < 3; ++i) V[i][k] = rest_xyz[3 * (size_t)tets[4 * e + k] + i];
+    const double a0 = V[0][1] - V[0][0], a1 = V[1][1] - V[1][0], a2 = V[2][1] - V[2][0];
+    const double b0 = V[0][2] - V[0][0], b1 = V[1][2] - V[1][0], b2 = V[2][2] - V[2][0];
+    const double c0 = V[0][3] - V[0][0], c1 = V[1][3] - V[1][0], c2 = V[2][3] - V[2][0];
+    const double vol = (a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0)) / 6.0;
+    if (!(vol > 0.0)) return sim->fail(CASIM_E_INVALID, "non-positive rest volume at tet " + std::to_string(e));
+    vol0[e] = vol;
+    vsum += vol;
+    double s2 = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      const double m = 0.25 * (V[i][0] + V[i][1] + V[i][2] + V[i][3]);
+      for (int k = 0; k < 4; ++k) {
+        const double c = V[i][k] - m;
+        Tc[12 * (size_t)e + 4 * i + k] = c;
+        s2 += c * c;
+      }
+    }
+    tt[e] = s2;
+  }
+  const double vmean = vsum / n_t;
+  sim->omega.resize(n_t);
+  for (int e = 0; e < n_t; ++e) sim->omega[e] = vol0[e] / vmean;
+  // ---- connected components must each hold a fixed vertex ----
+  {
+    std::vector<int> parent(n_v);
+    std::iota(parent.begin(), parent.end(), 0);
+    auto find = [&](int x) {
+      while (parent[x] != x) {
+        parent[x] = parent[parent[x]];
+        x = parent[x];
+      }
+      return x;
+    };
+    std::vector<char> used(n_v, 0);
+    for (int e = 0; e < n_t; ++e) {
+      for (int k = 0; k < 4; ++k) used[tets[4 * e + k]] = 1;
+      const int a = find(tets[4 * e]);
+      for (int k = 1; k < 4; ++k) {
+        const int b = find(tets[4 * e + k]);
+        if (a != b) parent[b] = a;
+      }
+    }
+    std::vector<char> has_fixed(n_v, 0);
+    for (int v = 0; v < n_v; ++v)
+      if (fixed[v]) has_fixed[find(v)] = 1;
+    for (int v = 0; v < n_v; ++v) {
+      if (!used[v] && !fixed[v])
+        return sim->fail(CASIM_E_SINGULAR, "free vertex " + std::to_string(v) + " belongs to no tet");
+      if (used[v] && !has_fixed[find(v)])
+        return sim->fail(CASIM_E_SINGULAR, "component of vertex " + std::to_string(v) + " has no fixed vertex");
+    }
+  }
+  // ---- internal numbering: free vertices first ----
+  sim->n_v = n_v;
+  sim->n_t = n_t;
+  sim->int_of_user.assign(n_v, -1);
+  sim->user_of_int.assign(n_v, -1);
+  int nf = 0;
+  for (int v = 0; v < n_v; ++v)
+    if (!fixed[v]) sim->int_of_user[v] = nf++;
+  sim->n_free = nf;
+  int nx = nf;
+  for (int v = 0; v < n_v; ++v)
+    if (fixed[v]) sim->int_of_user[v] = nx++;
+  for (int v = 0; v < n_v; ++v) sim->user_of_int[sim->int_of_user[v]] = v;
+  const int n_free = nf;
+  std::vector<int> tets_int(4 * (size_t)n_t);
+  for (size_t i = 0; i < tets_int.size(); ++i) tets_int[i] = sim->int_of_user[tets[i]];
+  std::vector<int> group(tet_group, tet_group + n_t);
+  sim->n_groups = max_group + 1;
+  std::vector<double> rest_int(3 * (size_t)n_v);
+  for (int v = 0; v < n_v; ++v)
+    for (int c = 0; c < 3; ++c) rest_int[3 * (size_t)sim->int_of_user[v] + c] = rest_xyz[3 * (size_t)v + c];
+  sim->X_fixed.assign(3 * (size_t)(n_v - n_free), 0.0);
+  for (int i = n_free; i < n_v; ++i)
+    for (int c = 0; c < 3; ++c) sim->X_fixed[3 * (size_t)(i - n_free) + c] = rest_int[3 * (size_t)i + c];
+  // ---- boundary faces: faces of exactly one tet, ordered by (tet, k) ----
+  std::vector<int> faces4;
+  {
+    std::vector<std::array<int, 4>> keys(4 * (size_t)n_t);  // sorted triple + index
+    for (int e = 0; e < n_t; ++e)
+      for (int k = 0; k < 4; ++k) {
+        int a = tets[4 * e + kTetFace[k][0]], b = tets[4 * e + kTetFace[k][1]], c = tets[4 * e + kTetFace[k][2]];
+        int t3[3] = {a, b, c};
+        std::sort(t3, t3 + 3);
+        keys[4 * (size_t)e + k] = {t3[0], t3[1], t3[2], 4 * e + k};
+      }
+    std::sort(keys.begin(), keys.end());
+    std::vector<char> once(4 * (size_t)n_t, 0);
+    for (size_t i = 0; i < keys.size();) {
+      size_t j = i + 1;
+      while (j < keys.size() && keys[j][0] == keys[i][0] && keys[j][1] == keys[i][1] && keys[j][2] == keys[i][2]) ++j;
+      if (j - i == 1) once[keys[i][3]] = 1;
+      i = j;
+    }
+    for (int idx = 0; idx < 4 * n_t; ++idx)
+      if (once[idx]) {
+        const int e = idx / 4, k = idx % 4;
+        faces4.push_back(tets_int[4 * e + kTetFace[k][0]]);
+        faces4.push_back(tets_int[4 * e + kTetFace[k][1]]);
+        faces4.push_back(tets_int[4 * e + kTetFace[k][2]]);
+        faces4.push_back(e);
+      }
+  }
+  sim->n_f = (int)(faces4.size() / 4);
+  // ---- query vertices (non-fixed boundary vertices) and incident faces ----
+  std::vector<char> on_surf(n_v, 0);
+  for (int f = 0; f < sim->n_f; ++f)
+    for (int k = 0; k < 3; ++k) on_surf[faces4[4 * f + k]] = 1;
+  sim->q_verts.clear();
+  std::vector<int> qidx(n_v, -1);
+  for (int i = 0; i < n_free; ++i)
+    if (on_surf[i]) {
+      qidx[i] = (int)sim->q_verts.size();
+      sim->q_verts.push_back(i);
+    }
+  sim->n_q = (int)sim->q_verts.size();
+  std::vector<int> qf_ptr(sim->n_q + 1, 0), qf;
+  for (int f = 0; f < sim->n_f; ++f)
+    for (int k = 0; k < 3; ++k)
+      if (qidx[faces4[4 * f + k]] >= 0) qf_ptr[qidx[faces4[4 * f + k]] + 1]++;
+  for (int q = 0; q < sim->n_q; ++q) qf_ptr[q + 1] += qf_ptr[q];
+  qf.assign(qf_ptr[sim->n_q], 0);
+  {
+    std::vector<int> cur(qf_ptr.begin(), qf_ptr.end() - 1);
+    for (int f = 0; f < sim->n_f; ++f)
+      for (int k = 0; k < 3; ++k) {
+        const int q = qidx[faces4[4 * f + k]];
+        if (q >= 0) qf[cur[q]++] = f;
+      }
+  }
+  // ---- incidence CSR of free vertices: entries tet*4 + slot, by tet ----
+  std::vector<int> inc_ptr(n_free + 1, 0), inc;
+  for (int e = 0; e < n_t; ++e)
+    for (int k = 0; k < 4; ++k)
+      if (tets_int[4 * e + k] < n_free) inc_ptr[tets_int[4 * e + k] + 1]++;
+  for (int v = 0; v < n_free; ++v) inc_ptr[v + 1] += inc_ptr[v];
+  inc.assign(inc_ptr[n_free], 0);
+  {
+    std::vector<int> cur(inc_ptr.begin(), inc_ptr.end() - 1);
+    for (int e = 0; e < n_t; ++e)
+      for (int k = 0; k < 4; ++k) {
+        const int v = tets_int[4 * e + k];
+        if (v < n_free) inc[cur[v]++] = 4 * e + k;
+      }
+  }
+  // ---- Laplacian L_w: 3/4 w on the diagonal, -1/4 w per element edge ----
+  std::vector<double> diagL(n_free, 0.0);
+  std::vector<int> rptr(n_free + 1, 0);
+  for (int e = 0; e < n_t; ++e)
+    for (int a = 0; a < 4; ++a)
+      if (tets_int[4 * e + a] < n_free) rptr[tets_int[4 * e + a] + 1] += 3;
+  for (int v = 0; v < n_free; ++v) rptr[v + 1] += rptr[v];
+  std::vector<std::pair<int, double>> ent(rptr[n_free]);
+  {
+    std::vector<int> cur(rptr.begin(), rptr.end() - 1);
+    for (int e = 0; e < n_t; ++e) {
+      const double w = sim->omega[e];
+      for (int a = 0; a < 4; ++a) {
+        const int va = tets_int[4 * e + a];
+        if (va >= n_free) continue;
+        diagL[va] += 0.75 * w;
+        for (int b = 0; b < 4; ++b)
+          if (b != a) ent[cur[va]++] = {tets_int[4 * e + b], -0.25 * w};
+      }
+    }
+  }
+  std::vector<int> row_len(n_free, 0);
+  std::vector<std::vector<std::pair<int, double>>> rows_ff(n_free);
+  sim->fx_ptr.assign(n_free + 1, 0);
+  sim->fx_col.clear();
+  sim->fx_val.clear();
+  for (int v = 0; v < n_free; ++v) {
+    auto beg = ent.begin() + rptr[v], end = ent.begin() + rptr[v + 1];
+    std::sort(beg, end, [](const std::pair<int, double>& x, const std::pair<int, double>& y) { return x.first < y.first; });
+    std::vector<std::pair<int, double>> merged;
+    for (auto it = beg; it != end; ++it) {
+      if (!merged.empty() && merged.back().first == it->first)
+        merged.back().second += it->second;
+      else
+        merged.push_back(*it);
+    }
+    for (auto& m : merged) {
+      if (m.first < n_free)
+        rows_ff[v].push_back(m);
+      else {
+        sim->fx_col.push_back(m.first);
+        sim->fx_val.push_back(m.second);
+      }
+    }
+    sim->fx_ptr[v + 1] = (int)sim->fx_col.size();
+  }
+  // ---- sliced ELL (32-row slices, column-major inside a slice) ----
+  sim->n_slices = (n_free + 31) / 32;
+  std::vector<int> sl_ptr(sim->n_slices + 1, 0), sl_col;
+  std::vector<double> sl_val;
+  for (int s = 0; s < sim->n_slices; ++s) {
+    int width = 0;
+    for (int l = 0; l < 32 && 32 * s + l < n_free; ++l) width = std::max(width, (int)rows_ff[32 * s + l].size());
+    sl_ptr[s + 1] = sl_ptr[s] + 32 * width;
+  }
+  sl_col.assign(sl_ptr[sim->n_slices], 0);
+  sl_val.assign(sl_ptr[sim->n_slices], 0.0);
+  for (int s = 0; s < sim->n_slices; ++s) {
+    const int width = (sl_ptr[s + 1] - sl_ptr[s]) / 32;
+    for (int l = 0; l < 32; ++l) {
+      const int row = 32 * s + l;
+      for (int j = 0; j < width; ++j) {
+        const size_t k = sl_ptr[s] + (size_t)j * 32 + l;
+        if (row < n_free && j < (int)rows_ff[row].size()) {
+          sl_col[k] = rows_ff[row][j].first;
+          sl_val[k] = rows_ff[row][j].second;
+        } else {
+          sl_col[k] = row < n_free ? row : 0;
+          sl_val[k] = 0.0;
+        }
+      }
+    }
+  }
+  // ---- spatial hash sizes ----
+  sim->H_t = (unsigned)pow2_at_least(2 * (size_t)n_t);
+  sim->H_f = (unsigned)pow2_at_least(2 * (size_t)std::max(sim->n_f, 1));
+  sim->cap_items = (int)std::min<long long>(16LL * (n_t + sim->n_f) + 4096, 2000000000LL);
+  // ---- PCG grid: co-resident blocks, no more than the rows need ----
+  const int maxg = sim->params.precision == CASIM_FP64 ? pcg_max_grid<double>() : pcg_max_grid<float>();
+  sim->pcg_grid = std::max(1, std::min(maxg, (n_free + PCG_THREADS - 1) / PCG_THREADS));
+  sim->rs = sim->params.precision == CASIM_FP64 ? 8 : 4;
+  int rc;
+  if (sim->params.precision == CASIM_FP64)
+    rc = upload_typed<double>(sim, rest_int, tets_int, group, Tc, vol0, tt, faces4, qf_ptr, qf, inc_ptr, inc, diagL,
+                              sl_ptr, sl_col, sl_val);
+  else
+    rc = upload_typed<float>(sim, rest_int, tets_int, group, Tc, vol0, tt, faces4, qf_ptr, qf, inc_ptr, inc, diagL,
+                             sl_ptr, sl_col, sl_val);
+  if (rc) {
+    sim->free_all();
+    return rc;
+  }
+  rc = sim->params.precision == CASIM_FP64 ? upload_bfix<double>(sim) : upload_bfix<float>(sim);
+  if (rc) {
+    sim->free_all();
+    return rc;
+  }
+  if (!sim->spheres.empty()) {
+    const int n = sim->n_spheres;
+    CK(cudaMemcpy(sim->spheres_d, sim->spheres.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice));
+  }
+  sim->iters = 0;
+  sim->has_mesh = true;
+  sim->graph_dirty = true;
+  if (sim->n_groups == 0) {
+    std::vector<double> none;
+    rc = sim->params.precision == CASIM_FP64 ? set_actuation_typed<double>(sim, none)
+                                             : set_actuation_typed<float>(sim, none);
+    if (rc) return rc;
+    sim->has_act = true;
+  }
+  return CASIM_OK;
+}
+
+int casim_set_actuation(casim_sim* sim, int32_t n_groups, const double* alpha) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  if (n_groups != sim->n_groups) return sim->fail(CASIM_E_INVALID, "n_groups must equal 1 + the largest group id");
+  if (n_groups > 0 && !alpha) return sim->fail(CASIM_E_INVALID, "null alpha");
+  std::vector<double> a(alpha, alpha + n_groups);
+  for (double x : a)
+    if (!(x > 0.0) || !std::isfinite(x)) return sim->fail(CASIM_E_INVALID, "volume ratio must be positive");
+  const int rc = sim->params.precision == CASIM_FP64 ? set_actuation_typed<double>(sim, a)
+                                                     : set_actuation_typed<float>(sim, a);
+  if (rc) return rc;
+  sim->has_act = true;
+  return CASIM_OK;
+}
+
+int casim_set_spheres(casim_sim* sim, int32_t n, const double* cxyzr) {
+  if (!sim) return CASIM_E_INVALID;
+  if (n < 0 || n > 64 || (n > 0 && !cxyzr)) return sim->fail(CASIM_E_INVALID, "0 <= n <= 64 spheres");
+  for (int i = 0; i < 4 * n; ++i)
+    if (!std::isfinite(cxyzr[i])) return sim->fail(CASIM_E_INVALID, "non-finite sphere");
+  for (int i = 0; i < n; ++i)
+    if (!(cxyzr[4 * i + 3] > 0.0)) return sim->fail(CASIM_E_INVALID, "sphere radius must be positive");
+  sim->spheres.assign(cxyzr, cxyzr + 4 * n);
+  sim->n_spheres = n;
+  if (sim->has_mesh && n > 0)
+    CK(cudaMemcpy(sim->spheres_d, sim->spheres.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice));
+  sim->graph_dirty = true;
+  return CASIM_OK;
+}
+
+int casim_set_positions(casim_sim* sim, const double* xyz) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  if (!xyz) return sim->fail(CASIM_E_INVALID, "null positions");
+  for (long long i = 0; i < 3LL * sim->n_v; ++i)
+    if (!std::isfinite(xyz[i])) return sim->fail(CASIM_E_INVALID, "non-finite position");
+  return sim->params.precision == CASIM_FP64 ? set_positions_typed<double>(sim, xyz)
+                                             : set_positions_typed<float>(sim, xyz);
+}
+
+int casim_reset(casim_sim* sim) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  const size_t nq = std::max(sim->n_q, 1);
+  CK(cudaMemcpyAsync(sim->X, sim->X0, 4 * sim->rs * (size_t)sim->n_v, cudaMemcpyDeviceToDevice, sim->stream));
+  CK(cudaMemsetAsync(sim->spring_c, 0, 4 * sim->rs * (size_t)std::max(sim->n_free, 1), sim->stream));
+  CK(cudaMemsetAsync(sim->sp.active, 0, sizeof(int) * nq, sim->stream));
+  CK(cudaMemsetAsync(sim->sp.kind, 0, sizeof(int) * nq, sim->stream));
+  CK(cudaMemsetAsync(sim->sp.face, 0xff, sizeof(int) * nq, sim->stream));
+  CK(cudaMemsetAsync(sim->sp.bary, 0, sizeof(double) * 2 * nq, sim->stream));
+  CK(cudaMemsetAsync(sim->sp.target, 0, sizeof(double) * 3 * nq, sim->stream));
+  return CASIM_OK;
+}
+
+int casim_step(casim_sim* sim, int32_t n_iters) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  if (!sim->has_act) return sim->fail(CASIM_E_STATE, "no actuation set");
+  if (n_iters < 0) return sim->fail(CASIM_E_INVALID, "n_iters < 0");
+  if (n_iters == 0) return CASIM_OK;
+  return sim->params.precision == CASIM_FP64 ? step_typed<double>(sim, n_iters) : step_typed<float>(sim, n_iters);
+}
+
+int casim_sync(casim_sim* sim) {
+  if (!sim) return CASIM_E_INVALID;
+  CK(cudaStreamSynchronize(sim->stream));
+  if (!sim->has_mesh) return CASIM_OK;
+  int st = 0;
+  CK(cudaMemcpy(&st, &sim->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemset(&sim->ctrl->status, 0, sizeof(int)));
+  int rc = CASIM_OK;
+  if (st & ST_TIMEOUT) rc = CASIM_E_TIMEOUT;
+  else if (st & ST_NONFINITE) rc = CASIM_E_NONFINITE;
+  else if (st & ST_OVERFLOW) rc = CASIM_E_OVERFLOW;
+  else if (st & ST_PCG_MAXIT) rc = CASIM_W_PCG_MAXIT;
+  sim->last_status = rc;
+  if (rc < 0) sim->err = "device status " + std::to_string(st);
+  return rc;
+}
+
+int casim_get_positions(casim_sim* sim, double* host_out, void* dev_out) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  return sim->params.precision == CASIM_FP64 ? get_positions_typed<double>(sim, host_out, dev_out)
+                                             : get_positions_typed<float>(sim, host_out, dev_out);
+}
+
+int casim_get_contacts(casim_sim* sim, int32_t* pairs, int64_t* n_pairs, int32_t* obstacle_verts, int64_t* n_obst) {
+  if (!sim || !n_pairs || !n_obst) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  const int n_q = sim->n_q, mp = sim->params.max_pairs_per_vertex;
+  std::vector<int> cnt(std::max(n_q, 1)), pt((size_t)std::max(n_q, 1) * mp), obs(std::max(n_q, 1));
+  CK(cudaStreamSynchronize(sim->stream));
+  if (n_q) {
+    CK(cudaMemcpy(cnt.data(), sim->pair_count, sizeof(int) * n_q, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(pt.data(), sim->pair_tet, sizeof(int) * (size_t)n_q * mp, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(obs.data(), sim->obs_sphere, sizeof(int) * n_q, cudaMemcpyDeviceToHost));
+  }
+  const int64_t cap_p = *n_pairs, cap_o = *n_obst;
+  int64_t np = 0, no = 0;
+  for (int q = 0; q < n_q; ++q) {
+    const int uv = sim->user_of_int[sim->q_verts[q]];
+    const int c = std::min(cnt[q], mp);
+    for (int j = 0; j < c; ++j) {
+      if (pairs && np < cap_p) {
+        pairs[2 * np] = uv;
+        pairs[2 * np + 1] = pt[(size_t)q * mp + j];
+      }
+      ++np;
+    }
+    if (obs[q] >= 0) {
+      if (obstacle_verts && no < cap_o) obstacle_verts[no] = uv;
+      ++no;
+    }
+  }
+  *n_pairs = np;
+  *n_obst = no;
+  if (np > cap_p || no > cap_o) return sim->fail(CASIM_E_CAPACITY, "contact buffer too small");
+  return CASIM_OK;
+}
+
+int casim_get_springs(casim_sim* sim, int64_t* n, int32_t* verts, uint8_t* active, int32_t* kind, int32_t* face,
+                      double* bary, double* target) {
+  if (!sim || !n) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  const int n_q = sim->n_q;
+  if (*n < n_q) {
+    *n = n_q;
+    return sim->fail(CASIM_E_CAPACITY, "spring buffer too small");
+  }
+  *n = n_q;
+  if (n_q == 0) return CASIM_OK;
+  std::vector<int> a(n_q), k(n_q), f(n_q);
+  std::vector<double> b(2 * (size_t)n_q), t(3 * (size_t)n_q);
+  CK(cudaStreamSynchronize(sim->stream));
+  CK(cudaMemcpy(a.data(), sim->sp.active, sizeof(int) * n_q, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(k.data(), sim->sp.kind, sizeof(int) * n_q, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(f.data(), sim->sp.face, sizeof(int) * n_q, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(b.data(), sim->sp.bary, sizeof(double) * 2 * n_q, cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(t.data(), sim->sp.target, sizeof(double) * 3 * n_q, cudaMemcpyDeviceToHost));
+  for (int q = 0; q < n_q; ++q) {
+    if (verts) verts[q] = sim->user_of_int[sim->q_verts[q]];
+    if (active) active[q] = (uint8_t)(a[q] != 0);
+    if (kind) kind[q] = k[q];
+    if (face) face[q] = f[q];
+    if (bary) {
+      bary[2 * q] = b[2 * q];
+      bary[2 * q + 1] = b[2 * q + 1];
+    }
+    if (target)
+      for (int c = 0; c < 3; ++c) target[3 * q + c] = t[3 * q + c];
+  }
+  return CASIM_OK;
+}
+
+int casim_set_springs(casim_sim* sim, int64_t n, const int32_t* verts, const uint8_t* active, const int32_t* kind,
+                      const int32_t* face, const double* bary, const double* target) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  const int n_q = sim->n_q;
+  if (n != n_q || !verts || !active || !kind || !face || !bary || !target)
+    return sim->fail(CASIM_E_INVALID, "spring records must cover every non-fixed boundary vertex");
+  std::vector<int> a(n_q), k(n_q), f(n_q);
+  for (int q = 0; q < n_q; ++q) {
+    if (verts[q] != sim->user_of_int[sim->q_verts[q]]) return sim->fail(CASIM_E_INVALID, "spring vertex order");
+    a[q] = active[q] ? 1 : 0;
+    k[q] = kind[q];
+    f[q] = face[q];
+    if (a[q] && (k[q] < 0 || k[q] > 1)) return sim->fail(CASIM_E_INVALID, "spring kind");
+    if (a[q] && k[q] == 0 && (f[q] < 0 || f[q] >= sim->n_f)) return sim->fail(CASIM_E_INVALID, "spring face id");
+    if (a[q] && k[q] == 1 && (f[q] < 0 || f[q] >= sim->n_spheres)) return sim->fail(CASIM_E_INVALID, "spring sphere id");
+  }
+  if (n_q == 0) return CASIM_OK;
+  CK(cudaMemcpy(sim->sp.active, a.data(), sizeof(int) * n_q, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sim->sp.kind, k.data(), sizeof(int) * n_q, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sim->sp.face, f.data(), sizeof(int) * n_q, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sim->sp.bary, bary, sizeof(double) * 2 * n_q, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(sim->sp.target, target, sizeof(double) * 3 * n_q, cudaMemcpyHostToDevice));
+  return CASIM_OK;
+}
+
+int casim_get_targets(casim_sim* sim, double* host_out) {
+  if (!sim || !host_out) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  return sim->params.precision == CASIM_FP64 ? get_targets_typed<double>(sim, host_out)
+                                             : get_targets_typed<float>(sim, host_out);
+}
+
+int casim_get_history(casim_sim* sim, int32_t cap, casim_iter_record* out, int32_t* n) {
+  if (!sim || !n || cap < 0 || (cap > 0 && !out)) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  CK(cudaStreamSynchronize(sim->stream));
+  long long done = 0;
+  CK(cudaMemcpy(&done, &sim->ctrl->iter, sizeof(long long), cudaMemcpyDeviceToHost));
+  std::vector<IterRec> h(sim->hist_cap);
+  CK(cudaMemcpy(h.data(), sim->hist, sizeof(IterRec) * sim->hist_cap, cudaMemcpyDeviceToHost));
+  const long long avail = std::min<long long>(done, sim->hist_cap);
+  const long long m = std::min<long long>(avail, cap);
+  for (long long j = 0; j < m; ++j) {
+    const IterRec& r = h[(done - m + j) % sim->hist_cap];
+    out[j].energy = r.energy;
+    out[j].pcg_rel_residual = r.pcg_rel_residual;
+    out[j].n_self_pairs = r.n_self_pairs;
+    out[j].n_obstacle_pairs = r.n_obstacle_pairs;
+    out[j].n_springs = r.n_springs;
+    out[j].pcg_iters = r.pcg_iters;
+  }
+  *n = (int32_t)m;
+  return CASIM_OK;
+}
+
+int casim_get_stats(casim_sim* sim, casim_stats* out) {
+  if (!sim || !out) return CASIM_E_INVALID;
+  std::memset(out, 0, sizeof(*out));
+  if (!sim->has_mesh) return CASIM_OK;
+  CK(cudaStreamSynchronize(sim->stream));
+  Ctrl c;
+  CK(cudaMemcpy(&c, sim->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost));
+  out->iterations = c.iter;
+  out->total_pcg_iters = c.total_pcg;
+  out->status = sim->last_status;
+  if (c.iter > 0) {
+    IterRec r;
+    CK(cudaMemcpy(&r, sim->hist + ((c.iter - 1) % sim->hist_cap), sizeof(IterRec), cudaMemcpyDeviceToHost));
+    out->last.energy = r.energy;
+    out->last.pcg_rel_residual = r.pcg_rel_residual;
+    out->last.n_self_pairs = r.n_self_pairs;
+    out->last.n_obstacle_pairs = r.n_obstacle_pairs;
+    out->last.n_springs = r.n_springs;
+    out->last.pcg_iters = r.pcg_iters;
+  }
+  return CASIM_OK;
+}
+
+// Checkpoint layout: header (magic, version, precision, n_v, n_q), positions
+// (n_v*3 doubles, caller order), then per spring vertex active, kind, face
+// (int32), bary (2 doubles), target (3 doubles).
+namespace {
+struct StateHeader {
+  uint32_t magic, version;
+  int32_t precision, n_v, n_q, pad;
+};
+const uint32_t kMagic = 0x4d495343u;  // "CSIM"
+}  // namespace
+
+int casim_save_state(casim_sim* sim, void* buf, size_t* len) {
+  if (!sim || !len) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  const size_t nq = sim->n_q;
+  const size_t need = sizeof(StateHeader) + sizeof(double) * 3 * sim->n_v + nq * (3 * sizeof(int32_t) + 5 * sizeof(double));
+  if (!buf) {
+    *len = need;
+    return CASIM_OK;
+  }
+  if (*len < need) {
+    *len = need;
+    return sim->fail(CASIM_E_CAPACITY, "state buffer too small");
+  }
+  char* o = static_cast<char*>(buf);
+  StateHeader h{kMagic, 1u, sim->params.precision, sim->n_v, sim->n_q, 0};
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  int rc = casim_get_positions(sim, reinterpret_cast<double*>(o), nullptr);
+  if (rc) return rc;
+  o += sizeof(double) * 3 * sim->n_v;
+  std::vector<int32_t> verts(nq), kind(nq), face(nq);
+  std::vector<uint8_t> act(nq);
+  std::vector<double> bary(2 * nq), tgt(3 * nq);
+  int64_t n = (int64_t)nq;
+  rc = casim_get_springs(sim, &n, verts.data(), act.data(), kind.data(), face.data(), bary.data(), tgt.data());
+  if (rc) return rc;
+  for (size_t q = 0; q < nq; ++q) {
+    const int32_t a = act[q];
+    std::memcpy(o, &a, 4);
+    std::memcpy(o + 4, &kind[q], 4);
+    std::memcpy(o + 8, &face[q], 4);
+    std::memcpy(o + 12, &bary[2 * q], 16);
+    std::memcpy(o + 28, &tgt[3 * q], 24);
+    o += 52;
+  }
+  *len = need;
+  return CASIM_OK;
+}
+
+int casim_load_state(casim_sim* sim, const void* buf, size_t len) {
+  if (!sim || !buf) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  const size_t nq = sim->n_q;
+  const size_t need = sizeof(StateHeader) + sizeof(double) * 3 * sim->n_v + nq * 52;
+  if (len < need) return sim->fail(CASIM_E_INVALID, "state buffer too short");
+  const char* o = static_cast<const char*>(buf);
+  StateHeader h;
+  std::memcpy(&h, o, sizeof(h));
+  if (h.magic != kMagic || h.version != 1u || h.n_v != sim->n_v || h.n_q != sim->n_q)
+    return sim->fail(CASIM_E_INVALID, "state does not match this mesh");
+  o += sizeof(h);
+  std::vector<double> X(3 * (size_t)sim->n_v);
+  std::memcpy(X.data(), o, sizeof(double) * X.size());
+  o += sizeof(double) * X.size();
+  int rc = casim_set_positions(sim, X.data());
+  if (rc) return rc;
+  std::vector<int32_t> verts(nq), kind(nq), face(nq);
+  std::vector<uint8_t> act(nq);
+  std::vector<double> bary(2 * nq), tgt(3 * nq);
+  for (size_t q = 0; q < nq; ++q) {
+    int32_t a;
+    std::memcpy(&a, o, 4);
+    act[q] = (uint8_t)(a != 0);
+    std::memcpy(&kind[q], o + 4, 4);
+    std::memcpy(&face[q], o + 8, 4);
+    std::memcpy(&bary[2 * q], o + 12, 16);
+    std::memcpy(&tgt[3 * q], o + 28, 24);
+    verts[q] = sim->user_of_int[sim->q_verts[q]];
+    o += 52;
+  }
+  return casim_set_springs(sim, (int64_t)nq, verts.data(), act.data(), kind.data(), face.data(), bary.data(), tgt.data());
+}
+
+int casim_get_sizes(casim_sim* sim, int32_t* n_verts, int32_t* n_tets, int32_t* n_free, int32_t* n_boundary_faces,
+                    int32_t* n_query_verts) {
+  if (!sim) return CASIM_E_INVALID;
+  if (n_verts) *n_verts = sim->n_v;
+  if (n_tets) *n_tets = sim->n_t;
+  if (n_free) *n_free = sim->n_free;
+  if (n_boundary_faces) *n_boundary_faces = sim->n_f;
+  if (n_query_verts) *n_query_verts = sim->n_q;
+  return CASIM_OK;
+}
+
+int casim_get_phase_times(casim_sim* sim, double* ms_out5) {
+  if (!sim || !ms_out5) return CASIM_E_INVALID;
+  for (int k = 0; k < 5; ++k) ms_out5[k] = sim->phase_ms[k];
+  return CASIM_OK;
+}
+
+void casim_destroy(casim_sim* sim) {
+  if (!sim) return;
+  cudaStreamSynchronize(sim->stream);
+  sim->free_all();
+  if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
+  delete sim;
+}
+
+const char* casim_last_error(const casim_sim* sim) {
+  if (!sim) return g_create_error.c_str();
+  return sim->err.c_str();
+}
+
+}  // extern "C"

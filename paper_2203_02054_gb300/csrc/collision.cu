@@ -1,0 +1,568 @@
+// Collision check (Sec. II-B, Eq. 3, Eq. 4) and spring update (Sec. II-C,
+// Eq. 5, Sec. III-A.3) kernels.
+//
+// Broad phase: one spatial hash over tets and one over boundary faces, rebuilt
+// every iteration from the current positions (counting sort: count, scan,
+// fill).  A point strictly inside a tet lies in the tet's closed bounding box,
+// whose cell range covers the point's cell, so the hash never drops a pair;
+// hash collisions only add candidates.
+//
+// Narrow phase: one thread per non-fixed boundary vertex tests the tets of its
+// cell with exact orientation signs (predicates.cuh), so the pair set equals
+// the brute-force definition bit for bit.
+//
+// Spring update: one thread per non-fixed boundary vertex; self-collision
+// targets by a ray cast along -n(v) (3D-DDA cell walk of Amanatides and Woo
+// 1987 over the face hash, Moller-Trumbore 1997 ray-triangle test), obstacle
+// targets in closed form, release by the paper's condition.  All spring
+// geometry is evaluated in FP64.
+#include "common.cuh"
+#include "kernels.h"
+#include "predicates.cuh"
+
+namespace casim {
+
+static constexpr int MAX_CELLS_PER_ITEM = 512;
+static constexpr int MAX_DDA_STEPS = 4096;
+
+template <typename T>
+__device__ __forceinline__ void load3(const R4<T>* X, int v, double& x, double& y, double& z) {
+  const R4<T> a = X[v];
+  x = (double)a.x;
+  y = (double)a.y;
+  z = (double)a.z;
+}
+
+// Bounding box of item i: tets are items [0, n_t), boundary faces [n_t, n_t + n_f).
+template <typename T>
+__device__ __forceinline__ bool item_box(const Dev<T>& d, int i, double lo[3], double hi[3]) {
+  int vs[4];
+  int nv;
+  if (i < d.n_t) {
+    const int4 t = d.tet[i];
+    vs[0] = t.x; vs[1] = t.y; vs[2] = t.z; vs[3] = t.w;
+    nv = 4;
+  } else {
+    const int4 f = d.faces[i - d.n_t];
+    vs[0] = f.x; vs[1] = f.y; vs[2] = f.z;
+    nv = 3;
+  }
+  bool ok = true;
+  for (int k = 0; k < nv; ++k) {
+    const R4<T> a = d.X[vs[k]];
+    const double c[3] = {(double)a.x, (double)a.y, (double)a.z};
+    for (int j = 0; j < 3; ++j) {
+      ok = ok && isfinite(c[j]);
+      if (k == 0) {
+        lo[j] = c[j];
+        hi[j] = c[j];
+      } else {
+        lo[j] = fmin(lo[j], c[j]);
+        hi[j] = fmax(hi[j], c[j]);
+      }
+    }
+  }
+  return ok;
+}
+
+template <typename T, bool FILL>
+__global__ void k_grid_bin(Dev<T> d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = d.n_t + d.n_f;
+  if (i >= n) return;
+  double lo[3], hi[3];
+  if (!item_box(d, i, lo, hi)) {
+    if (!FILL) set_status(d.ctrl, ST_NONFINITE);
+    return;
+  }
+  int c0[3], c1[3];
+  for (int j = 0; j < 3; ++j) {
+    c0[j] = cell_coord(lo[j], d.inv_cell);
+    c1[j] = cell_coord(hi[j], d.inv_cell);
+  }
+  const long long ncell =
+      (long long)(c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) * (c1[2] - c0[2] + 1);
+  if (ncell > MAX_CELLS_PER_ITEM) {
+    if (!FILL) set_status(d.ctrl, ST_OVERFLOW);
+    return;
+  }
+  const bool is_tet = i < d.n_t;
+  const unsigned base = is_tet ? 0u : d.H_t;
+  const unsigned mask = (is_tet ? d.H_t : d.H_f) - 1u;
+  for (int cz = c0[2]; cz <= c1[2]; ++cz)
+    for (int cy = c0[1]; cy <= c1[1]; ++cy)
+      for (int cx = c0[0]; cx <= c1[0]; ++cx) {
+        const unsigned h = base + (hash_cell(cx, cy, cz) & mask);
+        if (!FILL) {
+          atomicAdd(&d.cell_count[h], 1);
+        } else {
+          const int pos = d.cell_start[h] + atomicAdd(&d.cell_cursor[h], 1);
+          if (pos < d.cap_items) d.items[pos] = i;
+        }
+      }
+}
+
+// ---- exclusive scan of cell_count into cell_start (three small kernels) ----
+static constexpr int SCAN_THREADS = 256;
+static constexpr int SCAN_PER_THREAD = 8;
+static constexpr int SCAN_TILE = SCAN_THREADS * SCAN_PER_THREAD;
+
+__global__ void k_scan_tiles(const int* __restrict__ in, int* __restrict__ out, int* __restrict__ tile_sums,
+                             int n) {
+  __shared__ int sh[SCAN_THREADS];
+  const int base = blockIdx.x * SCAN_TILE + threadIdx.x * SCAN_PER_THREAD;
+  int v[SCAN_PER_THREAD];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+    int t = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  int run = sh[threadIdx.x] - s;  // exclusive prefix of this thread
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (threadIdx.x == SCAN_THREADS - 1) tile_sums[blockIdx.x] = sh[threadIdx.x];
+}
+
+// Single block: exclusive scan of the tile sums in place, total into *total.
+__global__ void k_scan_top(int* tile_sums, int n_tiles, int* total_out, Ctrl* ctrl, int cap) {
+  __shared__ int sh[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < n_tiles; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = (i < n_tiles) ? tile_sums[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      int t = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < n_tiles) tile_sums[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *total_out = carry;
+    ctrl->n_items = carry;
+    if (carry > cap) atomicOr(&ctrl->status, ST_OVERFLOW);
+  }
+}
+
+__global__ void k_scan_add(int* out, const int* tile_sums, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] += tile_sums[i / SCAN_TILE];
+}
+
+// ---- narrow phase ----
+template <typename T>
+__device__ __forceinline__ bool strictly_inside(const Dev<T>& d, double px, double py, double pz,
+                                                int4 t) {
+  double a[3], b[3], c[3], e[3];
+  load3(d.X, t.x, a[0], a[1], a[2]);
+  load3(d.X, t.y, b[0], b[1], b[2]);
+  load3(d.X, t.z, c[0], c[1], c[2]);
+  load3(d.X, t.w, e[0], e[1], e[2]);
+  // exact bounding-box reject
+  if (px < fmin(fmin(a[0], b[0]), fmin(c[0], e[0])) || px > fmax(fmax(a[0], b[0]), fmax(c[0], e[0])))
+    return false;
+  if (py < fmin(fmin(a[1], b[1]), fmin(c[1], e[1])) || py > fmax(fmax(a[1], b[1]), fmax(c[1], e[1])))
+    return false;
+  if (pz < fmin(fmin(a[2], b[2]), fmin(c[2], e[2])) || pz > fmax(fmax(a[2], b[2]), fmax(c[2], e[2])))
+    return false;
+  // p strictly inside iff each sub-tet with one vertex replaced by p is positive
+  if (orient_sign(px, py, pz, b[0], b[1], b[2], c[0], c[1], c[2], e[0], e[1], e[2]) <= 0) return false;
+  if (orient_sign(a[0], a[1], a[2], px, py, pz, c[0], c[1], c[2], e[0], e[1], e[2]) <= 0) return false;
+  if (orient_sign(a[0], a[1], a[2], b[0], b[1], b[2], px, py, pz, e[0], e[1], e[2]) <= 0) return false;
+  if (orient_sign(a[0], a[1], a[2], b[0], b[1], b[2], c[0], c[1], c[2], px, py, pz) <= 0) return false;
+  return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_narrow(Dev<T> d) {
+  __shared__ int shi[32];
+  const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+  int n_self = 0, n_obs = 0;
+  if (qi < d.n_q) {
+    const int v = d.q_verts[qi];
+    double px, py, pz;
+    load3(d.X, v, px, py, pz);
+    int cnt = 0;
+    bool over = false;
+    int* out = d.pair_tet + (size_t)qi * d.max_pairs;
+    if (d.collision >= 1 && isfinite(px) && isfinite(py) && isfinite(pz)) {
+      const unsigned h =
+          hash_cell(cell_coord(px, d.inv_cell), cell_coord(py, d.inv_cell), cell_coord(pz, d.inv_cell)) &
+          (d.H_t - 1u);
+      const int b0 = d.cell_start[h];
+      const int b1 = min(d.cell_start[h + 1], d.cap_items);
+      for (int k = b0; k < b1; ++k) {
+        const int e = d.items[k];
+        const int4 t = d.tet[e];
+        if (t.x == v || t.y == v || t.z == v || t.w == v) continue;
+        if (!strictly_inside(d, px, py, pz, t)) continue;
+        // sorted insert without duplicates (a tet may repeat in a bucket)
+        int pos = 0;
+        while (pos < cnt && out[pos] < e) ++pos;
+        if (pos < cnt && out[pos] == e) continue;
+        if (cnt == d.max_pairs) {
+          over = true;
+          if (pos == cnt) continue;
+          --cnt;  // drop the largest to keep the smallest ids
+        }
+        for (int j = cnt; j > pos; --j) out[j] = out[j - 1];
+        out[pos] = e;
+        ++cnt;
+      }
+    }
+    if (over) set_status(d.ctrl, ST_OVERFLOW);
+    d.pair_count[qi] = cnt;
+    n_self = cnt;
+    int best = -1;
+    if (d.collision >= 2) {
+      double bestd = 0.0;
+      for (int j = 0; j < d.n_spheres; ++j) {
+        const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
+        const double r = d.spheres[4 * j + 3];
+        const double dx = __dsub_rn(px, cx), dy = __dsub_rn(py, cy), dz = __dsub_rn(pz, cz);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+        if (d2 < __dmul_rn(r, r)) {
+          ++n_obs;
+          const double dist = sqrt(d2) - r;
+          if (best < 0 || dist < bestd) {
+            best = j;
+            bestd = dist;
+          }
+        }
+      }
+    }
+    d.obs_sphere[qi] = best;
+  }
+  const int s1 = block_sum_int(n_self, shi);
+  const int s2 = block_sum_int(n_obs, shi);
+  if (threadIdx.x == 0 && (s1 | s2)) {
+    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
+    atomicAdd(&rec->n_self_pairs, s1);
+    atomicAdd(&rec->n_obstacle_pairs, s2);
+  }
+}
+
+// ---- spring update ----
+struct V3 {
+  double x, y, z;
+};
+__device__ __forceinline__ V3 sub(V3 a, V3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ V3 add(V3 a, V3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ V3 scl(double s, V3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__device__ __forceinline__ double norm(V3 a) { return sqrt(dot(a, a)); }
+
+template <typename T>
+__device__ __forceinline__ V3 pos(const Dev<T>& d, int v) {
+  const R4<T> a = d.X[v];
+  return {(double)a.x, (double)a.y, (double)a.z};
+}
+
+// Moller-Trumbore with inclusive barycentrics and t > 0.
+__device__ __forceinline__ bool ray_tri(V3 o, V3 dir, V3 q0, V3 q1, V3 q2, double& t, double& b1,
+                                        double& b2) {
+  const V3 e1 = sub(q1, q0), e2 = sub(q2, q0);
+  const V3 pv = cross(dir, e2);
+  const double det = dot(e1, pv);
+  if (det == 0.0) return false;
+  const double inv = 1.0 / det;
+  const V3 tv = sub(o, q0);
+  b1 = dot(tv, pv) * inv;
+  const V3 qv = cross(tv, e1);
+  b2 = dot(dir, qv) * inv;
+  t = dot(e2, qv) * inv;
+  return b1 >= 0.0 && b2 >= 0.0 && b1 + b2 <= 1.0 && t > 0.0;
+}
+
+// Closest point of a triangle: plane projection when inside, else the nearest
+// edge projection.  Returns the barycentric weights of q1, q2.
+__device__ __forceinline__ V3 closest_tri(V3 p, V3 q0, V3 q1, V3 q2, double& b1, double& b2) {
+  const V3 e1 = sub(q1, q0), e2 = sub(q2, q0);
+  const V3 n = cross(e1, e2);
+  const double nn = dot(n, n);
+  if (nn > 0.0) {
+    const V3 x = sub(p, scl(dot(sub(p, q0), n) / nn, n));
+    const double d11 = dot(e1, e1), d12 = dot(e1, e2), d22 = dot(e2, e2);
+    const V3 r = sub(x, q0);
+    const double r1 = dot(r, e1), r2 = dot(r, e2);
+    const double den = d11 * d22 - d12 * d12;
+    const double c1 = (d22 * r1 - d12 * r2) / den, c2 = (d11 * r2 - d12 * r1) / den;
+    if (c1 >= 0.0 && c2 >= 0.0 && c1 + c2 <= 1.0) {
+      b1 = c1;
+      b2 = c2;
+      return x;
+    }
+  }
+  double bestd = 0.0;
+  V3 best = q0;
+  const V3 A[3] = {q0, q1, q2};
+  const V3 B[3] = {q1, q2, q0};
+  for (int k = 0; k < 3; ++k) {
+    const V3 ab = sub(B[k], A[k]);
+    const double den = dot(ab, ab);
+    const double s = den == 0.0 ? 0.0 : fmin(1.0, fmax(0.0, dot(sub(p, A[k]), ab) / den));
+    const V3 c = add(A[k], scl(s, ab));
+    const V3 dd = sub(p, c);
+    const double d2 = dot(dd, dd);
+    if (k == 0 || d2 < bestd) {
+      bestd = d2;
+      best = c;
+      if (k == 0) { b1 = s; b2 = 0.0; }
+      else if (k == 1) { b1 = 1.0 - s; b2 = s; }
+      else { b1 = 0.0; b2 = 1.0 - s; }
+    }
+  }
+  return best;
+}
+
+template <typename T>
+__device__ void face_verts(const Dev<T>& d, int f, V3& q0, V3& q1, V3& q2, int4& fv) {
+  fv = d.faces[f];
+  q0 = pos(d, fv.x);
+  q1 = pos(d, fv.y);
+  q2 = pos(d, fv.z);
+}
+
+// Self-collision correspondence of vertex v: first exit-face hit along dir.
+template <typename T>
+__device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, double& rb2) {
+  int best_f = -1;
+  double best_t = 0.0;
+  int cell[3] = {cell_coord(o.x, d.inv_cell), cell_coord(o.y, d.inv_cell), cell_coord(o.z, d.inv_cell)};
+  const double dv[3] = {dir.x, dir.y, dir.z};
+  const double ov[3] = {o.x, o.y, o.z};
+  int step[3];
+  double tmax[3], tdel[3];
+  for (int a = 0; a < 3; ++a) {
+    if (dv[a] > 0.0) {
+      step[a] = 1;
+      tmax[a] = ((cell[a] + 1) * d.cell - ov[a]) / dv[a];
+      tdel[a] = d.cell / dv[a];
+    } else if (dv[a] < 0.0) {
+      step[a] = -1;
+      tmax[a] = (cell[a] * d.cell - ov[a]) / dv[a];
+      tdel[a] = -d.cell / dv[a];
+    } else {
+      step[a] = 0;
+      tmax[a] = INFINITY;
+      tdel[a] = INFINITY;
+    }
+  }
+  for (int it = 0; it < MAX_DDA_STEPS; ++it) {
+    const unsigned h = d.H_t + (hash_cell(cell[0], cell[1], cell[2]) & (d.H_f - 1u));
+    const int k0 = d.cell_start[h], k1 = min(d.cell_start[h + 1], d.cap_items);
+    for (int k = k0; k < k1; ++k) {
+      const int f = d.items[k] - d.n_t;
+      V3 q0, q1, q2;
+      int4 fv;
+      face_verts(d, f, q0, q1, q2, fv);
+      if (fv.x == v || fv.y == v || fv.z == v) continue;
+      if (!(dot(dir, cross(sub(q1, q0), sub(q2, q0))) > 0.0)) continue;
+      double t, b1, b2;
+      if (!ray_tri(o, dir, q0, q1, q2, t, b1, b2)) continue;
+      if (best_f < 0 || t < best_t || (t == best_t && f < best_f)) {
+        best_f = f;
+        best_t = t;
+        rb1 = b1;
+        rb2 = b2;
+      }
+    }
+    const double texit = fmin(tmax[0], fmin(tmax[1], tmax[2]));
+    if (best_f >= 0 && best_t * (1.0 + 1e-9) < texit) return best_f;
+    if (!(texit < INFINITY)) break;
+    const int a = (tmax[0] <= tmax[1] && tmax[0] <= tmax[2]) ? 0 : (tmax[1] <= tmax[2] ? 1 : 2);
+    cell[a] += step[a];
+    tmax[a] += tdel[a];
+  }
+  if (best_f >= 0) return best_f;
+  // no exit face hit: closest point over all boundary faces not containing v
+  double bestd = 0.0;
+  for (int f = 0; f < d.n_f; ++f) {
+    V3 q0, q1, q2;
+    int4 fv;
+    face_verts(d, f, q0, q1, q2, fv);
+    if (fv.x == v || fv.y == v || fv.z == v) continue;
+    double b1, b2;
+    const V3 x = closest_tri(o, q0, q1, q2, b1, b2);
+    const V3 dd = sub(o, x);
+    const double d2 = dot(dd, dd);
+    if (best_f < 0 || d2 < bestd) {
+      best_f = f;
+      bestd = d2;
+      rb1 = b1;
+      rb2 = b2;
+    }
+  }
+  return best_f;
+}
+
+template <typename T>
+__device__ __forceinline__ V3 face_point(const Dev<T>& d, int f, double b1, double b2, V3& nunit) {
+  V3 q0, q1, q2;
+  int4 fv;
+  face_verts(d, f, q0, q1, q2, fv);
+  V3 n = cross(sub(q1, q0), sub(q2, q0));
+  nunit = scl(1.0 / norm(n), n);
+  return add(add(scl(1.0 - b1 - b2, q0), scl(b1, q1)), scl(b2, q2));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
+  __shared__ double shd[32];
+  __shared__ int shi[32];
+  const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+  double e_spring = 0.0;
+  int active_out = 0;
+  if (qi < d.n_q) {
+    const int v = d.q_verts[qi];
+    const V3 x = pos(d, v);
+    // area-weighted vertex normal of the incident boundary faces
+    V3 n = {0.0, 0.0, 0.0};
+    for (int k = d.qf_ptr[qi]; k < d.qf_ptr[qi + 1]; ++k) {
+      V3 q0, q1, q2;
+      int4 fv;
+      face_verts(d, d.qf[k], q0, q1, q2, fv);
+      n = add(n, cross(sub(q1, q0), sub(q2, q0)));
+    }
+    const double nl = norm(n);
+    n = nl > 0.0 ? scl(1.0 / nl, n) : V3{0.0, 0.0, 0.0};
+    int active = d.sp.active[qi];
+    int kind = d.sp.kind[qi];
+    int face = d.sp.face[qi];
+    double b1 = d.sp.bary[2 * qi], b2 = d.sp.bary[2 * qi + 1];
+    V3 tgt = {0.0, 0.0, 0.0};
+    const int js = d.obs_sphere[qi];
+    const double eps = d.eps;
+    if (js >= 0) {
+      const V3 c = {d.spheres[4 * js], d.spheres[4 * js + 1], d.spheres[4 * js + 2]};
+      const double r = d.spheres[4 * js + 3];
+      V3 u = sub(x, c);
+      const double nu = norm(u);
+      u = nu == 0.0 ? scl(-1.0, n) : scl(1.0 / nu, u);
+      active = 1;
+      kind = 1;
+      face = js;
+      b1 = b2 = 0.0;
+      tgt = add(c, scl(r + eps, u));
+    } else if (d.pair_count[qi] > 0) {
+      const int f = ray_cast(d, v, x, scl(-1.0, n), b1, b2);
+      if (f >= 0) {
+        V3 nf;
+        const V3 bp = face_point(d, f, b1, b2, nf);
+        active = 1;
+        kind = 0;
+        face = f;
+        tgt = add(bp, scl(eps, nf));
+      } else {
+        active = 0;
+      }
+    } else if (active) {
+      if (kind == 1) {
+        const V3 c = {d.spheres[4 * face], d.spheres[4 * face + 1], d.spheres[4 * face + 2]};
+        const double r = d.spheres[4 * face + 3];
+        V3 u = sub(x, c);
+        const double nu = norm(u);
+        if (nu - r > eps) {
+          active = 0;
+        } else {
+          u = nu == 0.0 ? scl(-1.0, n) : scl(1.0 / nu, u);
+          tgt = add(c, scl(r + eps, u));
+        }
+      } else {
+        V3 nf;
+        const V3 bp = face_point(d, face, b1, b2, nf);
+        if (dot(nf, sub(x, bp)) > eps) {
+          active = 0;
+        } else {
+          tgt = add(bp, scl(eps, nf));
+        }
+      }
+    }
+    if (!active) {
+      kind = 0;
+      face = -1;
+      b1 = b2 = 0.0;
+      tgt = {0.0, 0.0, 0.0};
+    }
+    d.sp.active[qi] = active;
+    d.sp.kind[qi] = kind;
+    d.sp.face[qi] = face;
+    d.sp.bary[2 * qi] = b1;
+    d.sp.bary[2 * qi + 1] = b2;
+    d.sp.target[3 * qi] = tgt.x;
+    d.sp.target[3 * qi + 1] = tgt.y;
+    d.sp.target[3 * qi + 2] = tgt.z;
+    R4<T> sc;
+    sc.x = (T)tgt.x;
+    sc.y = (T)tgt.y;
+    sc.z = (T)tgt.z;
+    sc.w = active ? T(1) : T(0);
+    d.spring_c[v] = sc;
+    if (active) {
+      const V3 dd = sub(x, tgt);
+      e_spring = d.k_spring * dot(dd, dd);
+      active_out = 1;
+    }
+  }
+  const double es = block_sum(e_spring, shd);
+  const int ns = block_sum_int(active_out, shi);
+  if (threadIdx.x == 0) {
+    d.e_partials[d.n_e_local + blockIdx.x] = es;
+    if (ns) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->n_springs, ns);
+  }
+}
+
+// ---- launchers ----
+template <typename T>
+void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t st) {
+  const int n_items = d.n_t + d.n_f;
+  const int H = (int)(d.H_t + d.H_f);
+  cudaMemsetAsync(d.cell_count, 0, sizeof(int) * (size_t)(H + 1), st);
+  cudaMemsetAsync(d.cell_cursor, 0, sizeof(int) * (size_t)H, st);
+  k_grid_bin<T, false><<<(n_items + 255) / 256, 256, 0, st>>>(d);
+  const int n_scan = H + 1;
+  const int n_tiles = (n_scan + SCAN_TILE - 1) / SCAN_TILE;
+  k_scan_tiles<<<n_tiles, SCAN_THREADS, 0, st>>>(d.cell_count, d.cell_start, cs.tile_sums, n_scan);
+  k_scan_top<<<1, 1024, 0, st>>>(cs.tile_sums, n_tiles, cs.total, d.ctrl, d.cap_items);
+  k_scan_add<<<(n_scan + 255) / 256, 256, 0, st>>>(d.cell_start, cs.tile_sums, n_scan);
+  k_grid_bin<T, true><<<(n_items + 255) / 256, 256, 0, st>>>(d);
+  if (d.n_q > 0) k_narrow<T><<<(d.n_q + 127) / 128, 128, 0, st>>>(d);
+}
+
+template <typename T>
+void launch_springs(const Dev<T>& d, cudaStream_t st) {
+  if (d.n_q > 0) k_springs<T><<<(d.n_q + 127) / 128, 128, 0, st>>>(d);
+}
+
+int spring_blocks(int n_q) { return (n_q + 127) / 128; }
+int scan_tiles(int n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+
+template void launch_collision<float>(const Dev<float>&, const CollisionScratch&, cudaStream_t);
+template void launch_collision<double>(const Dev<double>&, const CollisionScratch&, cudaStream_t);
+template void launch_springs<float>(const Dev<float>&, cudaStream_t);
+template void launch_springs<double>(const Dev<double>&, cudaStream_t);
+
+}  // namespace casim

@@ -1,0 +1,172 @@
+// Device-side data layout and helpers shared by the casim CUDA kernels.
+//
+// Layout in HBM (per simulation, T = float in MIXED mode, double in FP64):
+//   vertices  X[n_v] as R4<T> (x, y, z, pad); internal order = free vertices
+//             first, then fixed ones, each in the caller's relative order;
+//   elements  tet[n_t] int4 internal vertex ids (caller's tet order),
+//             Tc[3 n_t] rows x/y/z of the centered rest shape V N (Eq. 1),
+//             tinfo[n_t] (omega_e, Vol_e, |T_c|^2, group id as T),
+//             P[4 n_t] omega_e-weighted target columns written by the local step;
+//   system    incidence CSR of free vertices (tet*4 + slot), constant
+//             Laplacian off-diagonals in sliced ELL (32-row slices,
+//             column-major inside a slice), diagonal separate;
+//   PCG       r, u, p, s, w vectors R4<T>[n_free], FP64 block partials.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace casim {
+
+template <typename T>
+struct __align__(4 * sizeof(T)) R4 {
+  T x, y, z, w;
+};
+
+// Device status bits (OR-ed by kernels, mapped to CASIM_* codes on the host).
+enum : int {
+  ST_NONFINITE = 1,
+  ST_TIMEOUT = 2,
+  ST_PCG_MAXIT = 4,
+  ST_OVERFLOW = 8,
+};
+
+struct IterRec {
+  double energy;
+  double pcg_rel_residual;
+  int n_self_pairs;
+  int n_obstacle_pairs;
+  int n_springs;
+  int pcg_iters;
+};
+
+struct Ctrl {
+  int status;            // ST_* bits
+  int abort;             // set when a grid barrier gives up
+  unsigned bar_count;    // grid barrier arrival counter
+  unsigned bar_gen;      // grid barrier generation
+  long long iter;        // outer iterations completed (history index)
+  long long total_pcg;   // PCG iterations summed over outer iterations
+  int n_items;           // spatial-hash entries of this iteration
+  int pad;
+};
+
+struct SpringDev {
+  int* active;           // n_q
+  int* kind;             // n_q: 0 self, 1 obstacle
+  int* face;             // n_q: face id / sphere id / -1
+  double* bary;          // 2 n_q
+  double* target;        // 3 n_q
+};
+
+template <typename T>
+struct Dev {
+  int n_v, n_t, n_free, n_q, n_f, n_groups, n_spheres, n_knots;
+  // vertices and elements
+  R4<T>* X;
+  const int4* tet;
+  const R4<T>* Tc;
+  const R4<T>* tinfo;
+  R4<T>* P;
+  const T* cbrt_alpha;   // per chamber group
+  const double* knots;   // 2 n_knots
+  // system
+  const int* inc_ptr;    // n_free + 1
+  const int* inc;        // tet*4 + slot
+  const T* diagL;        // n_free
+  const R4<T>* bfix;     // n_free
+  R4<T>* b;              // n_free
+  T* diag;               // n_free (Laplacian diagonal + k mask)
+  int n_slices;
+  const int* sl_ptr;     // n_slices + 1 (entries)
+  const int* sl_col;     // entries
+  const T* sl_val;       // entries
+  R4<T>* r;
+  R4<T>* u;
+  R4<T>* p;
+  R4<T>* s;
+  R4<T>* w;
+  double* partials;      // 4 * pcg grid
+  // collision
+  const int* q_verts;    // n_q internal vertex ids (ascending)
+  const int* qf_ptr;     // n_q + 1 incident boundary faces
+  const int* qf;         // face ids
+  const int4* faces;     // n_f (v0, v1, v2, owning tet)
+  const double* spheres; // 4 n_spheres
+  unsigned H_t, H_f;     // hash sizes (powers of two)
+  int* cell_count;       // H_t + H_f (+1)
+  int* cell_start;       // H_t + H_f + 1
+  int* cell_cursor;      // H_t + H_f
+  int* items;            // cap_items
+  int cap_items;
+  int* pair_count;       // n_q
+  int* pair_tet;         // n_q * max_pairs
+  int* obs_sphere;       // n_q: sphere id or -1
+  int max_pairs;
+  SpringDev sp;
+  R4<T>* spring_c;       // n_free: (c, mask)
+  // parameters
+  double k_spring, eps, cell, inv_cell, tol2;
+  int max_iter, collision, stats;
+  unsigned long long wait_budget;
+  // control and statistics
+  Ctrl* ctrl;
+  IterRec* hist;
+  int hist_cap;
+  double* e_partials;    // energy partials (local-step blocks + spring blocks)
+  int n_e_local, n_e_spring;
+};
+
+__host__ __device__ inline unsigned hash_cell(int cx, int cy, int cz) {
+  // Spatial hash of Teschner et al. 2003 ("Optimized spatial hashing for
+  // collision detection of deformable objects").
+  return ((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^ ((unsigned)cz * 83492791u);
+}
+
+// Cell coordinate of one coordinate value: floor(x / cell), clamped so that
+// far-away or non-finite values cannot overflow the integer range.  The map is
+// monotone in x, so a point inside a closed box maps into the box's cell range.
+__device__ inline int cell_coord(double x, double inv_cell) {
+  double c = floor(x * inv_cell);
+  c = fmin(fmax(c, -1.0e6), 1.0e6);
+  return (int)c;
+}
+
+template <typename T>
+__device__ inline bool finite4(const R4<T>& a) {
+  return isfinite((double)a.x) && isfinite((double)a.y) && isfinite((double)a.z);
+}
+
+__device__ inline void set_status(Ctrl* c, int bits) { atomicOr(&c->status, bits); }
+
+// Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024); the
+// result is valid in thread 0.  Fixed reduction order -> deterministic.
+__device__ inline double block_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t += sh[i];
+  }
+  return t;
+}
+
+__device__ inline int block_sum_int(int v, int* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  int t = 0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) t += sh[i];
+  }
+  return t;
+}
+
+}  // namespace casim

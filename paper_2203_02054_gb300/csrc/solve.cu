@@ -1,0 +1,491 @@
+// Local step (Sec. III-A, Eq. 6, Eq. 7), right-hand-side gather and the
+// global step solve (Sec. III-B, Eq. 8) on the GPU.
+//
+// Global step: the normal equations of Eq. 8 are A X = b with
+//   A = L_w + k diag(mask),  L_w = sum_e w_e S_e^T N S_e  (3/4 w on the
+//   diagonal, -1/4 w per shared edge), b = sum_e w_e S_e^T P_e^T + k c - A_fx x_fixed,
+// the three coordinate columns sharing A.  They are solved together by
+// Jacobi-preconditioned conjugate gradients in the single-reduction form of
+// Chronopoulos and Gear (1989), inside one persistent cooperative kernel:
+// per iteration one grid barrier publishes the new preconditioned residual u
+// for the SpMV and one grid reduction produces (r.u, w.u, r.r) in FP64.
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "svd3.cuh"
+
+namespace casim {
+
+// ---------------------------------------------------------------- local step
+template <typename T>
+__device__ __forceinline__ T cbrt_t(T x);
+template <>
+__device__ __forceinline__ float cbrt_t<float>(float x) { return cbrtf(x); }
+template <>
+__device__ __forceinline__ double cbrt_t<double>(double x) { return cbrt(x); }
+
+__device__ __forceinline__ double w_table(const double* knots, int n, double eps) {
+  // piecewise linear through (eps_i, w_i), clamped at both ends
+  if (eps <= knots[0]) return knots[1];
+  for (int i = 0; i + 1 < n; ++i) {
+    const double x0 = knots[2 * i], x1 = knots[2 * i + 2];
+    if (eps < x1) {
+      const double y0 = knots[2 * i + 1], y1 = knots[2 * i + 3];
+      return y0 + (eps - x0) * (y1 - y0) / (x1 - x0);
+    }
+  }
+  return knots[2 * n - 1];
+}
+
+template <typename T, int SWEEPS>
+__global__ void __launch_bounds__(LOCAL_THREADS) k_local(Dev<T> d) {
+  __shared__ double shd[32];
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double en = 0.0;
+  if (e < d.n_t) {
+    const int4 t = d.tet[e];
+    const R4<T> x0 = d.X[t.x], x1 = d.X[t.y], x2 = d.X[t.z], x3 = d.X[t.w];
+    // centered deformed shape X_c = V^d N, formed from differences to x0
+    T Xc[3][4];
+    {
+      const T r1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
+      const T r2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
+      const T r3[3] = {x3.x - x0.x, x3.y - x0.y, x3.z - x0.z};
+      for (int i = 0; i < 3; ++i) {
+        const T m = (r1[i] + r2[i] + r3[i]) * T(0.25);
+        Xc[i][0] = -m;
+        Xc[i][1] = r1[i] - m;
+        Xc[i][2] = r2[i] - m;
+        Xc[i][3] = r3[i] - m;
+      }
+    }
+    const R4<T> tx = d.Tc[3 * (size_t)e], ty = d.Tc[3 * (size_t)e + 1], tz = d.Tc[3 * (size_t)e + 2];
+    const T Tm[3][4] = {{tx.x, tx.y, tx.z, tx.w}, {ty.x, ty.y, ty.z, ty.w}, {tz.x, tz.y, tz.z, tz.w}};
+    T D[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        D[i][j] = Xc[i][0] * Tm[j][0] + Xc[i][1] * Tm[j][1] + Xc[i][2] * Tm[j][2] + Xc[i][3] * Tm[j][3];
+    T R[3][3], tr;
+    kabsch_rotation<T, SWEEPS>(D, R, tr);
+    T RT[3][4];
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 4; ++k) RT[i][k] = R[i][0] * Tm[0][k] + R[i][1] * Tm[1][k] + R[i][2] * Tm[2][k];
+    const R4<T> info = d.tinfo[e];
+    const T omega = info.x, vol0 = info.y, tt = info.z;
+    const int g = (int)info.w;
+    T P[3][4];
+    if (g >= 0) {
+      // chamber element: every target vertex is the rest vertex scaled by cbrt(alpha_g)
+      const T s = d.cbrt_alpha[g];
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) P[i][k] = s * RT[i][k];
+    } else {
+      // body element: blend with w = R_omega(eps), then volume scaling (Eq. 6, Eq. 7)
+      T mis = T(0);
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) {
+          const T q = Xc[i][k] - RT[i][k];
+          mis += q * q;
+        }
+      const double strain = sqrt((double)mis / (double)tt);
+      const T w = (T)w_table(d.knots, d.n_knots, strain);
+      T B[3][4];
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) B[i][k] = (T(1) - w) * Xc[i][k] + w * RT[i][k];
+      const T a0 = B[0][1] - B[0][0], a1 = B[1][1] - B[1][0], a2 = B[2][1] - B[2][0];
+      const T b0 = B[0][2] - B[0][0], b1 = B[1][2] - B[1][0], b2 = B[2][2] - B[2][0];
+      const T c0 = B[0][3] - B[0][0], c1 = B[1][3] - B[1][0], c2 = B[2][3] - B[2][0];
+      const T volB = (a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0)) / T(6);
+      const T s = (volB > T(1e-3) * vol0) ? cbrt_t<T>(vol0 / volB) : T(1);
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) P[i][k] = s * B[i][k];
+    }
+    if (d.stats) {
+      double acc = 0.0;
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) {
+          const double q = (double)Xc[i][k] - (double)P[i][k];
+          acc += q * q;
+        }
+      en = (double)omega * acc;
+    }
+    R4<T>* out = d.P + 4 * (size_t)e;
+    for (int k = 0; k < 4; ++k) {
+      R4<T> c;
+      c.x = omega * P[0][k];
+      c.y = omega * P[1][k];
+      c.z = omega * P[2][k];
+      c.w = T(0);
+      out[k] = c;
+    }
+  }
+  const double s = block_sum(en, shd);
+  if (threadIdx.x == 0) d.e_partials[blockIdx.x] = s;
+}
+
+// ------------------------------------------------------------ RHS gather
+template <typename T>
+__global__ void __launch_bounds__(RHS_THREADS) k_rhs(Dev<T> d) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= d.n_free) return;
+  T bx = T(0), by = T(0), bz = T(0);
+  const int k1 = d.inc_ptr[i + 1];
+  for (int k = d.inc_ptr[i]; k < k1; ++k) {
+    const R4<T> p = d.P[d.inc[k]];
+    bx += p.x;
+    by += p.y;
+    bz += p.z;
+  }
+  const R4<T> sc = d.spring_c[i];
+  const T km = (T)d.k_spring * sc.w;
+  const R4<T> bf = d.bfix[i];
+  R4<T> bi;
+  bi.x = bx + km * sc.x - bf.x;
+  bi.y = by + km * sc.y - bf.y;
+  bi.z = bz + km * sc.z - bf.z;
+  bi.w = T(0);
+  d.b[i] = bi;
+  d.diag[i] = d.diagL[i] + km;
+}
+
+// ------------------------------------------------------------------ PCG
+struct GridCtx {
+  Ctrl* ctrl;
+  unsigned nblocks;
+  unsigned long long budget;
+};
+
+// Grid-wide barrier with a bounded wait.  Returns false when this or another
+// block gave up (the kernel must then return).
+__device__ __forceinline__ bool grid_sync(const GridCtx& g, int* sh_flag) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned* vgen = &g.ctrl->bar_gen;
+    volatile int* vab = &g.ctrl->abort;
+    const unsigned gen = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&g.ctrl->bar_count, 1u);
+    if (arrived == g.nblocks - 1u) {
+      atomicExch(&g.ctrl->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&g.ctrl->bar_gen, 1u);
+    } else {
+      const long long t0 = clock64();
+      while (*vgen == gen) {
+        if (*vab) {
+          ok = 0;
+          break;
+        }
+        if ((unsigned long long)(clock64() - t0) > g.budget) {
+          atomicExch(&g.ctrl->abort, 1);
+          atomicOr(&g.ctrl->status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    *sh_flag = ok;
+  }
+  __syncthreads();
+  return *sh_flag != 0;
+}
+
+// Grid-wide FP64 sum of NV values per thread; totals returned in tot[].
+// Partials alternate between two buffers so that a block running ahead to
+// the next reduction cannot overwrite values another block is still reading.
+template <int NV>
+__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* partials, int& parity,
+                                            const GridCtx& g, double* sh, double* tot, int* shf) {
+  double* buf = partials + (size_t)parity * 4 * gridDim.x;
+  for (int k = 0; k < NV; ++k) {
+    const double t = block_sum(v[k], sh);
+    if (threadIdx.x == 0) buf[4 * blockIdx.x + k] = t;
+  }
+  if (!grid_sync(g, shf)) return false;
+  if (threadIdx.x < 32) {
+    for (int k = 0; k < NV; ++k) {
+      double a = 0.0;
+      for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) a += __ldcg(buf + 4 * b + k);
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+      if (threadIdx.x == 0) tot[k] = a;
+    }
+  }
+  __syncthreads();
+  parity ^= 1;
+  return true;
+}
+
+// (A v)_i for one row of the sliced-ELL off-diagonal part plus the diagonal.
+template <typename T>
+__device__ __forceinline__ void spmv_row(const Dev<T>& d, int i, const R4<T>* __restrict__ src, T dg,
+                                         const R4<T>& self, T& ax, T& ay, T& az) {
+  ax = dg * self.x;
+  ay = dg * self.y;
+  az = dg * self.z;
+  const int s = i >> 5, lane = i & 31;
+  const int k1 = d.sl_ptr[s + 1];
+  for (int k = d.sl_ptr[s] + lane; k < k1; k += 32) {
+    const int c = d.sl_col[k];
+    const T a = d.sl_val[k];
+    const R4<T> x = src[c];
+    ax += a * x.x;
+    ay += a * x.y;
+    az += a * x.z;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(PCG_THREADS) k_pcg(Dev<T> d) {
+  __shared__ double sh[32];
+  __shared__ double tot[4];
+  __shared__ int shf;
+  const GridCtx g{d.ctrl, gridDim.x, d.wait_budget};
+  const int n = d.n_free;
+  const int G = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  int parity = 0;
+  R4<T>* __restrict__ X = d.X;
+  R4<T>* __restrict__ r = d.r;
+  R4<T>* __restrict__ u = d.u;
+  R4<T>* __restrict__ p = d.p;
+  R4<T>* __restrict__ s = d.s;
+  R4<T>* __restrict__ w = d.w;
+
+  // r = b - A x, u = M^-1 r
+  double a0[2] = {0.0, 0.0};
+  for (int i = tid; i < n; i += G) {
+    const T dg = d.diag[i];
+    const R4<T> xi = X[i];
+    T ax, ay, az;
+    spmv_row(d, i, X, dg, xi, ax, ay, az);
+    const R4<T> bi = d.b[i];
+    R4<T> ri, ui;
+    ri.x = bi.x - ax;
+    ri.y = bi.y - ay;
+    ri.z = bi.z - az;
+    ri.w = T(0);
+    ui.x = ri.x / dg;
+    ui.y = ri.y / dg;
+    ui.z = ri.z / dg;
+    ui.w = T(0);
+    r[i] = ri;
+    u[i] = ui;
+    a0[0] += (double)bi.x * bi.x + (double)bi.y * bi.y + (double)bi.z * bi.z;
+    a0[1] += (double)ri.x * ri.x + (double)ri.y * ri.y + (double)ri.z * ri.z;
+  }
+  if (!grid_reduce<2>(a0, d.partials, parity, g, sh, tot, &shf)) return;
+  const double bb = tot[0];
+  double rr = tot[1];
+  int it = 0;
+  if (bb > 0.0 && rr > d.tol2 * bb) {
+    // w = A u and the first scalars
+    double a1[3] = {0.0, 0.0, 0.0};
+    for (int i = tid; i < n; i += G) {
+      const T dg = d.diag[i];
+      const R4<T> ui = u[i], ri = r[i];
+      T ax, ay, az;
+      spmv_row(d, i, u, dg, ui, ax, ay, az);
+      R4<T> wi;
+      wi.x = ax;
+      wi.y = ay;
+      wi.z = az;
+      wi.w = T(0);
+      w[i] = wi;
+      a1[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
+      a1[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
+    }
+    if (!grid_reduce<3>(a1, d.partials, parity, g, sh, tot, &shf)) return;
+    double gamma = tot[0];
+    double alpha = gamma / tot[1];
+    double beta = 0.0;
+    bool first = true;
+    for (it = 1; it <= d.max_iter; ++it) {
+      const T ta = (T)alpha, tb = (T)beta;
+      for (int i = tid; i < n; i += G) {
+        const R4<T> ui = u[i], wi = w[i];
+        R4<T> pi, si;
+        if (first) {
+          pi = ui;
+          si = wi;
+        } else {
+          const R4<T> po = p[i], so = s[i];
+          pi.x = ui.x + tb * po.x;
+          pi.y = ui.y + tb * po.y;
+          pi.z = ui.z + tb * po.z;
+          si.x = wi.x + tb * so.x;
+          si.y = wi.y + tb * so.y;
+          si.z = wi.z + tb * so.z;
+        }
+        pi.w = T(0);
+        si.w = T(0);
+        p[i] = pi;
+        s[i] = si;
+        R4<T> xi = X[i], ri = r[i];
+        xi.x += ta * pi.x;
+        xi.y += ta * pi.y;
+        xi.z += ta * pi.z;
+        ri.x -= ta * si.x;
+        ri.y -= ta * si.y;
+        ri.z -= ta * si.z;
+        X[i] = xi;
+        r[i] = ri;
+        const T dg = d.diag[i];
+        R4<T> un;
+        un.x = ri.x / dg;
+        un.y = ri.y / dg;
+        un.z = ri.z / dg;
+        un.w = T(0);
+        u[i] = un;
+      }
+      if (!grid_sync(g, &shf)) return;
+      double a2[3] = {0.0, 0.0, 0.0};
+      for (int i = tid; i < n; i += G) {
+        const T dg = d.diag[i];
+        const R4<T> ui = u[i], ri = r[i];
+        T ax, ay, az;
+        spmv_row(d, i, u, dg, ui, ax, ay, az);
+        R4<T> wi;
+        wi.x = ax;
+        wi.y = ay;
+        wi.z = az;
+        wi.w = T(0);
+        w[i] = wi;
+        a2[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
+        a2[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
+        a2[2] += (double)ri.x * ri.x + (double)ri.y * ri.y + (double)ri.z * ri.z;
+      }
+      if (!grid_reduce<3>(a2, d.partials, parity, g, sh, tot, &shf)) return;
+      const double gnew = tot[0], delta = tot[1];
+      rr = tot[2];
+      if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
+        if (tid == 0) set_status(d.ctrl, ST_NONFINITE);
+        break;
+      }
+      if (rr <= d.tol2 * bb) break;
+      beta = gnew / gamma;
+      alpha = gnew / (delta - beta * gnew / alpha);
+      gamma = gnew;
+      first = false;
+    }
+    if (it > d.max_iter) {
+      it = d.max_iter;
+      if (tid == 0) set_status(d.ctrl, ST_PCG_MAXIT);
+    }
+  }
+  if (tid == 0) {
+    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
+    rec->pcg_iters = it;
+    d.ctrl->total_pcg += it;
+    rec->pcg_rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  }
+}
+
+// --------------------------------------------------------------- finalize
+template <typename T>
+__global__ void k_finalize(Dev<T> d) {
+  __shared__ double sh[32];
+  const int n = d.n_e_local + d.n_e_spring;
+  // fixed-order sum: thread-strided then a fixed tree
+  double a = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a += d.e_partials[i];
+  const double t = block_sum(a, sh);
+  if (threadIdx.x == 0) {
+    Ctrl* c = d.ctrl;
+    IterRec* rec = d.hist + (c->iter % d.hist_cap);
+    rec->energy = t;
+    if (!isfinite(t) && d.stats) c->status |= ST_NONFINITE;
+    c->iter += 1;
+    IterRec* nx = d.hist + (c->iter % d.hist_cap);
+    nx->energy = 0.0;
+    nx->pcg_rel_residual = 0.0;
+    nx->n_self_pairs = 0;
+    nx->n_obstacle_pairs = 0;
+    nx->n_springs = 0;
+    nx->pcg_iters = 0;
+  }
+}
+
+template <typename T>
+__global__ void k_gather_positions(const R4<T>* X, const int* int_of_user, int n, T* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const R4<T> x = X[int_of_user[i]];
+  out[3 * (size_t)i] = x.x;
+  out[3 * (size_t)i + 1] = x.y;
+  out[3 * (size_t)i + 2] = x.z;
+}
+
+// ---------------------------------------------------------------- launchers
+int local_blocks(int n_t) { return (n_t + LOCAL_THREADS - 1) / LOCAL_THREADS; }
+
+template <typename T>
+void launch_local(const Dev<T>& d, cudaStream_t st) {
+  if (d.n_t == 0) return;
+  if (sizeof(T) == 4)
+    k_local<T, 4><<<local_blocks(d.n_t), LOCAL_THREADS, 0, st>>>(d);
+  else
+    k_local<T, 6><<<local_blocks(d.n_t), LOCAL_THREADS, 0, st>>>(d);
+}
+
+template <typename T>
+void launch_rhs(const Dev<T>& d, cudaStream_t st) {
+  if (d.n_free == 0) return;
+  k_rhs<T><<<(d.n_free + RHS_THREADS - 1) / RHS_THREADS, RHS_THREADS, 0, st>>>(d);
+}
+
+template <typename T>
+int pcg_max_grid() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<T>, PCG_THREADS, 0);
+  return sms * (per > 0 ? per : 1);
+}
+
+template <typename T>
+cudaError_t launch_pcg(const Dev<T>& d, int grid, cudaStream_t st) {
+  if (d.n_free == 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(PCG_THREADS);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg<T>, d);
+}
+
+template <typename T>
+void launch_finalize(const Dev<T>& d, cudaStream_t st) {
+  k_finalize<T><<<1, 256, 0, st>>>(d);
+}
+
+template <typename T>
+void launch_gather_positions(const Dev<T>& d, const int* int_of_user, int n_user, T* out,
+                             cudaStream_t st) {
+  if (n_user == 0) return;
+  k_gather_positions<T><<<(n_user + 255) / 256, 256, 0, st>>>(d.X, int_of_user, n_user, out);
+}
+
+template void launch_local<float>(const Dev<float>&, cudaStream_t);
+template void launch_local<double>(const Dev<double>&, cudaStream_t);
+template void launch_rhs<float>(const Dev<float>&, cudaStream_t);
+template void launch_rhs<double>(const Dev<double>&, cudaStream_t);
+template cudaError_t launch_pcg<float>(const Dev<float>&, int, cudaStream_t);
+template cudaError_t launch_pcg<double>(const Dev<double>&, int, cudaStream_t);
+template int pcg_max_grid<float>();
+template int pcg_max_grid<double>();
+template void launch_finalize<float>(const Dev<float>&, cudaStream_t);
+template void launch_finalize<double>(const Dev<double>&, cudaStream_t);
+template void launch_gather_positions<float>(const Dev<float>&, const int*, int, float*, cudaStream_t);
+template void launch_gather_positions<double>(const Dev<double>&, const int*, int, double*,
+                                              cudaStream_t);
+
+}  // namespace casim

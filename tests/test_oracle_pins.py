@@ -436,3 +436,12 @@ def test_closest_point_triangle_brute_force():
         pts = (1 - B1[ok] - B2[ok])[:, None] * q[0] + B1[ok][:, None] * q[1] + B2[ok][:, None] * q[2]
         dmin = np.min(np.linalg.norm(pts - p, axis=1))
         assert np.linalg.norm(x - p) <= dmin + 1e-12
+
+
+def test_slab_prefilter_equals_plain_all_pairs():
+    m = synth.small_finger(nx=16, ny=4, nz=4, n_ch=3)
+    prep = loop.prepare(m.rest, m.tets, m.group, m.fixed)
+    X = synth.perturbed_positions(m, 0.35, seed=13)
+    a = collision.self_pairs(X, prep.tets, prep.query)
+    b = collision.self_pairs(X, prep.tets, prep.query, n_slabs=1)
+    assert np.array_equal(a, b) and a.shape[0] > 0
