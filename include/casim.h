@@ -83,6 +83,9 @@ typedef struct {
   uint64_t wait_budget_cycles;  /* SM clock cycles a grid-barrier wait may spin
                                    before the kernel gives up with CASIM_E_TIMEOUT;
                                    0 selects the default (about 2 s)                 */
+  int32_t pcg_kernel;       /* 0 auto; 1 streaming PCG (vectors in HBM, any size);
+                               2 register-resident PCG (one row per thread; used by
+                               auto when every row fits, else CASIM_E_INVALID)      */
 } casim_params;
 
 /* Per-iteration record (Eq. 8 energy at X_i with the targets of iteration i). */

@@ -57,6 +57,7 @@ class casim_params(ctypes.Structure):
         ("stats", ctypes.c_int32),
         ("max_pairs_per_vertex", ctypes.c_int32),
         ("wait_budget_cycles", ctypes.c_uint64),
+        ("pcg_kernel", ctypes.c_int32),
     ]
 
 
@@ -312,7 +313,8 @@ class Sim:
     """Owns one casim handle built from a generator ``Mesh`` (or raw arrays)."""
 
     def __init__(self, mesh, precision=None, collision=None, stream: int = 0, stats: int = 1,
-                 pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0):
+                 pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0,
+                 pcg_kernel=0):
         load_library()
         p = casim_default_params()
         p.precision = mesh.precision if precision is None else precision
@@ -329,6 +331,7 @@ class Sim:
         p.stats = stats
         p.max_pairs_per_vertex = max_pairs
         p.wait_budget_cycles = wait_budget_cycles
+        p.pcg_kernel = pcg_kernel
         self.params = p
         self.mesh = mesh
         self.h = casim_create(p, stream)

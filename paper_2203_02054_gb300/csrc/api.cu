@@ -7,6 +7,7 @@
 #include <array>
 #include <cstddef>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <numeric>
@@ -74,6 +75,7 @@ struct casim_sim {
   CollisionScratch cs{};
   unsigned H_t = 0, H_f = 0;
   int cap_items = 0, n_slices = 0, pcg_grid = 1, n_e_local = 0, n_e_spring = 0;
+  bool pcg_rr = false;  // register-resident PCG (one row per thread)
   // graph of one iteration
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
@@ -205,7 +207,7 @@ cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) 
   if (ev) cudaEventRecord(ev[4], st);
   // reset the grid-barrier words (abort, count, generation) before the PCG
   cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st);
-  cudaError_t e = launch_pcg<T>(d, sim->pcg_grid, st);
+  cudaError_t e = launch_pcg<T>(d, sim->pcg_grid, sim->pcg_rr, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[5], st);
   launch_finalize<T>(d, st);
@@ -517,6 +519,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.n_w_knots < 0 || (p.n_w_knots > 0 && !p.w_knots) || p.n_w_knots > 64) why = "w_knots";
   else if (!(p.cell_size > 0.0) || !std::isfinite(p.cell_size)) why = "cell_size";
   else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
+  else if (p.pcg_kernel < 0 || p.pcg_kernel > 2) why = "pcg_kernel";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
       if (!(p.w_knots[2 * i + 2] > p.w_knots[2 * i])) why = "w_knots must be strictly ascending";
@@ -801,8 +804,21 @@ int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, i
   sim->H_f = (unsigned)pow2_at_least(2 * (size_t)std::max(sim->n_f, 1));
   sim->cap_items = (int)std::min<long long>(16LL * (n_t + sim->n_f) + 4096, 2000000000LL);
   // ---- PCG grid: co-resident blocks, no more than the rows need ----
-  const int maxg = sim->params.precision == CASIM_FP64 ? pcg_max_grid<double>() : pcg_max_grid<float>();
-  sim->pcg_grid = std::max(1, std::min(maxg, (n_free + PCG_THREADS - 1) / PCG_THREADS));
+  int max_width = 0;
+  for (int s = 0; s < sim->n_slices; ++s) max_width = std::max(max_width, (sl_ptr[s + 1] - sl_ptr[s]) / 32);
+  const bool fp64 = sim->params.precision == CASIM_FP64;
+  const int rr_rows = fp64 ? pcg_rr_max_rows<double>() : pcg_rr_max_rows<float>();
+  const bool rr_fits = max_width <= PCG_RR_MAXW && n_free <= rr_rows;
+  if (sim->params.pcg_kernel == 2 && !rr_fits)
+    return sim->fail(CASIM_E_INVALID, "register-resident PCG: rows do not fit (" + std::to_string(n_free) + " rows, width " +
+                                          std::to_string(max_width) + ")");
+  sim->pcg_rr = rr_fits && sim->params.pcg_kernel != 1;
+  if (sim->pcg_rr) {
+    sim->pcg_grid = std::max(1, (n_free + PCG_RR_THREADS - 1) / PCG_RR_THREADS);
+  } else {
+    const int maxg = fp64 ? pcg_max_grid<double>() : pcg_max_grid<float>();
+    sim->pcg_grid = std::max(1, std::min(maxg, (n_free + PCG_THREADS - 1) / PCG_THREADS));
+  }
   sim->rs = sim->params.precision == CASIM_FP64 ? 8 : 4;
   int rc;
   if (sim->params.precision == CASIM_FP64)

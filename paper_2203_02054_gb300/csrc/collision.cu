@@ -7,7 +7,7 @@
 // whose cell range covers the point's cell, so the hash never drops a pair;
 // hash collisions only add candidates.
 //
-// Narrow phase: one thread per non-fixed boundary vertex tests the tets of its
+// Narrow phase: one warp per non-fixed boundary vertex tests the tets of its
 // cell with exact orientation signs (predicates.cuh), so the pair set equals
 // the brute-force definition bit for bit.
 //
@@ -193,10 +193,16 @@ __device__ __forceinline__ bool strictly_inside(const Dev<T>& d, double px, doub
   return true;
 }
 
+// One warp per query vertex: the lanes test the candidates of the vertex's
+// hash bucket in parallel; hits are merged by lane 0 into the vertex's sorted,
+// duplicate-free pair list.
+static constexpr int NARROW_THREADS = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_narrow(Dev<T> d) {
+__global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
   __shared__ int shi[32];
-  const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int qi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
   int n_self = 0, n_obs = 0;
   if (qi < d.n_q) {
     const int v = d.q_verts[qi];
@@ -211,47 +217,65 @@ __global__ void __launch_bounds__(128) k_narrow(Dev<T> d) {
           (d.H_t - 1u);
       const int b0 = d.cell_start[h];
       const int b1 = min(d.cell_start[h + 1], d.cap_items);
-      for (int k = b0; k < b1; ++k) {
-        const int e = d.items[k];
-        const int4 t = d.tet[e];
-        if (t.x == v || t.y == v || t.z == v || t.w == v) continue;
-        if (!strictly_inside(d, px, py, pz, t)) continue;
-        // sorted insert without duplicates (a tet may repeat in a bucket)
-        int pos = 0;
-        while (pos < cnt && out[pos] < e) ++pos;
-        if (pos < cnt && out[pos] == e) continue;
-        if (cnt == d.max_pairs) {
-          over = true;
-          if (pos == cnt) continue;
-          --cnt;  // drop the largest to keep the smallest ids
+      for (int base = b0; base < b1; base += 32) {
+        const int k = base + lane;
+        int e = -1;
+        bool hit = false;
+        if (k < b1) {
+          e = d.items[k];
+          const int4 t = d.tet[e];
+          if (t.x != v && t.y != v && t.z != v && t.w != v) hit = strictly_inside(d, px, py, pz, t);
         }
-        for (int j = cnt; j > pos; --j) out[j] = out[j - 1];
-        out[pos] = e;
-        ++cnt;
-      }
-    }
-    if (over) set_status(d.ctrl, ST_OVERFLOW);
-    d.pair_count[qi] = cnt;
-    n_self = cnt;
-    int best = -1;
-    if (d.collision >= 2) {
-      double bestd = 0.0;
-      for (int j = 0; j < d.n_spheres; ++j) {
-        const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
-        const double r = d.spheres[4 * j + 3];
-        const double dx = __dsub_rn(px, cx), dy = __dsub_rn(py, cy), dz = __dsub_rn(pz, cz);
-        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-        if (d2 < __dmul_rn(r, r)) {
-          ++n_obs;
-          const double dist = sqrt(d2) - r;
-          if (best < 0 || dist < bestd) {
-            best = j;
-            bestd = dist;
+        unsigned m = __ballot_sync(0xffffffffu, hit);
+        while (m) {
+          const int src = __ffs(m) - 1;
+          m &= m - 1;
+          const int eh = __shfl_sync(0xffffffffu, e, src);
+          if (lane == 0) {
+            // sorted insert without duplicates (a tet may repeat in a bucket)
+            int pos = 0;
+            while (pos < cnt && out[pos] < eh) ++pos;
+            if (!(pos < cnt && out[pos] == eh)) {
+              bool ins = true;
+              if (cnt == d.max_pairs) {
+                over = true;
+                if (pos == cnt) ins = false;
+                else --cnt;  // drop the largest to keep the smallest ids
+              }
+              if (ins) {
+                for (int j = cnt; j > pos; --j) out[j] = out[j - 1];
+                out[pos] = eh;
+                ++cnt;
+              }
+            }
           }
         }
       }
     }
-    d.obs_sphere[qi] = best;
+    int best = -1;
+    if (lane == 0) {
+      if (over) set_status(d.ctrl, ST_OVERFLOW);
+      d.pair_count[qi] = cnt;
+      n_self = cnt;
+      if (d.collision >= 2) {
+        double bestd = 0.0;
+        for (int j = 0; j < d.n_spheres; ++j) {
+          const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
+          const double r = d.spheres[4 * j + 3];
+          const double dx = __dsub_rn(px, cx), dy = __dsub_rn(py, cy), dz = __dsub_rn(pz, cz);
+          const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+          if (d2 < __dmul_rn(r, r)) {
+            ++n_obs;
+            const double dist = sqrt(d2) - r;
+            if (best < 0 || dist < bestd) {
+              best = j;
+              bestd = dist;
+            }
+          }
+        }
+      }
+      d.obs_sphere[qi] = best;
+    }
   }
   const int s1 = block_sum_int(n_self, shi);
   const int s2 = block_sum_int(n_obs, shi);
@@ -549,7 +573,10 @@ void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t 
   k_scan_top<<<1, 1024, 0, st>>>(cs.tile_sums, n_tiles, cs.total, d.ctrl, d.cap_items);
   k_scan_add<<<(n_scan + 255) / 256, 256, 0, st>>>(d.cell_start, cs.tile_sums, n_scan);
   k_grid_bin<T, true><<<(n_items + 255) / 256, 256, 0, st>>>(d);
-  if (d.n_q > 0) k_narrow<T><<<(d.n_q + 127) / 128, 128, 0, st>>>(d);
+  if (d.n_q > 0) {
+    const long long threads = 32LL * d.n_q;
+    k_narrow<T><<<(unsigned)((threads + NARROW_THREADS - 1) / NARROW_THREADS), NARROW_THREADS, 0, st>>>(d);
+  }
 }
 
 template <typename T>

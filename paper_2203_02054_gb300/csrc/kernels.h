@@ -15,6 +15,8 @@ struct CollisionScratch {
 static constexpr int LOCAL_THREADS = 128;
 static constexpr int RHS_THREADS = 256;
 static constexpr int PCG_THREADS = 512;
+static constexpr int PCG_RR_THREADS = 256;
+static constexpr int PCG_RR_MAXW = 16;   // widest sliced-ELL row kept in registers
 
 template <typename T>
 void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t st);
@@ -25,7 +27,9 @@ void launch_local(const Dev<T>& d, cudaStream_t st);
 template <typename T>
 void launch_rhs(const Dev<T>& d, cudaStream_t st);
 template <typename T>
-cudaError_t launch_pcg(const Dev<T>& d, int grid, cudaStream_t st);
+cudaError_t launch_pcg(const Dev<T>& d, int grid, bool rr, cudaStream_t st);
+template <typename T>
+int pcg_rr_max_rows();
 template <typename T>
 void launch_finalize(const Dev<T>& d, cudaStream_t st);
 template <typename T>

@@ -207,11 +207,19 @@ __device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* parti
   }
   if (!grid_sync(g, shf)) return false;
   if (threadIdx.x < 32) {
+    double a[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) a[k] = 0.0;
+#pragma unroll 4
+    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) a[k] += __ldcg(buf + 4 * b + k);
+    }
+#pragma unroll
     for (int k = 0; k < NV; ++k) {
-      double a = 0.0;
-      for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) a += __ldcg(buf + 4 * b + k);
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-      if (threadIdx.x == 0) tot[k] = a;
+      double t = a[k];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+      if (threadIdx.x == 0) tot[k] = t;
     }
   }
   __syncthreads();
@@ -384,6 +392,164 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(Dev<T> d) {
   }
 }
 
+// Register-resident variant: one row per thread.  The thread keeps its
+// sliced-ELL row, diagonal and all CG vectors (x, r, p, s, w, u) in registers
+// for the whole solve; per iteration only the preconditioned residual u is
+// written to memory and its neighbours' values gathered from L2.
+template <typename T>
+__device__ __forceinline__ R4<T> ld_cg(const R4<T>* a);
+template <>
+__device__ __forceinline__ R4<float> ld_cg<float>(const R4<float>* a) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(a));
+  return R4<float>{v.x, v.y, v.z, v.w};
+}
+template <>
+__device__ __forceinline__ R4<double> ld_cg<double>(const R4<double>* a) {
+  const double2 v0 = __ldcg(reinterpret_cast<const double2*>(a));
+  const double2 v1 = __ldcg(reinterpret_cast<const double2*>(a) + 1);
+  return R4<double>{v0.x, v0.y, v1.x, v1.y};
+}
+
+template <typename T, int MAXW>
+__global__ void __launch_bounds__(PCG_RR_THREADS) k_pcg_rr(Dev<T> d) {
+  __shared__ double sh[32];
+  __shared__ double tot[4];
+  __shared__ int shf;
+  const GridCtx g{d.ctrl, gridDim.x, d.wait_budget};
+  const int n = d.n_free;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = i < n;
+  int parity = 0;
+  int col[MAXW];
+  T val[MAXW];
+  int width = 0;
+  T dg = T(1);
+  T x[3] = {T(0), T(0), T(0)}, b[3] = {T(0), T(0), T(0)};
+  if (act) {
+    const int sl = i >> 5, lane = i & 31;
+    const int base = d.sl_ptr[sl];
+    width = (d.sl_ptr[sl + 1] - base) >> 5;
+#pragma unroll
+    for (int j = 0; j < MAXW; ++j) {
+      if (j < width) {
+        col[j] = d.sl_col[base + j * 32 + lane];
+        val[j] = d.sl_val[base + j * 32 + lane];
+      } else {
+        col[j] = i;
+        val[j] = T(0);
+      }
+    }
+    dg = d.diag[i];
+    const R4<T> xi = d.X[i], bi = d.b[i];
+    x[0] = xi.x; x[1] = xi.y; x[2] = xi.z;
+    b[0] = bi.x; b[1] = bi.y; b[2] = bi.z;
+  }
+  auto spmv = [&](const R4<T>* src, const T (&self)[3], T (&ax)[3]) {
+    ax[0] = dg * self[0];
+    ax[1] = dg * self[1];
+    ax[2] = dg * self[2];
+#pragma unroll
+    for (int j = 0; j < MAXW; ++j) {
+      if (j < width) {
+        const R4<T> v = ld_cg<T>(src + col[j]);
+        ax[0] += val[j] * v.x;
+        ax[1] += val[j] * v.y;
+        ax[2] += val[j] * v.z;
+      }
+    }
+  };
+  auto store_u = [&](const T (&u)[3]) {
+    R4<T> t;
+    t.x = u[0]; t.y = u[1]; t.z = u[2]; t.w = T(0);
+    d.u[i] = t;
+  };
+  T r[3], u[3], w[3], p[3], s[3];
+  double a0[2] = {0.0, 0.0};
+  if (act) {
+    T ax[3];
+    spmv(d.X, x, ax);
+    for (int c = 0; c < 3; ++c) {
+      r[c] = b[c] - ax[c];
+      u[c] = r[c] / dg;
+      a0[0] += (double)b[c] * b[c];
+      a0[1] += (double)r[c] * r[c];
+    }
+    store_u(u);
+  }
+  if (!grid_reduce<2>(a0, d.partials, parity, g, sh, tot, &shf)) return;
+  const double bb = tot[0];
+  double rr = tot[1];
+  int it = 0;
+  if (bb > 0.0 && rr > d.tol2 * bb) {
+    double a1[2] = {0.0, 0.0};
+    if (act) {
+      spmv(d.u, u, w);
+      for (int c = 0; c < 3; ++c) {
+        a1[0] += (double)r[c] * u[c];
+        a1[1] += (double)w[c] * u[c];
+        p[c] = u[c];
+        s[c] = w[c];
+      }
+    }
+    if (!grid_reduce<2>(a1, d.partials, parity, g, sh, tot, &shf)) return;
+    double gamma = tot[0];
+    double alpha = gamma / tot[1];
+    for (it = 1; it <= d.max_iter; ++it) {
+      const T ta = (T)alpha;
+      if (act) {
+        for (int c = 0; c < 3; ++c) {
+          x[c] += ta * p[c];
+          r[c] -= ta * s[c];
+          u[c] = r[c] / dg;
+        }
+        store_u(u);
+      }
+      if (!grid_sync(g, &shf)) return;
+      double a2[3] = {0.0, 0.0, 0.0};
+      if (act) {
+        spmv(d.u, u, w);
+        for (int c = 0; c < 3; ++c) {
+          a2[0] += (double)r[c] * u[c];
+          a2[1] += (double)w[c] * u[c];
+          a2[2] += (double)r[c] * r[c];
+        }
+      }
+      if (!grid_reduce<3>(a2, d.partials, parity, g, sh, tot, &shf)) return;
+      const double gnew = tot[0], delta = tot[1];
+      rr = tot[2];
+      if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
+        if (i == 0) set_status(d.ctrl, ST_NONFINITE);
+        break;
+      }
+      if (rr <= d.tol2 * bb) break;
+      const double beta = gnew / gamma;
+      alpha = gnew / (delta - beta * gnew / alpha);
+      gamma = gnew;
+      const T tb = (T)beta;
+      if (act)
+        for (int c = 0; c < 3; ++c) {
+          p[c] = u[c] + tb * p[c];
+          s[c] = w[c] + tb * s[c];
+        }
+    }
+    if (it > d.max_iter) {
+      it = d.max_iter;
+      if (i == 0) set_status(d.ctrl, ST_PCG_MAXIT);
+    }
+    if (act) {
+      R4<T> t;
+      t.x = x[0]; t.y = x[1]; t.z = x[2]; t.w = T(0);
+      d.X[i] = t;
+    }
+  }
+  if (i == 0) {
+    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
+    rec->pcg_iters = it;
+    d.ctrl->total_pcg += it;
+    rec->pcg_rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+  }
+}
+
 // --------------------------------------------------------------- finalize
 template <typename T>
 __global__ void k_finalize(Dev<T> d) {
@@ -447,11 +613,20 @@ int pcg_max_grid() {
 }
 
 template <typename T>
-cudaError_t launch_pcg(const Dev<T>& d, int grid, cudaStream_t st) {
+int pcg_rr_max_rows() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_rr<T, PCG_RR_MAXW>, PCG_RR_THREADS, 0);
+  return sms * per * PCG_RR_THREADS;
+}
+
+template <typename T>
+cudaError_t launch_pcg(const Dev<T>& d, int grid, bool rr, cudaStream_t st) {
   if (d.n_free == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(PCG_THREADS);
+  cfg.blockDim = dim3(rr ? PCG_RR_THREADS : PCG_THREADS);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -459,6 +634,7 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (rr) return cudaLaunchKernelEx(&cfg, k_pcg_rr<T, PCG_RR_MAXW>, d);
   return cudaLaunchKernelEx(&cfg, k_pcg<T>, d);
 }
 
@@ -478,8 +654,10 @@ template void launch_local<float>(const Dev<float>&, cudaStream_t);
 template void launch_local<double>(const Dev<double>&, cudaStream_t);
 template void launch_rhs<float>(const Dev<float>&, cudaStream_t);
 template void launch_rhs<double>(const Dev<double>&, cudaStream_t);
-template cudaError_t launch_pcg<float>(const Dev<float>&, int, cudaStream_t);
-template cudaError_t launch_pcg<double>(const Dev<double>&, int, cudaStream_t);
+template cudaError_t launch_pcg<float>(const Dev<float>&, int, bool, cudaStream_t);
+template cudaError_t launch_pcg<double>(const Dev<double>&, int, bool, cudaStream_t);
+template int pcg_rr_max_rows<float>();
+template int pcg_rr_max_rows<double>();
 template int pcg_max_grid<float>();
 template int pcg_max_grid<double>();
 template void launch_finalize<float>(const Dev<float>&, cudaStream_t);
