@@ -59,7 +59,8 @@ struct casim_sim {
   size_t rs = 4;  // bytes per real
   void *X = nullptr, *Tc = nullptr, *tinfo = nullptr, *P = nullptr, *cbrt_alpha = nullptr;
   void *diagL = nullptr, *bfix = nullptr, *b = nullptr, *diag = nullptr, *sl_val = nullptr;
-  void *r = nullptr, *u = nullptr, *p = nullptr, *s = nullptr, *w = nullptr, *spring_c = nullptr;
+  void *r = nullptr, *u = nullptr, *p = nullptr, *s = nullptr, *w = nullptr, *dx = nullptr, *spring_c = nullptr;
+  unsigned* gens = nullptr;
   void* pos_out = nullptr;
   void* X0 = nullptr;  // positions restored by casim_reset
   int4 *tet = nullptr, *faces = nullptr;
@@ -142,8 +143,8 @@ Dev<T> make_dev(casim_sim* sim) {
   d.inc_ptr = sim->inc_ptr;
   d.inc = sim->inc;
   d.diagL = (const T*)sim->diagL;
-  d.bfix = (const R4<T>*)sim->bfix;
-  d.b = (R4<T>*)sim->b;
+  d.bfix = (const R4<double>*)sim->bfix;
+  d.b = (R4<double>*)sim->b;
   d.diag = (T*)sim->diag;
   d.n_slices = sim->n_slices;
   d.sl_ptr = sim->sl_ptr;
@@ -154,7 +155,9 @@ Dev<T> make_dev(casim_sim* sim) {
   d.p = (R4<T>*)sim->p;
   d.s = (R4<T>*)sim->s;
   d.w = (R4<T>*)sim->w;
+  d.dx = (R4<T>*)sim->dx;
   d.partials = sim->partials;
+  d.gens = sim->gens;
   d.q_verts = sim->q_verts_d;
   d.qf_ptr = sim->qf_ptr;
   d.qf = sim->qf;
@@ -172,7 +175,7 @@ Dev<T> make_dev(casim_sim* sim) {
   d.obs_sphere = sim->obs_sphere;
   d.max_pairs = sim->params.max_pairs_per_vertex;
   d.sp = sim->sp;
-  d.spring_c = (R4<T>*)sim->spring_c;
+  d.spring_c = (R4<double>*)sim->spring_c;
   d.k_spring = sim->params.k_spring;
   d.eps = sim->params.eps;
   d.cell = sim->params.cell_size;
@@ -207,6 +210,7 @@ cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) 
   if (ev) cudaEventRecord(ev[4], st);
   // reset the grid-barrier words (abort, count, generation) before the PCG
   cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st);
+  cudaMemsetAsync(sim->gens, 0, sizeof(unsigned) * std::max(sim->pcg_grid, 1), st);
   cudaError_t e = launch_pcg<T>(d, sim->pcg_grid, sim->pcg_rr, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[5], st);
@@ -240,8 +244,8 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->inc_ptr = sim->dalloc<int>(n_free + 1);
   sim->inc = sim->dalloc<int>(inc.size());
   sim->diagL = sim->dalloc<T>(n_free);
-  sim->bfix = sim->dalloc<R4<T>>(n_free);
-  sim->b = sim->dalloc<R4<T>>(n_free);
+  sim->bfix = sim->dalloc<R4<double>>(n_free);
+  sim->b = sim->dalloc<R4<double>>(n_free);
   sim->diag = sim->dalloc<T>(n_free);
   sim->sl_ptr = sim->dalloc<int>(sl_ptr.size());
   sim->sl_col = sim->dalloc<int>(sl_col.size());
@@ -251,7 +255,9 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->p = sim->dalloc<R4<T>>(n_free);
   sim->s = sim->dalloc<R4<T>>(n_free);
   sim->w = sim->dalloc<R4<T>>(n_free);
-  sim->spring_c = sim->dalloc<R4<T>>(n_free);
+  sim->dx = sim->dalloc<R4<T>>(n_free);
+  sim->spring_c = sim->dalloc<R4<double>>(n_free);
+  sim->gens = sim->dalloc<unsigned>(std::max(sim->pcg_grid, 1));
   sim->partials = sim->dalloc<double>(2 * 4 * (size_t)std::max(sim->pcg_grid, 1));
   sim->q_verts_d = sim->dalloc<int>(n_q);
   sim->qf_ptr = sim->dalloc<int>(n_q + 1);
@@ -322,7 +328,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   if (!qf.empty()) CK(cudaMemcpyAsync(sim->qf, qf.data(), sizeof(int) * qf.size(), cudaMemcpyHostToDevice, st));
   if (n_f) CK(cudaMemcpyAsync(sim->faces, fh.data(), sizeof(int4) * n_f, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->int_of_user_d, sim->int_of_user.data(), sizeof(int) * n_v, cudaMemcpyHostToDevice, st));
-  CK(cudaMemsetAsync(sim->spring_c, 0, sizeof(R4<T>) * std::max(n_free, 1), st));
+  CK(cudaMemsetAsync(sim->spring_c, 0, sizeof(R4<double>) * std::max(n_free, 1), st));
   CK(cudaMemsetAsync(sim->sp.active, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->sp.kind, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->sp.face, 0xff, sizeof(int) * std::max(n_q, 1), st));
@@ -342,16 +348,16 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
 // position uploads).
 template <typename T>
 int upload_bfix(casim_sim* sim) {
-  std::vector<R4<T>> bf(std::max(sim->n_free, 1));
+  std::vector<R4<double>> bf(std::max(sim->n_free, 1));
   for (int v = 0; v < sim->n_free; ++v) {
     double a[3] = {0, 0, 0};
     for (int k = sim->fx_ptr[v]; k < sim->fx_ptr[v + 1]; ++k) {
       const int u = sim->fx_col[k] - sim->n_free;
       for (int c = 0; c < 3; ++c) a[c] += sim->fx_val[k] * sim->X_fixed[3 * (size_t)u + c];
     }
-    bf[v] = R4<T>{(T)a[0], (T)a[1], (T)a[2], T(0)};
+    bf[v] = R4<double>{a[0], a[1], a[2], 0.0};
   }
-  CK(cudaMemcpyAsync(sim->bfix, bf.data(), sizeof(R4<T>) * sim->n_free, cudaMemcpyHostToDevice, sim->stream));
+  CK(cudaMemcpyAsync(sim->bfix, bf.data(), sizeof(R4<double>) * sim->n_free, cudaMemcpyHostToDevice, sim->stream));
   CK(cudaStreamSynchronize(sim->stream));
   return CASIM_OK;
 }
@@ -898,7 +904,7 @@ int casim_reset(casim_sim* sim) {
   if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
   const size_t nq = std::max(sim->n_q, 1);
   CK(cudaMemcpyAsync(sim->X, sim->X0, 4 * sim->rs * (size_t)sim->n_v, cudaMemcpyDeviceToDevice, sim->stream));
-  CK(cudaMemsetAsync(sim->spring_c, 0, 4 * sim->rs * (size_t)std::max(sim->n_free, 1), sim->stream));
+  CK(cudaMemsetAsync(sim->spring_c, 0, sizeof(R4<double>) * (size_t)std::max(sim->n_free, 1), sim->stream));
   CK(cudaMemsetAsync(sim->sp.active, 0, sizeof(int) * nq, sim->stream));
   CK(cudaMemsetAsync(sim->sp.kind, 0, sizeof(int) * nq, sim->stream));
   CK(cudaMemsetAsync(sim->sp.face, 0xff, sizeof(int) * nq, sim->stream));

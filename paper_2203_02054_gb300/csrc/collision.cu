@@ -539,12 +539,7 @@ __global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
     d.sp.target[3 * qi] = tgt.x;
     d.sp.target[3 * qi + 1] = tgt.y;
     d.sp.target[3 * qi + 2] = tgt.z;
-    R4<T> sc;
-    sc.x = (T)tgt.x;
-    sc.y = (T)tgt.y;
-    sc.z = (T)tgt.z;
-    sc.w = active ? T(1) : T(0);
-    d.spring_c[v] = sc;
+    d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
     if (active) {
       const V3 dd = sub(x, tgt);
       e_spring = d.k_spring * dot(dd, dd);

@@ -10,7 +10,8 @@
 //   system    incidence CSR of free vertices (tet*4 + slot), constant
 //             Laplacian off-diagonals in sliced ELL (32-row slices,
 //             column-major inside a slice), diagonal separate;
-//   PCG       r, u, p, s, w vectors R4<T>[n_free], FP64 block partials.
+//   PCG       r, u, p, s, w, dx vectors R4<T>[n_free], FP64 block partials;
+//             right-hand side b and the fixed-vertex term in FP64.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -74,8 +75,8 @@ struct Dev {
   const int* inc_ptr;    // n_free + 1
   const int* inc;        // tet*4 + slot
   const T* diagL;        // n_free
-  const R4<T>* bfix;     // n_free
-  R4<T>* b;              // n_free
+  const R4<double>* bfix; // n_free, FP64
+  R4<double>* b;          // n_free, FP64 right-hand side
   T* diag;               // n_free (Laplacian diagonal + k mask)
   int n_slices;
   const int* sl_ptr;     // n_slices + 1 (entries)
@@ -86,7 +87,9 @@ struct Dev {
   R4<T>* p;
   R4<T>* s;
   R4<T>* w;
-  double* partials;      // 4 * pcg grid
+  R4<T>* dx;             // PCG correction (streaming kernel)
+  double* partials;      // 2 x 4 x pcg grid
+  unsigned* gens;        // per-block sync generations (pcg grid)
   // collision
   const int* q_verts;    // n_q internal vertex ids (ascending)
   const int* qf_ptr;     // n_q + 1 incident boundary faces
@@ -104,7 +107,7 @@ struct Dev {
   int* obs_sphere;       // n_q: sphere id or -1
   int max_pairs;
   SpringDev sp;
-  R4<T>* spring_c;       // n_free: (c, mask)
+  R4<double>* spring_c;  // n_free: (c, mask), FP64
   // parameters
   double k_spring, eps, cell, inv_cell, tol2;
   int max_iter, collision, stats;

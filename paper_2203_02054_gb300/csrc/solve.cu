@@ -125,109 +125,152 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local(Dev<T> d) {
 }
 
 // ------------------------------------------------------------ RHS gather
+// b_v = sum over incident (e, slot) of w_e P_e[:, slot] + k mask_v c_v - bfix_v,
+// accumulated in FP64 (the products of the FP32 targets need no rounding).
 template <typename T>
 __global__ void __launch_bounds__(RHS_THREADS) k_rhs(Dev<T> d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= d.n_free) return;
-  T bx = T(0), by = T(0), bz = T(0);
+  double bx = 0.0, by = 0.0, bz = 0.0;
   const int k1 = d.inc_ptr[i + 1];
   for (int k = d.inc_ptr[i]; k < k1; ++k) {
     const R4<T> p = d.P[d.inc[k]];
-    bx += p.x;
-    by += p.y;
-    bz += p.z;
+    bx += (double)p.x;
+    by += (double)p.y;
+    bz += (double)p.z;
   }
-  const R4<T> sc = d.spring_c[i];
-  const T km = (T)d.k_spring * sc.w;
-  const R4<T> bf = d.bfix[i];
-  R4<T> bi;
-  bi.x = bx + km * sc.x - bf.x;
-  bi.y = by + km * sc.y - bf.y;
-  bi.z = bz + km * sc.z - bf.z;
-  bi.w = T(0);
-  d.b[i] = bi;
-  d.diag[i] = d.diagL[i] + km;
+  const R4<double> sc = d.spring_c[i];
+  const double km = d.k_spring * sc.w;
+  const R4<double> bf = d.bfix[i];
+  d.b[i] = R4<double>{bx + km * sc.x - bf.x, by + km * sc.y - bf.y, bz + km * sc.z - bf.z, 0.0};
+  d.diag[i] = d.diagL[i] + (T)km;
 }
 
 // ------------------------------------------------------------------ PCG
+//
+// Both PCG kernels solve for the correction d of the warm start x:
+//   r0 = b - A x  in FP64 (FP32 products are exact in FP64),
+//   A d = r0      by Jacobi-preconditioned CG in the working precision,
+//   x <- x + d    once at the end,
+// so that the rounding of the working precision applies to the small
+// correction, not to the positions (one step of mixed-precision iterative
+// refinement per outer iteration).  The stopping test ||r|| <= tol ||b|| is the
+// same as for the plain system.
+//
+// Grid synchronisation without atomics: block k publishes its FP64 partial
+// sums, then (after a fence) its generation number gens[k]; warp 0 of every
+// block polls all generations, then reads and sums the partials in block
+// order (deterministic).  Partials alternate between two buffers, so a block
+// that runs ahead cannot overwrite values another block is still reading.
+// Every wait is bounded by a clock budget, after which the kernel records
+// ST_TIMEOUT, raises the abort word and returns.
 struct GridCtx {
   Ctrl* ctrl;
+  unsigned* gens;
+  double* partials;
   unsigned nblocks;
   unsigned long long budget;
 };
 
-// Grid-wide barrier with a bounded wait.  Returns false when this or another
-// block gave up (the kernel must then return).
-__device__ __forceinline__ bool grid_sync(const GridCtx& g, int* sh_flag) {
+// Publishes this block's sums bs[0..NV) (NV may be 0), waits for every block
+// of the same epoch, then leaves the grid totals in tot[0..NV).
+template <int NV, int NB>
+__device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& epoch, const double (&bs)[NB],
+                                                  double* tot, int* shf) {
+  ++epoch;
   __syncthreads();
+  double* buf = g.partials + (size_t)(epoch & 1u) * 4 * g.nblocks;
   if (threadIdx.x == 0) {
-    int ok = 1;
-    volatile unsigned* vgen = &g.ctrl->bar_gen;
-    volatile int* vab = &g.ctrl->abort;
-    const unsigned gen = *vgen;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) buf[4 * blockIdx.x + k] = bs[k];
     __threadfence();
-    const unsigned arrived = atomicAdd(&g.ctrl->bar_count, 1u);
-    if (arrived == g.nblocks - 1u) {
-      atomicExch(&g.ctrl->bar_count, 0u);
-      __threadfence();
-      atomicAdd(&g.ctrl->bar_gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == gen) {
-        if (*vab) {
-          ok = 0;
-          break;
-        }
-        if ((unsigned long long)(clock64() - t0) > g.budget) {
+    *(volatile unsigned*)(g.gens + blockIdx.x) = epoch;
+  }
+  if (threadIdx.x < 32) {
+    const long long t0 = clock64();
+    int ok = 1;
+    while (true) {
+      bool ready = true;
+      for (unsigned b = threadIdx.x; b < g.nblocks; b += 32)
+        ready = ready && ((int)(*(volatile unsigned*)(g.gens + b) - epoch) >= 0);
+      if (__all_sync(0xffffffffu, ready)) break;
+      int bad = 0;
+      if (threadIdx.x == 0) {
+        if (*(volatile int*)&g.ctrl->abort) {
+          bad = 1;
+        } else if ((unsigned long long)(clock64() - t0) > g.budget) {
           atomicExch(&g.ctrl->abort, 1);
           atomicOr(&g.ctrl->status, ST_TIMEOUT);
-          ok = 0;
-          break;
+          bad = 1;
         }
-        __nanosleep(32);
+      }
+      if (__shfl_sync(0xffffffffu, bad, 0)) {
+        ok = 0;
+        break;
       }
     }
     __threadfence();
-    *sh_flag = ok;
-  }
-  __syncthreads();
-  return *sh_flag != 0;
-}
-
-// Grid-wide FP64 sum of NV values per thread; totals returned in tot[].
-// Partials alternate between two buffers so that a block running ahead to
-// the next reduction cannot overwrite values another block is still reading.
-template <int NV>
-__device__ __forceinline__ bool grid_reduce(const double (&v)[NV], double* partials, int& parity,
-                                            const GridCtx& g, double* sh, double* tot, int* shf) {
-  double* buf = partials + (size_t)parity * 4 * gridDim.x;
-  for (int k = 0; k < NV; ++k) {
-    const double t = block_sum(v[k], sh);
-    if (threadIdx.x == 0) buf[4 * blockIdx.x + k] = t;
-  }
-  if (!grid_sync(g, shf)) return false;
-  if (threadIdx.x < 32) {
-    double a[NV];
+    if (NV > 0 && ok) {
+      double a[NB];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) a[k] = 0.0;
+      for (int k = 0; k < NB; ++k) a[k] = 0.0;
 #pragma unroll 4
-    for (unsigned b = threadIdx.x; b < gridDim.x; b += 32) {
+      for (unsigned b = threadIdx.x; b < g.nblocks; b += 32) {
 #pragma unroll
-      for (int k = 0; k < NV; ++k) a[k] += __ldcg(buf + 4 * b + k);
-    }
+        for (int k = 0; k < NV; ++k) a[k] += __ldcg(buf + 4 * b + k);
+      }
 #pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      double t = a[k];
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-      if (threadIdx.x == 0) tot[k] = t;
+      for (int k = 0; k < NV; ++k) {
+        double t = a[k];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) tot[k] = t;
+      }
     }
+    if (threadIdx.x == 0) *shf = ok;
   }
   __syncthreads();
-  parity ^= 1;
-  return true;
+  return *shf != 0;
 }
 
-// (A v)_i for one row of the sliced-ELL off-diagonal part plus the diagonal.
+template <int NV>
+__device__ __forceinline__ bool grid_sync_reduce(const GridCtx& g, unsigned& epoch, const double (&v)[NV],
+                                                 double* sh, double* tot, int* shf) {
+  double bs[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) bs[k] = block_sum(v[k], sh);
+  return grid_publish_wait<NV, NV>(g, epoch, bs, tot, shf);
+}
+
+__device__ __forceinline__ bool grid_sync(const GridCtx& g, unsigned& epoch, double* sh, double* tot, int* shf) {
+  const double none[1] = {0.0};
+  (void)sh;
+  return grid_publish_wait<0, 1>(g, epoch, none, tot, shf);
+}
+
+template <typename T>
+__device__ __forceinline__ R4<T> ld_cg(const R4<T>* a);
+template <>
+__device__ __forceinline__ R4<float> ld_cg<float>(const R4<float>* a) {
+  const float4 v = __ldcg(reinterpret_cast<const float4*>(a));
+  return R4<float>{v.x, v.y, v.z, v.w};
+}
+template <>
+__device__ __forceinline__ R4<double> ld_cg<double>(const R4<double>* a) {
+  const double2 v0 = __ldcg(reinterpret_cast<const double2*>(a));
+  const double2 v1 = __ldcg(reinterpret_cast<const double2*>(a) + 1);
+  return R4<double>{v0.x, v0.y, v1.x, v1.y};
+}
+
+__device__ __forceinline__ void write_pcg_record(const Ctrl* c, IterRec* hist, int cap, Ctrl* cw, int it, double rr,
+                                                 double bb) {
+  IterRec* rec = hist + (c->iter % cap);
+  rec->pcg_iters = it;
+  cw->total_pcg += it;
+  rec->pcg_rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+}
+
+// Streaming variant: any number of rows per thread (grid-stride); vectors in
+// HBM/L2, off-diagonals read from the sliced-ELL arrays every SpMV.
 template <typename T>
 __device__ __forceinline__ void spmv_row(const Dev<T>& d, int i, const R4<T>* __restrict__ src, T dg,
                                          const R4<T>& self, T& ax, T& ay, T& az) {
@@ -239,7 +282,7 @@ __device__ __forceinline__ void spmv_row(const Dev<T>& d, int i, const R4<T>* __
   for (int k = d.sl_ptr[s] + lane; k < k1; k += 32) {
     const int c = d.sl_col[k];
     const T a = d.sl_val[k];
-    const R4<T> x = src[c];
+    const R4<T> x = ld_cg<T>(src + c);
     ax += a * x.x;
     ay += a * x.y;
     az += a * x.z;
@@ -247,66 +290,68 @@ __device__ __forceinline__ void spmv_row(const Dev<T>& d, int i, const R4<T>* __
 }
 
 template <typename T>
-__global__ void __launch_bounds__(PCG_THREADS) k_pcg(Dev<T> d) {
+__global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
   __shared__ double sh[32];
   __shared__ double tot[4];
   __shared__ int shf;
-  const GridCtx g{d.ctrl, gridDim.x, d.wait_budget};
+  const GridCtx g{d.ctrl, d.gens, d.partials, gridDim.x, d.wait_budget};
+  unsigned epoch = 0;
   const int n = d.n_free;
   const int G = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  int parity = 0;
   R4<T>* __restrict__ X = d.X;
   R4<T>* __restrict__ r = d.r;
   R4<T>* __restrict__ u = d.u;
   R4<T>* __restrict__ p = d.p;
   R4<T>* __restrict__ s = d.s;
   R4<T>* __restrict__ w = d.w;
+  R4<T>* __restrict__ dx = d.dx;
+  const R4<T> zero = {T(0), T(0), T(0), T(0)};
 
-  // r = b - A x, u = M^-1 r
+  // r = b - A x in FP64, u = M^-1 r, d = 0
   double a0[2] = {0.0, 0.0};
   for (int i = tid; i < n; i += G) {
     const T dg = d.diag[i];
     const R4<T> xi = X[i];
-    T ax, ay, az;
-    spmv_row(d, i, X, dg, xi, ax, ay, az);
-    const R4<T> bi = d.b[i];
+    double ax = (double)dg * xi.x, ay = (double)dg * xi.y, az = (double)dg * xi.z;
+    const int sl = i >> 5, lane = i & 31;
+    const int k1 = d.sl_ptr[sl + 1];
+    for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
+      const double a = (double)d.sl_val[k];
+      const R4<T> xc = X[d.sl_col[k]];
+      ax += a * xc.x;
+      ay += a * xc.y;
+      az += a * xc.z;
+    }
+    const R4<double> bi = d.b[i];
+    const double rx = bi.x - ax, ry = bi.y - ay, rz = bi.z - az;
     R4<T> ri, ui;
-    ri.x = bi.x - ax;
-    ri.y = bi.y - ay;
-    ri.z = bi.z - az;
-    ri.w = T(0);
-    ui.x = ri.x / dg;
-    ui.y = ri.y / dg;
-    ui.z = ri.z / dg;
-    ui.w = T(0);
+    ri.x = (T)rx; ri.y = (T)ry; ri.z = (T)rz; ri.w = T(0);
+    ui.x = ri.x / dg; ui.y = ri.y / dg; ui.z = ri.z / dg; ui.w = T(0);
     r[i] = ri;
     u[i] = ui;
-    a0[0] += (double)bi.x * bi.x + (double)bi.y * bi.y + (double)bi.z * bi.z;
-    a0[1] += (double)ri.x * ri.x + (double)ri.y * ri.y + (double)ri.z * ri.z;
+    dx[i] = zero;
+    a0[0] += bi.x * bi.x + bi.y * bi.y + bi.z * bi.z;
+    a0[1] += rx * rx + ry * ry + rz * rz;
   }
-  if (!grid_reduce<2>(a0, d.partials, parity, g, sh, tot, &shf)) return;
+  if (!grid_sync_reduce<2>(g, epoch, a0, sh, tot, &shf)) return;
   const double bb = tot[0];
   double rr = tot[1];
   int it = 0;
   if (bb > 0.0 && rr > d.tol2 * bb) {
-    // w = A u and the first scalars
-    double a1[3] = {0.0, 0.0, 0.0};
+    double a1[2] = {0.0, 0.0};
     for (int i = tid; i < n; i += G) {
       const T dg = d.diag[i];
       const R4<T> ui = u[i], ri = r[i];
       T ax, ay, az;
       spmv_row(d, i, u, dg, ui, ax, ay, az);
       R4<T> wi;
-      wi.x = ax;
-      wi.y = ay;
-      wi.z = az;
-      wi.w = T(0);
+      wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
       w[i] = wi;
       a1[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
       a1[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
     }
-    if (!grid_reduce<3>(a1, d.partials, parity, g, sh, tot, &shf)) return;
+    if (!grid_sync_reduce<2>(g, epoch, a1, sh, tot, &shf)) return;
     double gamma = tot[0];
     double alpha = gamma / tot[1];
     double beta = 0.0;
@@ -321,35 +366,24 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(Dev<T> d) {
           si = wi;
         } else {
           const R4<T> po = p[i], so = s[i];
-          pi.x = ui.x + tb * po.x;
-          pi.y = ui.y + tb * po.y;
-          pi.z = ui.z + tb * po.z;
-          si.x = wi.x + tb * so.x;
-          si.y = wi.y + tb * so.y;
-          si.z = wi.z + tb * so.z;
+          pi.x = ui.x + tb * po.x; pi.y = ui.y + tb * po.y; pi.z = ui.z + tb * po.z;
+          si.x = wi.x + tb * so.x; si.y = wi.y + tb * so.y; si.z = wi.z + tb * so.z;
         }
         pi.w = T(0);
         si.w = T(0);
         p[i] = pi;
         s[i] = si;
-        R4<T> xi = X[i], ri = r[i];
-        xi.x += ta * pi.x;
-        xi.y += ta * pi.y;
-        xi.z += ta * pi.z;
-        ri.x -= ta * si.x;
-        ri.y -= ta * si.y;
-        ri.z -= ta * si.z;
-        X[i] = xi;
+        R4<T> di = dx[i], ri = r[i];
+        di.x += ta * pi.x; di.y += ta * pi.y; di.z += ta * pi.z;
+        ri.x -= ta * si.x; ri.y -= ta * si.y; ri.z -= ta * si.z;
+        dx[i] = di;
         r[i] = ri;
         const T dg = d.diag[i];
         R4<T> un;
-        un.x = ri.x / dg;
-        un.y = ri.y / dg;
-        un.z = ri.z / dg;
-        un.w = T(0);
+        un.x = ri.x / dg; un.y = ri.y / dg; un.z = ri.z / dg; un.w = T(0);
         u[i] = un;
       }
-      if (!grid_sync(g, &shf)) return;
+      if (!grid_sync(g, epoch, sh, tot, &shf)) return;
       double a2[3] = {0.0, 0.0, 0.0};
       for (int i = tid; i < n; i += G) {
         const T dg = d.diag[i];
@@ -357,16 +391,13 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(Dev<T> d) {
         T ax, ay, az;
         spmv_row(d, i, u, dg, ui, ax, ay, az);
         R4<T> wi;
-        wi.x = ax;
-        wi.y = ay;
-        wi.z = az;
-        wi.w = T(0);
+        wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
         w[i] = wi;
         a2[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
         a2[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
         a2[2] += (double)ri.x * ri.x + (double)ri.y * ri.y + (double)ri.z * ri.z;
       }
-      if (!grid_reduce<3>(a2, d.partials, parity, g, sh, tot, &shf)) return;
+      if (!grid_sync_reduce<3>(g, epoch, a2, sh, tot, &shf)) return;
       const double gnew = tot[0], delta = tot[1];
       rr = tot[2];
       if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
@@ -383,48 +414,35 @@ __global__ void __launch_bounds__(PCG_THREADS) k_pcg(Dev<T> d) {
       it = d.max_iter;
       if (tid == 0) set_status(d.ctrl, ST_PCG_MAXIT);
     }
+    for (int i = tid; i < n; i += G) {
+      R4<T> xi = X[i];
+      const R4<T> di = dx[i];
+      xi.x += di.x; xi.y += di.y; xi.z += di.z;
+      X[i] = xi;
+    }
   }
-  if (tid == 0) {
-    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
-    rec->pcg_iters = it;
-    d.ctrl->total_pcg += it;
-    rec->pcg_rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-  }
+  if (tid == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, bb);
 }
 
 // Register-resident variant: one row per thread.  The thread keeps its
-// sliced-ELL row, diagonal and all CG vectors (x, r, p, s, w, u) in registers
-// for the whole solve; per iteration only the preconditioned residual u is
-// written to memory and its neighbours' values gathered from L2.
-template <typename T>
-__device__ __forceinline__ R4<T> ld_cg(const R4<T>* a);
-template <>
-__device__ __forceinline__ R4<float> ld_cg<float>(const R4<float>* a) {
-  const float4 v = __ldcg(reinterpret_cast<const float4*>(a));
-  return R4<float>{v.x, v.y, v.z, v.w};
-}
-template <>
-__device__ __forceinline__ R4<double> ld_cg<double>(const R4<double>* a) {
-  const double2 v0 = __ldcg(reinterpret_cast<const double2*>(a));
-  const double2 v1 = __ldcg(reinterpret_cast<const double2*>(a) + 1);
-  return R4<double>{v0.x, v0.y, v1.x, v1.y};
-}
-
+// sliced-ELL row, diagonal and all CG vectors in registers for the whole
+// solve; per iteration only the preconditioned residual u is written to
+// memory and the neighbours' values are gathered from L2.
 template <typename T, int MAXW>
-__global__ void __launch_bounds__(PCG_RR_THREADS) k_pcg_rr(Dev<T> d) {
+__global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
   __shared__ double sh[32];
   __shared__ double tot[4];
   __shared__ int shf;
-  const GridCtx g{d.ctrl, gridDim.x, d.wait_budget};
+  const GridCtx g{d.ctrl, d.gens, d.partials, gridDim.x, d.wait_budget};
+  unsigned epoch = 0;
   const int n = d.n_free;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = i < n;
-  int parity = 0;
   int col[MAXW];
   T val[MAXW];
   int width = 0;
   T dg = T(1);
-  T x[3] = {T(0), T(0), T(0)}, b[3] = {T(0), T(0), T(0)};
+  T x[3] = {T(0), T(0), T(0)};
   if (act) {
     const int sl = i >> 5, lane = i & 31;
     const int base = d.sl_ptr[sl];
@@ -440,9 +458,8 @@ __global__ void __launch_bounds__(PCG_RR_THREADS) k_pcg_rr(Dev<T> d) {
       }
     }
     dg = d.diag[i];
-    const R4<T> xi = d.X[i], bi = d.b[i];
+    const R4<T> xi = d.X[i];
     x[0] = xi.x; x[1] = xi.y; x[2] = xi.z;
-    b[0] = bi.x; b[1] = bi.y; b[2] = bi.z;
   }
   auto spmv = [&](const R4<T>* src, const T (&self)[3], T (&ax)[3]) {
     ax[0] = dg * self[0];
@@ -458,25 +475,37 @@ __global__ void __launch_bounds__(PCG_RR_THREADS) k_pcg_rr(Dev<T> d) {
       }
     }
   };
-  auto store_u = [&](const T (&u)[3]) {
+  auto store_u = [&](const T (&uu)[3]) {
     R4<T> t;
-    t.x = u[0]; t.y = u[1]; t.z = u[2]; t.w = T(0);
+    t.x = uu[0]; t.y = uu[1]; t.z = uu[2]; t.w = T(0);
     d.u[i] = t;
   };
-  T r[3], u[3], w[3], p[3], s[3];
+  T r[3], u[3], w[3], p[3], s[3], dd[3] = {T(0), T(0), T(0)};
   double a0[2] = {0.0, 0.0};
   if (act) {
-    T ax[3];
-    spmv(d.X, x, ax);
+    // r = b - A x in FP64 (X is read-only in this phase)
+    double ax[3] = {(double)dg * x[0], (double)dg * x[1], (double)dg * x[2]};
+#pragma unroll
+    for (int j = 0; j < MAXW; ++j) {
+      if (j < width) {
+        const R4<T> v = d.X[col[j]];
+        ax[0] += (double)val[j] * v.x;
+        ax[1] += (double)val[j] * v.y;
+        ax[2] += (double)val[j] * v.z;
+      }
+    }
+    const R4<double> bi = d.b[i];
+    const double bv[3] = {bi.x, bi.y, bi.z};
     for (int c = 0; c < 3; ++c) {
-      r[c] = b[c] - ax[c];
+      const double rc = bv[c] - ax[c];
+      r[c] = (T)rc;
       u[c] = r[c] / dg;
-      a0[0] += (double)b[c] * b[c];
-      a0[1] += (double)r[c] * r[c];
+      a0[0] += bv[c] * bv[c];
+      a0[1] += rc * rc;
     }
     store_u(u);
   }
-  if (!grid_reduce<2>(a0, d.partials, parity, g, sh, tot, &shf)) return;
+  if (!grid_sync_reduce<2>(g, epoch, a0, sh, tot, &shf)) return;
   const double bb = tot[0];
   double rr = tot[1];
   int it = 0;
@@ -491,20 +520,20 @@ __global__ void __launch_bounds__(PCG_RR_THREADS) k_pcg_rr(Dev<T> d) {
         s[c] = w[c];
       }
     }
-    if (!grid_reduce<2>(a1, d.partials, parity, g, sh, tot, &shf)) return;
+    if (!grid_sync_reduce<2>(g, epoch, a1, sh, tot, &shf)) return;
     double gamma = tot[0];
     double alpha = gamma / tot[1];
     for (it = 1; it <= d.max_iter; ++it) {
       const T ta = (T)alpha;
       if (act) {
         for (int c = 0; c < 3; ++c) {
-          x[c] += ta * p[c];
+          dd[c] += ta * p[c];
           r[c] -= ta * s[c];
           u[c] = r[c] / dg;
         }
         store_u(u);
       }
-      if (!grid_sync(g, &shf)) return;
+      if (!grid_sync(g, epoch, sh, tot, &shf)) return;
       double a2[3] = {0.0, 0.0, 0.0};
       if (act) {
         spmv(d.u, u, w);
@@ -514,7 +543,7 @@ __global__ void __launch_bounds__(PCG_RR_THREADS) k_pcg_rr(Dev<T> d) {
           a2[2] += (double)r[c] * r[c];
         }
       }
-      if (!grid_reduce<3>(a2, d.partials, parity, g, sh, tot, &shf)) return;
+      if (!grid_sync_reduce<3>(g, epoch, a2, sh, tot, &shf)) return;
       const double gnew = tot[0], delta = tot[1];
       rr = tot[2];
       if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
@@ -538,16 +567,11 @@ __global__ void __launch_bounds__(PCG_RR_THREADS) k_pcg_rr(Dev<T> d) {
     }
     if (act) {
       R4<T> t;
-      t.x = x[0]; t.y = x[1]; t.z = x[2]; t.w = T(0);
+      t.x = x[0] + dd[0]; t.y = x[1] + dd[1]; t.z = x[2] + dd[2]; t.w = T(0);
       d.X[i] = t;
     }
   }
-  if (i == 0) {
-    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
-    rec->pcg_iters = it;
-    d.ctrl->total_pcg += it;
-    rec->pcg_rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
-  }
+  if (i == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, bb);
 }
 
 // --------------------------------------------------------------- finalize

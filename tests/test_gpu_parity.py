@@ -262,3 +262,15 @@ def test_host_validation_rejects_bad_input_before_launch():
         casim.casim_upload_mesh(sim.h, m.rest, m.tets, m.group, free)
     assert ei.value.code == casim.CASIM_E_SINGULAR
     sim.close()
+
+
+@pytest.mark.parametrize("kernel", [1, 2])
+def test_both_pcg_kernels_match_oracle(kernel):
+    m = synth.small_finger(nx=24, ny=4, nz=4, n_ch=4, seed=31, n_iters=8)
+    sim = casim.Sim(m, pcg_kernel=kernel)
+    sim.step(m.n_iters)
+    assert sim.sync() == 0
+    ref = loop.run_mesh(m)
+    err = np.abs(sim.positions() - ref.X).max()
+    assert err <= POS_TOL * m.bbox_diag(), err
+    sim.close()
