@@ -289,6 +289,7 @@ def main():
     kernels_per_iter = 11   # 2 hash binning + 3 scan + narrow + springs + local + rhs + pcg + finalize
     gpu_launches = kernels_per_iter * n_iters * args.steps
     stats = casim.casim_get_stats(sim.h)
+    hist = casim.casim_get_history(sim.h, n_iters)
 
     # ---- end-to-end through the public API with host buffers ----
     rest = np.ascontiguousarray(m.rest)
@@ -348,7 +349,11 @@ def main():
                                                "local": ph[2] / n_iters, "rhs": ph[3] / n_iters,
                                                "pcg": ph[4] / n_iters}},
             "clocks": clocks,
-            "solver": {"k_pcg_mean_timed": stats.total_pcg_iters / max(1, stats.iterations)},
+            "solver": {"k_pcg_mean_timed": stats.total_pcg_iters / max(1, stats.iterations),
+                       "last_step": {"max_self_pairs": max(h["n_self_pairs"] for h in hist),
+                                     "max_obstacle_pairs": max(h["n_obstacle_pairs"] for h in hist),
+                                     "max_springs": max(h["n_springs"] for h in hist),
+                                     "final_springs": hist[-1]["n_springs"]}},
         }
         # ---- CPU baseline: the oracle on a bounded sample of the same workload ----
         for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):

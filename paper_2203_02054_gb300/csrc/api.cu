@@ -60,7 +60,6 @@ struct casim_sim {
   void *X = nullptr, *Tc = nullptr, *tinfo = nullptr, *P = nullptr, *cbrt_alpha = nullptr;
   void *diagL = nullptr, *bfix = nullptr, *b = nullptr, *diag = nullptr, *sl_val = nullptr;
   void *r = nullptr, *u = nullptr, *p = nullptr, *s = nullptr, *w = nullptr, *dx = nullptr, *spring_c = nullptr;
-  unsigned* gens = nullptr;
   void* pos_out = nullptr;
   void* X0 = nullptr;  // positions restored by casim_reset
   int4 *tet = nullptr, *faces = nullptr;
@@ -157,7 +156,6 @@ Dev<T> make_dev(casim_sim* sim) {
   d.w = (R4<T>*)sim->w;
   d.dx = (R4<T>*)sim->dx;
   d.partials = sim->partials;
-  d.gens = sim->gens;
   d.q_verts = sim->q_verts_d;
   d.qf_ptr = sim->qf_ptr;
   d.qf = sim->qf;
@@ -210,7 +208,6 @@ cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) 
   if (ev) cudaEventRecord(ev[4], st);
   // reset the grid-barrier words (abort, count, generation) before the PCG
   cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st);
-  cudaMemsetAsync(sim->gens, 0, sizeof(unsigned) * std::max(sim->pcg_grid, 1), st);
   cudaError_t e = launch_pcg<T>(d, sim->pcg_grid, sim->pcg_rr, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[5], st);
@@ -257,7 +254,6 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->w = sim->dalloc<R4<T>>(n_free);
   sim->dx = sim->dalloc<R4<T>>(n_free);
   sim->spring_c = sim->dalloc<R4<double>>(n_free);
-  sim->gens = sim->dalloc<unsigned>(std::max(sim->pcg_grid, 1));
   sim->partials = sim->dalloc<double>(2 * 4 * (size_t)std::max(sim->pcg_grid, 1));
   sim->q_verts_d = sim->dalloc<int>(n_q);
   sim->qf_ptr = sim->dalloc<int>(n_q + 1);

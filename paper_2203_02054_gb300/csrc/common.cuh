@@ -44,8 +44,8 @@ struct IterRec {
 struct Ctrl {
   int status;            // ST_* bits
   int abort;             // set when a grid barrier gives up
-  unsigned bar_count;    // grid barrier arrival counter
-  unsigned bar_gen;      // grid barrier generation
+  unsigned bar_count;    // grid barrier arrival counter (top bit = round parity)
+  unsigned bar_gen;      // unused (kept zero)
   long long iter;        // outer iterations completed (history index)
   long long total_pcg;   // PCG iterations summed over outer iterations
   int n_items;           // spatial-hash entries of this iteration
@@ -89,7 +89,6 @@ struct Dev {
   R4<T>* w;
   R4<T>* dx;             // PCG correction (streaming kernel)
   double* partials;      // 2 x 4 x pcg grid
-  unsigned* gens;        // per-block sync generations (pcg grid)
   // collision
   const int* q_verts;    // n_q internal vertex ids (ascending)
   const int* qf_ptr;     // n_q + 1 incident boundary faces

@@ -157,23 +157,22 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs(Dev<T> d) {
 // refinement per outer iteration).  The stopping test ||r|| <= tol ||b|| is the
 // same as for the plain system.
 //
-// Grid synchronisation without atomics: block k publishes its FP64 partial
-// sums, then (after a fence) its generation number gens[k]; warp 0 of every
-// block polls all generations, then reads and sums the partials in block
-// order (deterministic).  Partials alternate between two buffers, so a block
-// that runs ahead cannot overwrite values another block is still reading.
-// Every wait is bounded by a clock budget, after which the kernel records
-// ST_TIMEOUT, raises the abort word and returns.
+// Grid barrier: one arrival counter whose top bit flips once per round.
+// Block 0 adds 0x80000000 - (nblocks - 1) and every other block adds 1, so a
+// full round adds exactly 0x80000000: the low bits return to their value and
+// the top bit changes, which every block waits for (no reset, one atomic per
+// block).  Block partial sums for the FP64 reductions are written before the
+// arrival and read after it, in block order (deterministic); they alternate
+// between two buffers, so a block that runs ahead cannot overwrite values
+// another block is still reading.  Every wait is bounded by a clock budget,
+// after which the kernel records ST_TIMEOUT, raises the abort word and returns.
 struct GridCtx {
   Ctrl* ctrl;
-  unsigned* gens;
   double* partials;
   unsigned nblocks;
   unsigned long long budget;
 };
 
-// Publishes this block's sums bs[0..NV) (NV may be 0), waits for every block
-// of the same epoch, then leaves the grid totals in tot[0..NV).
 template <int NV, int NB>
 __device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& epoch, const double (&bs)[NB],
                                                   double* tot, int* shf) {
@@ -183,34 +182,36 @@ __device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& ep
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) buf[4 * blockIdx.x + k] = bs[k];
+    const unsigned add = blockIdx.x == 0 ? (0x80000000u - (g.nblocks - 1u)) : 1u;
     __threadfence();
-    *(volatile unsigned*)(g.gens + blockIdx.x) = epoch;
-  }
-  if (threadIdx.x < 32) {
-    const long long t0 = clock64();
+    const unsigned old = atomicAdd(&g.ctrl->bar_count, add);
+    volatile unsigned* vc = &g.ctrl->bar_count;
     int ok = 1;
-    while (true) {
-      bool ready = true;
-      for (unsigned b = threadIdx.x; b < g.nblocks; b += 32)
-        ready = ready && ((int)(*(volatile unsigned*)(g.gens + b) - epoch) >= 0);
-      if (__all_sync(0xffffffffu, ready)) break;
-      int bad = 0;
-      if (threadIdx.x == 0) {
-        if (*(volatile int*)&g.ctrl->abort) {
-          bad = 1;
-        } else if ((unsigned long long)(clock64() - t0) > g.budget) {
-          atomicExch(&g.ctrl->abort, 1);
-          atomicOr(&g.ctrl->status, ST_TIMEOUT);
-          bad = 1;
+    if (((old ^ *vc) & 0x80000000u) == 0) {
+      const long long t0 = clock64();
+      unsigned spins = 0;
+      while (((old ^ *vc) & 0x80000000u) == 0) {
+        if ((++spins & 63u) == 0) {
+          if (*(volatile int*)&g.ctrl->abort) {
+            ok = 0;
+            break;
+          }
+          if ((unsigned long long)(clock64() - t0) > g.budget) {
+            atomicExch(&g.ctrl->abort, 1);
+            atomicOr(&g.ctrl->status, ST_TIMEOUT);
+            ok = 0;
+            break;
+          }
         }
-      }
-      if (__shfl_sync(0xffffffffu, bad, 0)) {
-        ok = 0;
-        break;
       }
     }
     __threadfence();
-    if (NV > 0 && ok) {
+    *shf = ok;
+  }
+  __syncthreads();
+  if (!*shf) return false;
+  if (NV > 0) {
+    if (threadIdx.x < 32) {
       double a[NB];
 #pragma unroll
       for (int k = 0; k < NB; ++k) a[k] = 0.0;
@@ -226,10 +227,9 @@ __device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& ep
         if (threadIdx.x == 0) tot[k] = t;
       }
     }
-    if (threadIdx.x == 0) *shf = ok;
+    __syncthreads();
   }
-  __syncthreads();
-  return *shf != 0;
+  return true;
 }
 
 template <int NV>
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
   __shared__ double sh[32];
   __shared__ double tot[4];
   __shared__ int shf;
-  const GridCtx g{d.ctrl, d.gens, d.partials, gridDim.x, d.wait_budget};
+  const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget};
   unsigned epoch = 0;
   const int n = d.n_free;
   const int G = gridDim.x * blockDim.x;
@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
   __shared__ double sh[32];
   __shared__ double tot[4];
   __shared__ int shf;
-  const GridCtx g{d.ctrl, d.gens, d.partials, gridDim.x, d.wait_budget};
+  const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget};
   unsigned epoch = 0;
   const int n = d.n_free;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -51,20 +51,72 @@ def test_beam_fp64_matches_oracle():
     sim.close()
 
 
-def test_small_finger_mixed_with_self_collision_matches_oracle():
-    m = synth.small_finger(n_iters=30)
+def test_small_finger_fp64_whole_loop_with_collision_matches_oracle():
+    """FP64 path, 30 free-running iterations with self-collision: same contact
+    and spring counts every iteration and positions within 1e-9 diag."""
+    m = synth.small_finger(n_iters=30, precision=synth.PRECISION_FP64)
     sim = casim.Sim(m)
     sim.step(m.n_iters)
     assert sim.sync() == 0
-    Xg = sim.positions()
     hist = sim.history()
     ref = loop.run_mesh(m)
-    diag = m.bbox_diag()
-    err = np.abs(Xg - ref.X).max()
-    assert err <= POS_TOL * diag, (err, diag)
-    ng = [h["n_springs"] for h in hist]
-    no = [h.n_springs for h in ref.history]
-    assert max(ng) > 0 and ng[:5] == no[:5]
+    assert np.abs(sim.positions() - ref.X).max() <= 1e-9 * m.bbox_diag()
+    assert [h["n_self_pairs"] for h in hist] == [h.n_self_pairs for h in ref.history]
+    assert [h["n_springs"] for h in hist] == [h.n_springs for h in ref.history]
+    assert max(h.n_springs for h in ref.history) > 0
+    sim.close()
+
+
+def _release_margin(X, prep, st, qi, spheres, eps):
+    """Oracle-side distance of spring qi's release test from its threshold."""
+    v = prep.query[qi]
+    if st.kind[qi] == osprings.KIND_OBSTACLE:
+        c, r = spheres[st.face[qi], :3], spheres[st.face[qi], 3]
+        return float(np.linalg.norm(X[v] - c) - r - eps)
+    f = prep.faces[st.face[qi]]
+    q0, q1, q2 = X[f[0]], X[f[1]], X[f[2]]
+    b1, b2 = st.bary[qi]
+    bp = (1 - b1 - b2) * q0 + b1 * q1 + b2 * q2
+    n = np.cross(q1 - q0, q2 - q0)
+    n = n / np.linalg.norm(n)
+    return float(np.dot(n, X[v] - bp) - eps)
+
+
+def test_small_finger_mixed_replay_every_iteration():
+    """MIXED path along the oracle's 30-iteration trajectory: from each oracle
+    state (rounded to FP32) one GPU iteration must give the same pair set bit
+    for bit, the same spring decisions (a decision may differ only where the
+    oracle's release test is within 1e-5 cm of its threshold) and positions
+    within 1e-5 of the bounding-box diagonal."""
+    m = synth.small_finger(n_iters=30)
+    prep = loop.prepare(m.rest, m.tets, m.group, m.fixed)
+    sim = casim.Sim(m)
+    X = m.rest.copy()
+    st = osprings.SpringState.empty(prep.query.shape[0])
+    compared = 0
+    for i in range(m.n_iters):
+        Xf = X.astype(np.float32).astype(np.float64)
+        sim.set_positions(Xf)
+        sim.set_springs(prep.query.astype(np.int32), st.active, st.kind.astype(np.int32), st.face.astype(np.int32),
+                        st.bary, st.target)
+        sim.step(1)
+        assert sim.sync() == 0
+        Xn, stn, rec, ps, po = loop.iterate(prep, Xf, st, m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps,
+                                            m.collision)
+        assert np.array_equal(sim.contacts()[0], ps), i
+        sp = sim.springs()
+        diff = np.nonzero(sp["active"] != stn.active)[0]
+        for qi in diff:
+            assert st.active[qi], (i, qi)          # only a release decision can tie
+            assert abs(_release_margin(Xf, prep, st, qi, m.spheres, m.eps)) < 1e-5, (i, qi)
+        if diff.size == 0:
+            same = stn.active
+            assert np.allclose(sp["target"][same], stn.target[same], atol=1e-9)
+            err = np.abs(sim.positions() - Xn).max()
+            assert err <= POS_TOL * m.bbox_diag(), (i, err)
+            compared += 1
+        X, st = Xn, stn
+    assert compared >= m.n_iters - 2
     sim.close()
 
 
