@@ -86,7 +86,14 @@ typedef struct {
   int32_t pcg_kernel;       /* 0 auto; 1 streaming PCG (vectors in HBM, any size);
                                2 register-resident PCG (one row per thread; used by
                                auto when every row fits, else CASIM_E_INVALID)      */
+  int32_t debug_flags;      /* test-only fault injection, 0 in normal use:
+                               CASIM_DEBUG_BARRIER_NEVER_COMPLETES makes the PCG
+                               grid barrier wait for one block more than it has,
+                               so every wait runs out of wait_budget_cycles and
+                               the step ends with CASIM_E_TIMEOUT               */
 } casim_params;
+
+#define CASIM_DEBUG_BARRIER_NEVER_COMPLETES 1
 
 /* Per-iteration record (Eq. 8 energy at X_i with the targets of iteration i). */
 typedef struct {

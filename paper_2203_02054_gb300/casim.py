@@ -33,6 +33,7 @@ CASIM_W_PCG_MAXIT = 1
 
 CASIM_FP64 = 0
 CASIM_MIXED = 1
+CASIM_DEBUG_BARRIER_NEVER_COMPLETES = 1
 
 EXPORTS = [
     "casim_default_params", "casim_create", "casim_upload_mesh", "casim_set_actuation",
@@ -58,6 +59,7 @@ class casim_params(ctypes.Structure):
         ("max_pairs_per_vertex", ctypes.c_int32),
         ("wait_budget_cycles", ctypes.c_uint64),
         ("pcg_kernel", ctypes.c_int32),
+        ("debug_flags", ctypes.c_int32),
     ]
 
 
@@ -314,7 +316,7 @@ class Sim:
 
     def __init__(self, mesh, precision=None, collision=None, stream: int = 0, stats: int = 1,
                  pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0,
-                 pcg_kernel=0):
+                 pcg_kernel=0, debug_flags=0):
         load_library()
         p = casim_default_params()
         p.precision = mesh.precision if precision is None else precision
@@ -332,6 +334,7 @@ class Sim:
         p.max_pairs_per_vertex = max_pairs
         p.wait_budget_cycles = wait_budget_cycles
         p.pcg_kernel = pcg_kernel
+        p.debug_flags = debug_flags
         self.params = p
         self.mesh = mesh
         self.h = casim_create(p, stream)

@@ -182,6 +182,7 @@ Dev<T> make_dev(casim_sim* sim) {
   d.max_iter = sim->params.pcg_max_iter;
   d.collision = sim->params.collision;
   d.stats = sim->params.stats;
+  d.bar_extra = (sim->params.debug_flags & CASIM_DEBUG_BARRIER_NEVER_COMPLETES) ? 1u : 0u;
   d.wait_budget = sim->params.wait_budget_cycles ? sim->params.wait_budget_cycles : 4000000000ull;
   d.ctrl = sim->ctrl;
   d.hist = sim->hist;
@@ -522,6 +523,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (!(p.cell_size > 0.0) || !std::isfinite(p.cell_size)) why = "cell_size";
   else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
   else if (p.pcg_kernel < 0 || p.pcg_kernel > 2) why = "pcg_kernel";
+  else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
       if (!(p.w_knots[2 * i + 2] > p.w_knots[2 * i])) why = "w_knots must be strictly ascending";

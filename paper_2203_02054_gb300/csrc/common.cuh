@@ -110,6 +110,7 @@ struct Dev {
   // parameters
   double k_spring, eps, cell, inv_cell, tol2;
   int max_iter, collision, stats;
+  unsigned bar_extra;    // 0; 1 = test-only: the barrier expects one more block
   unsigned long long wait_budget;
   // control and statistics
   Ctrl* ctrl;

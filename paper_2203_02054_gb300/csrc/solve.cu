@@ -171,6 +171,7 @@ struct GridCtx {
   double* partials;
   unsigned nblocks;
   unsigned long long budget;
+  unsigned extra;  // test-only: arrivals expected beyond the grid (never come)
 };
 
 template <int NV, int NB>
@@ -182,7 +183,7 @@ __device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& ep
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) buf[4 * blockIdx.x + k] = bs[k];
-    const unsigned add = blockIdx.x == 0 ? (0x80000000u - (g.nblocks - 1u)) : 1u;
+    const unsigned add = blockIdx.x == 0 ? (0x80000000u - (g.nblocks - 1u + g.extra)) : 1u;
     __threadfence();
     const unsigned old = atomicAdd(&g.ctrl->bar_count, add);
     volatile unsigned* vc = &g.ctrl->bar_count;
@@ -235,9 +236,28 @@ __device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& ep
 template <int NV>
 __device__ __forceinline__ bool grid_sync_reduce(const GridCtx& g, unsigned& epoch, const double (&v)[NV],
                                                  double* sh, double* tot, int* shf) {
+  // block sums of all NV values with one shared-memory round (sh >= 32*NV)
+  double t[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    t[k] = v[k];
+    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = t[k];
+  __syncthreads();
   double bs[NV];
 #pragma unroll
-  for (int k = 0; k < NV; ++k) bs[k] = block_sum(v[k], sh);
+  for (int k = 0; k < NV; ++k) bs[k] = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) bs[k] += sh[k * 32 + i];
+  }
   return grid_publish_wait<NV, NV>(g, epoch, bs, tot, shf);
 }
 
@@ -291,10 +311,10 @@ __device__ __forceinline__ void spmv_row(const Dev<T>& d, int i, const R4<T>* __
 
 template <typename T>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
-  __shared__ double sh[32];
+  __shared__ double sh[96];
   __shared__ double tot[4];
   __shared__ int shf;
-  const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget};
+  const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget, d.bar_extra};
   unsigned epoch = 0;
   const int n = d.n_free;
   const int G = gridDim.x * blockDim.x;
@@ -430,10 +450,10 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
 // memory and the neighbours' values are gathered from L2.
 template <typename T, int MAXW>
 __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
-  __shared__ double sh[32];
+  __shared__ double sh[96];
   __shared__ double tot[4];
   __shared__ int shf;
-  const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget};
+  const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget, d.bar_extra};
   unsigned epoch = 0;
   const int n = d.n_free;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;

@@ -283,9 +283,10 @@ def test_pcg_cap_warning_and_timeout_status():
     sim.step(1)
     assert sim.sync() == casim.CASIM_W_PCG_MAXIT
     sim.close()
-    # a grid-barrier wait budget of a few cycles must end the PCG with a
-    # timeout status; the context stays usable afterwards
-    sim = casim.Sim(m, wait_budget_cycles=4)
+    # a barrier that waits for a block that does not exist must give up after
+    # its clock budget (~10 ms here) with a timeout status; the context stays
+    # usable afterwards
+    sim = casim.Sim(m, wait_budget_cycles=20_000_000, debug_flags=casim.CASIM_DEBUG_BARRIER_NEVER_COMPLETES)
     sim.step(1)
     with pytest.raises(casim.CasimError) as ei:
         sim.sync()
