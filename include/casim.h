@@ -218,6 +218,44 @@ int casim_get_sizes(casim_sim* sim, int32_t* n_verts, int32_t* n_tets, int32_t* 
    measured with CUDA events when params.stats >= 2; zero otherwise. */
 int casim_get_phase_times(casim_sim* sim, double* ms_out5);
 
+/* Allocation-free contact check (no counterpart in the paper; a service for
+   callers that cannot allocate device memory while they run, such as real-time
+   controllers that must not allocate inside a control loop, or host programs
+   whose own allocator owns the GPU memory pool and forbids outside
+   cudaMalloc calls).
+
+   Computes the self-collision pairs of Eq. 3 exactly as a casim_step
+   iteration does (spatial hash + exact strict point-in-tet test), for
+   positions given by the caller, without allocating: all intermediate data
+   lives in one static device array of about 6.2 MiB that every GPU which
+   loads the library holds until the process exits.
+     n_verts, dev_xyz   device, n_verts*3 floats, vertex positions
+     n_tets, dev_tets   device, n_tets*4 int32 vertex ids (16-byte aligned),
+                        positively oriented
+     n_query, dev_query device, n_query int32 vertex ids to test
+     cell_size          hash cell edge (length units), > 0
+     max_pairs          pairs kept per query vertex, 1..16
+     dev_pair_count     device, n_query int32: number of tets strictly
+                        containing the vertex (capped at max_pairs)
+     dev_pair_tet       device, n_query*max_pairs int32: their tet ids,
+                        ascending, in the first dev_pair_count[q] slots
+     cuda_stream        cudaStream_t (NULL: default stream)
+   Limits: n_verts <= 32768, n_tets <= 65536, n_query <= 16384; larger sizes
+   are rejected with CASIM_E_INVALID before any GPU work.  Other errors:
+   CASIM_E_INVALID (null or misaligned pointer, id out of range, bad
+   cell_size / max_pairs), CASIM_E_OVERFLOW (more pairs than max_pairs for
+   some vertex, or more hash entries than the scratch holds),
+   CASIM_E_NONFINITE, CASIM_E_CUDA.
+   Calls no cudaMalloc or cudaFree.  The first call on a device looks up the
+   static array's device address (cudaGetSymbolAddress), so make that first
+   call outside any stream capture.  The call waits for its stream before it
+   returns.  Every call reuses the same array, which keeps the last call's
+   contents (the call clears what must start at zero): calls whose GPU work
+   overlaps, from several host threads or streams, race with each other. */
+int casim_contacts_noalloc(int32_t n_verts, const float* dev_xyz, int32_t n_tets, const int32_t* dev_tets,
+                           int32_t n_query, const int32_t* dev_query, double cell_size, int32_t max_pairs,
+                           int32_t* dev_pair_count, int32_t* dev_pair_tet, void* cuda_stream);
+
 void casim_destroy(casim_sim* sim);
 
 /* Message of the last failure on this handle (or of the last casim_create

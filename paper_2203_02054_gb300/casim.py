@@ -40,7 +40,8 @@ EXPORTS = [
     "casim_set_spheres", "casim_set_positions", "casim_reset", "casim_step", "casim_sync", "casim_get_positions",
     "casim_get_contacts", "casim_get_springs", "casim_set_springs", "casim_get_targets",
     "casim_get_history", "casim_get_stats", "casim_save_state", "casim_load_state",
-    "casim_get_sizes", "casim_get_phase_times", "casim_destroy", "casim_last_error",
+    "casim_get_sizes", "casim_get_phase_times", "casim_contacts_noalloc", "casim_destroy",
+    "casim_last_error",
 ]
 
 
@@ -127,6 +128,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.casim_load_state.argtypes = [_P, _P, ctypes.c_size_t]
     L.casim_get_sizes.argtypes = [_P, _I32, _I32, _I32, _I32, _I32]
     L.casim_get_phase_times.argtypes = [_P, _D]
+    L.casim_contacts_noalloc.argtypes = [ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P,
+                                         ctypes.c_double, ctypes.c_int32, _P, _P, _P]
     L.casim_destroy.argtypes = [_P]
     L.casim_destroy.restype = None
     L.casim_last_error.argtypes = [_P]
@@ -300,6 +303,16 @@ def casim_get_phase_times(sim) -> np.ndarray:
     out = np.zeros(5, np.float64)
     _check(load_library().casim_get_phase_times(sim, _ptr(out, ctypes.c_double)), sim)
     return out
+
+
+def casim_contacts_noalloc(n_verts: int, dev_xyz: int, n_tets: int, dev_tets: int, n_query: int, dev_query: int,
+                           cell_size: float, max_pairs: int, dev_pair_count: int, dev_pair_tet: int,
+                           stream: int = 0) -> int:
+    """Allocation-free contact check on caller-owned device buffers (pointers
+    as integers, e.g. torch ``data_ptr()``); returns the C status code."""
+    return load_library().casim_contacts_noalloc(
+        int(n_verts), _P(dev_xyz), int(n_tets), _P(dev_tets), int(n_query), _P(dev_query), float(cell_size),
+        int(max_pairs), _P(dev_pair_count), _P(dev_pair_tet), _P(stream or None))
 
 
 def casim_destroy(sim):
