@@ -83,9 +83,12 @@ typedef struct {
   uint64_t wait_budget_cycles;  /* SM clock cycles a grid-barrier wait may spin
                                    before the kernel gives up with CASIM_E_TIMEOUT;
                                    0 selects the default (about 2 s)                 */
-  int32_t pcg_kernel;       /* 0 auto; 1 streaming PCG (vectors in HBM, any size);
-                               2 register-resident PCG (one row per thread; used by
-                               auto when every row fits, else CASIM_E_INVALID)      */
+  int32_t pcg_kernel;       /* PCG kernel: 0 auto (3 if it fits, else 2 if it fits,
+                               else 1); 1 streaming (whole grid, vectors in memory,
+                               any size); 2 register-resident (whole grid, one row
+                               per thread); 3 cluster (one 16-CTA cluster per robot,
+                               vectors in shared memory).  A forced kernel that
+                               does not fit gives CASIM_E_INVALID at upload        */
   int32_t debug_flags;      /* test-only fault injection, 0 in normal use:
                                CASIM_DEBUG_BARRIER_NEVER_COMPLETES makes the PCG
                                grid barrier wait for one block more than it has,

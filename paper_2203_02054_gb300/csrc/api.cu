@@ -76,6 +76,10 @@ struct casim_sim {
   unsigned H_t = 0, H_f = 0;
   int cap_items = 0, n_slices = 0, pcg_grid = 1, n_e_local = 0, n_e_spring = 0;
   bool pcg_rr = false;  // register-resident PCG (one row per thread)
+  bool pcg_cl = false;  // cluster PCG (one cluster per robot, work queue)
+  int pcg_clusters = 0, cl_rows_cap = 0, n_robots = 1;
+  int* robot_row = nullptr;
+  std::vector<int> robot_row_h;
   // graph of one iteration
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
@@ -183,6 +187,9 @@ Dev<T> make_dev(casim_sim* sim) {
   d.collision = sim->params.collision;
   d.stats = sim->params.stats;
   d.bar_extra = (sim->params.debug_flags & CASIM_DEBUG_BARRIER_NEVER_COMPLETES) ? 1u : 0u;
+  d.n_robots = sim->n_robots;
+  d.robot_row = sim->robot_row;
+  d.cl_rows_cap = sim->cl_rows_cap;
   d.wait_budget = sim->params.wait_budget_cycles ? sim->params.wait_budget_cycles : 4000000000ull;
   d.ctrl = sim->ctrl;
   d.hist = sim->hist;
@@ -209,7 +216,8 @@ cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) 
   if (ev) cudaEventRecord(ev[4], st);
   // reset the grid-barrier words (abort, count, generation) before the PCG
   cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st);
-  cudaError_t e = launch_pcg<T>(d, sim->pcg_grid, sim->pcg_rr, st);
+  cudaError_t e = sim->pcg_cl ? launch_pcg_cluster<T>(d, sim->pcg_clusters, st)
+                              : launch_pcg<T>(d, sim->pcg_grid, sim->pcg_rr, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[5], st);
   launch_finalize<T>(d, st);
@@ -277,6 +285,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->sp.bary = sim->dalloc<double>(2 * (size_t)n_q);
   sim->sp.target = sim->dalloc<double>(3 * (size_t)n_q);
   sim->int_of_user_d = sim->dalloc<int>(n_v);
+  sim->robot_row = sim->dalloc<int>(sim->robot_row_h.size());
   sim->ctrl = sim->dalloc<Ctrl>(1);
   sim->hist = sim->dalloc<IterRec>(sim->hist_cap);
   sim->n_e_local = local_blocks(n_t);
@@ -325,6 +334,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   if (!qf.empty()) CK(cudaMemcpyAsync(sim->qf, qf.data(), sizeof(int) * qf.size(), cudaMemcpyHostToDevice, st));
   if (n_f) CK(cudaMemcpyAsync(sim->faces, fh.data(), sizeof(int4) * n_f, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->int_of_user_d, sim->int_of_user.data(), sizeof(int) * n_v, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(sim->robot_row, sim->robot_row_h.data(), sizeof(int) * sim->robot_row_h.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(sim->spring_c, 0, sizeof(R4<double>) * std::max(n_free, 1), st));
   CK(cudaMemsetAsync(sim->sp.active, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->sp.kind, 0, sizeof(int) * std::max(n_q, 1), st));
@@ -522,7 +532,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.n_w_knots < 0 || (p.n_w_knots > 0 && !p.w_knots) || p.n_w_knots > 64) why = "w_knots";
   else if (!(p.cell_size > 0.0) || !std::isfinite(p.cell_size)) why = "cell_size";
   else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
-  else if (p.pcg_kernel < 0 || p.pcg_kernel > 2) why = "pcg_kernel";
+  else if (p.pcg_kernel < 0 || p.pcg_kernel > 3) why = "pcg_kernel";
   else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
@@ -813,10 +823,25 @@ int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, i
   const bool fp64 = sim->params.precision == CASIM_FP64;
   const int rr_rows = fp64 ? pcg_rr_max_rows<double>() : pcg_rr_max_rows<float>();
   const bool rr_fits = max_width <= PCG_RR_MAXW && n_free <= rr_rows;
-  if (sim->params.pcg_kernel == 2 && !rr_fits)
-    return sim->fail(CASIM_E_INVALID, "register-resident PCG: rows do not fit (" + std::to_string(n_free) + " rows, width " +
-                                          std::to_string(max_width) + ")");
-  sim->pcg_rr = rr_fits && sim->params.pcg_kernel != 1;
+  // cluster PCG: every robot's rows must fit the cluster's shared memory
+  sim->n_robots = 1;
+  sim->robot_row_h = {0, n_free};
+  int max_robot_rows = 0;
+  for (int r = 0; r < sim->n_robots; ++r)
+    max_robot_rows = std::max(max_robot_rows, sim->robot_row_h[r + 1] - sim->robot_row_h[r]);
+  const int cap = fp64 ? pcg_cluster_rows_cap<double>() : pcg_cluster_rows_cap<float>();
+  const int need = (((max_robot_rows + PCG_CL_SIZE - 1) / PCG_CL_SIZE) + 31) & ~31;
+  int max_clusters = 0;
+  if (need <= cap) max_clusters = fp64 ? pcg_cluster_max_clusters<double>(cap) : pcg_cluster_max_clusters<float>(cap);
+  const bool cl_fits = need <= cap && max_clusters > 0;
+  const int kern = sim->params.pcg_kernel;
+  if ((kern == 2 && !rr_fits) || (kern == 3 && !cl_fits))
+    return sim->fail(CASIM_E_INVALID, "requested PCG kernel does not fit this mesh (" + std::to_string(n_free) +
+                                          " rows, width " + std::to_string(max_width) + ")");
+  sim->pcg_cl = (kern == 3) || (kern == 0 && cl_fits);
+  sim->pcg_rr = !sim->pcg_cl && ((kern == 2) || (kern == 0 && rr_fits));
+  sim->cl_rows_cap = cap;
+  sim->pcg_clusters = std::max(1, std::min(max_clusters, sim->n_robots));
   if (sim->pcg_rr) {
     sim->pcg_grid = std::max(1, (n_free + PCG_RR_THREADS - 1) / PCG_RR_THREADS);
   } else {

@@ -45,7 +45,7 @@ struct Ctrl {
   int status;            // ST_* bits
   int abort;             // set when a grid barrier gives up
   unsigned bar_count;    // grid barrier arrival counter (top bit = round parity)
-  unsigned bar_gen;      // unused (kept zero)
+  unsigned queue;        // next robot for the cluster PCG work queue
   long long iter;        // outer iterations completed (history index)
   long long total_pcg;   // PCG iterations summed over outer iterations
   int n_items;           // spatial-hash entries of this iteration
@@ -110,6 +110,9 @@ struct Dev {
   // parameters
   double k_spring, eps, cell, inv_cell, tol2;
   int max_iter, collision, stats;
+  int n_robots;          // independent systems (robots) in the mesh
+  const int* robot_row;  // n_robots + 1: first free row of each robot
+  int cl_rows_cap;       // rows per CTA the cluster PCG's shared memory holds
   unsigned bar_extra;    // 0; 1 = test-only: the barrier expects one more block
   unsigned long long wait_budget;
   // control and statistics

@@ -17,6 +17,8 @@ static constexpr int RHS_THREADS = 256;
 static constexpr int PCG_THREADS = 512;
 static constexpr int PCG_RR_THREADS = 256;
 static constexpr int PCG_RR_MAXW = 16;   // widest sliced-ELL row kept in registers
+static constexpr int PCG_CL_THREADS = 1024;
+static constexpr int PCG_CL_SIZE = 16;   // CTAs per cluster (non-portable size)
 
 template <typename T>
 void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t st);
@@ -30,6 +32,12 @@ template <typename T>
 cudaError_t launch_pcg(const Dev<T>& d, int grid, bool rr, cudaStream_t st);
 template <typename T>
 int pcg_rr_max_rows();
+template <typename T>
+int pcg_cluster_rows_cap();
+template <typename T>
+int pcg_cluster_max_clusters(int rows_cap);
+template <typename T>
+cudaError_t launch_pcg_cluster(const Dev<T>& d, int n_clusters, cudaStream_t st);
 template <typename T>
 void launch_finalize(const Dev<T>& d, cudaStream_t st);
 template <typename T>

@@ -594,6 +594,203 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
   if (i == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, bb);
 }
 
+// Cluster variant: one thread-block cluster of PCG_CL_SIZE CTAs solves one
+// robot's system at a time, taking robots from a work queue (one persistent
+// launch serves any number of independent robots).  Each CTA owns a
+// contiguous range of the robot's rows and keeps all of its CG vectors in
+// shared memory; the preconditioned residual u of neighbouring rows is read
+// from the owning CTA's shared memory (distributed shared memory), and the
+// FP64 reductions exchange one partial per CTA through distributed shared
+// memory.  All synchronisation is the cluster's hardware barrier.
+namespace cgx = cooperative_groups;
+
+template <typename T>
+__global__ void __launch_bounds__(PCG_CL_THREADS, 1) k_pcg_cluster(Dev<T> d) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sh[96];
+  __shared__ double part[4];
+  __shared__ double tot[4];
+  __shared__ int s_robot;
+  cgx::cluster_group cl = cgx::this_cluster();
+  const int crank = (int)cl.block_rank();
+  const int csz = (int)cl.num_blocks();
+  const int cap = d.cl_rows_cap;
+  R4<T>* su = reinterpret_cast<R4<T>*>(smem);
+  T* sr = reinterpret_cast<T*>(su + cap);
+  T* sp = sr + 3 * cap;
+  T* ss = sp + 3 * cap;
+  T* sw = ss + 3 * cap;
+  T* sd = sw + 3 * cap;
+  T* sg = sd + 3 * cap;  // diagonal
+
+  // cluster-wide FP64 sums of NV values (deterministic: ranks in order)
+  auto cluster_reduce = [&](const double* v, int nv) {
+    for (int k = 0; k < nv; ++k) {
+      const double b = block_sum(v[k], sh);
+      if (threadIdx.x == 0) part[k] = b;
+    }
+    cl.sync();
+    if (threadIdx.x == 0) {
+      double a[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int rk = 0; rk < csz; ++rk) {
+        const double* rp = cl.map_shared_rank(part, rk);
+        for (int k = 0; k < nv; ++k) a[k] += rp[k];
+      }
+      for (int k = 0; k < nv; ++k) tot[k] = a[k];
+    }
+    __syncthreads();
+  };
+
+  while (true) {
+    if (crank == 0 && threadIdx.x == 0) s_robot = (int)atomicAdd(&d.ctrl->queue, 1u);
+    cl.sync();
+    const int robot = *cl.map_shared_rank(&s_robot, 0);
+    cl.sync();  // every rank has read rank 0's word before any rank moves on or exits
+    if (robot >= d.n_robots) break;
+    const int row0 = d.robot_row[robot];
+    const int n = d.robot_row[robot + 1] - row0;
+    const int rpc = (((n + csz - 1) / csz) + 31) & ~31;  // rows per CTA (host checks rpc <= cap)
+    const int my0 = crank * rpc;
+    const int my1 = min(n, my0 + rpc);
+    const int nmine = my1 > my0 ? my1 - my0 : 0;
+    // SpMV of local rows: diag * own + sum of off-diagonals over neighbours' u
+    auto spmv_u = [&](int j, T& ax, T& ay, T& az) {
+      const int i = row0 + my0 + j;
+      const T dg = sg[j];
+      const R4<T> self = su[j];
+      ax = dg * self.x;
+      ay = dg * self.y;
+      az = dg * self.z;
+      const int sl = i >> 5, lane = i & 31;
+      const int k1 = d.sl_ptr[sl + 1];
+      for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
+        const T a = d.sl_val[k];
+        if (a == T(0)) continue;
+        const int c = d.sl_col[k] - row0;
+        const int owner = c / rpc;
+        const R4<T>* ru = cl.map_shared_rank(su, owner);
+        const R4<T> v = ru[c - owner * rpc];
+        ax += a * v.x;
+        ay += a * v.y;
+        az += a * v.z;
+      }
+    };
+    // r = b - A x in FP64, u = r / diag, correction d = 0
+    double a0[2] = {0.0, 0.0};
+    for (int j = threadIdx.x; j < nmine; j += blockDim.x) {
+      const int i = row0 + my0 + j;
+      const T dg = d.diag[i];
+      sg[j] = dg;
+      const R4<T> xi = d.X[i];
+      double ax = (double)dg * xi.x, ay = (double)dg * xi.y, az = (double)dg * xi.z;
+      const int sl = i >> 5, lane = i & 31;
+      const int k1 = d.sl_ptr[sl + 1];
+      for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
+        const double a = (double)d.sl_val[k];
+        const R4<T> xc = d.X[d.sl_col[k]];
+        ax += a * xc.x;
+        ay += a * xc.y;
+        az += a * xc.z;
+      }
+      const R4<double> bi = d.b[i];
+      const double rx = bi.x - ax, ry = bi.y - ay, rz = bi.z - az;
+      sr[3 * j] = (T)rx;
+      sr[3 * j + 1] = (T)ry;
+      sr[3 * j + 2] = (T)rz;
+      su[j] = R4<T>{sr[3 * j] / dg, sr[3 * j + 1] / dg, sr[3 * j + 2] / dg, T(0)};
+      sd[3 * j] = sd[3 * j + 1] = sd[3 * j + 2] = T(0);
+      a0[0] += bi.x * bi.x + bi.y * bi.y + bi.z * bi.z;
+      a0[1] += rx * rx + ry * ry + rz * rz;
+    }
+    cluster_reduce(a0, 2);  // also publishes u
+    const double bb = tot[0];
+    double rr = tot[1];
+    int it = 0;
+    if (bb > 0.0 && rr > d.tol2 * bb) {
+      double a1[2] = {0.0, 0.0};
+      for (int j = threadIdx.x; j < nmine; j += blockDim.x) {
+        T ax, ay, az;
+        spmv_u(j, ax, ay, az);
+        const R4<T> uj = su[j];
+        sw[3 * j] = ax; sw[3 * j + 1] = ay; sw[3 * j + 2] = az;
+        sp[3 * j] = uj.x; sp[3 * j + 1] = uj.y; sp[3 * j + 2] = uj.z;
+        ss[3 * j] = ax; ss[3 * j + 1] = ay; ss[3 * j + 2] = az;
+        a1[0] += (double)sr[3 * j] * uj.x + (double)sr[3 * j + 1] * uj.y + (double)sr[3 * j + 2] * uj.z;
+        a1[1] += (double)ax * uj.x + (double)ay * uj.y + (double)az * uj.z;
+      }
+      cluster_reduce(a1, 2);
+      double gamma = tot[0];
+      double alpha = gamma / tot[1];
+      for (it = 1; it <= d.max_iter; ++it) {
+        const T ta = (T)alpha;
+        for (int j = threadIdx.x; j < nmine; j += blockDim.x) {
+          const T dg = sg[j];
+          T un[3];
+          for (int c = 0; c < 3; ++c) {
+            sd[3 * j + c] += ta * sp[3 * j + c];
+            sr[3 * j + c] -= ta * ss[3 * j + c];
+            un[c] = sr[3 * j + c] / dg;
+          }
+          su[j] = R4<T>{un[0], un[1], un[2], T(0)};
+        }
+        cl.sync();  // u published to the cluster
+        double a2[3] = {0.0, 0.0, 0.0};
+        for (int j = threadIdx.x; j < nmine; j += blockDim.x) {
+          T ax, ay, az;
+          spmv_u(j, ax, ay, az);
+          const R4<T> uj = su[j];
+          sw[3 * j] = ax; sw[3 * j + 1] = ay; sw[3 * j + 2] = az;
+          const T r0 = sr[3 * j], r1 = sr[3 * j + 1], r2 = sr[3 * j + 2];
+          a2[0] += (double)r0 * uj.x + (double)r1 * uj.y + (double)r2 * uj.z;
+          a2[1] += (double)ax * uj.x + (double)ay * uj.y + (double)az * uj.z;
+          a2[2] += (double)r0 * r0 + (double)r1 * r1 + (double)r2 * r2;
+        }
+        cluster_reduce(a2, 3);
+        const double gnew = tot[0], delta = tot[1];
+        rr = tot[2];
+        if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
+          if (crank == 0 && threadIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
+          break;
+        }
+        if (rr <= d.tol2 * bb) break;
+        const double beta = gnew / gamma;
+        alpha = gnew / (delta - beta * gnew / alpha);
+        gamma = gnew;
+        const T tb = (T)beta;
+        for (int j = threadIdx.x; j < nmine; j += blockDim.x) {
+          const R4<T> uj = su[j];
+          const T uu[3] = {uj.x, uj.y, uj.z};
+          for (int c = 0; c < 3; ++c) {
+            sp[3 * j + c] = uu[c] + tb * sp[3 * j + c];
+            ss[3 * j + c] = sw[3 * j + c] + tb * ss[3 * j + c];
+          }
+        }
+      }
+      if (it > d.max_iter) {
+        it = d.max_iter;
+        if (crank == 0 && threadIdx.x == 0) set_status(d.ctrl, ST_PCG_MAXIT);
+      }
+      for (int j = threadIdx.x; j < nmine; j += blockDim.x) {
+        const int i = row0 + my0 + j;
+        R4<T> xi = d.X[i];
+        xi.x += sd[3 * j];
+        xi.y += sd[3 * j + 1];
+        xi.z += sd[3 * j + 2];
+        d.X[i] = xi;
+      }
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
+      atomicMax(&rec->pcg_iters, it);
+      atomicAdd(reinterpret_cast<unsigned long long*>(&d.ctrl->total_pcg), (unsigned long long)it);
+      const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+      atomicMax(reinterpret_cast<unsigned long long*>(&rec->pcg_rel_residual),
+                (unsigned long long)__double_as_longlong(rel));
+    }
+    cl.sync();  // shared memory is reused by the next robot
+  }
+}
+
 // --------------------------------------------------------------- finalize
 template <typename T>
 __global__ void k_finalize(Dev<T> d) {
@@ -694,6 +891,65 @@ void launch_gather_positions(const Dev<T>& d, const int* int_of_user, int n_user
   k_gather_positions<T><<<(n_user + 255) / 256, 256, 0, st>>>(d.X, int_of_user, n_user, out);
 }
 
+template <typename T>
+int pcg_cluster_rows_cap() {
+  // per row: u (R4) + r, p, s, w, d, diag (3+3+3+3+3+1 values)
+  const size_t per_row = sizeof(R4<T>) + 16 * sizeof(T);
+  const size_t avail = 220 * 1024;
+  return (int)((avail / per_row) & ~size_t(31));
+}
+
+template <typename T>
+int pcg_cluster_max_clusters(int rows_cap) {
+  const size_t smem = (sizeof(R4<T>) + 16 * sizeof(T)) * (size_t)rows_cap;
+  if (cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  if (cudaFuncSetAttribute(k_pcg_cluster<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(PCG_CL_SIZE);
+  cfg.blockDim = dim3(PCG_CL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = PCG_CL_SIZE;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, k_pcg_cluster<T>, &cfg) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+
+template <typename T>
+cudaError_t launch_pcg_cluster(const Dev<T>& d, int n_clusters, cudaStream_t st) {
+  if (d.n_free == 0) return cudaSuccess;
+  const size_t smem = (sizeof(R4<T>) + 16 * sizeof(T)) * (size_t)d.cl_rows_cap;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(PCG_CL_SIZE * n_clusters);
+  cfg.blockDim = dim3(PCG_CL_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = PCG_CL_SIZE;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, d);
+}
+
+template int pcg_cluster_rows_cap<float>();
+template int pcg_cluster_rows_cap<double>();
+template int pcg_cluster_max_clusters<float>(int);
+template int pcg_cluster_max_clusters<double>(int);
+template cudaError_t launch_pcg_cluster<float>(const Dev<float>&, int, cudaStream_t);
+template cudaError_t launch_pcg_cluster<double>(const Dev<double>&, int, cudaStream_t);
 template void launch_local<float>(const Dev<float>&, cudaStream_t);
 template void launch_local<double>(const Dev<double>&, cudaStream_t);
 template void launch_rhs<float>(const Dev<float>&, cudaStream_t);
