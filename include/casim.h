@@ -91,7 +91,9 @@ typedef struct {
                                does not fit gives CASIM_E_INVALID at upload        */
   int32_t debug_flags;      /* test-only fault injection, 0 in normal use:
                                CASIM_DEBUG_BARRIER_NEVER_COMPLETES makes the PCG
-                               grid barrier wait for one block more than it has,
+                               grid barrier (kernels 1 and 2; the cluster kernel
+                               uses the hardware cluster barrier) wait for one
+                               block more than it has,
                                so every wait runs out of wait_budget_cycles and
                                the step ends with CASIM_E_TIMEOUT               */
 } casim_params;
@@ -136,6 +138,29 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
    fixed vertex), CASIM_E_CUDA. */
 int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, int32_t n_tets,
                       const int32_t* tets, const int32_t* tet_group, const uint8_t* fixed);
+
+/* One robot of a batch (same conventions as casim_upload_mesh). */
+typedef struct {
+  int32_t n_verts;
+  const double* rest_xyz;    /* n_verts*3 */
+  int32_t n_tets;
+  const int32_t* tets;       /* n_tets*4, ids local to this robot */
+  const int32_t* tet_group;  /* n_tets: -1 body, g >= 0 this robot's chamber g */
+  const uint8_t* fixed;      /* n_verts */
+} casim_mesh_desc;
+
+/* Uploads n_robots independent robots (no counterpart in the paper, which
+   simulates one robot; a batching service).  They are simulated together:
+   one collision check over all robots that never pairs a vertex with another
+   robot's tet, one local step over all tets, and one PCG solve per robot
+   (independent stopping tests), all in the same launches.  Afterwards the
+   robots behave as one mesh whose vertices, tets and chamber groups are the
+   robots' own, concatenated in robot order (robot r's chamber g becomes group
+   g + the number of groups of robots 0..r-1), so casim_set_actuation takes
+   the concatenated ratios and casim_get_positions the concatenated vertices.
+   Obstacle spheres act on every robot.  Each robot needs a fixed vertex in
+   every connected component.  Errors as casim_upload_mesh. */
+int casim_upload_batch(casim_sim* sim, int32_t n_robots, const casim_mesh_desc* robots);
 
 /* Volume ratios alpha_g per chamber group (Eq. 2; chamber targets are scaled
    by cbrt(alpha_g), Sec. III-A.1).  n_groups must equal 1 + the largest group

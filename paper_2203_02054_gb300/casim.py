@@ -36,7 +36,7 @@ CASIM_MIXED = 1
 CASIM_DEBUG_BARRIER_NEVER_COMPLETES = 1
 
 EXPORTS = [
-    "casim_default_params", "casim_create", "casim_upload_mesh", "casim_set_actuation",
+    "casim_default_params", "casim_create", "casim_upload_mesh", "casim_upload_batch", "casim_set_actuation",
     "casim_set_spheres", "casim_set_positions", "casim_reset", "casim_step", "casim_sync", "casim_get_positions",
     "casim_get_contacts", "casim_get_springs", "casim_set_springs", "casim_get_targets",
     "casim_get_history", "casim_get_stats", "casim_save_state", "casim_load_state",
@@ -84,6 +84,17 @@ class casim_stats(ctypes.Structure):
     ]
 
 
+class casim_mesh_desc(ctypes.Structure):
+    _fields_ = [
+        ("n_verts", ctypes.c_int32),
+        ("rest_xyz", ctypes.POINTER(ctypes.c_double)),
+        ("n_tets", ctypes.c_int32),
+        ("tets", ctypes.POINTER(ctypes.c_int32)),
+        ("tet_group", ctypes.POINTER(ctypes.c_int32)),
+        ("fixed", ctypes.POINTER(ctypes.c_uint8)),
+    ]
+
+
 class CasimError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__("casim error %d: %s" % (code, msg))
@@ -111,6 +122,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.casim_default_params.restype = None
     L.casim_create.argtypes = [ctypes.POINTER(casim_params), _P, ctypes.POINTER(_P)]
     L.casim_upload_mesh.argtypes = [_P, ctypes.c_int32, _D, ctypes.c_int32, _I32, _I32, _U8]
+    L.casim_upload_batch.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(casim_mesh_desc)]
     L.casim_set_actuation.argtypes = [_P, ctypes.c_int32, _D]
     L.casim_set_spheres.argtypes = [_P, ctypes.c_int32, _D]
     L.casim_set_positions.argtypes = [_P, _D]
@@ -175,6 +187,24 @@ def casim_upload_mesh(sim, rest, tets, group, fixed):
     rc = load_library().casim_upload_mesh(sim, rest.shape[0], _ptr(rest, ctypes.c_double), tets.shape[0],
                                           _ptr(tets, ctypes.c_int32), _ptr(group, ctypes.c_int32),
                                           _ptr(fixed, ctypes.c_uint8))
+    return _check(rc, sim)
+
+
+def casim_upload_batch(sim, meshes):
+    """meshes: sequence of (rest, tets, group, fixed) array tuples."""
+    keep = []
+    descs = (casim_mesh_desc * len(meshes))()
+    for i, (rest, tets, group, fixed) in enumerate(meshes):
+        rest = np.ascontiguousarray(rest, dtype=np.float64)
+        tets = np.ascontiguousarray(tets, dtype=np.int32)
+        group = np.ascontiguousarray(group, dtype=np.int32)
+        fixed = np.ascontiguousarray(fixed, dtype=np.uint8)
+        keep.append((rest, tets, group, fixed))
+        descs[i] = casim_mesh_desc(rest.shape[0], _ptr(rest, ctypes.c_double), tets.shape[0],
+                                   _ptr(tets, ctypes.c_int32), _ptr(group, ctypes.c_int32),
+                                   _ptr(fixed, ctypes.c_uint8))
+    rc = load_library().casim_upload_batch(sim, len(meshes), descs)
+    del keep
     return _check(rc, sim)
 
 
@@ -325,12 +355,17 @@ def casim_last_error(sim=None) -> str:
 
 # ---- convenience wrapper ---------------------------------------------------
 class Sim:
-    """Owns one casim handle built from a generator ``Mesh`` (or raw arrays)."""
+    """Owns one casim handle built from a generator ``Mesh``, or from a list of
+    them (a batch of independent robots; parameters from the first)."""
 
     def __init__(self, mesh, precision=None, collision=None, stream: int = 0, stats: int = 1,
                  pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0,
                  pcg_kernel=0, debug_flags=0):
         load_library()
+        self.batch = None
+        if isinstance(mesh, (list, tuple)):
+            self.batch = list(mesh)
+            mesh = self.batch[0]
         p = casim_default_params()
         p.precision = mesh.precision if precision is None else precision
         p.collision = mesh.collision if collision is None else collision
@@ -352,9 +387,14 @@ class Sim:
         self.mesh = mesh
         self.h = casim_create(p, stream)
         try:
-            casim_upload_mesh(self.h, mesh.rest, mesh.tets, mesh.group, mesh.fixed)
-            if mesh.n_groups:
-                casim_set_actuation(self.h, mesh.alpha)
+            if self.batch is None:
+                casim_upload_mesh(self.h, mesh.rest, mesh.tets, mesh.group, mesh.fixed)
+                alpha = mesh.alpha
+            else:
+                casim_upload_batch(self.h, [(b.rest, b.tets, b.group, b.fixed) for b in self.batch])
+                alpha = np.concatenate([b.alpha for b in self.batch])
+            if len(alpha):
+                casim_set_actuation(self.h, alpha)
             if mesh.spheres is not None and len(mesh.spheres):
                 casim_set_spheres(self.h, mesh.spheres)
         except Exception:

@@ -80,6 +80,8 @@ struct casim_sim {
   int pcg_clusters = 0, cl_rows_cap = 0, n_robots = 1;
   int* robot_row = nullptr;
   std::vector<int> robot_row_h;
+  std::vector<int> robot_of_vert_h, robot_of_tet_h, robot_of_face_h;
+  int *robot_of_vert = nullptr, *robot_of_tet = nullptr, *robot_of_face = nullptr;
   // graph of one iteration
   cudaGraphExec_t gexec = nullptr;
   bool graph_dirty = true;
@@ -188,6 +190,9 @@ Dev<T> make_dev(casim_sim* sim) {
   d.stats = sim->params.stats;
   d.bar_extra = (sim->params.debug_flags & CASIM_DEBUG_BARRIER_NEVER_COMPLETES) ? 1u : 0u;
   d.n_robots = sim->n_robots;
+  d.robot_of_vert = sim->robot_of_vert;
+  d.robot_of_tet = sim->robot_of_tet;
+  d.robot_of_face = sim->robot_of_face;
   d.robot_row = sim->robot_row;
   d.cl_rows_cap = sim->cl_rows_cap;
   d.wait_budget = sim->params.wait_budget_cycles ? sim->params.wait_budget_cycles : 4000000000ull;
@@ -286,6 +291,13 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->sp.target = sim->dalloc<double>(3 * (size_t)n_q);
   sim->int_of_user_d = sim->dalloc<int>(n_v);
   sim->robot_row = sim->dalloc<int>(sim->robot_row_h.size());
+  if (sim->n_robots > 1) {
+    sim->robot_of_vert = sim->dalloc<int>(n_v);
+    sim->robot_of_tet = sim->dalloc<int>(n_t);
+    sim->robot_of_face = sim->dalloc<int>(std::max(n_f, 1));
+  } else {
+    sim->robot_of_vert = sim->robot_of_tet = sim->robot_of_face = nullptr;
+  }
   sim->ctrl = sim->dalloc<Ctrl>(1);
   sim->hist = sim->dalloc<IterRec>(sim->hist_cap);
   sim->n_e_local = local_blocks(n_t);
@@ -335,6 +347,12 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   if (n_f) CK(cudaMemcpyAsync(sim->faces, fh.data(), sizeof(int4) * n_f, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->int_of_user_d, sim->int_of_user.data(), sizeof(int) * n_v, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->robot_row, sim->robot_row_h.data(), sizeof(int) * sim->robot_row_h.size(), cudaMemcpyHostToDevice, st));
+  if (sim->n_robots > 1) {
+    CK(cudaMemcpyAsync(sim->robot_of_vert, sim->robot_of_vert_h.data(), sizeof(int) * n_v, cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sim->robot_of_tet, sim->robot_of_tet_h.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, st));
+    if (n_f)
+      CK(cudaMemcpyAsync(sim->robot_of_face, sim->robot_of_face_h.data(), sizeof(int) * n_f, cudaMemcpyHostToDevice, st));
+  }
   CK(cudaMemsetAsync(sim->spring_c, 0, sizeof(R4<double>) * std::max(n_free, 1), st));
   CK(cudaMemsetAsync(sim->sp.active, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->sp.kind, 0, sizeof(int) * std::max(n_q, 1), st));
@@ -565,8 +583,12 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   return CASIM_OK;
 }
 
-int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, int32_t n_tets,
-                      const int32_t* tets, const int32_t* tet_group, const uint8_t* fixed) {
+}  // extern "C"
+
+// Upload of R >= 1 independent robots given as one concatenated mesh
+// (robot_of_tet says which robot each tet belongs to; robots share no vertex).
+static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz, int32_t n_tets, const int32_t* tets,
+                         const int32_t* tet_group, const uint8_t* fixed, int n_robots, const int* robot_of_tet) {
   if (!sim) return CASIM_E_INVALID;
   if (n_verts <= 0 || n_tets <= 0 || !rest_xyz || !tets || !tet_group || !fixed)
     return sim->fail(CASIM_E_INVALID, "empty mesh or null pointer");
@@ -613,9 +635,24 @@ int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, i
     }
     tt[e] = s2;
   }
-  const double vmean = vsum / n_t;
+  (void)vsum;
+  // omega_e = Vol(e) / mean Vol over the tet's own robot
+  std::vector<double> rsum(n_robots, 0.0);
+  std::vector<long long> rcnt(n_robots, 0);
+  for (int e = 0; e < n_t; ++e) {
+    rsum[robot_of_tet[e]] += vol0[e];
+    rcnt[robot_of_tet[e]] += 1;
+  }
   sim->omega.resize(n_t);
-  for (int e = 0; e < n_t; ++e) sim->omega[e] = vol0[e] / vmean;
+  for (int e = 0; e < n_t; ++e) sim->omega[e] = vol0[e] / (rsum[robot_of_tet[e]] / rcnt[robot_of_tet[e]]);
+  // robot of every vertex (from its tets; robots must not share vertices)
+  std::vector<int> robot_of_vert_user(n_v, -1);
+  for (int e = 0; e < n_t; ++e)
+    for (int k = 0; k < 4; ++k) {
+      int& rv = robot_of_vert_user[tets[4 * e + k]];
+      if (rv >= 0 && rv != robot_of_tet[e]) return sim->fail(CASIM_E_INVALID, "robots share a vertex");
+      rv = robot_of_tet[e];
+    }
   // ---- connected components must each hold a fixed vertex ----
   {
     std::vector<int> parent(n_v);
@@ -660,6 +697,23 @@ int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, i
     if (fixed[v]) sim->int_of_user[v] = nx++;
   for (int v = 0; v < n_v; ++v) sim->user_of_int[sim->int_of_user[v]] = v;
   const int n_free = nf;
+  // free rows of each robot are contiguous (robots occupy increasing id ranges)
+  sim->n_robots = n_robots;
+  sim->robot_row_h.assign(n_robots + 1, 0);
+  {
+    int prev = 0;
+    for (int i = 0; i < n_free; ++i) {
+      int r = robot_of_vert_user[sim->user_of_int[i]];
+      if (r < 0) r = prev;
+      if (r < prev) return sim->fail(CASIM_E_INVALID, "robot vertex ranges must be contiguous and ascending");
+      prev = r;
+      sim->robot_row_h[r + 1]++;
+    }
+    for (int r = 0; r < n_robots; ++r) sim->robot_row_h[r + 1] += sim->robot_row_h[r];
+  }
+  sim->robot_of_vert_h.assign(n_v, 0);
+  for (int v = 0; v < n_v; ++v) sim->robot_of_vert_h[sim->int_of_user[v]] = std::max(0, robot_of_vert_user[v]);
+  sim->robot_of_tet_h.assign(robot_of_tet, robot_of_tet + n_t);
   std::vector<int> tets_int(4 * (size_t)n_t);
   for (size_t i = 0; i < tets_int.size(); ++i) tets_int[i] = sim->int_of_user[tets[i]];
   std::vector<int> group(tet_group, tet_group + n_t);
@@ -699,6 +753,8 @@ int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, i
       }
   }
   sim->n_f = (int)(faces4.size() / 4);
+  sim->robot_of_face_h.resize(sim->n_f);
+  for (int f = 0; f < sim->n_f; ++f) sim->robot_of_face_h[f] = robot_of_tet[faces4[4 * f + 3]];
   // ---- query vertices (non-fixed boundary vertices) and incident faces ----
   std::vector<char> on_surf(n_v, 0);
   for (int f = 0; f < sim->n_f; ++f)
@@ -824,8 +880,6 @@ int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, i
   const int rr_rows = fp64 ? pcg_rr_max_rows<double>() : pcg_rr_max_rows<float>();
   const bool rr_fits = max_width <= PCG_RR_MAXW && n_free <= rr_rows;
   // cluster PCG: every robot's rows must fit the cluster's shared memory
-  sim->n_robots = 1;
-  sim->robot_row_h = {0, n_free};
   int max_robot_rows = 0;
   for (int r = 0; r < sim->n_robots; ++r)
     max_robot_rows = std::max(max_robot_rows, sim->robot_row_h[r + 1] - sim->robot_row_h[r]);
@@ -838,7 +892,11 @@ int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, i
   if ((kern == 2 && !rr_fits) || (kern == 3 && !cl_fits))
     return sim->fail(CASIM_E_INVALID, "requested PCG kernel does not fit this mesh (" + std::to_string(n_free) +
                                           " rows, width " + std::to_string(max_width) + ")");
-  sim->pcg_cl = (kern == 3) || (kern == 0 && cl_fits);
+  // auto: a single system runs fastest on the whole-grid register-resident
+  // kernel (latency bound); several robots share the GPU through the cluster
+  // kernel's work queue
+  const bool many = sim->n_robots > 1;
+  sim->pcg_cl = (kern == 3) || (kern == 0 && cl_fits && (many || !rr_fits));
   sim->pcg_rr = !sim->pcg_cl && ((kern == 2) || (kern == 0 && rr_fits));
   sim->cl_rows_cap = cap;
   sim->pcg_clusters = std::max(1, std::min(max_clusters, sim->n_robots));
@@ -880,6 +938,59 @@ int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, i
     sim->has_act = true;
   }
   return CASIM_OK;
+}
+
+extern "C" {
+
+int casim_upload_mesh(casim_sim* sim, int32_t n_verts, const double* rest_xyz, int32_t n_tets, const int32_t* tets,
+                      const int32_t* tet_group, const uint8_t* fixed) {
+  if (!sim) return CASIM_E_INVALID;
+  if (n_tets <= 0) return sim->fail(CASIM_E_INVALID, "empty mesh or null pointer");
+  std::vector<int> robot(n_tets, 0);
+  return upload_robots(sim, n_verts, rest_xyz, n_tets, tets, tet_group, fixed, 1, robot.data());
+}
+
+int casim_upload_batch(casim_sim* sim, int32_t n_robots, const casim_mesh_desc* robots) {
+  if (!sim) return CASIM_E_INVALID;
+  if (n_robots < 1 || !robots) return sim->fail(CASIM_E_INVALID, "n_robots >= 1 and robots required");
+  long long nv = 0, nt = 0;
+  for (int r = 0; r < n_robots; ++r) {
+    const casim_mesh_desc& m = robots[r];
+    if (m.n_verts <= 0 || m.n_tets <= 0 || !m.rest_xyz || !m.tets || !m.tet_group || !m.fixed)
+      return sim->fail(CASIM_E_INVALID, "robot " + std::to_string(r) + ": empty mesh or null pointer");
+    nv += m.n_verts;
+    nt += m.n_tets;
+  }
+  if (nv > 2000000000LL || nt > 500000000LL) return sim->fail(CASIM_E_INVALID, "batch too large");
+  std::vector<double> rest(3 * (size_t)nv);
+  std::vector<int> tets(4 * (size_t)nt), group(nt), robot(nt);
+  std::vector<uint8_t> fixed(nv);
+  long long vo = 0, to = 0;
+  int go = 0;
+  for (int r = 0; r < n_robots; ++r) {
+    const casim_mesh_desc& m = robots[r];
+    std::copy(m.rest_xyz, m.rest_xyz + 3 * (size_t)m.n_verts, rest.begin() + 3 * vo);
+    std::copy(m.fixed, m.fixed + m.n_verts, fixed.begin() + vo);
+    int gmax = -1;
+    for (int e = 0; e < m.n_tets; ++e) {
+      for (int k = 0; k < 4; ++k) {
+        const int v = m.tets[4 * e + k];
+        if (v < 0 || v >= m.n_verts)
+          return sim->fail(CASIM_E_INVALID, "robot " + std::to_string(r) + ": tet vertex id out of range");
+        tets[4 * (to + e) + k] = (int)(v + vo);
+      }
+      const int g = m.tet_group[e];
+      if (g < -1) return sim->fail(CASIM_E_INVALID, "group id < -1");
+      group[to + e] = g < 0 ? -1 : g + go;
+      robot[to + e] = r;
+      gmax = std::max(gmax, g);
+    }
+    go += gmax + 1;
+    vo += m.n_verts;
+    to += m.n_tets;
+  }
+  return upload_robots(sim, (int)nv, rest.data(), (int)nt, tets.data(), group.data(), fixed.data(), n_robots,
+                       robot.data());
 }
 
 int casim_set_actuation(casim_sim* sim, int32_t n_groups, const double* alpha) {

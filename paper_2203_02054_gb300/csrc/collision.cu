@@ -89,10 +89,11 @@ __global__ void k_grid_bin(Dev<T> d) {
   const bool is_tet = i < d.n_t;
   const unsigned base = is_tet ? 0u : d.H_t;
   const unsigned mask = (is_tet ? d.H_t : d.H_f) - 1u;
+  const int robot = is_tet ? (d.robot_of_tet ? d.robot_of_tet[i] : 0) : (d.robot_of_face ? d.robot_of_face[i - d.n_t] : 0);
   for (int cz = c0[2]; cz <= c1[2]; ++cz)
     for (int cy = c0[1]; cy <= c1[1]; ++cy)
       for (int cx = c0[0]; cx <= c1[0]; ++cx) {
-        const unsigned h = base + (hash_cell(cx, cy, cz) & mask);
+        const unsigned h = base + (hash_cell(cx, cy, cz, robot) & mask);
         if (!FILL) {
           atomicAdd(&d.cell_count[h], 1);
         } else {
@@ -211,9 +212,10 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
     int cnt = 0;
     bool over = false;
     int* out = d.pair_tet + (size_t)qi * d.max_pairs;
+    const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
     if (d.collision >= 1 && isfinite(px) && isfinite(py) && isfinite(pz)) {
       const unsigned h =
-          hash_cell(cell_coord(px, d.inv_cell), cell_coord(py, d.inv_cell), cell_coord(pz, d.inv_cell)) &
+          hash_cell(cell_coord(px, d.inv_cell), cell_coord(py, d.inv_cell), cell_coord(pz, d.inv_cell), rv) &
           (d.H_t - 1u);
       const int b0 = d.cell_start[h];
       const int b1 = min(d.cell_start[h + 1], d.cap_items);
@@ -224,7 +226,8 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
         if (k < b1) {
           e = d.items[k];
           const int4 t = d.tet[e];
-          if (t.x != v && t.y != v && t.z != v && t.w != v) hit = strictly_inside(d, px, py, pz, t);
+          const bool same_robot = !d.robot_of_tet || d.robot_of_tet[e] == rv;
+          if (same_robot && t.x != v && t.y != v && t.z != v && t.w != v) hit = strictly_inside(d, px, py, pz, t);
         }
         unsigned m = __ballot_sync(0xffffffffu, hit);
         while (m) {
@@ -373,6 +376,7 @@ __device__ void face_verts(const Dev<T>& d, int f, V3& q0, V3& q1, V3& q2, int4&
 // Self-collision correspondence of vertex v: first exit-face hit along dir.
 template <typename T>
 __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, double& rb2) {
+  const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
   int best_f = -1;
   double best_t = 0.0;
   int cell[3] = {cell_coord(o.x, d.inv_cell), cell_coord(o.y, d.inv_cell), cell_coord(o.z, d.inv_cell)};
@@ -396,10 +400,11 @@ __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, doubl
     }
   }
   for (int it = 0; it < MAX_DDA_STEPS; ++it) {
-    const unsigned h = d.H_t + (hash_cell(cell[0], cell[1], cell[2]) & (d.H_f - 1u));
+    const unsigned h = d.H_t + (hash_cell(cell[0], cell[1], cell[2], rv) & (d.H_f - 1u));
     const int k0 = d.cell_start[h], k1 = min(d.cell_start[h + 1], d.cap_items);
     for (int k = k0; k < k1; ++k) {
       const int f = d.items[k] - d.n_t;
+      if (d.robot_of_face && d.robot_of_face[f] != rv) continue;
       V3 q0, q1, q2;
       int4 fv;
       face_verts(d, f, q0, q1, q2, fv);
@@ -425,6 +430,7 @@ __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, doubl
   // no exit face hit: closest point over all boundary faces not containing v
   double bestd = 0.0;
   for (int f = 0; f < d.n_f; ++f) {
+    if (d.robot_of_face && d.robot_of_face[f] != rv) continue;
     V3 q0, q1, q2;
     int4 fv;
     face_verts(d, f, q0, q1, q2, fv);

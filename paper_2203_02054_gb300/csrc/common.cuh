@@ -113,6 +113,9 @@ struct Dev {
   int n_robots;          // independent systems (robots) in the mesh
   const int* robot_row;  // n_robots + 1: first free row of each robot
   int cl_rows_cap;       // rows per CTA the cluster PCG's shared memory holds
+  const int* robot_of_vert;  // n_v (internal order); null for a single robot
+  const int* robot_of_tet;   // n_t; null for a single robot
+  const int* robot_of_face;  // n_f; null for a single robot
   unsigned bar_extra;    // 0; 1 = test-only: the barrier expects one more block
   unsigned long long wait_budget;
   // control and statistics
@@ -123,10 +126,12 @@ struct Dev {
   int n_e_local, n_e_spring;
 };
 
-__host__ __device__ inline unsigned hash_cell(int cx, int cy, int cz) {
+__host__ __device__ inline unsigned hash_cell(int cx, int cy, int cz, int robot = 0) {
   // Spatial hash of Teschner et al. 2003 ("Optimized spatial hashing for
-  // collision detection of deformable objects").
-  return ((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^ ((unsigned)cz * 83492791u);
+  // collision detection of deformable objects"), with the robot id mixed in
+  // so that robots placed at the same location do not share buckets.
+  return ((unsigned)cx * 73856093u) ^ ((unsigned)cy * 19349663u) ^ ((unsigned)cz * 83492791u) ^
+         ((unsigned)robot * 2654435761u);
 }
 
 // Cell coordinate of one coordinate value: floor(x / cell), clamped so that

@@ -662,17 +662,32 @@ __global__ void __launch_bounds__(PCG_CL_THREADS, 1) k_pcg_cluster(Dev<T> d) {
       ay = dg * self.y;
       az = dg * self.z;
       const int sl = i >> 5, lane = i & 31;
-      const int k1 = d.sl_ptr[sl + 1];
-      for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
-        const T a = d.sl_val[k];
-        if (a == T(0)) continue;
-        const int c = d.sl_col[k] - row0;
-        const int owner = c / rpc;
-        const R4<T>* ru = cl.map_shared_rank(su, owner);
-        const R4<T> v = ru[c - owner * rpc];
-        ax += a * v.x;
-        ay += a * v.y;
-        az += a * v.z;
+      const int base = d.sl_ptr[sl] + lane;
+      const int width = (d.sl_ptr[sl + 1] - d.sl_ptr[sl]) >> 5;
+      // chunks of 8 entries: all column/value loads first, then the
+      // distributed-shared-memory gathers, so the loads overlap
+      for (int j0 = 0; j0 < width; j0 += 8) {
+        int cc[8];
+        T aa[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (j0 + q < width) {
+            cc[q] = d.sl_col[base + (j0 + q) * 32];
+            aa[q] = d.sl_val[base + (j0 + q) * 32];
+          } else {
+            cc[q] = row0 + my0 + j;
+            aa[q] = T(0);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int c = cc[q] - row0;
+          const int owner = c / rpc;
+          const R4<T> v = cl.map_shared_rank(su, owner)[c - owner * rpc];
+          ax += aa[q] * v.x;
+          ay += aa[q] * v.y;
+          az += aa[q] * v.z;
+        }
       }
     };
     // r = b - A x in FP64, u = r / diag, correction d = 0

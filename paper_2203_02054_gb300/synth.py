@@ -155,34 +155,36 @@ def _voxel_kuhn(nx, ny, nz, h, slit_levels=(), s=0, group_of_voxel=None):
         if dup_rows else base_xyz
 
     slit_index = {P: q for q, P in enumerate(slit_levels)}
+    # voxel grid in (k, j, i) order, i fastest: voxel index i + nx (j + ny k)
+    kk, jj, ii = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ii, jj, kk = ii.ravel(), jj.ravel(), kk.ravel()
+    if group_of_voxel is None:
+        gvox = np.full(ii.shape[0], -1, dtype=np.int32)
+    else:
+        gvox = np.array([group_of_voxel(a, b, c) for a, b, c in zip(ii.tolist(), jj.tolist(), kk.tolist())],
+                        dtype=np.int32)
 
-    def vid(i, j, k, I_, J_, K_):
-        # i is the voxel x index; I_, J_, K_ the corner vertex levels
-        if I_ in slit_index and i == I_ and K_ > s:
-            q = slit_index[I_]
-            return n_base + q * n_lev * nvy + (K_ - s - 1) * nvy + J_
-        return I_ + nvx * (J_ + nvy * K_)
+    def vid(I_, J_, K_):
+        """Vertex ids of corner levels (I_, J_, K_) for voxels with x index ii."""
+        out = I_ + nvx * (J_ + nvy * K_)
+        for P, q in slit_index.items():
+            sel = (I_ == P) & (ii == P) & (K_ > s)
+            out = np.where(sel, n_base + q * n_lev * nvy + (K_ - s - 1) * nvy + J_, out)
+        return out
 
-    tets = np.empty((nx * ny * nz * 6, 4), dtype=np.int32)
-    group = np.full(nx * ny * nz * 6, -1, dtype=np.int32)
-    t = 0
-    for k in range(nz):
-        for j in range(ny):
-            for i in range(nx):
-                g = -1 if group_of_voxel is None else group_of_voxel(i, j, k)
-                for p, (a, b, _c) in enumerate(_PERMS):
-                    c0 = (0, 0, 0)
-                    c1 = [0, 0, 0]
-                    c1[a] = 1
-                    c2 = list(c1)
-                    c2[b] = 1
-                    corners = [c0, tuple(c1), tuple(c2), (1, 1, 1)]
-                    ids = [vid(i, j, k, i + d[0], j + d[1], k + d[2]) for d in corners]
-                    if not _PERM_EVEN[p]:
-                        ids[1], ids[2] = ids[2], ids[1]
-                    tets[t] = ids
-                    group[t] = g
-                    t += 1
+    tets = np.empty((nx * ny * nz, 6, 4), dtype=np.int64)
+    for p, (a, b, _c) in enumerate(_PERMS):
+        c1 = [0, 0, 0]
+        c1[a] = 1
+        c2 = list(c1)
+        c2[b] = 1
+        corners = [(0, 0, 0), tuple(c1), tuple(c2), (1, 1, 1)]
+        ids = [vid(ii + dd[0], jj + dd[1], kk + dd[2]) for dd in corners]
+        if not _PERM_EVEN[p]:
+            ids[1], ids[2] = ids[2], ids[1]
+        tets[:, p, :] = np.stack(ids, axis=1)
+    tets = tets.reshape(-1, 4).astype(np.int32)
+    group = np.repeat(gvox, 6).astype(np.int32)
     fixed = np.zeros(rest.shape[0], dtype=np.uint8)
     fixed[np.isclose(rest[:, 0], 0.0) & (np.arange(rest.shape[0]) < n_base)] = 1
     return rest, tets, group, fixed

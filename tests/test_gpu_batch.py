@@ -1,0 +1,113 @@
+"""Batched form: several independent robots in one simulation (one set of
+launches, one PCG per robot in the cluster kernel's work queue).  Every robot
+must behave exactly as it does alone: compared with the FP64 oracle run on
+each robot separately."""
+import numpy as np
+import pytest
+
+from paper_2203_02054_gb300 import casim, synth
+from oracle import loop, springs as osprings
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    casim.load_library()
+
+
+def _small_batch(precision, n_iters):
+    shapes = [(20, 4, 4, 4, 3), (23, 5, 5, 3, 4), (16, 4, 4, 3, 5), (26, 6, 6, 5, 6)]
+    return [synth.small_finger(nx, ny, nz, nc, seed=seed, n_iters=n_iters, precision=precision)
+            for nx, ny, nz, nc, seed in shapes]
+
+
+def _offsets(batch):
+    vo = np.cumsum([0] + [m.n_verts for m in batch])
+    to = np.cumsum([0] + [m.n_tets for m in batch])
+    return vo, to
+
+
+def test_batch_fp64_each_robot_matches_its_own_oracle_run():
+    batch = _small_batch(synth.PRECISION_FP64, 15)
+    sim = casim.Sim(batch)
+    sim.step(15)
+    assert sim.sync() == 0
+    X = sim.positions()
+    hist = sim.history()
+    vo, _ = _offsets(batch)
+    pair_sum = np.zeros(15, int)
+    for r, m in enumerate(batch):
+        ref = loop.run_mesh(m, n_iters=15)
+        err = np.abs(X[vo[r]:vo[r + 1]] - ref.X).max()
+        assert err <= 1e-9 * m.bbox_diag(), (r, err)
+        pair_sum += np.array([h.n_self_pairs for h in ref.history])
+    assert [h["n_self_pairs"] for h in hist] == pair_sum.tolist()
+    assert pair_sum.max() > 0
+    sim.close()
+
+
+def test_batch_mixed_one_iteration_replay_and_robot_isolation():
+    """All robots share the same region of space (same rest placement); the
+    pair set must still be the union of the robots' own pair sets."""
+    batch = _small_batch(synth.PRECISION_MIXED, 1)
+    X0s = [synth.perturbed_positions(m, 0.3, seed=200 + r, dtype=np.float32) for r, m in enumerate(batch)]
+    sim = casim.Sim(batch)
+    sim.set_positions(np.concatenate(X0s))
+    sim.step(1)
+    assert sim.sync() == 0
+    pairs, _ = sim.contacts()
+    X = sim.positions()
+    vo, to = _offsets(batch)
+    expect = []
+    for r, m in enumerate(batch):
+        prep = loop.prepare(m.rest, m.tets, m.group, m.fixed)
+        Xn, st, rec, ps, po = loop.iterate(prep, X0s[r], osprings.SpringState.empty(prep.query.shape[0]),
+                                           m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps, m.collision)
+        expect.append(ps + np.array([vo[r], to[r]]))
+        err = np.abs(X[vo[r]:vo[r + 1]] - Xn).max()
+        assert err <= 1e-5 * m.bbox_diag(), (r, err)
+    expect = np.concatenate(expect)
+    assert expect.shape[0] > 0
+    assert np.array_equal(pairs, expect)
+    sim.close()
+
+
+def test_batch_matches_plain_runs_on_gpu():
+    batch = _small_batch(synth.PRECISION_MIXED, 10)
+    sim = casim.Sim(batch)
+    sim.step(10)
+    assert sim.sync() == 0
+    X = sim.positions()
+    vo, _ = _offsets(batch)
+    for r, m in enumerate(batch):
+        one = casim.Sim(m)
+        one.step(10)
+        assert one.sync() == 0
+        err = np.abs(X[vo[r]:vo[r + 1]] - one.positions()).max()
+        assert err <= 1e-5 * m.bbox_diag(), (r, err)
+        one.close()
+    sim.close()
+
+
+def test_full_batch_of_256_fingers_properties():
+    batch = synth.config4_batch()
+    n_t = sum(m.n_tets for m in batch)
+    assert n_t > 12_000_000
+    sim = casim.Sim(batch)
+    sim.step(5)
+    assert sim.sync() == 0
+    hist = sim.history()
+    assert all(h["pcg_rel_residual"] <= 1e-6 for h in hist)
+    X = sim.positions()
+    assert np.all(np.isfinite(X))
+    # spot check: three robots against their own plain GPU runs
+    vo, _ = _offsets(batch)
+    for r in (0, 97, 255):
+        one = casim.Sim(batch[r])
+        one.step(5)
+        assert one.sync() == 0
+        err = np.abs(X[vo[r]:vo[r + 1]] - one.positions()).max()
+        assert err <= 1e-5 * batch[r].bbox_diag(), (r, err)
+        one.close()
+    sim.close()

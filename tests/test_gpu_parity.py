@@ -286,7 +286,8 @@ def test_pcg_cap_warning_and_timeout_status():
     # a barrier that waits for a block that does not exist must give up after
     # its clock budget (~10 ms here) with a timeout status; the context stays
     # usable afterwards
-    sim = casim.Sim(m, wait_budget_cycles=20_000_000, debug_flags=casim.CASIM_DEBUG_BARRIER_NEVER_COMPLETES)
+    sim = casim.Sim(m, wait_budget_cycles=20_000_000, debug_flags=casim.CASIM_DEBUG_BARRIER_NEVER_COMPLETES,
+                    pcg_kernel=2)
     sim.step(1)
     with pytest.raises(casim.CasimError) as ei:
         sim.sync()
