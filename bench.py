@@ -341,7 +341,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * 3 * m.n_verts + 8 * m.n_groups,
                     "d2h_bytes_per_step": 8 * 3 * m.n_verts},
             "gpu_launches": gpu_launches,
-            "roofline": {"bound": "hbm", "kernel": "k_pcg (persistent Chronopoulos-Gear PCG)",
+            "roofline": {"bound": "hbm", "kernel": {1: "k_pcg (streaming)", 2: "k_pcg_rr (register-resident)",
+                                                    3: "k_pcg_cluster", 4: "k_pcg_pipe (pipelined, register-resident)"}
+                         .get(stats.pcg_kernel, "k_pcg"),
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": recorded_traffic("k_pcg"),
                          "bytes_per_launch": bpl, "ms_per_launch": pcg_ms, "k_pcg_mean": k_pcg,

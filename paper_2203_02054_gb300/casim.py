@@ -81,6 +81,7 @@ class casim_stats(ctypes.Structure):
         ("total_pcg_iters", ctypes.c_int64),
         ("last", casim_iter_record),
         ("status", ctypes.c_int32),
+        ("pcg_kernel", ctypes.c_int32),
     ]
 
 

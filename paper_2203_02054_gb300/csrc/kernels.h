@@ -29,7 +29,7 @@ void launch_local(const Dev<T>& d, cudaStream_t st);
 template <typename T>
 void launch_rhs(const Dev<T>& d, cudaStream_t st);
 template <typename T>
-cudaError_t launch_pcg(const Dev<T>& d, int grid, bool rr, cudaStream_t st);
+cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st);
 template <typename T>
 int pcg_rr_max_rows();
 template <typename T>
