@@ -170,6 +170,23 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def aggregate(ms_local: float, units_local: float, pg=None, device=None):
+    """Whole-job throughput: the work of all ranks over the slowest rank's
+    time (max over ranks of the timed milliseconds)."""
+    import torch
+
+    t = torch.tensor([ms_local, units_local], dtype=torch.float64, device=device)
+    if pg is not None:
+        mx = t[:1].clone()
+        pg.all_reduce(mx, op=pg.ReduceOp.MAX)
+        tot = t[1:].clone()
+        pg.all_reduce(tot, op=pg.ReduceOp.SUM)
+        ms, units = float(mx.item()), float(tot.item())
+    else:
+        ms, units = float(t[0].item()), float(t[1].item())
+    return units / (ms / 1e3), ms
+
+
 # ------------------------------------------------------------------ oracle arm
 def oracle_sample(m, prep=None):
     """One outer iteration of the FP64 oracle from the rest shape; returns
@@ -280,12 +297,8 @@ def main():
         sampler.stop()
     status = casim.casim_sync(sim.h)
     ms = sum(a.elapsed_time(b) for a, b in evs)
-    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if pg is not None:
-        pg.all_reduce(t_local, op=pg.ReduceOp.MAX)
-    ms_max = float(t_local.item())
     units = float(m.n_tets) * n_iters * args.steps * world
-    value = units / (ms_max / 1e3)
+    value, ms_max = aggregate(ms, float(m.n_tets) * n_iters * args.steps, pg, "cuda")
     kernels_per_iter = 11   # 2 hash binning + 3 scan + narrow + springs + local + rhs + pcg + finalize
     gpu_launches = kernels_per_iter * n_iters * args.steps
     stats = casim.casim_get_stats(sim.h)
@@ -305,11 +318,7 @@ def main():
         casim.casim_get_positions(sim.h, m.n_verts)
     barrier()
     e2e_s = time.perf_counter() - t0
-    if pg is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = units / e2e_s
+    e2e_value, _ = aggregate(1e3 * e2e_s, float(m.n_tets) * n_iters * args.steps, pg, "cuda")
     del out
 
     line = None
@@ -342,7 +351,7 @@ def main():
                     "d2h_bytes_per_step": 8 * 3 * m.n_verts},
             "gpu_launches": gpu_launches,
             "roofline": {"bound": "hbm", "kernel": {1: "k_pcg (streaming)", 2: "k_pcg_rr (register-resident)",
-                                                    3: "k_pcg_cluster", 4: "k_pcg_pipe (pipelined, register-resident)"}
+                                                    3: "k_pcg_cluster"}
                          .get(stats.pcg_kernel, "k_pcg"),
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": recorded_traffic("k_pcg"),

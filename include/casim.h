@@ -83,15 +83,13 @@ typedef struct {
   uint64_t wait_budget_cycles;  /* SM clock cycles a grid-barrier wait may spin
                                    before the kernel gives up with CASIM_E_TIMEOUT;
                                    0 selects the default (about 2 s)                 */
-  int32_t pcg_kernel;       /* PCG kernel: 0 auto (one robot: 4 if it fits, else 1;
+  int32_t pcg_kernel;       /* PCG kernel: 0 auto (one robot: 2 if it fits, else 1;
                                several robots: 3 if it fits, else 1); 1 streaming
                                (whole grid, vectors in memory, any size); 2
-                               register-resident (whole grid, one row per thread,
-                               two grid barriers per iteration); 3 cluster (one
-                               16-CTA cluster per robot, vectors in shared
-                               memory); 4 pipelined register-resident (one grid
-                               barrier per iteration).  A forced kernel that does
-                               not fit gives CASIM_E_INVALID at upload             */
+                               register-resident (whole grid, one row per thread);
+                               3 cluster (one 16-CTA cluster per robot, vectors in
+                               shared memory).  A forced kernel that does not fit
+                               gives CASIM_E_INVALID at upload                      */
   int32_t debug_flags;      /* test-only fault injection, 0 in normal use:
                                CASIM_DEBUG_BARRIER_NEVER_COMPLETES makes the PCG
                                grid barrier (kernels 1 and 2; the cluster kernel
@@ -118,7 +116,7 @@ typedef struct {
   int64_t total_pcg_iters;
   casim_iter_record last;   /* record of the most recent iteration                   */
   int32_t status;           /* device status code of the last casim_sync             */
-  int32_t pcg_kernel;       /* PCG kernel chosen at upload (1..4, see casim_params)   */
+  int32_t pcg_kernel;       /* PCG kernel chosen at upload (1..3, see casim_params)   */
 } casim_stats;
 
 /* Fills *p with the defaults: MIXED, self collision, k = 1, eps = 0.005,

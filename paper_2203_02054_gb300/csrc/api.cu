@@ -77,7 +77,7 @@ struct casim_sim {
   int cap_items = 0, n_slices = 0, pcg_grid = 1, n_e_local = 0, n_e_spring = 0;
   bool pcg_rr = false;  // register-resident PCG (one row per thread)
   bool pcg_cl = false;  // cluster PCG (one cluster per robot, work queue)
-  int pcg_variant = 1;  // whole-grid kernel: 1 streaming, 2 register-resident, 4 pipelined
+  int pcg_variant = 1;  // whole-grid kernel: 1 streaming, 2 register-resident
   int pcg_clusters = 0, cl_rows_cap = 0, n_robots = 1;
   int* robot_row = nullptr;
   std::vector<int> robot_row_h;
@@ -551,7 +551,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.n_w_knots < 0 || (p.n_w_knots > 0 && !p.w_knots) || p.n_w_knots > 64) why = "w_knots";
   else if (!(p.cell_size > 0.0) || !std::isfinite(p.cell_size)) why = "cell_size";
   else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
-  else if (p.pcg_kernel < 0 || p.pcg_kernel > 4) why = "pcg_kernel";
+  else if (p.pcg_kernel < 0 || p.pcg_kernel > 3) why = "pcg_kernel";
   else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
@@ -890,7 +890,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   if (need <= cap) max_clusters = fp64 ? pcg_cluster_max_clusters<double>(cap) : pcg_cluster_max_clusters<float>(cap);
   const bool cl_fits = need <= cap && max_clusters > 0;
   const int kern = sim->params.pcg_kernel;
-  if (((kern == 2 || kern == 4) && !rr_fits) || (kern == 3 && !cl_fits))
+  if ((kern == 2 && !rr_fits) || (kern == 3 && !cl_fits))
     return sim->fail(CASIM_E_INVALID, "requested PCG kernel does not fit this mesh (" + std::to_string(n_free) +
                                           " rows, width " + std::to_string(max_width) + ")");
   // auto: a single system runs fastest on the whole-grid register-resident
@@ -898,8 +898,8 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   // kernel's work queue
   const bool many = sim->n_robots > 1;
   sim->pcg_cl = (kern == 3) || (kern == 0 && cl_fits && (many || !rr_fits));
-  sim->pcg_rr = !sim->pcg_cl && ((kern == 2) || (kern == 4) || (kern == 0 && rr_fits));
-  sim->pcg_variant = sim->pcg_rr ? (kern == 2 ? 2 : 4) : 1;
+  sim->pcg_rr = !sim->pcg_cl && ((kern == 2) || (kern == 0 && rr_fits));
+  sim->pcg_variant = sim->pcg_rr ? 2 : 1;
   sim->cl_rows_cap = cap;
   sim->pcg_clusters = std::max(1, std::min(max_clusters, sim->n_robots));
   if (sim->pcg_rr) {

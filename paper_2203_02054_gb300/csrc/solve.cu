@@ -596,163 +596,6 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
   if (i == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, bb);
 }
 
-// Pipelined register-resident variant: the preconditioned conjugate
-// gradient recurrences of Ghysels and Vanroose (2014, "Hiding global
-// synchronization latency in the preconditioned conjugate gradient
-// algorithm"), which carry u = M^-1 r, w = A u and their search-direction
-// counterparts so that the one SpMV of an iteration (n = A m, m = M^-1 w) and
-// the iteration's dot products need the same, single grid barrier.  m is
-// published through two alternating buffers: a block that has passed barrier
-// i may write m_{i+1} while a slower block still gathers m_i.
-template <typename T, int MAXW>
-__global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_pipe(Dev<T> d) {
-  __shared__ double sh[96];
-  __shared__ double tot[4];
-  __shared__ int shf;
-  const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget, d.bar_extra};
-  unsigned epoch = 0;
-  const int n = d.n_free;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool act = i < n;
-  R4<T>* mbuf[2] = {d.u, d.w};
-  int col[MAXW];
-  T val[MAXW];
-  int width = 0;
-  T dg = T(1);
-  T x[3] = {T(0), T(0), T(0)};
-  if (act) {
-    const int sl = i >> 5, lane = i & 31;
-    const int base = d.sl_ptr[sl];
-    width = (d.sl_ptr[sl + 1] - base) >> 5;
-#pragma unroll
-    for (int j = 0; j < MAXW; ++j) {
-      if (j < width) {
-        col[j] = d.sl_col[base + j * 32 + lane];
-        val[j] = d.sl_val[base + j * 32 + lane];
-      } else {
-        col[j] = i;
-        val[j] = T(0);
-      }
-    }
-    dg = d.diag[i];
-    const R4<T> xi = d.X[i];
-    x[0] = xi.x; x[1] = xi.y; x[2] = xi.z;
-  }
-  auto spmv = [&](const R4<T>* src, const T (&self)[3], T (&ax)[3]) {
-    ax[0] = dg * self[0];
-    ax[1] = dg * self[1];
-    ax[2] = dg * self[2];
-#pragma unroll
-    for (int j = 0; j < MAXW; ++j) {
-      if (j < width) {
-        const R4<T> v = ld_cg<T>(src + col[j]);
-        ax[0] += val[j] * v.x;
-        ax[1] += val[j] * v.y;
-        ax[2] += val[j] * v.z;
-      }
-    }
-  };
-  auto store = [&](R4<T>* dst, const T (&v)[3]) {
-    R4<T> t;
-    t.x = v[0]; t.y = v[1]; t.z = v[2]; t.w = T(0);
-    dst[i] = t;
-  };
-  T r[3], u[3], w[3], z[3], q[3], s[3], p[3], m[3], dd[3] = {T(0), T(0), T(0)};
-  double a0[2] = {0.0, 0.0};
-  if (act) {
-    double ax[3] = {(double)dg * x[0], (double)dg * x[1], (double)dg * x[2]};
-#pragma unroll
-    for (int j = 0; j < MAXW; ++j) {
-      if (j < width) {
-        const R4<T> v = d.X[col[j]];
-        ax[0] += (double)val[j] * v.x;
-        ax[1] += (double)val[j] * v.y;
-        ax[2] += (double)val[j] * v.z;
-      }
-    }
-    const R4<double> bi = d.b[i];
-    const double bv[3] = {bi.x, bi.y, bi.z};
-    for (int c = 0; c < 3; ++c) {
-      const double rc = bv[c] - ax[c];
-      r[c] = (T)rc;
-      u[c] = r[c] / dg;
-      a0[0] += bv[c] * bv[c];
-      a0[1] += rc * rc;
-    }
-    store(d.p, u);  // u_0 for w_0 = A u_0
-  }
-  if (!grid_sync_reduce<2>(g, epoch, a0, sh, tot, &shf)) return;
-  const double bb = tot[0];
-  double rr = tot[1];
-  int it = 0;
-  if (bb > 0.0 && rr > d.tol2 * bb) {
-    if (act) spmv(d.p, u, w);
-    double gamma_prev = 0.0, alpha_prev = 0.0;
-    for (;; ++it) {
-      double a2[3] = {0.0, 0.0, 0.0};
-      if (act) {
-        for (int c = 0; c < 3; ++c) {
-          m[c] = w[c] / dg;
-          a2[0] += (double)r[c] * u[c];
-          a2[1] += (double)w[c] * u[c];
-          a2[2] += (double)r[c] * r[c];
-        }
-        store(mbuf[it & 1], m);
-      }
-      if (!grid_sync_reduce<3>(g, epoch, a2, sh, tot, &shf)) return;
-      const double gam = tot[0], delta = tot[1];
-      rr = tot[2];
-      if (!isfinite(gam) || !isfinite(delta) || !isfinite(rr)) {
-        if (i == 0) set_status(d.ctrl, ST_NONFINITE);
-        break;
-      }
-      if (rr <= d.tol2 * bb) break;
-      if (it >= d.max_iter) {
-        if (i == 0) set_status(d.ctrl, ST_PCG_MAXIT);
-        break;
-      }
-      double alpha, beta;
-      if (it == 0) {
-        beta = 0.0;
-        alpha = gam / delta;
-      } else {
-        beta = gam / gamma_prev;
-        alpha = gam / (delta - beta * gam / alpha_prev);
-      }
-      gamma_prev = gam;
-      alpha_prev = alpha;
-      if (act) {
-        T nn[3];
-        spmv(mbuf[it & 1], m, nn);
-        const T ta = (T)alpha, tb = (T)beta;
-        for (int c = 0; c < 3; ++c) {
-          if (it == 0) {
-            z[c] = nn[c];
-            q[c] = m[c];
-            s[c] = w[c];
-            p[c] = u[c];
-          } else {
-            z[c] = nn[c] + tb * z[c];
-            q[c] = m[c] + tb * q[c];
-            s[c] = w[c] + tb * s[c];
-            p[c] = u[c] + tb * p[c];
-          }
-          dd[c] += ta * p[c];
-          r[c] -= ta * s[c];
-          u[c] -= ta * q[c];
-          w[c] -= ta * z[c];
-        }
-      }
-    }
-    if (act) {
-      R4<T> t;
-      t.x = x[0] + dd[0]; t.y = x[1] + dd[1]; t.z = x[2] + dd[2]; t.w = T(0);
-      d.X[i] = t;
-    }
-  }
-  if (i == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, bb);
-}
-
 // Cluster variant: one thread-block cluster of PCG_CL_SIZE CTAs solves one
 // robot's system at a time, taking robots from a work queue (one persistent
 // launch serves any number of independent robots).  Each CTA owns a
@@ -1049,10 +892,8 @@ int pcg_rr_max_rows() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  int per2 = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_rr<T, PCG_RR_MAXW>, PCG_RR_THREADS, 0);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, k_pcg_pipe<T, PCG_RR_MAXW>, PCG_RR_THREADS, 0);
-  return sms * std::min(per, per2) * PCG_RR_THREADS;
+  return sms * per * PCG_RR_THREADS;
 }
 
 template <typename T>
@@ -1069,7 +910,6 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st) 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (variant == 4) return cudaLaunchKernelEx(&cfg, k_pcg_pipe<T, PCG_RR_MAXW>, d);
   if (variant == 2) return cudaLaunchKernelEx(&cfg, k_pcg_rr<T, PCG_RR_MAXW>, d);
   return cudaLaunchKernelEx(&cfg, k_pcg<T>, d);
 }
