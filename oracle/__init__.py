@@ -27,3 +27,4 @@ closed forms, invariants, brute force or library routines; functions without
 such a pin say "parity unpinned" in their docstring.
 """
 from . import mesh, local, collision, springs, global_step, loop  # noqa: F401
+# ``oracle.adjoint`` needs PyTorch and is imported on demand.
