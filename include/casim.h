@@ -185,6 +185,28 @@ int casim_reset(casim_sim* sim);
    Errors: CASIM_E_STATE (no mesh or actuation), CASIM_E_CUDA. */
 int casim_step(casim_sim* sim, int32_t n_iters);
 
+/* Runs n_iters outer iterations from the current state (like casim_step)
+   while saving a checkpoint of the positions and spring records before
+   iterations 0, ckpt_every, 2*ckpt_every, ... for casim_backward (no
+   counterpart in the paper; the adjoint is a service built on its loop).
+   Memory: ceil(n_iters/ckpt_every) checkpoints plus ckpt_every recomputed
+   position sets.  Synchronous with respect to the stream's earlier work only
+   through the copies it enqueues; errors as casim_step. */
+int casim_forward_ckpt(casim_sim* sim, int32_t n_iters, int32_t ckpt_every);
+
+/* Reverse pass of the last casim_forward_ckpt: given dL/dX of the final
+   positions (host, n_verts*3 doubles, caller order; rows of fixed vertices
+   are ignored) writes dL/dalpha (host, n_groups doubles) for the chamber
+   volume ratios.  The discrete decisions of each iteration (contact pairs,
+   spring kinds, faces and spheres, which springs were cast) are held fixed,
+   so the result is the derivative of the unrolled map on the region of
+   parameters where those decisions do not change.  Each segment between
+   checkpoints is recomputed; the final forward state and the history
+   counters are restored afterwards.  Errors: CASIM_E_STATE (no preceding
+   casim_forward_ckpt, or the actuation or positions changed since),
+   CASIM_E_NONFINITE, CASIM_E_CUDA.  Synchronises the stream. */
+int casim_backward(casim_sim* sim, const double* dL_dX, double* dL_dalpha);
+
 /* Waits for the stream and returns the device status: CASIM_OK,
    CASIM_W_PCG_MAXIT, CASIM_E_NONFINITE, CASIM_E_TIMEOUT or CASIM_E_OVERFLOW.
    The device status is cleared after it is read. */

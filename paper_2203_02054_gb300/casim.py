@@ -37,7 +37,8 @@ CASIM_DEBUG_BARRIER_NEVER_COMPLETES = 1
 
 EXPORTS = [
     "casim_default_params", "casim_create", "casim_upload_mesh", "casim_upload_batch", "casim_set_actuation",
-    "casim_set_spheres", "casim_set_positions", "casim_reset", "casim_step", "casim_sync", "casim_get_positions",
+    "casim_set_spheres", "casim_set_positions", "casim_reset", "casim_step", "casim_forward_ckpt",
+    "casim_backward", "casim_sync", "casim_get_positions",
     "casim_get_contacts", "casim_get_springs", "casim_set_springs", "casim_get_targets",
     "casim_get_history", "casim_get_stats", "casim_save_state", "casim_load_state",
     "casim_get_sizes", "casim_get_phase_times", "casim_contacts_noalloc", "casim_destroy",
@@ -129,6 +130,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.casim_set_positions.argtypes = [_P, _D]
     L.casim_reset.argtypes = [_P]
     L.casim_step.argtypes = [_P, ctypes.c_int32]
+    L.casim_forward_ckpt.argtypes = [_P, ctypes.c_int32, ctypes.c_int32]
+    L.casim_backward.argtypes = [_P, _D, _D]
     L.casim_sync.argtypes = [_P]
     L.casim_get_positions.argtypes = [_P, _D, _P]
     L.casim_get_contacts.argtypes = [_P, _I32, _I64, _I32, _I64]
@@ -230,6 +233,17 @@ def casim_reset(sim):
 
 def casim_step(sim, n_iters: int):
     return _check(load_library().casim_step(sim, int(n_iters)), sim)
+
+
+def casim_forward_ckpt(sim, n_iters: int, ckpt_every: int):
+    return _check(load_library().casim_forward_ckpt(sim, int(n_iters), int(ckpt_every)), sim)
+
+
+def casim_backward(sim, dL_dX, n_groups: int) -> np.ndarray:
+    g = np.ascontiguousarray(dL_dX, dtype=np.float64)
+    out = np.zeros(max(n_groups, 1), dtype=np.float64)
+    _check(load_library().casim_backward(sim, _ptr(g, ctypes.c_double), _ptr(out, ctypes.c_double)), sim)
+    return out[:n_groups]
 
 
 def casim_sync(sim) -> int:
@@ -403,6 +417,7 @@ class Sim:
             self.h = None
             raise
         self.sizes = casim_get_sizes(self.h)
+        self.n_groups = int(len(alpha))
 
     def step(self, n: int):
         casim_step(self.h, n)
@@ -447,3 +462,29 @@ class Sim:
             self.close()
         except Exception:
             pass
+
+
+def actuation_to_positions(sim: "Sim", alpha, n_iters: int, ckpt_every: int = 10):
+    """Differentiable map alpha -> final positions (torch tensors, CPU, float64)
+    through ``casim_forward_ckpt`` / ``casim_backward``: every forward call
+    resets the simulation to its rest state, sets the ratios and runs
+    ``n_iters`` iterations with checkpoints; the backward pass returns
+    dL/dalpha from the library's adjoint."""
+    import torch
+
+    class _ActuationToPositions(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, a):
+            an = a.detach().cpu().double().numpy()
+            casim_set_actuation(sim.h, an)
+            casim_reset(sim.h)
+            casim_forward_ckpt(sim.h, n_iters, ckpt_every)
+            casim_sync(sim.h)
+            return torch.from_numpy(sim.positions())
+
+        @staticmethod
+        def backward(ctx, gX):
+            ga = casim_backward(sim.h, gX.detach().cpu().double().numpy(), sim.n_groups)
+            return torch.from_numpy(ga)
+
+    return _ActuationToPositions.apply(alpha)

@@ -90,6 +90,30 @@ struct casim_sim {
   long long iters = 0;
   int last_status = 0;
   double phase_ms[5] = {0, 0, 0, 0, 0};
+  std::vector<double> alpha_h;  // current volume ratios (host copy, for the adjoint)
+  // adjoint: checkpoints of the last casim_forward_ckpt and reverse-pass buffers
+  struct Adj {
+    int n_iters = 0, every = 0, n_ckpt = 0, cap_ckpt = 0, cap_every = 0;
+    bool valid = false;
+    void* ckX = nullptr;      // n_ckpt x n_v positions
+    int *ck_act = nullptr, *ck_kind = nullptr, *ck_face = nullptr;
+    double *ck_bary = nullptr, *ck_tgt = nullptr;
+    void* segX = nullptr;     // every x n_v positions of a recomputed segment
+    int *seg_act = nullptr, *seg_kind = nullptr, *seg_face = nullptr, *seg_flag = nullptr;
+    double* seg_bary = nullptr;
+    void* mu = nullptr;
+    R4<double>* g = nullptr;
+    R4<double>* xbar_tet = nullptr;
+    double *xbar_vert = nullptr, *betabar = nullptr, *alpha_part = nullptr, *alpha_d = nullptr, *abar = nullptr;
+    void* finX = nullptr;     // final forward state, restored after the reverse pass
+    int *fin_act = nullptr, *fin_kind = nullptr, *fin_face = nullptr;
+    double *fin_bary = nullptr, *fin_tgt = nullptr;
+    std::vector<void*> allocs;
+  } adj;
+  void free_adj() {
+    for (void* q : adj.allocs) cudaFree(q);
+    adj = Adj();
+  }
 
   int fail(int code, const std::string& msg) {
     err = msg;
@@ -111,6 +135,7 @@ struct casim_sim {
     return q;
   }
   void free_all() {
+    free_adj();
     if (gexec) cudaGraphExecDestroy(gexec);
     gexec = nullptr;
     for (void* q : allocs) cudaFree(q);
@@ -586,6 +611,205 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
 
 }  // extern "C"
 
+
+// ---- adjoint: checkpointed forward and reverse pass ------------------------
+namespace {
+
+template <class X>
+X* adj_alloc(casim_sim* sim, size_t n) {
+  void* q = nullptr;
+  if (cudaMalloc(&q, (n ? n : 1) * sizeof(X)) != cudaSuccess) return nullptr;
+  sim->adj.allocs.push_back(q);
+  return static_cast<X*>(q);
+}
+
+template <typename T>
+int adj_reserve(casim_sim* sim, int n_ckpt, int every) {
+  auto& A = sim->adj;
+  if (A.allocs.size() && A.cap_ckpt >= n_ckpt && A.cap_every >= every) return CASIM_OK;
+  sim->free_adj();
+  const size_t nv = sim->n_v, nq = std::max(sim->n_q, 1), nt = sim->n_t, nf = std::max(sim->n_free, 1);
+  const int ng = std::max(sim->n_groups, 1);
+  A.ckX = adj_alloc<R4<T>>(sim, (size_t)n_ckpt * nv);
+  A.ck_act = adj_alloc<int>(sim, (size_t)n_ckpt * nq);
+  A.ck_kind = adj_alloc<int>(sim, (size_t)n_ckpt * nq);
+  A.ck_face = adj_alloc<int>(sim, (size_t)n_ckpt * nq);
+  A.ck_bary = adj_alloc<double>(sim, (size_t)n_ckpt * 2 * nq);
+  A.ck_tgt = adj_alloc<double>(sim, (size_t)n_ckpt * 3 * nq);
+  A.segX = adj_alloc<R4<T>>(sim, (size_t)every * nv);
+  A.seg_act = adj_alloc<int>(sim, (size_t)every * nq);
+  A.seg_kind = adj_alloc<int>(sim, (size_t)every * nq);
+  A.seg_face = adj_alloc<int>(sim, (size_t)every * nq);
+  A.seg_flag = adj_alloc<int>(sim, (size_t)every * nq);
+  A.seg_bary = adj_alloc<double>(sim, (size_t)every * 2 * nq);
+  A.mu = adj_alloc<R4<T>>(sim, nf);
+  A.g = adj_alloc<R4<double>>(sim, nf);
+  A.xbar_tet = adj_alloc<R4<double>>(sim, 4 * nt);
+  A.xbar_vert = adj_alloc<double>(sim, 3 * nv);
+  A.betabar = adj_alloc<double>(sim, 2 * nq);
+  A.alpha_part = adj_alloc<double>(sim, (size_t)local_blocks(sim->n_t) * ng);
+  A.alpha_d = adj_alloc<double>(sim, ng);
+  A.abar = adj_alloc<double>(sim, ng);
+  A.finX = adj_alloc<R4<T>>(sim, nv);
+  A.fin_act = adj_alloc<int>(sim, nq);
+  A.fin_kind = adj_alloc<int>(sim, nq);
+  A.fin_face = adj_alloc<int>(sim, nq);
+  A.fin_bary = adj_alloc<double>(sim, 2 * nq);
+  A.fin_tgt = adj_alloc<double>(sim, 3 * nq);
+  for (void* q : A.allocs)
+    if (!q) {
+      sim->free_adj();
+      return sim->fail(CASIM_E_CUDA, "cudaMalloc failed (adjoint buffers)");
+    }
+  A.cap_ckpt = n_ckpt;
+  A.cap_every = every;
+  return CASIM_OK;
+}
+
+// copies (positions, spring records) between the live state and a slot
+template <typename T>
+cudaError_t adj_copy_state(casim_sim* sim, void* X, int* act, int* kind, int* face, double* bary, double* tgt,
+                           bool save) {
+  const size_t nv = sim->n_v, nq = sim->n_q;
+  cudaStream_t st = sim->stream;
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st);
+  };
+  cudaError_t e = save ? cp(X, sim->X, sizeof(R4<T>) * nv) : cp(sim->X, X, sizeof(R4<T>) * nv);
+  if (e || nq == 0) return e;
+  if (save) {
+    if ((e = cp(act, sim->sp.active, sizeof(int) * nq))) return e;
+    if ((e = cp(kind, sim->sp.kind, sizeof(int) * nq))) return e;
+    if ((e = cp(face, sim->sp.face, sizeof(int) * nq))) return e;
+    if ((e = cp(bary, sim->sp.bary, sizeof(double) * 2 * nq))) return e;
+    if (tgt) e = cp(tgt, sim->sp.target, sizeof(double) * 3 * nq);
+  } else {
+    if ((e = cp(sim->sp.active, act, sizeof(int) * nq))) return e;
+    if ((e = cp(sim->sp.kind, kind, sizeof(int) * nq))) return e;
+    if ((e = cp(sim->sp.face, face, sizeof(int) * nq))) return e;
+    if ((e = cp(sim->sp.bary, bary, sizeof(double) * 2 * nq))) return e;
+    if (tgt) e = cp(sim->sp.target, tgt, sizeof(double) * 3 * nq);
+  }
+  return e;
+}
+
+template <typename T>
+int forward_ckpt_typed(casim_sim* sim, int n_iters, int every) {
+  const int n_ckpt = (n_iters + every - 1) / every;
+  int rc = adj_reserve<T>(sim, n_ckpt, every);
+  if (rc) return rc;
+  auto& A = sim->adj;
+  const size_t nv = sim->n_v, nq = std::max(sim->n_q, 1);
+  int done = 0;
+  for (int c = 0; c < n_ckpt; ++c) {
+    CK((adj_copy_state<T>(sim, (R4<T>*)A.ckX + c * nv, A.ck_act + c * nq, A.ck_kind + c * nq, A.ck_face + c * nq,
+                          A.ck_bary + c * 2 * nq, A.ck_tgt + c * 3 * nq, true)));
+    const int m = std::min(every, n_iters - done);
+    rc = step_typed<T>(sim, m);
+    if (rc) return rc;
+    done += m;
+  }
+  CK((adj_copy_state<T>(sim, A.finX, A.fin_act, A.fin_kind, A.fin_face, A.fin_bary, A.fin_tgt, true)));
+  A.n_iters = n_iters;
+  A.every = every;
+  A.n_ckpt = n_ckpt;
+  A.valid = true;
+  return CASIM_OK;
+}
+
+template <typename T>
+int backward_typed(casim_sim* sim, const double* dL_dX, double* dL_dalpha) {
+  auto& A = sim->adj;
+  cudaStream_t st = sim->stream;
+  const size_t nv = sim->n_v, nq = std::max(sim->n_q, 1);
+  const int nf = sim->n_free, ng = sim->n_groups;
+  // g = dL/dX_n on the free rows (internal order)
+  std::vector<R4<double>> gh(std::max(nf, 1));
+  for (int uv = 0; uv < sim->n_v; ++uv) {
+    const int i = sim->int_of_user[uv];
+    if (i < nf) gh[i] = R4<double>{dL_dX[3 * (size_t)uv], dL_dX[3 * (size_t)uv + 1], dL_dX[3 * (size_t)uv + 2], 0.0};
+  }
+  CK(cudaMemcpyAsync(A.g, gh.data(), sizeof(R4<double>) * std::max(nf, 1), cudaMemcpyHostToDevice, st));
+  CK(cudaMemsetAsync(A.abar, 0, sizeof(double) * std::max(ng, 1), st));
+  CK(cudaMemsetAsync(A.betabar, 0, sizeof(double) * 2 * nq, st));
+  CK(cudaMemsetAsync(A.xbar_vert, 0, sizeof(double) * 3 * nv, st));
+  if (ng) CK(cudaMemcpyAsync(A.alpha_d, sim->alpha_h.data(), sizeof(double) * ng, cudaMemcpyHostToDevice, st));
+  // keep the history counters of the forward pass
+  Ctrl saved;
+  CK(cudaMemcpyAsync(&saved, sim->ctrl, sizeof(Ctrl), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  Dev<T> d = make_dev<T>(sim);
+  Dev<T> dpcg = d;
+  dpcg.X = (R4<T>*)A.mu;
+  dpcg.b = A.g;
+  for (int c = A.n_ckpt - 1; c >= 0; --c) {
+    const int first = c * A.every;
+    const int m = std::min(A.every, A.n_iters - first);
+    CK((adj_copy_state<T>(sim, (R4<T>*)A.ckX + c * nv, A.ck_act + c * nq, A.ck_kind + c * nq, A.ck_face + c * nq,
+                          A.ck_bary + c * 2 * nq, A.ck_tgt + c * 3 * nq, false)));
+    // recompute the segment, keeping X_i and the spring decisions of each iteration
+    for (int j = 0; j < m; ++j) {
+      CK(cudaMemcpyAsync((R4<T>*)A.segX + j * nv, sim->X, sizeof(R4<T>) * nv, cudaMemcpyDeviceToDevice, st));
+      int rc = step_typed<T>(sim, 1);
+      if (rc) return rc;
+      if (sim->n_q) {
+        CK(cudaMemcpyAsync(A.seg_act + j * nq, sim->sp.active, sizeof(int) * nq, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(A.seg_kind + j * nq, sim->sp.kind, sizeof(int) * nq, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(A.seg_face + j * nq, sim->sp.face, sizeof(int) * nq, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(A.seg_bary + j * 2 * nq, sim->sp.bary, sizeof(double) * 2 * nq, cudaMemcpyDeviceToDevice,
+                           st));
+        launch_adjoint_flags<T>(d, A.seg_flag + j * nq, st);
+      } else {
+        CK(cudaMemsetAsync(A.seg_act + j * nq, 0, sizeof(int) * nq, st));
+      }
+    }
+    // reverse through the segment
+    for (int j = m - 1; j >= 0; --j) {
+      AdjDev<T> a{};
+      a.Xi = (const R4<T>*)A.segX + j * nv;
+      a.mu = (const R4<T>*)A.mu;
+      a.sp_active = A.seg_act + j * nq;
+      a.sp_kind = A.seg_kind + j * nq;
+      a.sp_face = A.seg_face + j * nq;
+      a.sp_bary = A.seg_bary + j * 2 * nq;
+      a.sp_flag = A.seg_flag + j * nq;
+      a.xbar_tet = A.xbar_tet;
+      a.xbar_vert = A.xbar_vert;
+      a.betabar = A.betabar;
+      a.alpha_part = A.alpha_part;
+      a.alpha = A.alpha_d;
+      a.abar = A.abar;
+      a.g = A.g;
+      a.n_groups = ng;
+      if (sim->params.collision == 0 || sim->n_q == 0) {
+        CK(cudaMemsetAsync(A.seg_act + j * nq, 0, sizeof(int) * nq, st));
+      }
+      launch_adjoint_diag<T>(d, a, st);
+      CK(cudaMemsetAsync(A.mu, 0, sizeof(R4<T>) * std::max(nf, 1), st));
+      CK(cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st));
+      cudaError_t e = sim->pcg_cl ? launch_pcg_cluster<T>(dpcg, sim->pcg_clusters, st)
+                                  : launch_pcg<T>(dpcg, sim->pcg_grid, sim->pcg_variant, st);
+      if (e != cudaSuccess) return sim->fail(CASIM_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(e));
+      launch_adjoint_step<T>(d, a, st);
+      CK(cudaGetLastError());
+    }
+  }
+  std::vector<double> ab(std::max(ng, 1));
+  if (ng) CK(cudaMemcpyAsync(ab.data(), A.abar, sizeof(double) * ng, cudaMemcpyDeviceToHost, st));
+  // restore the final forward state and the counters
+  CK((adj_copy_state<T>(sim, A.finX, A.fin_act, A.fin_kind, A.fin_face, A.fin_bary, A.fin_tgt, false)));
+  int st_bits = 0;
+  CK(cudaMemcpyAsync(&st_bits, &sim->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  saved.status |= st_bits;
+  CK(cudaMemcpy(sim->ctrl, &saved, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  for (int gi = 0; gi < ng; ++gi) dL_dalpha[gi] = ab[gi];
+  if (st_bits & (ST_TIMEOUT | ST_NONFINITE)) return sim->fail(CASIM_E_NONFINITE, "adjoint pass: device status");
+  return CASIM_OK;
+}
+
+}  // namespace
+
 // Upload of R >= 1 independent robots given as one concatenated mesh
 // (robot_of_tet says which robot each tet belongs to; robots share no vertex).
 static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz, int32_t n_tets, const int32_t* tets,
@@ -1006,6 +1230,8 @@ int casim_set_actuation(casim_sim* sim, int32_t n_groups, const double* alpha) {
   const int rc = sim->params.precision == CASIM_FP64 ? set_actuation_typed<double>(sim, a)
                                                      : set_actuation_typed<float>(sim, a);
   if (rc) return rc;
+  sim->alpha_h = a;
+  sim->adj.valid = false;
   sim->has_act = true;
   return CASIM_OK;
 }
@@ -1027,6 +1253,7 @@ int casim_set_spheres(casim_sim* sim, int32_t n, const double* cxyzr) {
 
 int casim_set_positions(casim_sim* sim, const double* xyz) {
   if (!sim) return CASIM_E_INVALID;
+  sim->adj.valid = false;
   if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
   if (!xyz) return sim->fail(CASIM_E_INVALID, "null positions");
   for (long long i = 0; i < 3LL * sim->n_v; ++i)
@@ -1056,6 +1283,23 @@ int casim_step(casim_sim* sim, int32_t n_iters) {
   if (n_iters < 0) return sim->fail(CASIM_E_INVALID, "n_iters < 0");
   if (n_iters == 0) return CASIM_OK;
   return sim->params.precision == CASIM_FP64 ? step_typed<double>(sim, n_iters) : step_typed<float>(sim, n_iters);
+}
+
+int casim_forward_ckpt(casim_sim* sim, int32_t n_iters, int32_t ckpt_every) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  if (!sim->has_act) return sim->fail(CASIM_E_STATE, "no actuation set");
+  if (n_iters < 1 || ckpt_every < 1) return sim->fail(CASIM_E_INVALID, "n_iters and ckpt_every must be >= 1");
+  return sim->params.precision == CASIM_FP64 ? forward_ckpt_typed<double>(sim, n_iters, ckpt_every)
+                                             : forward_ckpt_typed<float>(sim, n_iters, ckpt_every);
+}
+
+int casim_backward(casim_sim* sim, const double* dL_dX, double* dL_dalpha) {
+  if (!sim || !dL_dX || (!dL_dalpha && sim->n_groups > 0)) return CASIM_E_INVALID;
+  if (!sim->has_mesh || !sim->adj.valid)
+    return sim->fail(CASIM_E_STATE, "casim_backward needs a preceding casim_forward_ckpt with the same actuation");
+  return sim->params.precision == CASIM_FP64 ? backward_typed<double>(sim, dL_dX, dL_dalpha)
+                                             : backward_typed<float>(sim, dL_dX, dL_dalpha);
 }
 
 int casim_sync(casim_sim* sim) {

@@ -46,6 +46,33 @@ void launch_gather_positions(const Dev<T>& d, const int* int_of_user, int n_user
 template <typename T>
 int pcg_max_grid();
 
+// Device view of one reverse step of the adjoint (iteration i of a segment).
+template <typename T>
+struct AdjDev {
+  const R4<T>* Xi;        // positions X_i (n_v)
+  const R4<T>* mu;        // A_i^-1 g on the free rows
+  const int* sp_active;   // spring records after iteration i's update (n_q)
+  const int* sp_kind;
+  const int* sp_face;
+  const double* sp_bary;  // 2 n_q
+  const int* sp_flag;     // 1: self spring cast in iteration i
+  R4<double>* xbar_tet;   // 4 n_t per-tet pullbacks
+  double* xbar_vert;      // 3 n_v spring pullbacks (FP64 atomics)
+  double* betabar;        // 2 n_q barycentric adjoints of kept springs
+  double* alpha_part;     // local blocks x n_groups
+  const double* alpha;    // n_groups
+  double* abar;           // n_groups, accumulated dL/dalpha
+  R4<double>* g;          // n_free: dL/dX_i on exit
+  int n_groups;
+};
+
+template <typename T>
+void launch_adjoint_step(const Dev<T>& d, const AdjDev<T>& a, cudaStream_t st);
+template <typename T>
+void launch_adjoint_diag(const Dev<T>& d, const AdjDev<T>& a, cudaStream_t st);
+template <typename T>
+void launch_adjoint_flags(const Dev<T>& d, int* flag, cudaStream_t st);
+
 int spring_blocks(int n_q);
 int local_blocks(int n_t);
 int scan_tiles(int n);
