@@ -68,60 +68,66 @@ def test_gpu_adjoint_mixed_close_to_fp64():
     assert np.allclose(g32, g64, rtol=2e-3, atol=2e-3 * np.abs(g64).max())
 
 
-def _decisions(sim):
+def _decisions(sim, n_iters):
+    """Spring decisions of the last run: springs per iteration and the final
+    records (pair counts are left out: a vertex already in contact may gain or
+    lose a second pair without changing any spring)."""
     sp = sim.springs()
     hist = sim.history()
-    return ([h["n_self_pairs"] for h in hist][-20:], [h["n_springs"] for h in hist][-20:],
-            sp["active"].tolist(), sp["kind"].tolist(), sp["face"].tolist())
+    return ([h["n_springs"] for h in hist][-n_iters:], sp["active"].tolist(), sp["kind"].tolist(),
+            sp["face"].tolist())
+
+
+def _fd(sim, m, tips, targets, gi, h, n_iters):
+    vals, decs = [], []
+    for sgn in (1.0, -1.0):
+        a = m.alpha.copy()
+        a[gi] += sgn * h
+        casim.casim_set_actuation(sim.h, a)
+        sim.reset()
+        sim.step(n_iters)
+        assert sim.sync() == 0
+        X = sim.positions()
+        vals.append(float(np.sum((X[tips] - targets) ** 2)))
+        decs.append(_decisions(sim, n_iters))
+    return (vals[0] - vals[1]) / (2 * h), decs
 
 
 def test_gpu_adjoint_central_differences_on_20k_copy():
     """The 20,736-tet copy of the adjoint workload (96x6x6 voxels, 16
-    chambers), FP64 forward, 20 iterations, checkpoints every 5.  A group is
-    compared only when every recorded decision (pair and spring counts of all
-    iterations, final spring records) is the same at alpha +- h."""
+    chambers), FP64 forward, 20 iterations, checkpoints every 5.  With
+    h = 1e-4 a group is compared only where the spring decisions at alpha +- h
+    equal those at alpha; h = 1e-6 differences are compared as well."""
     m = synth.config5_adjoint(nx=96, ny=6, nz=6, n_ch=16, n_iters=20)
     m.precision = synth.PRECISION_FP64
     tips, targets = m.tip_verts, m.tip_targets
     sim = casim.Sim(m)
     L, g, _ = _gpu_grad(sim, m, tips, targets, 20, 5)
-    sim.reset()
     casim.casim_set_actuation(sim.h, m.alpha)
+    sim.reset()
     sim.step(20)
     sim.sync()
-    base = _decisions(sim)
-    h = 1e-4
+    base = _decisions(sim, 20)
     checked = 0
-    for gi in range(m.n_groups):
-        vals = []
-        same = True
-        for sgn in (1.0, -1.0):
-            a = m.alpha.copy()
-            a[gi] += sgn * h
-            casim.casim_set_actuation(sim.h, a)
-            sim.reset()
-            sim.step(20)
-            assert sim.sync() == 0
-            X = sim.positions()
-            vals.append(float(np.sum((X[tips] - targets) ** 2)))
-            same = same and _decisions(sim) == base
-        if not same:
-            continue
-        fd = (vals[0] - vals[1]) / (2 * h)
-        assert abs(g[gi] - fd) <= 1e-4 * max(abs(fd), 1e-2 * np.abs(g).max()), (gi, g[gi], fd)
-        checked += 1
-    assert checked >= 4
+    for gi in range(0, m.n_groups, 2):
+        fd, decs = _fd(sim, m, tips, targets, gi, 1e-4, 20)
+        if decs[0] == base and decs[1] == base:
+            assert abs(g[gi] - fd) <= 1e-4 * abs(fd), (gi, g[gi], fd)
+            checked += 1
+        fd6, _ = _fd(sim, m, tips, targets, gi, 1e-6, 20)
+        assert abs(g[gi] - fd6) <= 5e-5 * abs(fd6), (gi, g[gi], fd6)
+    assert checked >= 3
     sim.close()
 
 
 def test_gpu_adjoint_matches_oracle_adjoint_on_20k_copy():
-    m = synth.config5_adjoint(nx=96, ny=6, nz=6, n_ch=16, n_iters=10)
+    m = synth.config5_adjoint(nx=96, ny=6, nz=6, n_ch=16, n_iters=6)
     m.precision = synth.PRECISION_FP64
     tips, targets = m.tip_verts, m.tip_targets
     sim = casim.Sim(m)
-    L, g, X = _gpu_grad(sim, m, tips, targets, 10, 5)
+    L, g, X = _gpu_grad(sim, m, tips, targets, 6, 3)
     sim.close()
-    Lo, go, Xo, _ = oadj.loss_and_grad(m, 10, tips, targets)
+    Lo, go, Xo, _ = oadj.loss_and_grad(m, 6, tips, targets)
     assert np.abs(X - Xo).max() < 1e-8
     assert np.allclose(g, go, rtol=1e-6, atol=1e-8 * np.abs(go).max()), np.abs(g - go).max()
 
