@@ -84,12 +84,15 @@ typedef struct {
                                    before the kernel gives up with CASIM_E_TIMEOUT;
                                    0 selects the default (about 2 s)                 */
   int32_t pcg_kernel;       /* PCG kernel: 0 auto (one robot: 2 if it fits, else 1;
-                               several robots: 3 if it fits, else 1); 1 streaming
-                               (whole grid, vectors in memory, any size); 2
-                               register-resident (whole grid, one row per thread);
-                               3 cluster (one 16-CTA cluster per robot, vectors in
-                               shared memory).  A forced kernel that does not fit
-                               gives CASIM_E_INVALID at upload                      */
+                               several robots: 4 if it fits, else 3, else 1);
+                               1 streaming (whole grid, vectors in memory, any
+                               size); 2 register-resident (whole grid, one row per
+                               thread); 3 cluster (one 16-CTA cluster per robot,
+                               vectors in shared memory, robots from a work
+                               queue); 4 segmented streaming (blocks assigned to
+                               robots, one CG per robot, shared grid barriers).
+                               A forced kernel that does not fit gives
+                               CASIM_E_INVALID at upload                           */
   int32_t debug_flags;      /* test-only fault injection, 0 in normal use:
                                CASIM_DEBUG_BARRIER_NEVER_COMPLETES makes the PCG
                                grid barrier (kernels 1 and 2; the cluster kernel
@@ -116,7 +119,7 @@ typedef struct {
   int64_t total_pcg_iters;
   casim_iter_record last;   /* record of the most recent iteration                   */
   int32_t status;           /* device status code of the last casim_sync             */
-  int32_t pcg_kernel;       /* PCG kernel chosen at upload (1..3, see casim_params)   */
+  int32_t pcg_kernel;       /* PCG kernel chosen at upload (1..4, see casim_params)   */
 } casim_stats;
 
 /* Fills *p with the defaults: MIXED, self collision, k = 1, eps = 0.005,

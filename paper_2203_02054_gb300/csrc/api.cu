@@ -78,6 +78,10 @@ struct casim_sim {
   bool pcg_rr = false;  // register-resident PCG (one row per thread)
   bool pcg_cl = false;  // cluster PCG (one cluster per robot, work queue)
   int pcg_variant = 1;  // whole-grid kernel: 1 streaming, 2 register-resident
+  bool pcg_seg = false; // segmented streaming PCG (batches: blocks per robot)
+  int seg_blocks = 0;
+  std::vector<int> seg_h;  // 4 x seg_blocks: lo, hi, rb0, rb1
+  int* seg_d = nullptr;
   int pcg_clusters = 0, cl_rows_cap = 0, n_robots = 1;
   int* robot_row = nullptr;
   std::vector<int> robot_row_h;
@@ -219,6 +223,10 @@ Dev<T> make_dev(casim_sim* sim) {
   d.robot_of_vert = sim->robot_of_vert;
   d.robot_of_tet = sim->robot_of_tet;
   d.robot_of_face = sim->robot_of_face;
+  d.seg_lo = sim->seg_d;
+  d.seg_hi = sim->seg_d ? sim->seg_d + sim->seg_blocks : nullptr;
+  d.seg_rb0 = sim->seg_d ? sim->seg_d + 2 * sim->seg_blocks : nullptr;
+  d.seg_rb1 = sim->seg_d ? sim->seg_d + 3 * sim->seg_blocks : nullptr;
   d.robot_row = sim->robot_row;
   d.cl_rows_cap = sim->cl_rows_cap;
   d.wait_budget = sim->params.wait_budget_cycles ? sim->params.wait_budget_cycles : 4000000000ull;
@@ -247,8 +255,9 @@ cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) 
   if (ev) cudaEventRecord(ev[4], st);
   // reset the grid-barrier words (abort, count, generation) before the PCG
   cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st);
-  cudaError_t e = sim->pcg_cl ? launch_pcg_cluster<T>(d, sim->pcg_clusters, st)
-                              : launch_pcg<T>(d, sim->pcg_grid, sim->pcg_variant, st);
+  cudaError_t e = sim->pcg_seg  ? launch_pcg_seg<T>(d, sim->seg_blocks, st)
+                  : sim->pcg_cl ? launch_pcg_cluster<T>(d, sim->pcg_clusters, st)
+                                : launch_pcg<T>(d, sim->pcg_grid, sim->pcg_variant, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[5], st);
   launch_finalize<T>(d, st);
@@ -317,6 +326,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->sp.target = sim->dalloc<double>(3 * (size_t)n_q);
   sim->int_of_user_d = sim->dalloc<int>(n_v);
   sim->robot_row = sim->dalloc<int>(sim->robot_row_h.size());
+  sim->seg_d = sim->seg_blocks ? sim->dalloc<int>(sim->seg_h.size()) : nullptr;
   if (sim->n_robots > 1) {
     sim->robot_of_vert = sim->dalloc<int>(n_v);
     sim->robot_of_tet = sim->dalloc<int>(n_t);
@@ -373,6 +383,8 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   if (n_f) CK(cudaMemcpyAsync(sim->faces, fh.data(), sizeof(int4) * n_f, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->int_of_user_d, sim->int_of_user.data(), sizeof(int) * n_v, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->robot_row, sim->robot_row_h.data(), sizeof(int) * sim->robot_row_h.size(), cudaMemcpyHostToDevice, st));
+  if (sim->seg_blocks)
+    CK(cudaMemcpyAsync(sim->seg_d, sim->seg_h.data(), sizeof(int) * sim->seg_h.size(), cudaMemcpyHostToDevice, st));
   if (sim->n_robots > 1) {
     CK(cudaMemcpyAsync(sim->robot_of_vert, sim->robot_of_vert_h.data(), sizeof(int) * n_v, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(sim->robot_of_tet, sim->robot_of_tet_h.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, st));
@@ -576,7 +588,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.n_w_knots < 0 || (p.n_w_knots > 0 && !p.w_knots) || p.n_w_knots > 64) why = "w_knots";
   else if (!(p.cell_size > 0.0) || !std::isfinite(p.cell_size)) why = "cell_size";
   else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
-  else if (p.pcg_kernel < 0 || p.pcg_kernel > 3) why = "pcg_kernel";
+  else if (p.pcg_kernel < 0 || p.pcg_kernel > 4) why = "pcg_kernel";
   else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
@@ -787,8 +799,9 @@ int backward_typed(casim_sim* sim, const double* dL_dX, double* dL_dalpha) {
       launch_adjoint_diag<T>(d, a, st);
       CK(cudaMemsetAsync(A.mu, 0, sizeof(R4<T>) * std::max(nf, 1), st));
       CK(cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st));
-      cudaError_t e = sim->pcg_cl ? launch_pcg_cluster<T>(dpcg, sim->pcg_clusters, st)
-                                  : launch_pcg<T>(dpcg, sim->pcg_grid, sim->pcg_variant, st);
+      cudaError_t e = sim->pcg_seg  ? launch_pcg_seg<T>(dpcg, sim->seg_blocks, st)
+                      : sim->pcg_cl ? launch_pcg_cluster<T>(dpcg, sim->pcg_clusters, st)
+                                    : launch_pcg<T>(dpcg, sim->pcg_grid, sim->pcg_variant, st);
       if (e != cudaSuccess) return sim->fail(CASIM_E_CUDA, std::string("adjoint solve: ") + cudaGetErrorString(e));
       launch_adjoint_step<T>(d, a, st);
       CK(cudaGetLastError());
@@ -1121,12 +1134,55 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   // kernel (latency bound); several robots share the GPU through the cluster
   // kernel's work queue
   const bool many = sim->n_robots > 1;
-  sim->pcg_cl = (kern == 3) || (kern == 0 && cl_fits && (many || !rr_fits));
-  sim->pcg_rr = !sim->pcg_cl && ((kern == 2) || (kern == 0 && rr_fits));
+  // segmented streaming PCG: every robot needs at least one co-resident block
+  const int seg_max = fp64 ? pcg_seg_max_blocks<double>() : pcg_seg_max_blocks<float>();
+  const bool seg_fits = sim->n_robots <= seg_max && seg_max > 0;
+  if (kern == 4 && !seg_fits) return sim->fail(CASIM_E_INVALID, "segmented PCG: more robots than co-resident blocks");
+  sim->pcg_seg = (kern == 4) || (kern == 0 && many && seg_fits);
+  sim->seg_h.clear();
+  sim->seg_blocks = 0;
+  if (sim->pcg_seg) {
+    // blocks per robot: one each, the rest in proportion to the rows
+    const int R = sim->n_robots;
+    const long long total = std::max(1, n_free);
+    std::vector<int> nb(R);
+    int used = 0;
+    for (int r = 0; r < R; ++r) {
+      const long long rows = sim->robot_row_h[r + 1] - sim->robot_row_h[r];
+      nb[r] = 1 + (int)((rows * (long long)(seg_max - R)) / total);
+      used += nb[r];
+    }
+    std::vector<int> lo, hi, rb0, rb1;
+    int bidx = 0;
+    for (int r = 0; r < R; ++r) {
+      const int r0 = sim->robot_row_h[r], rows = sim->robot_row_h[r + 1] - r0;
+      const int first = bidx;
+      for (int k = 0; k < nb[r]; ++k) {
+        lo.push_back(r0 + (int)((long long)rows * k / nb[r]));
+        hi.push_back(r0 + (int)((long long)rows * (k + 1) / nb[r]));
+        ++bidx;
+      }
+      for (int k = 0; k < nb[r]; ++k) {
+        rb0.push_back(first);
+        rb1.push_back(bidx);
+      }
+    }
+    sim->seg_blocks = used;
+    sim->seg_h.reserve(4 * used);
+    sim->seg_h.insert(sim->seg_h.end(), lo.begin(), lo.end());
+    sim->seg_h.insert(sim->seg_h.end(), hi.begin(), hi.end());
+    sim->seg_h.insert(sim->seg_h.end(), rb0.begin(), rb0.end());
+    sim->seg_h.insert(sim->seg_h.end(), rb1.begin(), rb1.end());
+    sim->pcg_grid = std::max(sim->pcg_grid, used);
+  }
+  sim->pcg_cl = !sim->pcg_seg && ((kern == 3) || (kern == 0 && cl_fits && (many || !rr_fits)));
+  sim->pcg_rr = !sim->pcg_cl && !sim->pcg_seg && ((kern == 2) || (kern == 0 && rr_fits));
   sim->pcg_variant = sim->pcg_rr ? 2 : 1;
   sim->cl_rows_cap = cap;
   sim->pcg_clusters = std::max(1, std::min(max_clusters, sim->n_robots));
-  if (sim->pcg_rr) {
+  if (sim->pcg_seg) {
+    // partials buffer is sized by pcg_grid (already >= seg_blocks)
+  } else if (sim->pcg_rr) {
     sim->pcg_grid = std::max(1, (n_free + PCG_RR_THREADS - 1) / PCG_RR_THREADS);
   } else {
     const int maxg = fp64 ? pcg_max_grid<double>() : pcg_max_grid<float>();
@@ -1460,7 +1516,7 @@ int casim_get_stats(casim_sim* sim, casim_stats* out) {
   out->iterations = c.iter;
   out->total_pcg_iters = c.total_pcg;
   out->status = sim->last_status;
-  out->pcg_kernel = sim->pcg_cl ? 3 : sim->pcg_variant;
+  out->pcg_kernel = sim->pcg_seg ? 4 : sim->pcg_cl ? 3 : sim->pcg_variant;
   if (c.iter > 0) {
     IterRec r;
     CK(cudaMemcpy(&r, sim->hist + ((c.iter - 1) % sim->hist_cap), sizeof(IterRec), cudaMemcpyDeviceToHost));

@@ -116,6 +116,10 @@ struct Dev {
   const int* robot_of_vert;  // n_v (internal order); null for a single robot
   const int* robot_of_tet;   // n_t; null for a single robot
   const int* robot_of_face;  // n_f; null for a single robot
+  const int* seg_lo;     // segmented PCG: per block, first row
+  const int* seg_hi;     //   one past the last row
+  const int* seg_rb0;    //   first block of the block's robot
+  const int* seg_rb1;    //   one past the robot's last block
   unsigned bar_extra;    // 0; 1 = test-only: the barrier expects one more block
   unsigned long long wait_budget;
   // control and statistics

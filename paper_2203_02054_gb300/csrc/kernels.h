@@ -18,6 +18,7 @@ static constexpr int PCG_THREADS = 512;
 static constexpr int PCG_RR_THREADS = 256;
 static constexpr int PCG_RR_MAXW = 16;   // widest sliced-ELL row kept in registers
 static constexpr int PCG_CL_THREADS = 1024;
+static constexpr int PCG_SEG_THREADS = 256;
 static constexpr int PCG_CL_SIZE = 16;   // CTAs per cluster (non-portable size)
 
 template <typename T>
@@ -32,6 +33,10 @@ template <typename T>
 cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st);
 template <typename T>
 int pcg_rr_max_rows();
+template <typename T>
+int pcg_seg_max_blocks();
+template <typename T>
+cudaError_t launch_pcg_seg(const Dev<T>& d, int blocks, cudaStream_t st);
 template <typename T>
 int pcg_cluster_rows_cap();
 template <typename T>

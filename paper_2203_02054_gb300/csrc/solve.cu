@@ -176,7 +176,7 @@ struct GridCtx {
   unsigned extra;  // test-only: arrivals expected beyond the grid (never come)
 };
 
-template <int NV, int NB>
+template <int NV, int NB, bool READ = true>
 __device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& epoch, const double (&bs)[NB],
                                                   double* tot, int* shf) {
   ++epoch;
@@ -213,7 +213,7 @@ __device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& ep
   }
   __syncthreads();
   if (!*shf) return false;
-  if (NV > 0) {
+  if (NV > 0 && READ) {
     if (threadIdx.x < 32) {
       double a[NB];
 #pragma unroll
@@ -261,6 +261,35 @@ __device__ __forceinline__ bool grid_sync_reduce(const GridCtx& g, unsigned& epo
       for (int k = 0; k < NV; ++k) bs[k] += sh[k * 32 + i];
   }
   return grid_publish_wait<NV, NV>(g, epoch, bs, tot, shf);
+}
+
+// Publishes this block's sums of NV values and waits for all blocks; the
+// caller sums whichever partials it needs.
+template <int NV>
+__device__ __forceinline__ bool grid_sync_reduce_local(const GridCtx& g, unsigned& epoch, const double (&v)[NV],
+                                                       double* sh, int* shf) {
+  double t[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    t[k] = v[k];
+    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = t[k];
+  __syncthreads();
+  double bs[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) bs[k] = 0.0;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) bs[k] += sh[k * 32 + i];
+  }
+  return grid_publish_wait<NV, NV, false>(g, epoch, bs, nullptr, shf);
 }
 
 __device__ __forceinline__ bool grid_sync(const GridCtx& g, unsigned& epoch, double* sh, double* tot, int* shf) {
@@ -594,6 +623,197 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
     }
   }
   if (i == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, bb);
+}
+
+// Segmented streaming variant for batches: block b works on a contiguous row
+// range of one robot (every robot owns at least one block; blocks are given
+// to robots in proportion to their rows), so each robot runs its own CG with
+// its own scalars and stopping test while all robots share the two grid
+// barriers of an iteration.  Robot totals are the sums of the partials of the
+// robot's blocks in block order (deterministic).  A robot that has converged
+// stops updating; the launch ends when every robot has converged (a counter
+// that the robot's first block increments, read after the next barrier so
+// every block sees the same value) or at the iteration cap.
+template <typename T>
+__global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
+  __shared__ double sh[96];
+  __shared__ double tot[4];
+  __shared__ int shf;
+  const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget, d.bar_extra};
+  unsigned epoch = 0;
+  const int b = blockIdx.x;
+  const int lo = d.seg_lo[b], hi = d.seg_hi[b];
+  const int rb0 = d.seg_rb0[b], rb1 = d.seg_rb1[b];
+  R4<T>* __restrict__ X = d.X;
+  R4<T>* __restrict__ r = d.r;
+  R4<T>* __restrict__ u = d.u;
+  R4<T>* __restrict__ p = d.p;
+  R4<T>* __restrict__ s = d.s;
+  R4<T>* __restrict__ w = d.w;
+  R4<T>* __restrict__ dx = d.dx;
+  const R4<T> zero = {T(0), T(0), T(0), T(0)};
+  // robot totals of NV values: partials of blocks rb0..rb1 in order
+  auto robot_reduce = [&](const double* v, int nv) -> bool {
+    double t[3];
+    for (int k = 0; k < nv; ++k) t[k] = v[k];
+    if (nv == 2) {
+      const double vv[2] = {t[0], t[1]};
+      if (!grid_sync_reduce_local<2>(g, epoch, vv, sh, &shf)) return false;
+    } else {
+      const double vv[3] = {t[0], t[1], t[2]};
+      if (!grid_sync_reduce_local<3>(g, epoch, vv, sh, &shf)) return false;
+    }
+    const double* buf = g.partials + (size_t)(epoch & 1u) * 4 * g.nblocks;
+    if (threadIdx.x < 32) {
+      double a[3] = {0.0, 0.0, 0.0};
+      for (int q = rb0 + (int)threadIdx.x; q < rb1; q += 32)
+        for (int k = 0; k < nv; ++k) a[k] += __ldcg(buf + 4 * q + k);
+      for (int k = 0; k < nv; ++k) {
+        for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+        if (threadIdx.x == 0) tot[k] = a[k];
+      }
+    }
+    __syncthreads();
+    return true;
+  };
+  double a0[2] = {0.0, 0.0};
+  for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
+    const T dg = d.diag[i];
+    const R4<T> xi = X[i];
+    double ax = (double)dg * xi.x, ay = (double)dg * xi.y, az = (double)dg * xi.z;
+    const int sl = i >> 5, lane = i & 31;
+    const int k1 = d.sl_ptr[sl + 1];
+    for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
+      const double av = (double)d.sl_val[k];
+      const R4<T> xc = X[d.sl_col[k]];
+      ax += av * xc.x;
+      ay += av * xc.y;
+      az += av * xc.z;
+    }
+    const R4<double> bi = d.b[i];
+    const double rx = bi.x - ax, ry = bi.y - ay, rz = bi.z - az;
+    R4<T> ri, ui;
+    ri.x = (T)rx; ri.y = (T)ry; ri.z = (T)rz; ri.w = T(0);
+    ui.x = ri.x / dg; ui.y = ri.y / dg; ui.z = ri.z / dg; ui.w = T(0);
+    r[i] = ri;
+    u[i] = ui;
+    dx[i] = zero;
+    a0[0] += bi.x * bi.x + bi.y * bi.y + bi.z * bi.z;
+    a0[1] += rx * rx + ry * ry + rz * rz;
+  }
+  if (!robot_reduce(a0, 2)) return;
+  const double bb = tot[0];
+  double rr = tot[1];
+  bool done = !(bb > 0.0 && rr > d.tol2 * bb);
+  int it_done = 0;
+  if (done && b == rb0 && threadIdx.x == 0) atomicAdd(&d.ctrl->queue, 1u);
+  double a1[2] = {0.0, 0.0};
+  if (!done) {
+    for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
+      const T dg = d.diag[i];
+      const R4<T> ui = u[i], ri = r[i];
+      T ax, ay, az;
+      spmv_row(d, i, u, dg, ui, ax, ay, az);
+      R4<T> wi;
+      wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
+      w[i] = wi;
+      a1[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
+      a1[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
+    }
+  }
+  if (!robot_reduce(a1, 2)) return;
+  double gamma = tot[0];
+  double alpha = done ? 0.0 : gamma / tot[1];
+  double beta = 0.0;
+  bool first = true;
+  int it = 1;
+  for (;; ++it) {
+    if (!done) {
+      const T ta = (T)alpha, tb = (T)beta;
+      for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
+        const R4<T> ui = u[i], wi = w[i];
+        R4<T> pi, si;
+        if (first) {
+          pi = ui;
+          si = wi;
+        } else {
+          const R4<T> po = p[i], so = s[i];
+          pi.x = ui.x + tb * po.x; pi.y = ui.y + tb * po.y; pi.z = ui.z + tb * po.z;
+          si.x = wi.x + tb * so.x; si.y = wi.y + tb * so.y; si.z = wi.z + tb * so.z;
+        }
+        pi.w = T(0);
+        si.w = T(0);
+        p[i] = pi;
+        s[i] = si;
+        R4<T> di = dx[i], ri = r[i];
+        di.x += ta * pi.x; di.y += ta * pi.y; di.z += ta * pi.z;
+        ri.x -= ta * si.x; ri.y -= ta * si.y; ri.z -= ta * si.z;
+        dx[i] = di;
+        r[i] = ri;
+        const T dg = d.diag[i];
+        R4<T> un;
+        un.x = ri.x / dg; un.y = ri.y / dg; un.z = ri.z / dg; un.w = T(0);
+        u[i] = un;
+      }
+    }
+    if (!grid_sync(g, epoch, sh, tot, &shf)) return;
+    // every block reads the same count: increments happen before this barrier
+    const unsigned n_done = __ldcg(&d.ctrl->queue);
+    if ((int)n_done >= d.n_robots || it > d.max_iter) break;
+    double a2[3] = {0.0, 0.0, 0.0};
+    if (!done) {
+      for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
+        const T dg = d.diag[i];
+        const R4<T> ui = u[i], ri = r[i];
+        T ax, ay, az;
+        spmv_row(d, i, u, dg, ui, ax, ay, az);
+        R4<T> wi;
+        wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
+        w[i] = wi;
+        a2[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
+        a2[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
+        a2[2] += (double)ri.x * ri.x + (double)ri.y * ri.y + (double)ri.z * ri.z;
+      }
+    }
+    if (!robot_reduce(a2, 3)) return;
+    if (!done) {
+      const double gnew = tot[0], delta = tot[1];
+      rr = tot[2];
+      if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
+        if (b == rb0 && threadIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
+        done = true;
+      } else if (rr <= d.tol2 * bb) {
+        done = true;
+      } else {
+        beta = gnew / gamma;
+        alpha = gnew / (delta - beta * gnew / alpha);
+        gamma = gnew;
+        first = false;
+      }
+      if (done) {
+        it_done = it;
+        if (b == rb0 && threadIdx.x == 0) atomicAdd(&d.ctrl->queue, 1u);
+      }
+    }
+  }
+  if (!done) {
+    it_done = d.max_iter;
+    if (b == rb0 && threadIdx.x == 0) set_status(d.ctrl, ST_PCG_MAXIT);
+  }
+  for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
+    R4<T> xi = X[i];
+    const R4<T> di = dx[i];
+    xi.x += di.x; xi.y += di.y; xi.z += di.z;
+    X[i] = xi;
+  }
+  if (b == rb0 && threadIdx.x == 0) {
+    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
+    atomicMax(&rec->pcg_iters, it_done);
+    atomicAdd(reinterpret_cast<unsigned long long*>(&d.ctrl->total_pcg), (unsigned long long)it_done);
+    const double rel = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+    atomicMax(reinterpret_cast<unsigned long long*>(&rec->pcg_rel_residual),
+              (unsigned long long)__double_as_longlong(rel));
+  }
 }
 
 // Cluster variant: one thread-block cluster of PCG_CL_SIZE CTAs solves one
@@ -979,6 +1199,34 @@ cudaError_t launch_pcg_cluster(const Dev<T>& d, int n_clusters, cudaStream_t st)
   return cudaLaunchKernelEx(&cfg, k_pcg_cluster<T>, d);
 }
 
+template <typename T>
+int pcg_seg_max_blocks() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_seg<T>, PCG_SEG_THREADS, 0);
+  return sms * per;
+}
+
+template <typename T>
+cudaError_t launch_pcg_seg(const Dev<T>& d, int blocks, cudaStream_t st) {
+  if (d.n_free == 0) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(PCG_SEG_THREADS);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg_seg<T>, d);
+}
+
+template int pcg_seg_max_blocks<float>();
+template int pcg_seg_max_blocks<double>();
+template cudaError_t launch_pcg_seg<float>(const Dev<float>&, int, cudaStream_t);
+template cudaError_t launch_pcg_seg<double>(const Dev<double>&, int, cudaStream_t);
 template int pcg_cluster_rows_cap<float>();
 template int pcg_cluster_rows_cap<double>();
 template int pcg_cluster_max_clusters<float>(int);

@@ -73,9 +73,11 @@ def test_batch_mixed_one_iteration_replay_and_robot_isolation():
     sim.close()
 
 
-def test_batch_matches_plain_runs_on_gpu():
+@pytest.mark.parametrize("kernel", [3, 4])
+def test_batch_matches_plain_runs_on_gpu(kernel):
     batch = _small_batch(synth.PRECISION_MIXED, 10)
-    sim = casim.Sim(batch)
+    sim = casim.Sim(batch, pcg_kernel=kernel)
+    assert sim.stats().pcg_kernel == kernel
     sim.step(10)
     assert sim.sync() == 0
     X = sim.positions()
