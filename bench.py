@@ -240,6 +240,92 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------- batched and adjoint forms
+def _event_ms(stream, fn):
+    import torch
+
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b)
+
+
+def bench_batched(stream, plain_value, n_iters=100, n_seq=16):
+    """256 independent fingers (12.1M tets) in one simulation, 100 iterations
+    per step, against the same robots solved one after another (a seeded
+    subset of ``n_seq`` robots, scaled by tets)."""
+    import numpy as np
+
+    from paper_2203_02054_gb300 import casim, synth
+
+    batch = synth.config4_batch(n_iters=n_iters)
+    n_t = sum(m.n_tets for m in batch)
+    sim = casim.Sim(batch, stream=stream.cuda_stream, stats=0)
+    kern = sim.stats().pcg_kernel
+    step = lambda: (casim.casim_reset(sim.h), casim.casim_step(sim.h, n_iters))
+    casim.casim_reset(sim.h)
+    casim.casim_step(sim.h, 5)
+    casim.casim_sync(sim.h)
+    ms = _event_ms(stream, step)
+    status = casim.casim_sync(sim.h)
+    st = casim.casim_get_stats(sim.h)
+    sim.close()
+    rng = np.random.default_rng(1004)
+    sub = sorted(rng.choice(len(batch), n_seq, replace=False).tolist())
+    seq_ms = 0.0
+    seq_t = 0
+    for r in sub:
+        one = casim.Sim(batch[r], stream=stream.cuda_stream, stats=0)
+        f = lambda: (casim.casim_reset(one.h), casim.casim_step(one.h, n_iters))
+        casim.casim_step(one.h, 2)
+        casim.casim_sync(one.h)
+        seq_ms += _event_ms(stream, f)
+        seq_t += batch[r].n_tets
+        one.close()
+    value = n_t * n_iters / (ms / 1e3)
+    seq_value = seq_t * n_iters / (seq_ms / 1e3)
+    return {"workload": "256 pneumatic fingers (20k x 4k x 4k voxels, k~U{1..4}, 4-10 chambers), "
+                        "12,119,040 tets, self-collision per robot", "n_robots": len(batch), "n_tets": n_t,
+            "n_iters": n_iters, "value": value, "unit": UNIT, "ms_per_step": ms, "device_status": status,
+            "pcg_kernel": kern, "k_pcg_max_mean": st.total_pcg_iters / max(1, st.iterations) / len(batch),
+            "sequential": {"robots": n_seq, "value": seq_value, "how": "each robot alone, same GPU, scaled by tets"},
+            "vs_sequential": value / seq_value, "vs_plain": value / plain_value}
+
+
+def bench_adjoint(stream, n_iters=100, every=10):
+    """Adjoint workload: 983,040-tet finger (160x32x32, 16 chambers), loss on
+    64 tip vertices, checkpointed forward + reverse pass through 100
+    iterations, against the plain forward of the same iterations."""
+    import numpy as np
+
+    from paper_2203_02054_gb300 import casim, synth
+
+    m = synth.config5_adjoint(n_iters=n_iters)
+    sim = casim.Sim(m, stream=stream.cuda_stream, stats=0)
+    casim.casim_step(sim.h, 2)
+    casim.casim_sync(sim.h)
+    fwd_ms = _event_ms(stream, lambda: (casim.casim_reset(sim.h), casim.casim_step(sim.h, n_iters)))
+    ck_ms = _event_ms(stream, lambda: (casim.casim_reset(sim.h), casim.casim_forward_ckpt(sim.h, n_iters, every)))
+    X = sim.positions()
+    gX = np.zeros_like(X)
+    gX[m.tip_verts] = 2.0 * (X[m.tip_verts] - m.tip_targets)
+    t0 = time.perf_counter()
+    grad = casim.casim_backward(sim.h, gX, m.n_groups)
+    bwd_ms = 1e3 * (time.perf_counter() - t0)
+    sim.close()
+    plain = m.n_tets * n_iters / (fwd_ms / 1e3)
+    value = m.n_tets * n_iters / ((ck_ms + bwd_ms) / 1e3)
+    return {"workload": "finger 160x32x32 voxels, 16 chambers, 983,040 tets; loss on 64 tip vertices; "
+                        "checkpoint every 10", "n_tets": m.n_tets, "n_iters": n_iters, "value": value,
+            "unit": UNIT + " (forward + backward)", "forward_ms": ck_ms, "backward_ms": bwd_ms,
+            "plain_forward_value": plain, "vs_plain_forward": value / plain,
+            "grad_finite": bool(np.all(np.isfinite(grad))), "grad_norm": float(np.linalg.norm(grad))}
+
+
 # -------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -366,6 +452,8 @@ def main():
                                      "max_springs": max(h["n_springs"] for h in hist),
                                      "final_springs": hist[-1]["n_springs"]}},
         }
+        line["batched"] = bench_batched(stream, value)
+        line["adjoint"] = bench_adjoint(stream)
         # ---- CPU baseline: the oracle on a bounded sample of the same workload ----
         for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             os.environ.setdefault(v, "1")
