@@ -52,6 +52,9 @@ extern "C" {
 #define CASIM_E_TIMEOUT (-7)   /* a device-side wait ran out of its budget       */
 #define CASIM_E_OVERFLOW (-8)  /* a device work list exceeded its capacity       */
 #define CASIM_W_PCG_MAXIT 1    /* PCG stopped at its iteration cap (warning)     */
+#define CASIM_W_PAIRS_TRUNCATED 2 /* a vertex lay in more tets than
+                                     max_pairs_per_vertex; its pair list (not its
+                                     spring) was truncated (warning)             */
 
 /* ---- precision modes ---------------------------------------------------- */
 #define CASIM_FP64 0   /* every quantity in FP64                                  */
@@ -211,7 +214,9 @@ int casim_forward_ckpt(casim_sim* sim, int32_t n_iters, int32_t ckpt_every);
 int casim_backward(casim_sim* sim, const double* dL_dX, double* dL_dalpha);
 
 /* Waits for the stream and returns the device status: CASIM_OK,
-   CASIM_W_PCG_MAXIT, CASIM_E_NONFINITE, CASIM_E_TIMEOUT or CASIM_E_OVERFLOW.
+   CASIM_W_PCG_MAXIT, CASIM_W_PAIRS_TRUNCATED, CASIM_E_NONFINITE,
+   CASIM_E_TIMEOUT or CASIM_E_OVERFLOW (a tet's box spans more than 512 hash
+   cells or the hash entries exceed 16 per tet and face: contacts may be lost).
    The device status is cleared after it is read. */
 int casim_sync(casim_sim* sim);
 
@@ -226,8 +231,8 @@ int casim_get_positions(casim_sim* sim, double* host_out, void* dev_out);
    vertices inside an obstacle sphere (sorted) into obstacle_verts.  On entry
    *n_pairs / *n_obst hold the capacities (in pairs / vertices); on exit the
    counts.  Returns CASIM_E_CAPACITY (with the counts set) when too small.
-   A vertex whose self pairs exceeded max_pairs_per_vertex sets the
-   CASIM_E_OVERFLOW device status. */
+   A vertex whose self pairs exceeded max_pairs_per_vertex keeps the smallest
+   tet ids and sets the CASIM_W_PAIRS_TRUNCATED device status. */
 int casim_get_contacts(casim_sim* sim, int32_t* pairs, int64_t* n_pairs, int32_t* obstacle_verts,
                        int64_t* n_obst);
 

@@ -30,6 +30,7 @@ CASIM_E_NONFINITE = -6
 CASIM_E_TIMEOUT = -7
 CASIM_E_OVERFLOW = -8
 CASIM_W_PCG_MAXIT = 1
+CASIM_W_PAIRS_TRUNCATED = 2
 
 CASIM_FP64 = 0
 CASIM_MIXED = 1

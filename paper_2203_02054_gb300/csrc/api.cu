@@ -816,6 +816,8 @@ int backward_typed(casim_sim* sim, const double* dL_dX, double* dL_dalpha) {
   CK(cudaStreamSynchronize(st));
   saved.status |= st_bits;
   CK(cudaMemcpy(sim->ctrl, &saved, sizeof(Ctrl), cudaMemcpyHostToDevice));
+  // the recomputation used the history slots from here on: clear the next one
+  CK(cudaMemset(sim->hist + (saved.iter % sim->hist_cap), 0, sizeof(IterRec)));
   for (int gi = 0; gi < ng; ++gi) dL_dalpha[gi] = ab[gi];
   if (st_bits & (ST_TIMEOUT | ST_NONFINITE)) return sim->fail(CASIM_E_NONFINITE, "adjoint pass: device status");
   return CASIM_OK;
@@ -1370,6 +1372,7 @@ int casim_sync(casim_sim* sim) {
   else if (st & ST_NONFINITE) rc = CASIM_E_NONFINITE;
   else if (st & ST_OVERFLOW) rc = CASIM_E_OVERFLOW;
   else if (st & ST_PCG_MAXIT) rc = CASIM_W_PCG_MAXIT;
+  else if (st & ST_PAIRS_TRUNC) rc = CASIM_W_PAIRS_TRUNCATED;
   sim->last_status = rc;
   if (rc < 0) sim->err = "device status " + std::to_string(st);
   return rc;

@@ -257,7 +257,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
     }
     int best = -1;
     if (lane == 0) {
-      if (over) set_status(d.ctrl, ST_OVERFLOW);
+      if (over) set_status(d.ctrl, ST_PAIRS_TRUNC);
       d.pair_count[qi] = cnt;
       n_self = cnt;
       if (d.collision >= 2) {

@@ -30,6 +30,7 @@ enum : int {
   ST_TIMEOUT = 2,
   ST_PCG_MAXIT = 4,
   ST_OVERFLOW = 8,
+  ST_PAIRS_TRUNC = 16,   // a vertex had more self pairs than max_pairs_per_vertex
 };
 
 struct IterRec {

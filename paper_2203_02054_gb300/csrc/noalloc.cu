@@ -160,6 +160,7 @@ extern "C" int casim_contacts_noalloc(int32_t n_verts, const float* dev_xyz, int
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(CASIM_E_CUDA, std::string("contact check: ") + cudaGetErrorString(e));
   if (status & ST_NONFINITE) return fail(CASIM_E_NONFINITE, "non-finite position");
-  if (status & ST_OVERFLOW) return fail(CASIM_E_OVERFLOW, "more contacts or hash entries than the scratch holds");
+  if (status & (ST_OVERFLOW | ST_PAIRS_TRUNC))
+    return fail(CASIM_E_OVERFLOW, "more contacts or hash entries than the scratch holds");
   return CASIM_OK;
 }
