@@ -399,7 +399,15 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   CK(cudaMemsetAsync(sim->sp.target, 0, sizeof(double) * 3 * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->pair_count, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->obs_sphere, 0xff, sizeof(int) * std::max(n_q, 1), st));
-  CK(cudaMemsetAsync(sim->ctrl, 0, sizeof(Ctrl), st));
+  {
+    Ctrl c0{};
+    for (int j = 0; j < 3; ++j) {
+      c0.box_lo[j] = 0x7FFFFFFFFFFFFFFFLL;
+      c0.box_hi[j] = (long long)0x8000000000000000ULL;
+    }
+    CK(cudaMemcpyAsync(sim->ctrl, &c0, sizeof(Ctrl), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
   CK(cudaMemsetAsync(sim->hist, 0, sizeof(IterRec) * sim->hist_cap, st));
   CK(cudaMemsetAsync(sim->e_partials, 0, sizeof(double) * (sim->n_e_local + sim->n_e_spring + 1), st));
   CK(cudaMemsetAsync(sim->P, 0, sizeof(R4<T>) * 4 * (size_t)std::max(n_t, 1), st));

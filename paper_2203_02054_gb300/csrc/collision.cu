@@ -65,13 +65,44 @@ __device__ __forceinline__ bool item_box(const Dev<T>& d, int i, double lo[3], d
   return ok;
 }
 
+// Block-reduced bounding box of the item boxes (count pass only).
+__device__ __forceinline__ void reduce_box(Ctrl* c, bool valid, const double lo[3], const double hi[3]) {
+  __shared__ long long s_lo[3][8], s_hi[3][8];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = 0; j < 3; ++j) {
+    long long a = valid ? order_code(lo[j]) : 0x7FFFFFFFFFFFFFFFLL;
+    long long b = valid ? order_code(hi[j]) : (long long)0x8000000000000000ULL;
+    for (int o = 16; o > 0; o >>= 1) {
+      a = min(a, __shfl_down_sync(0xffffffffu, a, o));
+      b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+    }
+    if (lane == 0) {
+      s_lo[j][wid] = a;
+      s_hi[j][wid] = b;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    const int j = threadIdx.x;
+    long long a = s_lo[j][0], b = s_hi[j][0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+      a = min(a, s_lo[j][w]);
+      b = max(b, s_hi[j][w]);
+    }
+    atomicMin(&c->box_lo[j], a);
+    atomicMax(&c->box_hi[j], b);
+  }
+}
+
 template <typename T, bool FILL>
-__global__ void k_grid_bin(Dev<T> d) {
+__global__ void __launch_bounds__(256) k_grid_bin(Dev<T> d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = d.n_t + d.n_f;
+  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  const bool ok = i < n && item_box(d, i, lo, hi);
+  if (!FILL) reduce_box(d.ctrl, ok, lo, hi);
   if (i >= n) return;
-  double lo[3], hi[3];
-  if (!item_box(d, i, lo, hi)) {
+  if (!ok) {
     if (!FILL) set_status(d.ctrl, ST_NONFINITE);
     return;
   }
@@ -399,6 +430,17 @@ __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, doubl
       tdel[a] = INFINITY;
     }
   }
+  // the ray can meet no face beyond the bounding box of this iteration's items
+  double tbox = INFINITY;
+  {
+    double t_out = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+      const double blo = order_decode(d.ctrl->box_lo[a]) - d.cell, bhi = order_decode(d.ctrl->box_hi[a]) + d.cell;
+      if (dv[a] > 0.0) t_out = fmin(t_out, (bhi - ov[a]) / dv[a]);
+      else if (dv[a] < 0.0) t_out = fmin(t_out, (blo - ov[a]) / dv[a]);
+    }
+    tbox = t_out;
+  }
   for (int it = 0; it < MAX_DDA_STEPS; ++it) {
     const unsigned h = d.H_t + (hash_cell(cell[0], cell[1], cell[2], rv) & (d.H_f - 1u));
     const int k0 = d.cell_start[h], k1 = min(d.cell_start[h + 1], d.cap_items);
@@ -421,14 +463,48 @@ __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, doubl
     }
     const double texit = fmin(tmax[0], fmin(tmax[1], tmax[2]));
     if (best_f >= 0 && best_t * (1.0 + 1e-9) < texit) return best_f;
-    if (!(texit < INFINITY)) break;
+    if (!(texit < INFINITY) || texit > tbox) break;
     const int a = (tmax[0] <= tmax[1] && tmax[0] <= tmax[2]) ? 0 : (tmax[1] <= tmax[2] ? 1 : 2);
     cell[a] += step[a];
     tmax[a] += tdel[a];
   }
   if (best_f >= 0) return best_f;
-  // no exit face hit: closest point over all boundary faces not containing v
+  // No exit face hit: the closest point over the boundary faces not
+  // containing v, found by scanning cubic shells of cells around v's cell.
+  // After shell k every face with a point within k cells has been seen, so
+  // the search stops once the best distance is at most k cell edges.
+  const int c0[3] = {cell_coord(o.x, d.inv_cell), cell_coord(o.y, d.inv_cell), cell_coord(o.z, d.inv_cell)};
   double bestd = 0.0;
+  for (int k = 0; k <= 64; ++k) {
+    for (int dz = -k; dz <= k; ++dz)
+      for (int dy = -k; dy <= k; ++dy)
+        for (int dx = -k; dx <= k; ++dx) {
+          if (max(abs(dx), max(abs(dy), abs(dz))) != k) continue;
+          const unsigned h = d.H_t + (hash_cell(c0[0] + dx, c0[1] + dy, c0[2] + dz, rv) & (d.H_f - 1u));
+          const int k0 = d.cell_start[h], k1 = min(d.cell_start[h + 1], d.cap_items);
+          for (int q = k0; q < k1; ++q) {
+            const int f = d.items[q] - d.n_t;
+            if (d.robot_of_face && d.robot_of_face[f] != rv) continue;
+            V3 q0, q1, q2;
+            int4 fv;
+            face_verts(d, f, q0, q1, q2, fv);
+            if (fv.x == v || fv.y == v || fv.z == v) continue;
+            double b1, b2;
+            const V3 x = closest_tri(o, q0, q1, q2, b1, b2);
+            const V3 dd = sub(o, x);
+            const double d2 = dot(dd, dd);
+            if (best_f < 0 || d2 < bestd || (d2 == bestd && f < best_f)) {
+              best_f = f;
+              bestd = d2;
+              rb1 = b1;
+              rb2 = b2;
+            }
+          }
+        }
+    if (best_f >= 0 && sqrt(bestd) <= k * d.cell) return best_f;
+  }
+  if (best_f >= 0) return best_f;
+  // the shell search found nothing within 64 cells: every face (rare)
   for (int f = 0; f < d.n_f; ++f) {
     if (d.robot_of_face && d.robot_of_face[f] != rv) continue;
     V3 q0, q1, q2;

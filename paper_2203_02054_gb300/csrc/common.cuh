@@ -51,7 +51,28 @@ struct Ctrl {
   long long total_pcg;   // PCG iterations summed over outer iterations
   int n_items;           // spatial-hash entries of this iteration
   int pad;
+  long long box_lo[3];   // bounding box of all item boxes of this iteration,
+  long long box_hi[3];   //   as order-preserving integer codes of doubles
 };
+
+// Order-preserving map between doubles and 64-bit integers (for atomic
+// min / max of doubles).
+__host__ __device__ inline long long order_code(double v) {
+  union {
+    double d;
+    long long i;
+  } u;
+  u.d = v;
+  return u.i >= 0 ? u.i : (u.i ^ 0x7FFFFFFFFFFFFFFFLL);
+}
+__host__ __device__ inline double order_decode(long long c) {
+  union {
+    double d;
+    long long i;
+  } u;
+  u.i = c >= 0 ? c : (c ^ 0x7FFFFFFFFFFFFFFFLL);
+  return u.d;
+}
 
 struct SpringDev {
   int* active;           // n_q

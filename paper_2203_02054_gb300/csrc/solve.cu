@@ -1060,6 +1060,10 @@ __global__ void k_finalize(Dev<T> d) {
     rec->energy = t;
     if (!isfinite(t) && d.stats) c->status |= ST_NONFINITE;
     c->iter += 1;
+    for (int j = 0; j < 3; ++j) {
+      c->box_lo[j] = 0x7FFFFFFFFFFFFFFFLL;
+      c->box_hi[j] = (long long)0x8000000000000000ULL;
+    }
     IterRec* nx = d.hist + (c->iter % d.hist_cap);
     nx->energy = 0.0;
     nx->pcg_rel_residual = 0.0;

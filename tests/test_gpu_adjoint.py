@@ -99,7 +99,10 @@ def test_gpu_adjoint_central_differences_on_20k_copy(n_iters, h, need):
     chambers), FP64 forward, checkpoints every 5.  A group is compared only
     where the spring decisions at alpha +- h equal those at alpha (over 20
     iterations some release test lies within h's reach for most groups, so the
-    h = 1e-4 check runs 8 iterations)."""
+    h = 1e-4 check runs 8 iterations).  The strain table w(eps) is piecewise
+    linear, so a difference with h = 1e-4 may also straddle a knot crossing of
+    some body tet: most eligible groups must agree within 1e-4, all within
+    1e-3; with h = 1e-6 every eligible group must agree within 1e-4."""
     m = synth.config5_adjoint(nx=96, ny=6, nz=6, n_ch=16, n_iters=n_iters)
     m.precision = synth.PRECISION_FP64
     tips, targets = m.tip_verts, m.tip_targets
@@ -111,12 +114,16 @@ def test_gpu_adjoint_central_differences_on_20k_copy(n_iters, h, need):
     sim.sync()
     base = _decisions(sim, n_iters)
     checked = 0
+    close = 0
     for gi in range(m.n_groups):
         fd, decs = _fd(sim, m, tips, targets, gi, h, n_iters)
         if decs[0] == base and decs[1] == base:
-            assert abs(g[gi] - fd) <= 1e-4 * abs(fd), (gi, g[gi], fd)
+            rel = abs(g[gi] - fd) / abs(fd)
+            assert rel <= (1e-4 if h < 1e-5 else 1e-3), (gi, g[gi], fd)
+            close += rel <= 1e-4
             checked += 1
     assert checked >= need, checked
+    assert close >= max(need, (3 * checked) // 4), (close, checked)
     sim.close()
 
 
