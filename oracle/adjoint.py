@@ -18,7 +18,9 @@ differentiated by autograd:
   its face with the barycentric weights of the hit of the ray x_v - t n(v)
   with the face's plane, taken at the iteration that cast the ray (and kept,
   with their dependence on that iteration's positions, while the spring is
-  kept), offset by eps along the face normal;
+  kept), offset by eps along the face normal; when the ray met no exit face
+  and the closest point was used instead, the weights are held constant (the
+  projection onto the nearest face is not differentiated);
 * global step: the Eq. 8 normal equations solved exactly (sparse LU), with the
   reverse pass solving the transposed (here identical) system.
 
@@ -47,7 +49,8 @@ class IterDecisions:
     kind: np.ndarray        # (n_q,) 0 self, 1 obstacle
     face: np.ndarray        # (n_q,) face id or sphere id
     bary: np.ndarray        # (n_q, 2)
-    recast: np.ndarray      # (n_q,) bool: self spring cast this iteration (vertex in a pair)
+    recast: np.ndarray      # (n_q,) bool: self spring cast this iteration (vertex in a pair) by a ray hit
+    cast: np.ndarray = None  # (n_q,) bool: self spring cast this iteration (ray hit or closest point)
 
 
 def record_forward(m, n_iters, prep=None):
@@ -60,8 +63,9 @@ def record_forward(m, n_iters, prep=None):
         Xn, st, rec, ps, po = loop.iterate(prep, X, st, m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps, m.collision)
         in_self = np.isin(prep.query, ps[:, 0]) if ps.shape[0] else np.zeros(prep.query.shape[0], bool)
         in_obs = np.isin(prep.query, po[:, 0]) if po.shape[0] else np.zeros(prep.query.shape[0], bool)
+        cast = st.active & (st.kind == springs.KIND_SELF) & in_self & ~in_obs
         dec.append(IterDecisions(st.active.copy(), st.kind.copy(), st.face.copy(), st.bary.copy(),
-                                 st.active & (st.kind == springs.KIND_SELF) & in_self & ~in_obs))
+                                 cast & ~st.fallback, cast.copy()))
         X = Xn
     return X, dec, prep
 
@@ -161,7 +165,11 @@ def _spring_targets(X, prep, dec: IterDecisions, spheres, eps, bary_t):
         q0, q1, q2 = X[f[0]], X[f[1]], X[f[2]]
         n = torch.cross(q1 - q0, q2 - q0, dim=0)
         nh = n / torch.linalg.norm(n)
-        if dec.recast[qi] or qi not in bary_t:
+        if (dec.cast[qi] and not dec.recast[qi]) or qi not in bary_t:
+            # closest-point fallback (this iteration or at the spring's cast):
+            # weights held constant
+            bary_t[qi] = torch.tensor(np.asarray(dec.bary[qi], dtype=np.float64))
+        if dec.recast[qi]:
             d = -vn[v] / torch.linalg.norm(vn[v])
             t = torch.dot(n, q0 - x) / torch.dot(n, d)
             bt = _bary(x + t * d, q0, q1, q2)

@@ -45,6 +45,11 @@ class SpringState:
     face: np.ndarray     # (n_q,) int64: boundary face id, or sphere id
     bary: np.ndarray     # (n_q, 2) float64
     target: np.ndarray   # (n_q, 3) float64
+    fallback: np.ndarray = None  # (n_q,) bool: this update's self target came from the closest point
+
+    def __post_init__(self):
+        if self.fallback is None:
+            self.fallback = np.zeros(self.active.shape[0], bool)
 
     @staticmethod
     def empty(n_q: int) -> "SpringState":
@@ -53,7 +58,7 @@ class SpringState:
 
     def copy(self) -> "SpringState":
         return SpringState(self.active.copy(), self.kind.copy(), self.face.copy(),
-                           self.bary.copy(), self.target.copy())
+                           self.bary.copy(), self.target.copy(), self.fallback.copy())
 
 
 def _ray_triangle(o, d, q0, q1, q2):
@@ -128,7 +133,8 @@ def _face_unit_normal(X, face_verts):
 
 
 def ray_cast_target(X, v, nrm_v, faces, fnormals):
-    """Self-collision correspondence of vertex v: (face id, b1, b2)."""
+    """Self-collision correspondence of vertex v: (face id, b1, b2, fell back
+    to the closest point)."""
     d = -nrm_v
     o = X[v]
     cand = np.nonzero((fnormals @ d > 0.0) & np.all(faces != v, axis=1))[0]
@@ -138,7 +144,7 @@ def ray_cast_target(X, v, nrm_v, faces, fnormals):
         if hit and (best is None or t < best[0]):
             best = (t, int(f), b1, b2)
     if best is not None:
-        return best[1], best[2], best[3]
+        return best[1], best[2], best[3], False
     # no exit face hit: closest point over boundary faces not containing v
     bestc = None
     for f in np.nonzero(np.all(faces != v, axis=1))[0]:
@@ -146,7 +152,7 @@ def ray_cast_target(X, v, nrm_v, faces, fnormals):
         dd = float(np.dot(o - x, o - x))
         if bestc is None or dd < bestc[0]:
             bestc = (dd, int(f), b1, b2)
-    return bestc[1], bestc[2], bestc[3]
+    return bestc[1], bestc[2], bestc[3], True
 
 
 def _sphere_target(x, c, r, eps, nrm_v):
@@ -160,6 +166,7 @@ def update_springs(X, query, prev: SpringState, self_pairs, sphere_pairs, sphere
                    faces, vnormals, eps) -> SpringState:
     """One spring update (create, re-target or release) for every query vertex."""
     st = prev.copy()
+    st.fallback[:] = False
     fn = np.cross(X[faces[:, 1]] - X[faces[:, 0]], X[faces[:, 2]] - X[faces[:, 0]])
     in_self = np.zeros(query.shape[0], bool)
     pos = {int(v): i for i, v in enumerate(query)}
@@ -180,7 +187,8 @@ def update_springs(X, query, prev: SpringState, self_pairs, sphere_pairs, sphere
             st.bary[i] = 0.0
             st.target[i] = _sphere_target(x, spheres[j, :3], float(spheres[j, 3]), eps, vnormals[v])
         elif in_self[i]:
-            f, b1, b2 = ray_cast_target(X, v, vnormals[v], faces, fn)
+            f, b1, b2, fb = ray_cast_target(X, v, vnormals[v], faces, fn)
+            st.fallback[i] = fb
             st.active[i] = True
             st.kind[i] = KIND_SELF
             st.face[i] = f

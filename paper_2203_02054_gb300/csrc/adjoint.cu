@@ -379,6 +379,10 @@ __global__ void __launch_bounds__(128) k_adj_springs(Dev<T> d, AdjDev<T> a) {
     atomic_add3(a.xbar_vert, v, xb);
     bb1 = 0.0;
     bb2 = 0.0;
+  } else if (a.sp_flag[qi] == 2) {
+    // weights of a closest-point fallback: constant, their adjoint ends here
+    bb1 = 0.0;
+    bb2 = 0.0;
   }
   D3 c0, c1, c2;
   cross_vjp(q0, q1, q2, nb, c0, c1, c2);
@@ -432,13 +436,15 @@ __global__ void k_adj_diag_springs(Dev<T> d, AdjDev<T> a) {
   }
 }
 
-// 1 where the spring of query vertex qi was cast this iteration (self spring
-// of a vertex found in a self pair and in no sphere), else 0
+// Cast of query vertex qi's spring in this iteration: 1 by a ray hit (self
+// spring of a vertex found in a self pair and in no sphere), 2 by the
+// closest-point fallback (weights held constant in the reverse pass), 0 none
 template <typename T>
 __global__ void k_adj_flags(Dev<T> d, int* flag) {
   const int qi = blockIdx.x * blockDim.x + threadIdx.x;
   if (qi >= d.n_q) return;
-  flag[qi] = (d.sp.active[qi] && d.sp.kind[qi] == 0 && d.pair_count[qi] > 0 && d.obs_sphere[qi] < 0) ? 1 : 0;
+  const bool cast = d.sp.active[qi] && d.sp.kind[qi] == 0 && d.pair_count[qi] > 0 && d.obs_sphere[qi] < 0;
+  flag[qi] = cast ? (d.sp.fallback[qi] ? 2 : 1) : 0;
 }
 
 __global__ void k_adj_alpha_reduce(const double* part, int n_blocks, int n_groups, double* abar) {

@@ -324,6 +324,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->sp.face = sim->dalloc<int>(n_q);
   sim->sp.bary = sim->dalloc<double>(2 * (size_t)n_q);
   sim->sp.target = sim->dalloc<double>(3 * (size_t)n_q);
+  sim->sp.fallback = sim->dalloc<int>(n_q);
   sim->int_of_user_d = sim->dalloc<int>(n_v);
   sim->robot_row = sim->dalloc<int>(sim->robot_row_h.size());
   sim->seg_d = sim->seg_blocks ? sim->dalloc<int>(sim->seg_h.size()) : nullptr;
@@ -397,6 +398,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   CK(cudaMemsetAsync(sim->sp.face, 0xff, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->sp.bary, 0, sizeof(double) * 2 * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->sp.target, 0, sizeof(double) * 3 * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->sp.fallback, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->pair_count, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->obs_sphere, 0xff, sizeof(int) * std::max(n_q, 1), st));
   {

@@ -406,7 +406,8 @@ __device__ void face_verts(const Dev<T>& d, int f, V3& q0, V3& q1, V3& q2, int4&
 
 // Self-collision correspondence of vertex v: first exit-face hit along dir.
 template <typename T>
-__device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, double& rb2) {
+__device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, double& rb2, int& fell_back) {
+  fell_back = 0;
   const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
   int best_f = -1;
   double best_t = 0.0;
@@ -469,6 +470,7 @@ __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, doubl
     tmax[a] += tdel[a];
   }
   if (best_f >= 0) return best_f;
+  fell_back = 1;
   // No exit face hit: the closest point over the boundary faces not
   // containing v, found by scanning cubic shells of cells around v's cell.
   // After shell k every face with a point within k cells has been seen, so
@@ -556,6 +558,7 @@ __global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
     const double nl = norm(n);
     n = nl > 0.0 ? scl(1.0 / nl, n) : V3{0.0, 0.0, 0.0};
     int active = d.sp.active[qi];
+    int fell_back = 0;
     int kind = d.sp.kind[qi];
     int face = d.sp.face[qi];
     double b1 = d.sp.bary[2 * qi], b2 = d.sp.bary[2 * qi + 1];
@@ -574,7 +577,7 @@ __global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
       b1 = b2 = 0.0;
       tgt = add(c, scl(r + eps, u));
     } else if (d.pair_count[qi] > 0) {
-      const int f = ray_cast(d, v, x, scl(-1.0, n), b1, b2);
+      const int f = ray_cast(d, v, x, scl(-1.0, n), b1, b2, fell_back);
       if (f >= 0) {
         V3 nf;
         const V3 bp = face_point(d, f, b1, b2, nf);
@@ -614,6 +617,7 @@ __global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
       tgt = {0.0, 0.0, 0.0};
     }
     d.sp.active[qi] = active;
+    d.sp.fallback[qi] = fell_back;
     d.sp.kind[qi] = kind;
     d.sp.face[qi] = face;
     d.sp.bary[2 * qi] = b1;

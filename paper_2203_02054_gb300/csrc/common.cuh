@@ -80,6 +80,7 @@ struct SpringDev {
   int* face;             // n_q: face id / sphere id / -1
   double* bary;          // 2 n_q
   double* target;        // 3 n_q
+  int* fallback;         // n_q: 1 if this update's self target is a closest point
 };
 
 template <typename T>

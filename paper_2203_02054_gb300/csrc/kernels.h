@@ -60,7 +60,7 @@ struct AdjDev {
   const int* sp_kind;
   const int* sp_face;
   const double* sp_bary;  // 2 n_q
-  const int* sp_flag;     // 1: self spring cast in iteration i
+  const int* sp_flag;     // self spring cast in iteration i: 1 by a ray hit, 2 by the closest point
   R4<double>* xbar_tet;   // 4 n_t per-tet pullbacks
   double* xbar_vert;      // 3 n_v spring pullbacks (FP64 atomics)
   double* betabar;        // 2 n_q barycentric adjoints of kept springs
