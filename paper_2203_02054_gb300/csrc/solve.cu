@@ -8,7 +8,8 @@
 // Jacobi-preconditioned conjugate gradients in the single-reduction form of
 // Chronopoulos and Gear (1989), inside one persistent cooperative kernel:
 // per iteration one grid barrier publishes the new preconditioned residual u
-// for the SpMV and one grid reduction produces (r.u, w.u, r.r) in FP64.
+// for the SpMV and one grid reduction produces (r.u, w.u, r.r) to FP64
+// accuracy.
 #include <cooperative_groups.h>
 
 #include <algorithm>
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs(Dev<T> d) {
 
 // ------------------------------------------------------------------ PCG
 //
-// Both PCG kernels solve for the correction d of the warm start x:
+// The PCG kernels solve for the correction d of the warm start x:
 //   r0 = b - A x  in FP64 (FP32 products are exact in FP64),
 //   A d = r0      by Jacobi-preconditioned CG in the working precision,
 //   x <- x + d    once at the end,
@@ -159,15 +160,23 @@ __global__ void __launch_bounds__(RHS_THREADS) k_rhs(Dev<T> d) {
 // refinement per outer iteration).  The stopping test ||r|| <= tol ||b|| is the
 // same as for the plain system.
 //
+// Per CG iteration there are two grid barriers: one publishes the new
+// preconditioned residual u for the neighbours' SpMV, one completes the
+// reduction of (r.u, w.u, r.r).
+//
 // Grid barrier: one arrival counter whose top bit flips once per round.
 // Block 0 adds 0x80000000 - (nblocks - 1) and every other block adds 1, so a
 // full round adds exactly 0x80000000: the low bits return to their value and
 // the top bit changes, which every block waits for (no reset, one atomic per
-// block).  Block partial sums for the FP64 reductions are written before the
-// arrival and read after it, in block order (deterministic); they alternate
-// between two buffers, so a block that runs ahead cannot overwrite values
-// another block is still reading.  Every wait is bounded by a clock budget,
-// after which the kernel records ST_TIMEOUT, raises the abort word and returns.
+// block).  Every wait is bounded by a clock budget, after which the kernel
+// records ST_TIMEOUT, raises the abort word and returns.
+//
+// Reductions: each block forms its sums (below), lane 0 of warp 0 stores them
+// as the block's partials and arrives; after the barrier warp 0 alone adds the
+// partials in block order (deterministic), computes the CG scalars once for
+// the block and hands them to the other warps through shared memory.  Partials
+// are stored value-major, partials[(parity * 4 + k) * nblocks + block], in two
+// buffers chosen by the barrier count's parity.
 struct GridCtx {
   Ctrl* ctrl;
   double* partials;
@@ -176,127 +185,235 @@ struct GridCtx {
   unsigned extra;  // test-only: arrivals expected beyond the grid (never come)
 };
 
-template <int NV, int NB, bool READ = true>
-__device__ __forceinline__ bool grid_publish_wait(const GridCtx& g, unsigned& epoch, const double (&bs)[NB],
-                                                  double* tot, int* shf) {
-  ++epoch;
-  __syncthreads();
-  double* buf = g.partials + (size_t)(epoch & 1u) * 4 * g.nblocks;
-  if (threadIdx.x == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) buf[4 * blockIdx.x + k] = bs[k];
-    const unsigned add = blockIdx.x == 0 ? (0x80000000u - (g.nblocks - 1u + g.extra)) : 1u;
-    __threadfence();
-    const unsigned old = atomicAdd(&g.ctrl->bar_count, add);
-    volatile unsigned* vc = &g.ctrl->bar_count;
-    int ok = 1;
-    if (((old ^ *vc) & 0x80000000u) == 0) {
-      const long long t0 = clock64();
-      unsigned spins = 0;
-      while (((old ^ *vc) & 0x80000000u) == 0) {
-        if ((++spins & 63u) == 0) {
-          if (*(volatile int*)&g.ctrl->abort) {
-            ok = 0;
-            break;
-          }
-          if ((unsigned long long)(clock64() - t0) > g.budget) {
-            atomicExch(&g.ctrl->abort, 1);
-            atomicOr(&g.ctrl->status, ST_TIMEOUT);
-            ok = 0;
-            break;
-          }
+// One thread of the block arrives and waits for the round to complete.
+// Returns 0 when the wait gave up (timeout) or another block aborted.
+__device__ __forceinline__ int arrive_and_wait(const GridCtx& g) {
+  const unsigned add = blockIdx.x == 0 ? (0x80000000u - (g.nblocks - 1u + g.extra)) : 1u;
+  __threadfence();
+  const unsigned old = atomicAdd(&g.ctrl->bar_count, add);
+  volatile unsigned* vc = &g.ctrl->bar_count;
+  int ok = 1;
+  if (((old ^ *vc) & 0x80000000u) == 0) {
+    const long long t0 = clock64();
+    unsigned spins = 0;
+    while (((old ^ *vc) & 0x80000000u) == 0) {
+      if ((++spins & 63u) == 0) {
+        if (*(volatile int*)&g.ctrl->abort) {
+          ok = 0;
+          break;
+        }
+        if ((unsigned long long)(clock64() - t0) > g.budget) {
+          atomicExch(&g.ctrl->abort, 1);
+          atomicOr(&g.ctrl->status, ST_TIMEOUT);
+          ok = 0;
+          break;
         }
       }
     }
-    __threadfence();
-    *shf = ok;
+  }
+  __threadfence();
+  return ok;
+}
+
+// Plain grid barrier (makes every block's prior global writes visible).
+__device__ __forceinline__ bool grid_barrier(const GridCtx& g, unsigned& epoch, int* shf) {
+  ++epoch;
+  __syncthreads();
+  if (threadIdx.x == 0) *shf = arrive_and_wait(g);
+  __syncthreads();
+  return *shf != 0;
+}
+
+// ---- FP64-grade dot products
+// The CG dot products are accumulated to FP64 accuracy.  FP64 arithmetic is
+// slow on this part (a dependent FP64 add takes about 64 cycles and an SM
+// retires about two FP64 lanes per cycle, against 4.5 cycles and 128 lanes for
+// FP32), so for FP32 vectors the per-row products and the in-block trees use
+// double-word (float-float) arithmetic built from error-free transformations
+// on the FP32 pipes:
+//   TwoProd by FMA (the rounding error of a*b is fma(a, b, -a*b)),
+//   TwoSum (Knuth) and Fast2Sum (Dekker),
+//   the compensated dot product Dot2 of Ogita, Rump and Oishi (2005), kept
+//   unrounded as a double word,
+//   the accurate double-word addition of Joldes, Muller and Popescu (2017),
+//   relative error at most 3u^2 (u = 2^-24) per addition.
+// Every operation is an explicitly rounded intrinsic, so the compiler can
+// neither contract nor reassociate them.  A block's double-word sum is
+// converted to FP64 once and the block partials are summed in FP64.
+struct DW {
+  float hi, lo;
+};
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// requires a == 0 or exponent(a) >= exponent(b)
+__device__ __forceinline__ void fast_two_sum_f(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ DW dw_add(DW x, DW y) {
+  float sh, sl, th, tl, vh, vl;
+  two_sum_f(x.hi, y.hi, sh, sl);
+  two_sum_f(x.lo, y.lo, th, tl);
+  const float c = __fadd_rn(sl, th);
+  fast_two_sum_f(sh, c, vh, vl);
+  const float w = __fadd_rn(tl, vl);
+  DW z;
+  fast_two_sum_f(vh, w, z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ DW dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
+  float p = __fmul_rn(a0, b0);
+  float e = __fmaf_rn(a0, b0, -p);
+  const float h1 = __fmul_rn(a1, b1), q1 = __fmaf_rn(a1, b1, -h1);
+  const float h2 = __fmul_rn(a2, b2), q2 = __fmaf_rn(a2, b2, -h2);
+  float s, t;
+  two_sum_f(p, h1, s, t);
+  p = s;
+  e = __fadd_rn(e, __fadd_rn(q1, t));
+  two_sum_f(p, h2, s, t);
+  p = s;
+  e = __fadd_rn(e, __fadd_rn(q2, t));
+  DW z;
+  two_sum_f(p, e, z.hi, z.lo);
+  return z;
+}
+
+__device__ __forceinline__ double dot3(double a0, double a1, double a2, double b0, double b1, double b2) {
+  return fma(a2, b2, fma(a1, b1, a0 * b0));
+}
+
+__device__ __forceinline__ DW acc_add(DW a, DW b) { return dw_add(a, b); }
+__device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
+__device__ __forceinline__ DW shfl_down(DW v, int o) {
+  return DW{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+}
+__device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
+__device__ __forceinline__ double acc_to_f64(DW a) { return (double)a.hi + (double)a.lo; }
+__device__ __forceinline__ double acc_to_f64(double a) { return a; }
+
+template <typename A>
+__device__ __forceinline__ A acc_zero();
+template <>
+__device__ __forceinline__ DW acc_zero<DW>() { return DW{0.0f, 0.0f}; }
+template <>
+__device__ __forceinline__ double acc_zero<double>() { return 0.0; }
+
+// per-thread accumulator of the CG dot products for vectors of type T
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<float> {
+  using type = DW;
+};
+template <>
+struct DotAcc<double> {
+  using type = double;
+};
+
+// Block sums of NV per-thread values by fixed shuffle trees (within each warp,
+// then over the NW warp sums); the FP64 result is valid in lane 0 of warp 0.
+// Contains one __syncthreads; sh holds at least 32 * NV doubles.
+template <int NV, int NW, typename A>
+__device__ __forceinline__ void block_sums(A (&v)[NV], double* sh, double (&bs)[NV]) {
+  static_assert(sizeof(A) == sizeof(double), "accumulator must fit a double slot");
+  static_assert(NW >= 1 && NW <= 32 && (NW & (NW - 1)) == 0, "warps per block must be a power of two");
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  A* sa = reinterpret_cast<A*>(sh);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = acc_add(v[k], shfl_down(v[k], o));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sa[k * 32 + wid] = v[k];
   }
   __syncthreads();
-  if (!*shf) return false;
-  if (NV > 0 && READ) {
-    if (threadIdx.x < 32) {
-      double a[NB];
+  if (wid == 0) {
 #pragma unroll
-      for (int k = 0; k < NB; ++k) a[k] = 0.0;
-#pragma unroll 4
-      for (unsigned b = threadIdx.x; b < g.nblocks; b += 32) {
+    for (int k = 0; k < NV; ++k) {
+      A t = lane < NW ? sa[k * 32 + lane] : acc_zero<A>();
 #pragma unroll
-        for (int k = 0; k < NV; ++k) a[k] += __ldcg(buf + 4 * b + k);
-      }
-#pragma unroll
-      for (int k = 0; k < NV; ++k) {
-        double t = a[k];
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-        if (threadIdx.x == 0) tot[k] = t;
-      }
+      for (int o = NW >> 1; o > 0; o >>= 1) t = acc_add(t, shfl_down(t, o));
+      bs[k] = acc_to_f64(t);
     }
-    __syncthreads();
+  }
+}
+
+// Called by all of warp 0 after block_sums.  Lane 0 stores the block's sums
+// as its partials, arrives and waits; the warp then adds the partials of
+// blocks [b0, b1) in block order: each lane its blocks in increasing order,
+// then a fixed shuffle tree.  tot is valid in lane 0.  Returns false
+// (warp-uniform) when the wait gave up or another block aborted.
+template <int NV>
+__device__ __forceinline__ bool warp0_reduce(const GridCtx& g, unsigned& epoch, const double (&bs)[NV], int b0,
+                                             int b1, double (&tot)[NV]) {
+  ++epoch;
+  const int lane = threadIdx.x & 31;
+  const size_t nb = g.nblocks;
+  const double* buf = g.partials + (size_t)(epoch & 1u) * 4 * nb;
+  int ok = 1;
+  if (lane == 0) {
+    double* wb = g.partials + (size_t)(epoch & 1u) * 4 * nb;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) wb[k * nb + blockIdx.x] = bs[k];
+    ok = arrive_and_wait(g);
+  }
+  __syncwarp();
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (!ok) return false;
+  double a[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) a[k] = 0.0;
+#pragma unroll 2
+  for (int b = b0 + lane; b < b1; b += 32) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) a[k] += __ldcg(buf + k * nb + b);
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    tot[k] = a[k];
   }
   return true;
 }
 
-template <int NV>
-__device__ __forceinline__ bool grid_sync_reduce(const GridCtx& g, unsigned& epoch, const double (&v)[NV],
-                                                 double* sh, double* tot, int* shf) {
-  // block sums of all NV values with one shared-memory round (sh >= 32*NV)
-  double t[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    t[k] = v[k];
-    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = t[k];
-  __syncthreads();
-  double bs[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) bs[k] = 0.0;
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) bs[k] += sh[k * 32 + i];
-  }
-  return grid_publish_wait<NV, NV>(g, epoch, bs, tot, shf);
+enum { CG_CONTINUE = 0, CG_DONE = 1, CG_NONFINITE = 2, CG_ABORT = 3 };
+
+// CG scalars after the reduction of (gamma_k, delta_k, rr) (lane 0 of warp 0).
+// alpha_k = gamma_k / (delta_k - beta_k gamma_k / alpha_{k-1}) with
+// beta_k = gamma_k / gamma_{k-1}, rearranged with q = gamma_{k-1} alpha_{k-1}
+// to alpha_k = gamma_k q / (delta_k q - gamma_k^2), so that one division lies
+// on the dependent path (beta_k's division runs beside it).
+__device__ __forceinline__ int cg_scalars(const double (&t)[3], double bb, double tol2, double& gamma, double& alpha,
+                                          double& beta, double& rr) {
+  const double gnew = t[0], delta = t[1];
+  rr = t[2];
+  if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) return CG_NONFINITE;
+  if (rr <= tol2 * bb) return CG_DONE;
+  beta = gnew / gamma;
+  const double q = gamma * alpha;
+  alpha = (gnew * q) / (delta * q - gnew * gnew);
+  gamma = gnew;
+  return CG_CONTINUE;
 }
 
-// Publishes this block's sums of NV values and waits for all blocks; the
-// caller sums whichever partials it needs.
-template <int NV>
-__device__ __forceinline__ bool grid_sync_reduce_local(const GridCtx& g, unsigned& epoch, const double (&v)[NV],
-                                                       double* sh, int* shf) {
-  double t[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    t[k] = v[k];
-    for (int o = 16; o > 0; o >>= 1) t[k] += __shfl_down_sync(0xffffffffu, t[k], o);
-  }
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = t[k];
-  __syncthreads();
-  double bs[NV];
-#pragma unroll
-  for (int k = 0; k < NV; ++k) bs[k] = 0.0;
-  if (threadIdx.x == 0) {
-    const int nw = (blockDim.x + 31) >> 5;
-    for (int i = 0; i < nw; ++i)
-#pragma unroll
-      for (int k = 0; k < NV; ++k) bs[k] += sh[k * 32 + i];
-  }
-  return grid_publish_wait<NV, NV, false>(g, epoch, bs, nullptr, shf);
-}
-
-__device__ __forceinline__ bool grid_sync(const GridCtx& g, unsigned& epoch, double* sh, double* tot, int* shf) {
-  const double none[1] = {0.0};
-  (void)sh;
-  return grid_publish_wait<0, 1>(g, epoch, none, tot, shf);
-}
+// shared state of one block of a PCG kernel
+template <typename T>
+struct CgShared {
+  double sh[96];
+  T ta, tb;
+  int flag;
+  int ok;
+};
 
 template <typename T>
 __device__ __forceinline__ R4<T> ld_cg(const R4<T>* a);
@@ -318,6 +435,29 @@ __device__ __forceinline__ void write_pcg_record(const Ctrl* c, IterRec* hist, i
   rec->pcg_iters = it;
   cw->total_pcg += it;
   rec->pcg_rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
+}
+
+// r_i = b_i - (A x)_i in FP64 and ||b_i||^2, ||r_i||^2 (the first residual of
+// the correction form; X is read-only while it is formed).
+template <typename T>
+__device__ __forceinline__ void residual_row_f64(const Dev<T>& d, int i, T dg, double (&rv)[3], double (&a0)[2]) {
+  const R4<T> xi = d.X[i];
+  double ax = (double)dg * xi.x, ay = (double)dg * xi.y, az = (double)dg * xi.z;
+  const int sl = i >> 5, lane = i & 31;
+  const int k1 = d.sl_ptr[sl + 1];
+  for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
+    const double a = (double)d.sl_val[k];
+    const R4<T> xc = d.X[d.sl_col[k]];
+    ax += a * xc.x;
+    ay += a * xc.y;
+    az += a * xc.z;
+  }
+  const R4<double> bi = d.b[i];
+  rv[0] = bi.x - ax;
+  rv[1] = bi.y - ay;
+  rv[2] = bi.z - az;
+  a0[0] += bi.x * bi.x + bi.y * bi.y + bi.z * bi.z;
+  a0[1] += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
 }
 
 // Streaming variant: any number of rows per thread (grid-stride); vectors in
@@ -342,11 +482,13 @@ __device__ __forceinline__ void spmv_row(const Dev<T>& d, int i, const R4<T>* __
 
 template <typename T>
 __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
-  __shared__ double sh[96];
-  __shared__ double tot[4];
-  __shared__ int shf;
+  using A = typename DotAcc<T>::type;
+  constexpr int NW = PCG_THREADS / 32;
+  __shared__ CgShared<T> cs;
   const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget, d.bar_extra};
   unsigned epoch = 0;
+  const int lane = threadIdx.x & 31;
+  const bool w0 = threadIdx.x < 32;
   const int n = d.n_free;
   const int G = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -358,39 +500,39 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
   R4<T>* __restrict__ w = d.w;
   R4<T>* __restrict__ dx = d.dx;
   const R4<T> zero = {T(0), T(0), T(0), T(0)};
+  // CG scalars: meaningful in lane 0 of warp 0
+  double bb = 0.0, rr = 0.0, gamma = 0.0, alpha = 0.0, beta = 0.0;
 
   // r = b - A x in FP64, u = M^-1 r, d = 0
   double a0[2] = {0.0, 0.0};
   for (int i = tid; i < n; i += G) {
     const T dg = d.diag[i];
-    const R4<T> xi = X[i];
-    double ax = (double)dg * xi.x, ay = (double)dg * xi.y, az = (double)dg * xi.z;
-    const int sl = i >> 5, lane = i & 31;
-    const int k1 = d.sl_ptr[sl + 1];
-    for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
-      const double a = (double)d.sl_val[k];
-      const R4<T> xc = X[d.sl_col[k]];
-      ax += a * xc.x;
-      ay += a * xc.y;
-      az += a * xc.z;
-    }
-    const R4<double> bi = d.b[i];
-    const double rx = bi.x - ax, ry = bi.y - ay, rz = bi.z - az;
+    double rv[3];
+    residual_row_f64(d, i, dg, rv, a0);
     R4<T> ri, ui;
-    ri.x = (T)rx; ri.y = (T)ry; ri.z = (T)rz; ri.w = T(0);
+    ri.x = (T)rv[0]; ri.y = (T)rv[1]; ri.z = (T)rv[2]; ri.w = T(0);
     ui.x = ri.x / dg; ui.y = ri.y / dg; ui.z = ri.z / dg; ui.w = T(0);
     r[i] = ri;
     u[i] = ui;
     dx[i] = zero;
-    a0[0] += bi.x * bi.x + bi.y * bi.y + bi.z * bi.z;
-    a0[1] += rx * rx + ry * ry + rz * rz;
   }
-  if (!grid_sync_reduce<2>(g, epoch, a0, sh, tot, &shf)) return;
-  const double bb = tot[0];
-  double rr = tot[1];
+  {
+    double bs[2], t[2];
+    block_sums<2, NW>(a0, cs.sh, bs);
+    if (w0) {
+      const bool ok = warp0_reduce<2>(g, epoch, bs, 0, gridDim.x, t);
+      if (lane == 0) {
+        bb = t[0];
+        rr = t[1];
+        cs.flag = !ok ? CG_ABORT : ((bb > 0.0 && rr > d.tol2 * bb) ? CG_CONTINUE : CG_DONE);
+      }
+    }
+    __syncthreads();
+  }
+  if (cs.flag == CG_ABORT) return;
   int it = 0;
-  if (bb > 0.0 && rr > d.tol2 * bb) {
-    double a1[2] = {0.0, 0.0};
+  if (cs.flag == CG_CONTINUE) {
+    A a1[2] = {acc_zero<A>(), acc_zero<A>()};
     for (int i = tid; i < n; i += G) {
       const T dg = d.diag[i];
       const R4<T> ui = u[i], ri = r[i];
@@ -399,16 +541,30 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
       R4<T> wi;
       wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
       w[i] = wi;
-      a1[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
-      a1[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
+      a1[0] = acc_add(a1[0], dot3(ri.x, ri.y, ri.z, ui.x, ui.y, ui.z));
+      a1[1] = acc_add(a1[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
     }
-    if (!grid_sync_reduce<2>(g, epoch, a1, sh, tot, &shf)) return;
-    double gamma = tot[0];
-    double alpha = gamma / tot[1];
-    double beta = 0.0;
+    {
+      double bs[2], t[2];
+      block_sums<2, NW>(a1, cs.sh, bs);
+      if (w0) {
+        const bool ok = warp0_reduce<2>(g, epoch, bs, 0, gridDim.x, t);
+        if (lane == 0) {
+          if (ok) {
+            gamma = t[0];
+            alpha = gamma / t[1];
+            cs.ta = (T)alpha;
+            cs.tb = T(0);
+          }
+          cs.flag = ok ? CG_CONTINUE : CG_ABORT;
+        }
+      }
+      __syncthreads();
+    }
+    if (cs.flag == CG_ABORT) return;
+    T ta = cs.ta, tb = T(0);
     bool first = true;
     for (it = 1; it <= d.max_iter; ++it) {
-      const T ta = (T)alpha, tb = (T)beta;
       for (int i = tid; i < n; i += G) {
         const R4<T> ui = u[i], wi = w[i];
         R4<T> pi, si;
@@ -434,8 +590,8 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
         un.x = ri.x / dg; un.y = ri.y / dg; un.z = ri.z / dg; un.w = T(0);
         u[i] = un;
       }
-      if (!grid_sync(g, epoch, sh, tot, &shf)) return;
-      double a2[3] = {0.0, 0.0, 0.0};
+      if (!grid_barrier(g, epoch, &cs.ok)) return;
+      A a2[3] = {acc_zero<A>(), acc_zero<A>(), acc_zero<A>()};
       for (int i = tid; i < n; i += G) {
         const T dg = d.diag[i];
         const R4<T> ui = u[i], ri = r[i];
@@ -444,21 +600,33 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
         R4<T> wi;
         wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
         w[i] = wi;
-        a2[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
-        a2[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
-        a2[2] += (double)ri.x * ri.x + (double)ri.y * ri.y + (double)ri.z * ri.z;
+        a2[0] = acc_add(a2[0], dot3(ri.x, ri.y, ri.z, ui.x, ui.y, ui.z));
+        a2[1] = acc_add(a2[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
+        a2[2] = acc_add(a2[2], dot3(ri.x, ri.y, ri.z, ri.x, ri.y, ri.z));
       }
-      if (!grid_sync_reduce<3>(g, epoch, a2, sh, tot, &shf)) return;
-      const double gnew = tot[0], delta = tot[1];
-      rr = tot[2];
-      if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
-        if (tid == 0) set_status(d.ctrl, ST_NONFINITE);
-        break;
+      {
+        double bs[3], t[3];
+        block_sums<3, NW>(a2, cs.sh, bs);
+        if (w0) {
+          const bool ok = warp0_reduce<3>(g, epoch, bs, 0, gridDim.x, t);
+          if (lane == 0) {
+            int f = CG_ABORT;
+            if (ok) {
+              f = cg_scalars(t, bb, d.tol2, gamma, alpha, beta, rr);
+              if (f == CG_NONFINITE && blockIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
+              cs.ta = (T)alpha;
+              cs.tb = (T)beta;
+            }
+            cs.flag = f;
+          }
+        }
+        __syncthreads();
       }
-      if (rr <= d.tol2 * bb) break;
-      beta = gnew / gamma;
-      alpha = gnew / (delta - beta * gnew / alpha);
-      gamma = gnew;
+      const int f = cs.flag;
+      if (f == CG_ABORT) return;
+      if (f != CG_CONTINUE) break;
+      ta = cs.ta;
+      tb = cs.tb;
       first = false;
     }
     if (it > d.max_iter) {
@@ -481,11 +649,13 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
 // memory and the neighbours' values are gathered from L2.
 template <typename T, int MAXW>
 __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
-  __shared__ double sh[96];
-  __shared__ double tot[4];
-  __shared__ int shf;
+  using A = typename DotAcc<T>::type;
+  constexpr int NW = PCG_RR_THREADS / 32;
+  __shared__ CgShared<T> cs;
   const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget, d.bar_extra};
   unsigned epoch = 0;
+  const int lane = threadIdx.x & 31;
+  const bool w0 = threadIdx.x < 32;
   const int n = d.n_free;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = i < n;
@@ -495,14 +665,14 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
   T dg = T(1);
   T x[3] = {T(0), T(0), T(0)};
   if (act) {
-    const int sl = i >> 5, lane = i & 31;
+    const int sl = i >> 5, ln = i & 31;
     const int base = d.sl_ptr[sl];
     width = (d.sl_ptr[sl + 1] - base) >> 5;
 #pragma unroll
     for (int j = 0; j < MAXW; ++j) {
       if (j < width) {
-        col[j] = d.sl_col[base + j * 32 + lane];
-        val[j] = d.sl_val[base + j * 32 + lane];
+        col[j] = d.sl_col[base + j * 32 + ln];
+        val[j] = d.sl_val[base + j * 32 + ln];
       } else {
         col[j] = i;
         val[j] = T(0);
@@ -531,51 +701,64 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
     t.x = uu[0]; t.y = uu[1]; t.z = uu[2]; t.w = T(0);
     d.u[i] = t;
   };
+  // CG scalars: meaningful in lane 0 of warp 0
+  double bb = 0.0, rr = 0.0, gamma = 0.0, alpha = 0.0, beta = 0.0;
   T r[3], u[3], w[3], p[3], s[3], dd[3] = {T(0), T(0), T(0)};
   double a0[2] = {0.0, 0.0};
   if (act) {
-    // r = b - A x in FP64 (X is read-only in this phase)
-    double ax[3] = {(double)dg * x[0], (double)dg * x[1], (double)dg * x[2]};
-#pragma unroll
-    for (int j = 0; j < MAXW; ++j) {
-      if (j < width) {
-        const R4<T> v = d.X[col[j]];
-        ax[0] += (double)val[j] * v.x;
-        ax[1] += (double)val[j] * v.y;
-        ax[2] += (double)val[j] * v.z;
-      }
-    }
-    const R4<double> bi = d.b[i];
-    const double bv[3] = {bi.x, bi.y, bi.z};
+    double rv[3];
+    residual_row_f64(d, i, dg, rv, a0);
     for (int c = 0; c < 3; ++c) {
-      const double rc = bv[c] - ax[c];
-      r[c] = (T)rc;
+      r[c] = (T)rv[c];
       u[c] = r[c] / dg;
-      a0[0] += bv[c] * bv[c];
-      a0[1] += rc * rc;
     }
     store_u(u);
   }
-  if (!grid_sync_reduce<2>(g, epoch, a0, sh, tot, &shf)) return;
-  const double bb = tot[0];
-  double rr = tot[1];
+  {
+    double bs[2], t[2];
+    block_sums<2, NW>(a0, cs.sh, bs);
+    if (w0) {
+      const bool ok = warp0_reduce<2>(g, epoch, bs, 0, gridDim.x, t);
+      if (lane == 0) {
+        bb = t[0];
+        rr = t[1];
+        cs.flag = !ok ? CG_ABORT : ((bb > 0.0 && rr > d.tol2 * bb) ? CG_CONTINUE : CG_DONE);
+      }
+    }
+    __syncthreads();
+  }
+  if (cs.flag == CG_ABORT) return;
   int it = 0;
-  if (bb > 0.0 && rr > d.tol2 * bb) {
-    double a1[2] = {0.0, 0.0};
+  if (cs.flag == CG_CONTINUE) {
+    A a1[2] = {acc_zero<A>(), acc_zero<A>()};
     if (act) {
       spmv(d.u, u, w);
+      a1[0] = dot3(r[0], r[1], r[2], u[0], u[1], u[2]);
+      a1[1] = dot3(w[0], w[1], w[2], u[0], u[1], u[2]);
       for (int c = 0; c < 3; ++c) {
-        a1[0] += (double)r[c] * u[c];
-        a1[1] += (double)w[c] * u[c];
         p[c] = u[c];
         s[c] = w[c];
       }
     }
-    if (!grid_sync_reduce<2>(g, epoch, a1, sh, tot, &shf)) return;
-    double gamma = tot[0];
-    double alpha = gamma / tot[1];
+    {
+      double bs[2], t[2];
+      block_sums<2, NW>(a1, cs.sh, bs);
+      if (w0) {
+        const bool ok = warp0_reduce<2>(g, epoch, bs, 0, gridDim.x, t);
+        if (lane == 0) {
+          if (ok) {
+            gamma = t[0];
+            alpha = gamma / t[1];
+            cs.ta = (T)alpha;
+          }
+          cs.flag = ok ? CG_CONTINUE : CG_ABORT;
+        }
+      }
+      __syncthreads();
+    }
+    if (cs.flag == CG_ABORT) return;
+    T ta = cs.ta;
     for (it = 1; it <= d.max_iter; ++it) {
-      const T ta = (T)alpha;
       if (act) {
         for (int c = 0; c < 3; ++c) {
           dd[c] += ta * p[c];
@@ -584,28 +767,37 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
         }
         store_u(u);
       }
-      if (!grid_sync(g, epoch, sh, tot, &shf)) return;
-      double a2[3] = {0.0, 0.0, 0.0};
+      if (!grid_barrier(g, epoch, &cs.ok)) return;
+      A a2[3] = {acc_zero<A>(), acc_zero<A>(), acc_zero<A>()};
       if (act) {
         spmv(d.u, u, w);
-        for (int c = 0; c < 3; ++c) {
-          a2[0] += (double)r[c] * u[c];
-          a2[1] += (double)w[c] * u[c];
-          a2[2] += (double)r[c] * r[c];
+        a2[0] = dot3(r[0], r[1], r[2], u[0], u[1], u[2]);
+        a2[1] = dot3(w[0], w[1], w[2], u[0], u[1], u[2]);
+        a2[2] = dot3(r[0], r[1], r[2], r[0], r[1], r[2]);
+      }
+      {
+        double bs[3], t[3];
+        block_sums<3, NW>(a2, cs.sh, bs);
+        if (w0) {
+          const bool ok = warp0_reduce<3>(g, epoch, bs, 0, gridDim.x, t);
+          if (lane == 0) {
+            int f = CG_ABORT;
+            if (ok) {
+              f = cg_scalars(t, bb, d.tol2, gamma, alpha, beta, rr);
+              if (f == CG_NONFINITE && blockIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
+              cs.ta = (T)alpha;
+              cs.tb = (T)beta;
+            }
+            cs.flag = f;
+          }
         }
+        __syncthreads();
       }
-      if (!grid_sync_reduce<3>(g, epoch, a2, sh, tot, &shf)) return;
-      const double gnew = tot[0], delta = tot[1];
-      rr = tot[2];
-      if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
-        if (i == 0) set_status(d.ctrl, ST_NONFINITE);
-        break;
-      }
-      if (rr <= d.tol2 * bb) break;
-      const double beta = gnew / gamma;
-      alpha = gnew / (delta - beta * gnew / alpha);
-      gamma = gnew;
-      const T tb = (T)beta;
+      const int f = cs.flag;
+      if (f == CG_ABORT) return;
+      if (f != CG_CONTINUE) break;
+      ta = cs.ta;
+      const T tb = cs.tb;
       if (act)
         for (int c = 0; c < 3; ++c) {
           p[c] = u[c] + tb * p[c];
@@ -636,14 +828,17 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
 // every block sees the same value) or at the iteration cap.
 template <typename T>
 __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
-  __shared__ double sh[96];
-  __shared__ double tot[4];
-  __shared__ int shf;
+  using A = typename DotAcc<T>::type;
+  constexpr int NW = PCG_SEG_THREADS / 32;
+  __shared__ CgShared<T> cs;
   const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget, d.bar_extra};
   unsigned epoch = 0;
+  const int lane = threadIdx.x & 31;
+  const bool w0 = threadIdx.x < 32;
   const int b = blockIdx.x;
   const int lo = d.seg_lo[b], hi = d.seg_hi[b];
   const int rb0 = d.seg_rb0[b], rb1 = d.seg_rb1[b];
+  const bool lead = b == rb0 && threadIdx.x == 0;  // the robot's first block, lane 0
   R4<T>* __restrict__ X = d.X;
   R4<T>* __restrict__ r = d.r;
   R4<T>* __restrict__ u = d.u;
@@ -652,62 +847,40 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
   R4<T>* __restrict__ w = d.w;
   R4<T>* __restrict__ dx = d.dx;
   const R4<T> zero = {T(0), T(0), T(0), T(0)};
-  // robot totals of NV values: partials of blocks rb0..rb1 in order
-  auto robot_reduce = [&](const double* v, int nv) -> bool {
-    double t[3];
-    for (int k = 0; k < nv; ++k) t[k] = v[k];
-    if (nv == 2) {
-      const double vv[2] = {t[0], t[1]};
-      if (!grid_sync_reduce_local<2>(g, epoch, vv, sh, &shf)) return false;
-    } else {
-      const double vv[3] = {t[0], t[1], t[2]};
-      if (!grid_sync_reduce_local<3>(g, epoch, vv, sh, &shf)) return false;
-    }
-    const double* buf = g.partials + (size_t)(epoch & 1u) * 4 * g.nblocks;
-    if (threadIdx.x < 32) {
-      double a[3] = {0.0, 0.0, 0.0};
-      for (int q = rb0 + (int)threadIdx.x; q < rb1; q += 32)
-        for (int k = 0; k < nv; ++k) a[k] += __ldcg(buf + 4 * q + k);
-      for (int k = 0; k < nv; ++k) {
-        for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
-        if (threadIdx.x == 0) tot[k] = a[k];
-      }
-    }
-    __syncthreads();
-    return true;
-  };
+  // robot CG scalars: meaningful in lane 0 of warp 0
+  double bb = 0.0, rr = 0.0, gamma = 0.0, alpha = 0.0, beta = 0.0;
+  int it_done = 0;
+
   double a0[2] = {0.0, 0.0};
   for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
     const T dg = d.diag[i];
-    const R4<T> xi = X[i];
-    double ax = (double)dg * xi.x, ay = (double)dg * xi.y, az = (double)dg * xi.z;
-    const int sl = i >> 5, lane = i & 31;
-    const int k1 = d.sl_ptr[sl + 1];
-    for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
-      const double av = (double)d.sl_val[k];
-      const R4<T> xc = X[d.sl_col[k]];
-      ax += av * xc.x;
-      ay += av * xc.y;
-      az += av * xc.z;
-    }
-    const R4<double> bi = d.b[i];
-    const double rx = bi.x - ax, ry = bi.y - ay, rz = bi.z - az;
+    double rv[3];
+    residual_row_f64(d, i, dg, rv, a0);
     R4<T> ri, ui;
-    ri.x = (T)rx; ri.y = (T)ry; ri.z = (T)rz; ri.w = T(0);
+    ri.x = (T)rv[0]; ri.y = (T)rv[1]; ri.z = (T)rv[2]; ri.w = T(0);
     ui.x = ri.x / dg; ui.y = ri.y / dg; ui.z = ri.z / dg; ui.w = T(0);
     r[i] = ri;
     u[i] = ui;
     dx[i] = zero;
-    a0[0] += bi.x * bi.x + bi.y * bi.y + bi.z * bi.z;
-    a0[1] += rx * rx + ry * ry + rz * rz;
   }
-  if (!robot_reduce(a0, 2)) return;
-  const double bb = tot[0];
-  double rr = tot[1];
-  bool done = !(bb > 0.0 && rr > d.tol2 * bb);
-  int it_done = 0;
-  if (done && b == rb0 && threadIdx.x == 0) atomicAdd(&d.ctrl->queue, 1u);
-  double a1[2] = {0.0, 0.0};
+  {
+    double bs[2], t[2];
+    block_sums<2, NW>(a0, cs.sh, bs);
+    if (w0) {
+      const bool ok = warp0_reduce<2>(g, epoch, bs, rb0, rb1, t);
+      if (lane == 0) {
+        bb = t[0];
+        rr = t[1];
+        const bool conv = !(bb > 0.0 && rr > d.tol2 * bb);
+        if (ok && conv && b == rb0) atomicAdd(&d.ctrl->queue, 1u);
+        cs.flag = !ok ? CG_ABORT : (conv ? CG_DONE : CG_CONTINUE);
+      }
+    }
+    __syncthreads();
+  }
+  if (cs.flag == CG_ABORT) return;
+  bool done = cs.flag != CG_CONTINUE;
+  A a1[2] = {acc_zero<A>(), acc_zero<A>()};
   if (!done) {
     for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
       const T dg = d.diag[i];
@@ -717,19 +890,33 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
       R4<T> wi;
       wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
       w[i] = wi;
-      a1[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
-      a1[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
+      a1[0] = acc_add(a1[0], dot3(ri.x, ri.y, ri.z, ui.x, ui.y, ui.z));
+      a1[1] = acc_add(a1[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
     }
   }
-  if (!robot_reduce(a1, 2)) return;
-  double gamma = tot[0];
-  double alpha = done ? 0.0 : gamma / tot[1];
-  double beta = 0.0;
+  {
+    double bs[2], t[2];
+    block_sums<2, NW>(a1, cs.sh, bs);
+    if (w0) {
+      const bool ok = warp0_reduce<2>(g, epoch, bs, rb0, rb1, t);
+      if (lane == 0) {
+        if (ok && !done) {
+          gamma = t[0];
+          alpha = gamma / t[1];
+        }
+        cs.ta = (T)alpha;
+        cs.tb = T(0);
+        cs.flag = ok ? CG_CONTINUE : CG_ABORT;
+      }
+    }
+    __syncthreads();
+  }
+  if (cs.flag == CG_ABORT) return;
+  T ta = cs.ta, tb = T(0);
   bool first = true;
   int it = 1;
   for (;; ++it) {
     if (!done) {
-      const T ta = (T)alpha, tb = (T)beta;
       for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
         const R4<T> ui = u[i], wi = w[i];
         R4<T> pi, si;
@@ -756,11 +943,11 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
         u[i] = un;
       }
     }
-    if (!grid_sync(g, epoch, sh, tot, &shf)) return;
+    if (!grid_barrier(g, epoch, &cs.ok)) return;
     // every block reads the same count: increments happen before this barrier
     const unsigned n_done = __ldcg(&d.ctrl->queue);
     if ((int)n_done >= d.n_robots || it > d.max_iter) break;
-    double a2[3] = {0.0, 0.0, 0.0};
+    A a2[3] = {acc_zero<A>(), acc_zero<A>(), acc_zero<A>()};
     if (!done) {
       for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
         const T dg = d.diag[i];
@@ -770,35 +957,46 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
         R4<T> wi;
         wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
         w[i] = wi;
-        a2[0] += (double)ri.x * ui.x + (double)ri.y * ui.y + (double)ri.z * ui.z;
-        a2[1] += (double)ax * ui.x + (double)ay * ui.y + (double)az * ui.z;
-        a2[2] += (double)ri.x * ri.x + (double)ri.y * ri.y + (double)ri.z * ri.z;
+        a2[0] = acc_add(a2[0], dot3(ri.x, ri.y, ri.z, ui.x, ui.y, ui.z));
+        a2[1] = acc_add(a2[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
+        a2[2] = acc_add(a2[2], dot3(ri.x, ri.y, ri.z, ri.x, ri.y, ri.z));
       }
     }
-    if (!robot_reduce(a2, 3)) return;
-    if (!done) {
-      const double gnew = tot[0], delta = tot[1];
-      rr = tot[2];
-      if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) {
-        if (b == rb0 && threadIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
-        done = true;
-      } else if (rr <= d.tol2 * bb) {
-        done = true;
-      } else {
-        beta = gnew / gamma;
-        alpha = gnew / (delta - beta * gnew / alpha);
-        gamma = gnew;
-        first = false;
+    {
+      double bs[3], t[3];
+      block_sums<3, NW>(a2, cs.sh, bs);
+      if (w0) {
+        const bool ok = warp0_reduce<3>(g, epoch, bs, rb0, rb1, t);
+        if (lane == 0) {
+          int f = CG_ABORT;
+          if (ok) {
+            f = CG_DONE;
+            if (!done) {
+              f = cg_scalars(t, bb, d.tol2, gamma, alpha, beta, rr);
+              if (f == CG_NONFINITE && b == rb0) set_status(d.ctrl, ST_NONFINITE);
+              if (f != CG_CONTINUE) {
+                it_done = it;
+                if (b == rb0) atomicAdd(&d.ctrl->queue, 1u);
+              }
+            }
+            cs.ta = (T)alpha;
+            cs.tb = (T)beta;
+          }
+          cs.flag = f;
+        }
       }
-      if (done) {
-        it_done = it;
-        if (b == rb0 && threadIdx.x == 0) atomicAdd(&d.ctrl->queue, 1u);
-      }
+      __syncthreads();
     }
+    const int f = cs.flag;
+    if (f == CG_ABORT) return;
+    if (f != CG_CONTINUE) done = true;
+    ta = cs.ta;
+    tb = cs.tb;
+    first = false;
   }
-  if (!done) {
+  if (!done && lead) {
     it_done = d.max_iter;
-    if (b == rb0 && threadIdx.x == 0) set_status(d.ctrl, ST_PCG_MAXIT);
+    set_status(d.ctrl, ST_PCG_MAXIT);
   }
   for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
     R4<T> xi = X[i];
@@ -806,7 +1004,7 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
     xi.x += di.x; xi.y += di.y; xi.z += di.z;
     X[i] = xi;
   }
-  if (b == rb0 && threadIdx.x == 0) {
+  if (lead) {
     IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
     atomicMax(&rec->pcg_iters, it_done);
     atomicAdd(reinterpret_cast<unsigned long long*>(&d.ctrl->total_pcg), (unsigned long long)it_done);
