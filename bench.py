@@ -385,7 +385,7 @@ def main():
     ms = sum(a.elapsed_time(b) for a, b in evs)
     units = float(m.n_tets) * n_iters * args.steps * world
     value, ms_max = aggregate(ms, float(m.n_tets) * n_iters * args.steps, pg, "cuda")
-    kernels_per_iter = 11   # 2 hash binning + 3 scan + narrow + springs + local + rhs + pcg + finalize
+    kernels_per_iter = 12   # 2 hash binning + 3 scan + narrow + springs + ray casts + local + rhs + pcg + finalize
     gpu_launches = kernels_per_iter * n_iters * args.steps
     stats = casim.casim_get_stats(sim.h)
     hist = casim.casim_get_history(sim.h, n_iters)

@@ -67,6 +67,8 @@ struct casim_sim {
   int *q_verts_d = nullptr, *qf_ptr = nullptr, *qf = nullptr;
   int *cell_count = nullptr, *cell_start = nullptr, *cell_cursor = nullptr, *items = nullptr;
   int *pair_count = nullptr, *pair_tet = nullptr, *obs_sphere = nullptr, *int_of_user_d = nullptr;
+  int* cast_list = nullptr;
+  double* cast_nrm = nullptr;
   double *knots_d = nullptr, *spheres_d = nullptr, *partials = nullptr, *e_partials = nullptr;
   SpringDev sp{};
   Ctrl* ctrl = nullptr;
@@ -209,6 +211,8 @@ Dev<T> make_dev(casim_sim* sim) {
   d.obs_sphere = sim->obs_sphere;
   d.max_pairs = sim->params.max_pairs_per_vertex;
   d.sp = sim->sp;
+  d.cast_list = sim->cast_list;
+  d.cast_nrm = sim->cast_nrm;
   d.spring_c = (R4<double>*)sim->spring_c;
   d.k_spring = sim->params.k_spring;
   d.eps = sim->params.eps;
@@ -325,6 +329,8 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->sp.bary = sim->dalloc<double>(2 * (size_t)n_q);
   sim->sp.target = sim->dalloc<double>(3 * (size_t)n_q);
   sim->sp.fallback = sim->dalloc<int>(n_q);
+  sim->cast_list = sim->dalloc<int>(n_q);
+  sim->cast_nrm = sim->dalloc<double>(3 * (size_t)n_q);
   sim->int_of_user_d = sim->dalloc<int>(n_v);
   sim->robot_row = sim->dalloc<int>(sim->robot_row_h.size());
   sim->seg_d = sim->seg_blocks ? sim->dalloc<int>(sim->seg_h.size()) : nullptr;
@@ -338,7 +344,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->ctrl = sim->dalloc<Ctrl>(1);
   sim->hist = sim->dalloc<IterRec>(sim->hist_cap);
   sim->n_e_local = local_blocks(n_t);
-  sim->n_e_spring = spring_blocks(n_q);
+  sim->n_e_spring = rhs_blocks(n_free);
   sim->e_partials = sim->dalloc<double>(sim->n_e_local + sim->n_e_spring + 1);
   for (void* q : sim->allocs)
     if (!q) return sim->fail(CASIM_E_CUDA, "cudaMalloc failed");

@@ -11,11 +11,13 @@
 // cell with exact orientation signs (predicates.cuh), so the pair set equals
 // the brute-force definition bit for bit.
 //
-// Spring update: one thread per non-fixed boundary vertex; self-collision
+// Spring update: one thread per non-fixed boundary vertex for obstacle
+// targets (closed form) and the paper's release condition; self-collision
 // targets by a ray cast along -n(v) (3D-DDA cell walk of Amanatides and Woo
-// 1987 over the face hash, Moller-Trumbore 1997 ray-triangle test), obstacle
-// targets in closed form, release by the paper's condition.  All spring
-// geometry is evaluated in FP64.
+// 1987 over the face hash, Moller-Trumbore 1997 ray-triangle test), one warp
+// per casting vertex.  All spring geometry is evaluated in FP64.
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "predicates.cuh"
@@ -47,20 +49,22 @@ __device__ __forceinline__ bool item_box(const Dev<T>& d, int i, double lo[3], d
     vs[0] = f.x; vs[1] = f.y; vs[2] = f.z;
     nv = 3;
   }
-  bool ok = true;
-  for (int k = 0; k < nv; ++k) {
+  // min/max in the positions' own precision, converted once (exact)
+  const R4<T> a0 = d.X[vs[0]];
+  T l[3] = {a0.x, a0.y, a0.z}, h[3] = {a0.x, a0.y, a0.z};
+  bool ok = isfinite(a0.x) && isfinite(a0.y) && isfinite(a0.z);
+  for (int k = 1; k < nv; ++k) {
     const R4<T> a = d.X[vs[k]];
-    const double c[3] = {(double)a.x, (double)a.y, (double)a.z};
+    const T c[3] = {a.x, a.y, a.z};
     for (int j = 0; j < 3; ++j) {
       ok = ok && isfinite(c[j]);
-      if (k == 0) {
-        lo[j] = c[j];
-        hi[j] = c[j];
-      } else {
-        lo[j] = fmin(lo[j], c[j]);
-        hi[j] = fmax(hi[j], c[j]);
-      }
+      l[j] = fmin(l[j], c[j]);
+      h[j] = fmax(h[j], c[j]);
     }
+  }
+  for (int j = 0; j < 3; ++j) {
+    lo[j] = (double)l[j];
+    hi[j] = (double)h[j];
   }
   return ok;
 }
@@ -202,26 +206,37 @@ __global__ void k_scan_add(int* out, const int* tile_sums, int n) {
 }
 
 // ---- narrow phase ----
+__device__ __forceinline__ int orient_t(float ax, float ay, float az, float bx, float by, float bz, float cx, float cy,
+                                        float cz, float dx, float dy, float dz) {
+  return orient_sign_f(ax, ay, az, bx, by, bz, cx, cy, cz, dx, dy, dz);
+}
+__device__ __forceinline__ int orient_t(double ax, double ay, double az, double bx, double by, double bz, double cx,
+                                        double cy, double cz, double dx, double dy, double dz) {
+  return orient_sign(ax, ay, az, bx, by, bz, cx, cy, cz, dx, dy, dz);
+}
+
 template <typename T>
-__device__ __forceinline__ bool strictly_inside(const Dev<T>& d, double px, double py, double pz,
-                                                int4 t) {
-  double a[3], b[3], c[3], e[3];
-  load3(d.X, t.x, a[0], a[1], a[2]);
-  load3(d.X, t.y, b[0], b[1], b[2]);
-  load3(d.X, t.z, c[0], c[1], c[2]);
-  load3(d.X, t.w, e[0], e[1], e[2]);
-  // exact bounding-box reject
-  if (px < fmin(fmin(a[0], b[0]), fmin(c[0], e[0])) || px > fmax(fmax(a[0], b[0]), fmax(c[0], e[0])))
-    return false;
-  if (py < fmin(fmin(a[1], b[1]), fmin(c[1], e[1])) || py > fmax(fmax(a[1], b[1]), fmax(c[1], e[1])))
-    return false;
-  if (pz < fmin(fmin(a[2], b[2]), fmin(c[2], e[2])) || pz > fmax(fmax(a[2], b[2]), fmax(c[2], e[2])))
-    return false;
+__device__ __forceinline__ T min4(T a, T b, T c, T e) {
+  return fmin(fmin(a, b), fmin(c, e));
+}
+template <typename T>
+__device__ __forceinline__ T max4(T a, T b, T c, T e) {
+  return fmax(fmax(a, b), fmax(c, e));
+}
+
+// p strictly inside tet t, evaluated in the positions' own precision (the
+// box reject compares exactly; the orientation signs are exact).
+template <typename T>
+__device__ __forceinline__ bool strictly_inside(const Dev<T>& d, T px, T py, T pz, int4 t) {
+  const R4<T> a = d.X[t.x], b = d.X[t.y], c = d.X[t.z], e = d.X[t.w];
+  if (px < min4(a.x, b.x, c.x, e.x) || px > max4(a.x, b.x, c.x, e.x)) return false;
+  if (py < min4(a.y, b.y, c.y, e.y) || py > max4(a.y, b.y, c.y, e.y)) return false;
+  if (pz < min4(a.z, b.z, c.z, e.z) || pz > max4(a.z, b.z, c.z, e.z)) return false;
   // p strictly inside iff each sub-tet with one vertex replaced by p is positive
-  if (orient_sign(px, py, pz, b[0], b[1], b[2], c[0], c[1], c[2], e[0], e[1], e[2]) <= 0) return false;
-  if (orient_sign(a[0], a[1], a[2], px, py, pz, c[0], c[1], c[2], e[0], e[1], e[2]) <= 0) return false;
-  if (orient_sign(a[0], a[1], a[2], b[0], b[1], b[2], px, py, pz, e[0], e[1], e[2]) <= 0) return false;
-  if (orient_sign(a[0], a[1], a[2], b[0], b[1], b[2], c[0], c[1], c[2], px, py, pz) <= 0) return false;
+  if (orient_t(px, py, pz, b.x, b.y, b.z, c.x, c.y, c.z, e.x, e.y, e.z) <= 0) return false;
+  if (orient_t(a.x, a.y, a.z, px, py, pz, c.x, c.y, c.z, e.x, e.y, e.z) <= 0) return false;
+  if (orient_t(a.x, a.y, a.z, b.x, b.y, b.z, px, py, pz, e.x, e.y, e.z) <= 0) return false;
+  if (orient_t(a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z, px, py, pz) <= 0) return false;
   return true;
 }
 
@@ -238,15 +253,16 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
   int n_self = 0, n_obs = 0;
   if (qi < d.n_q) {
     const int v = d.q_verts[qi];
-    double px, py, pz;
-    load3(d.X, v, px, py, pz);
+    const R4<T> pv = d.X[v];
+    const T px = pv.x, py = pv.y, pz = pv.z;
     int cnt = 0;
     bool over = false;
     int* out = d.pair_tet + (size_t)qi * d.max_pairs;
     const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
     if (d.collision >= 1 && isfinite(px) && isfinite(py) && isfinite(pz)) {
       const unsigned h =
-          hash_cell(cell_coord(px, d.inv_cell), cell_coord(py, d.inv_cell), cell_coord(pz, d.inv_cell), rv) &
+          hash_cell(cell_coord((double)px, d.inv_cell), cell_coord((double)py, d.inv_cell),
+                    cell_coord((double)pz, d.inv_cell), rv) &
           (d.H_t - 1u);
       const int b0 = d.cell_start[h];
       const int b1 = min(d.cell_start[h + 1], d.cap_items);
@@ -296,7 +312,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
         for (int j = 0; j < d.n_spheres; ++j) {
           const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
           const double r = d.spheres[4 * j + 3];
-          const double dx = __dsub_rn(px, cx), dy = __dsub_rn(py, cy), dz = __dsub_rn(pz, cz);
+          const double dx = __dsub_rn((double)px, cx), dy = __dsub_rn((double)py, cy), dz = __dsub_rn((double)pz, cz);
           const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
           if (d2 < __dmul_rn(r, r)) {
             ++n_obs;
@@ -404,13 +420,59 @@ __device__ void face_verts(const Dev<T>& d, int f, V3& q0, V3& q1, V3& q2, int4&
   q2 = pos(d, fv.z);
 }
 
-// Self-collision correspondence of vertex v: first exit-face hit along dir.
+// Warp argmin of (key, face id) over the lanes (face id < 0: no candidate);
+// every lane ends with the minimum and its barycentrics.  The order is total,
+// so the result does not depend on which lane held which face.
+__device__ __forceinline__ void warp_argmin(int& f, double& key, double& b1, double& b2) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const int of = __shfl_xor_sync(0xffffffffu, f, o);
+    const double ok = __shfl_xor_sync(0xffffffffu, key, o);
+    const double o1 = __shfl_xor_sync(0xffffffffu, b1, o);
+    const double o2 = __shfl_xor_sync(0xffffffffu, b2, o);
+    if (of >= 0 && (f < 0 || ok < key || (ok == key && of < f))) {
+      f = of;
+      key = ok;
+      b1 = o1;
+      b2 = o2;
+    }
+  }
+}
+
+// Closest-point candidate of face f for point o (lane-local running minimum).
 template <typename T>
-__device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, double& rb2, int& fell_back) {
+__device__ __forceinline__ void closest_candidate(const Dev<T>& d, int v, int rv, int f, V3 o, int& lf, double& ld,
+                                                  double& l1, double& l2) {
+  if (d.robot_of_face && d.robot_of_face[f] != rv) return;
+  V3 q0, q1, q2;
+  int4 fv;
+  face_verts(d, f, q0, q1, q2, fv);
+  if (fv.x == v || fv.y == v || fv.z == v) return;
+  double b1, b2;
+  const V3 x = closest_tri(o, q0, q1, q2, b1, b2);
+  const V3 dd = sub(o, x);
+  const double d2 = dot(dd, dd);
+  if (lf < 0 || d2 < ld || (d2 == ld && f < lf)) {
+    lf = f;
+    ld = d2;
+    l1 = b1;
+    l2 = b2;
+  }
+}
+
+// Self-collision correspondence of vertex v: first exit-face hit along dir,
+// by one warp.  Every lane walks the same cells (3D-DDA); the faces listed in
+// a cell are split over the lanes and the cell's first hit is the warp
+// minimum of (t, face id), merged into the running first hit.  The result is
+// the same as a serial walk's.
+template <typename T>
+__device__ int ray_cast_warp(const Dev<T>& d, int v, int rv, V3 o, V3 dir, double& rb1, double& rb2,
+                             int& fell_back) {
+  const int lane = threadIdx.x & 31;
   fell_back = 0;
-  const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
   int best_f = -1;
   double best_t = 0.0;
+  rb1 = rb2 = 0.0;
   int cell[3] = {cell_coord(o.x, d.inv_cell), cell_coord(o.y, d.inv_cell), cell_coord(o.z, d.inv_cell)};
   const double dv[3] = {dir.x, dir.y, dir.z};
   const double ov[3] = {o.x, o.y, o.z};
@@ -433,19 +495,17 @@ __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, doubl
   }
   // the ray can meet no face beyond the bounding box of this iteration's items
   double tbox = INFINITY;
-  {
-    double t_out = INFINITY;
-    for (int a = 0; a < 3; ++a) {
-      const double blo = order_decode(d.ctrl->box_lo[a]) - d.cell, bhi = order_decode(d.ctrl->box_hi[a]) + d.cell;
-      if (dv[a] > 0.0) t_out = fmin(t_out, (bhi - ov[a]) / dv[a]);
-      else if (dv[a] < 0.0) t_out = fmin(t_out, (blo - ov[a]) / dv[a]);
-    }
-    tbox = t_out;
+  for (int a = 0; a < 3; ++a) {
+    const double blo = order_decode(d.ctrl->box_lo[a]) - d.cell, bhi = order_decode(d.ctrl->box_hi[a]) + d.cell;
+    if (dv[a] > 0.0) tbox = fmin(tbox, (bhi - ov[a]) / dv[a]);
+    else if (dv[a] < 0.0) tbox = fmin(tbox, (blo - ov[a]) / dv[a]);
   }
   for (int it = 0; it < MAX_DDA_STEPS; ++it) {
     const unsigned h = d.H_t + (hash_cell(cell[0], cell[1], cell[2], rv) & (d.H_f - 1u));
     const int k0 = d.cell_start[h], k1 = min(d.cell_start[h + 1], d.cap_items);
-    for (int k = k0; k < k1; ++k) {
+    int lf = -1;
+    double lt = 0.0, l1 = 0.0, l2 = 0.0;
+    for (int k = k0 + lane; k < k1; k += 32) {
       const int f = d.items[k] - d.n_t;
       if (d.robot_of_face && d.robot_of_face[f] != rv) continue;
       V3 q0, q1, q2;
@@ -455,11 +515,20 @@ __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, doubl
       if (!(dot(dir, cross(sub(q1, q0), sub(q2, q0))) > 0.0)) continue;
       double t, b1, b2;
       if (!ray_tri(o, dir, q0, q1, q2, t, b1, b2)) continue;
-      if (best_f < 0 || t < best_t || (t == best_t && f < best_f)) {
-        best_f = f;
-        best_t = t;
-        rb1 = b1;
-        rb2 = b2;
+      if (lf < 0 || t < lt || (t == lt && f < lf)) {
+        lf = f;
+        lt = t;
+        l1 = b1;
+        l2 = b2;
+      }
+    }
+    if (__any_sync(0xffffffffu, lf >= 0)) {
+      warp_argmin(lf, lt, l1, l2);
+      if (best_f < 0 || lt < best_t || (lt == best_t && lf < best_f)) {
+        best_f = lf;
+        best_t = lt;
+        rb1 = l1;
+        rb2 = l2;
       }
     }
     const double texit = fmin(tmax[0], fmin(tmax[1], tmax[2]));
@@ -472,59 +541,42 @@ __device__ int ray_cast(const Dev<T>& d, int v, V3 o, V3 dir, double& rb1, doubl
   if (best_f >= 0) return best_f;
   fell_back = 1;
   // No exit face hit: the closest point over the boundary faces not
-  // containing v, found by scanning cubic shells of cells around v's cell.
-  // After shell k every face with a point within k cells has been seen, so
-  // the search stops once the best distance is at most k cell edges.
+  // containing v, found by scanning cubic shells of cells around v's cell
+  // (the cells of a shell split over the lanes).  After shell k every face
+  // with a point within k cells has been seen, so the search stops once the
+  // best distance is at most k cell edges.
   const int c0[3] = {cell_coord(o.x, d.inv_cell), cell_coord(o.y, d.inv_cell), cell_coord(o.z, d.inv_cell)};
   double bestd = 0.0;
   for (int k = 0; k <= 64; ++k) {
-    for (int dz = -k; dz <= k; ++dz)
-      for (int dy = -k; dy <= k; ++dy)
-        for (int dx = -k; dx <= k; ++dx) {
-          if (max(abs(dx), max(abs(dy), abs(dz))) != k) continue;
-          const unsigned h = d.H_t + (hash_cell(c0[0] + dx, c0[1] + dy, c0[2] + dz, rv) & (d.H_f - 1u));
-          const int k0 = d.cell_start[h], k1 = min(d.cell_start[h + 1], d.cap_items);
-          for (int q = k0; q < k1; ++q) {
-            const int f = d.items[q] - d.n_t;
-            if (d.robot_of_face && d.robot_of_face[f] != rv) continue;
-            V3 q0, q1, q2;
-            int4 fv;
-            face_verts(d, f, q0, q1, q2, fv);
-            if (fv.x == v || fv.y == v || fv.z == v) continue;
-            double b1, b2;
-            const V3 x = closest_tri(o, q0, q1, q2, b1, b2);
-            const V3 dd = sub(o, x);
-            const double d2 = dot(dd, dd);
-            if (best_f < 0 || d2 < bestd || (d2 == bestd && f < best_f)) {
-              best_f = f;
-              bestd = d2;
-              rb1 = b1;
-              rb2 = b2;
-            }
-          }
-        }
+    const int side = 2 * k + 1;
+    const int ncell = side * side * side;
+    int lf = -1;
+    double ld = 0.0, l1 = 0.0, l2 = 0.0;
+    for (int idx = lane; idx < ncell; idx += 32) {
+      const int dx = idx % side - k, dy = (idx / side) % side - k, dz = idx / (side * side) - k;
+      if (max(abs(dx), max(abs(dy), abs(dz))) != k) continue;
+      const unsigned h = d.H_t + (hash_cell(c0[0] + dx, c0[1] + dy, c0[2] + dz, rv) & (d.H_f - 1u));
+      const int k0 = d.cell_start[h], k1 = min(d.cell_start[h + 1], d.cap_items);
+      for (int q = k0; q < k1; ++q) closest_candidate(d, v, rv, d.items[q] - d.n_t, o, lf, ld, l1, l2);
+    }
+    warp_argmin(lf, ld, l1, l2);
+    if (lf >= 0 && (best_f < 0 || ld < bestd || (ld == bestd && lf < best_f))) {
+      best_f = lf;
+      bestd = ld;
+      rb1 = l1;
+      rb2 = l2;
+    }
     if (best_f >= 0 && sqrt(bestd) <= k * d.cell) return best_f;
   }
   if (best_f >= 0) return best_f;
   // the shell search found nothing within 64 cells: every face (rare)
-  for (int f = 0; f < d.n_f; ++f) {
-    if (d.robot_of_face && d.robot_of_face[f] != rv) continue;
-    V3 q0, q1, q2;
-    int4 fv;
-    face_verts(d, f, q0, q1, q2, fv);
-    if (fv.x == v || fv.y == v || fv.z == v) continue;
-    double b1, b2;
-    const V3 x = closest_tri(o, q0, q1, q2, b1, b2);
-    const V3 dd = sub(o, x);
-    const double d2 = dot(dd, dd);
-    if (best_f < 0 || d2 < bestd) {
-      best_f = f;
-      bestd = d2;
-      rb1 = b1;
-      rb2 = b2;
-    }
-  }
-  return best_f;
+  int lf = -1;
+  double ld = 0.0, l1 = 0.0, l2 = 0.0;
+  for (int f = lane; f < d.n_f; f += 32) closest_candidate(d, v, rv, f, o, lf, ld, l1, l2);
+  warp_argmin(lf, ld, l1, l2);
+  rb1 = l1;
+  rb2 = l2;
+  return lf;
 }
 
 template <typename T>
@@ -537,12 +589,16 @@ __device__ __forceinline__ V3 face_point(const Dev<T>& d, int f, double b1, doub
   return add(add(scl(1.0 - b1 - b2, q0), scl(b1, q1)), scl(b2, q2));
 }
 
+// Spring update, one thread per query vertex.  A vertex in a self pair (and
+// in no obstacle pair) needs a ray cast: it is appended to the cast list with
+// its unit normal and finished by k_cast; every other vertex is finished here.
+static constexpr int SPRING_THREADS = 128;
+static constexpr int CAST_THREADS = 256;
+
 template <typename T>
-__global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
-  __shared__ double shd[32];
+__global__ void __launch_bounds__(SPRING_THREADS) k_springs(Dev<T> d) {
   __shared__ int shi[32];
   const int qi = blockIdx.x * blockDim.x + threadIdx.x;
-  double e_spring = 0.0;
   int active_out = 0;
   if (qi < d.n_q) {
     const int v = d.q_verts[qi];
@@ -558,13 +614,13 @@ __global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
     const double nl = norm(n);
     n = nl > 0.0 ? scl(1.0 / nl, n) : V3{0.0, 0.0, 0.0};
     int active = d.sp.active[qi];
-    int fell_back = 0;
     int kind = d.sp.kind[qi];
     int face = d.sp.face[qi];
     double b1 = d.sp.bary[2 * qi], b2 = d.sp.bary[2 * qi + 1];
     V3 tgt = {0.0, 0.0, 0.0};
     const int js = d.obs_sphere[qi];
     const double eps = d.eps;
+    bool deferred = false;
     if (js >= 0) {
       const V3 c = {d.spheres[4 * js], d.spheres[4 * js + 1], d.spheres[4 * js + 2]};
       const double r = d.spheres[4 * js + 3];
@@ -577,17 +633,12 @@ __global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
       b1 = b2 = 0.0;
       tgt = add(c, scl(r + eps, u));
     } else if (d.pair_count[qi] > 0) {
-      const int f = ray_cast(d, v, x, scl(-1.0, n), b1, b2, fell_back);
-      if (f >= 0) {
-        V3 nf;
-        const V3 bp = face_point(d, f, b1, b2, nf);
-        active = 1;
-        kind = 0;
-        face = f;
-        tgt = add(bp, scl(eps, nf));
-      } else {
-        active = 0;
-      }
+      deferred = true;
+      const int slot = atomicAdd(&d.ctrl->n_cast, 1);  // < n_q: each vertex enters once
+      d.cast_list[slot] = qi;
+      d.cast_nrm[3 * qi] = n.x;
+      d.cast_nrm[3 * qi + 1] = n.y;
+      d.cast_nrm[3 * qi + 2] = n.z;
     } else if (active) {
       if (kind == 1) {
         const V3 c = {d.spheres[4 * face], d.spheres[4 * face + 1], d.spheres[4 * face + 2]};
@@ -610,34 +661,74 @@ __global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
         }
       }
     }
-    if (!active) {
-      kind = 0;
-      face = -1;
-      b1 = b2 = 0.0;
-      tgt = {0.0, 0.0, 0.0};
-    }
-    d.sp.active[qi] = active;
-    d.sp.fallback[qi] = fell_back;
-    d.sp.kind[qi] = kind;
-    d.sp.face[qi] = face;
-    d.sp.bary[2 * qi] = b1;
-    d.sp.bary[2 * qi + 1] = b2;
-    d.sp.target[3 * qi] = tgt.x;
-    d.sp.target[3 * qi + 1] = tgt.y;
-    d.sp.target[3 * qi + 2] = tgt.z;
-    d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
-    if (active) {
-      const V3 dd = sub(x, tgt);
-      e_spring = d.k_spring * dot(dd, dd);
-      active_out = 1;
+    if (!deferred) {
+      if (!active) {
+        kind = 0;
+        face = -1;
+        b1 = b2 = 0.0;
+        tgt = {0.0, 0.0, 0.0};
+      }
+      d.sp.active[qi] = active;
+      d.sp.fallback[qi] = 0;
+      d.sp.kind[qi] = kind;
+      d.sp.face[qi] = face;
+      d.sp.bary[2 * qi] = b1;
+      d.sp.bary[2 * qi + 1] = b2;
+      d.sp.target[3 * qi] = tgt.x;
+      d.sp.target[3 * qi + 1] = tgt.y;
+      d.sp.target[3 * qi + 2] = tgt.z;
+      d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
+      active_out = active;
     }
   }
-  const double es = block_sum(e_spring, shd);
   const int ns = block_sum_int(active_out, shi);
-  if (threadIdx.x == 0) {
-    d.e_partials[d.n_e_local + blockIdx.x] = es;
-    if (ns) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->n_springs, ns);
+  if (threadIdx.x == 0 && ns) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->n_springs, ns);
+}
+
+// Self springs of the listed vertices: one warp per vertex shares the ray
+// cast (persistent grid, warps stride over the list); lane 0 writes the
+// spring record, v_c = hit point + eps n_f.
+template <typename T>
+__global__ void __launch_bounds__(CAST_THREADS) k_cast(Dev<T> d) {
+  __shared__ int shi[32];
+  const int lane = threadIdx.x & 31;
+  const int n_warps = gridDim.x * (CAST_THREADS / 32);
+  const int n_cast = d.ctrl->n_cast;
+  int active_out = 0;
+  for (int j = (int)((blockIdx.x * (unsigned)CAST_THREADS + threadIdx.x) >> 5); j < n_cast; j += n_warps) {
+    const int qi = d.cast_list[j];
+    const int v = d.q_verts[qi];
+    const V3 x = pos(d, v);
+    const V3 n = {d.cast_nrm[3 * qi], d.cast_nrm[3 * qi + 1], d.cast_nrm[3 * qi + 2]};
+    const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
+    double b1, b2;
+    int fell_back;
+    const int f = ray_cast_warp(d, v, rv, x, scl(-1.0, n), b1, b2, fell_back);
+    if (lane == 0) {
+      V3 tgt = {0.0, 0.0, 0.0};
+      if (f >= 0) {
+        V3 nf;
+        const V3 bp = face_point(d, f, b1, b2, nf);
+        tgt = add(bp, scl(d.eps, nf));
+      } else {
+        b1 = b2 = 0.0;
+      }
+      const int active = f >= 0;
+      d.sp.active[qi] = active;
+      d.sp.fallback[qi] = fell_back;
+      d.sp.kind[qi] = 0;
+      d.sp.face[qi] = f;
+      d.sp.bary[2 * qi] = b1;
+      d.sp.bary[2 * qi + 1] = b2;
+      d.sp.target[3 * qi] = tgt.x;
+      d.sp.target[3 * qi + 1] = tgt.y;
+      d.sp.target[3 * qi + 2] = tgt.z;
+      d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
+      active_out += active;
+    }
   }
+  const int ns = block_sum_int(active_out, shi);
+  if (threadIdx.x == 0 && ns) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->n_springs, ns);
 }
 
 // ---- launchers ----
@@ -662,10 +753,13 @@ void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t 
 
 template <typename T>
 void launch_springs(const Dev<T>& d, cudaStream_t st) {
-  if (d.n_q > 0) k_springs<T><<<(d.n_q + 127) / 128, 128, 0, st>>>(d);
+  if (d.n_q <= 0) return;
+  k_springs<T><<<(d.n_q + SPRING_THREADS - 1) / SPRING_THREADS, SPRING_THREADS, 0, st>>>(d);
+  // enough warps for one pass over a list of up to 8,192 casts
+  const int per_block = CAST_THREADS / 32;
+  const int blocks = std::min((d.n_q + per_block - 1) / per_block, 1024);
+  k_cast<T><<<blocks, CAST_THREADS, 0, st>>>(d);
 }
-
-int spring_blocks(int n_q) { return (n_q + 127) / 128; }
 int scan_tiles(int n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
 
 template void launch_collision<float>(const Dev<float>&, const CollisionScratch&, cudaStream_t);

@@ -50,7 +50,7 @@ struct Ctrl {
   long long iter;        // outer iterations completed (history index)
   long long total_pcg;   // PCG iterations summed over outer iterations
   int n_items;           // spatial-hash entries of this iteration
-  int pad;
+  int n_cast;            // ray-cast list length of this iteration (reset at its end)
   long long box_lo[3];   // bounding box of all item boxes of this iteration,
   long long box_hi[3];   //   as order-preserving integer codes of doubles
 };
@@ -129,6 +129,8 @@ struct Dev {
   int* obs_sphere;       // n_q: sphere id or -1
   int max_pairs;
   SpringDev sp;
+  int* cast_list;        // n_q: query indices whose spring needs a ray cast
+  double* cast_nrm;      // 3 n_q: unit vertex normal of each listed query vertex
   R4<double>* spring_c;  // n_free: (c, mask), FP64
   // parameters
   double k_spring, eps, cell, inv_cell, tol2;
@@ -149,7 +151,8 @@ struct Dev {
   Ctrl* ctrl;
   IterRec* hist;
   int hist_cap;
-  double* e_partials;    // energy partials (local-step blocks + spring blocks)
+  double* e_partials;    // energy partials (local-step blocks + RHS blocks, whose
+                         //   rows carry the spring energy)
   int n_e_local, n_e_spring;
 };
 

@@ -78,8 +78,8 @@ void launch_adjoint_diag(const Dev<T>& d, const AdjDev<T>& a, cudaStream_t st);
 template <typename T>
 void launch_adjoint_flags(const Dev<T>& d, int* flag, cudaStream_t st);
 
-int spring_blocks(int n_q);
 int local_blocks(int n_t);
+int rhs_blocks(int n_free);
 int scan_tiles(int n);
 
 }  // namespace casim

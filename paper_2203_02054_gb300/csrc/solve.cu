@@ -130,23 +130,36 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local(Dev<T> d) {
 // ------------------------------------------------------------ RHS gather
 // b_v = sum over incident (e, slot) of w_e P_e[:, slot] + k mask_v c_v - bfix_v,
 // accumulated in FP64 (the products of the FP32 targets need no rounding).
+// The rows also carry the spring energy k mask_v |x_v - c_v|^2 (Eq. 5) of
+// this iteration's springs (positions are unchanged since the spring update),
+// summed per block in row order.
 template <typename T>
 __global__ void __launch_bounds__(RHS_THREADS) k_rhs(Dev<T> d) {
+  __shared__ double shd[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= d.n_free) return;
-  double bx = 0.0, by = 0.0, bz = 0.0;
-  const int k1 = d.inc_ptr[i + 1];
-  for (int k = d.inc_ptr[i]; k < k1; ++k) {
-    const R4<T> p = d.P[d.inc[k]];
-    bx += (double)p.x;
-    by += (double)p.y;
-    bz += (double)p.z;
+  double es = 0.0;
+  if (i < d.n_free) {
+    double bx = 0.0, by = 0.0, bz = 0.0;
+    const int k1 = d.inc_ptr[i + 1];
+    for (int k = d.inc_ptr[i]; k < k1; ++k) {
+      const R4<T> p = d.P[d.inc[k]];
+      bx += (double)p.x;
+      by += (double)p.y;
+      bz += (double)p.z;
+    }
+    const R4<double> sc = d.spring_c[i];
+    const double km = d.k_spring * sc.w;
+    const R4<double> bf = d.bfix[i];
+    d.b[i] = R4<double>{bx + km * sc.x - bf.x, by + km * sc.y - bf.y, bz + km * sc.z - bf.z, 0.0};
+    d.diag[i] = d.diagL[i] + (T)km;
+    if (sc.w != 0.0) {
+      const R4<T> xi = d.X[i];
+      const double ex = (double)xi.x - sc.x, ey = (double)xi.y - sc.y, ez = (double)xi.z - sc.z;
+      es = km * (ex * ex + ey * ey + ez * ez);
+    }
   }
-  const R4<double> sc = d.spring_c[i];
-  const double km = d.k_spring * sc.w;
-  const R4<double> bf = d.bfix[i];
-  d.b[i] = R4<double>{bx + km * sc.x - bf.x, by + km * sc.y - bf.y, bz + km * sc.z - bf.z, 0.0};
-  d.diag[i] = d.diagL[i] + (T)km;
+  const double s = block_sum(es, shd);
+  if (threadIdx.x == 0) d.e_partials[d.n_e_local + blockIdx.x] = s;
 }
 
 // ------------------------------------------------------------------ PCG
@@ -1258,6 +1271,7 @@ __global__ void k_finalize(Dev<T> d) {
     rec->energy = t;
     if (!isfinite(t) && d.stats) c->status |= ST_NONFINITE;
     c->iter += 1;
+    c->n_cast = 0;
     for (int j = 0; j < 3; ++j) {
       c->box_lo[j] = 0x7FFFFFFFFFFFFFFFLL;
       c->box_hi[j] = (long long)0x8000000000000000ULL;
@@ -1284,6 +1298,7 @@ __global__ void k_gather_positions(const R4<T>* X, const int* int_of_user, int n
 
 // ---------------------------------------------------------------- launchers
 int local_blocks(int n_t) { return (n_t + LOCAL_THREADS - 1) / LOCAL_THREADS; }
+int rhs_blocks(int n_free) { return (n_free + RHS_THREADS - 1) / RHS_THREADS; }
 
 template <typename T>
 void launch_local(const Dev<T>& d, cudaStream_t st) {
@@ -1297,7 +1312,7 @@ void launch_local(const Dev<T>& d, cudaStream_t st) {
 template <typename T>
 void launch_rhs(const Dev<T>& d, cudaStream_t st) {
   if (d.n_free == 0) return;
-  k_rhs<T><<<(d.n_free + RHS_THREADS - 1) / RHS_THREADS, RHS_THREADS, 0, st>>>(d);
+  k_rhs<T><<<rhs_blocks(d.n_free), RHS_THREADS, 0, st>>>(d);
 }
 
 template <typename T>
