@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="casim", choices=["casim", "reference"])
     ap.add_argument("--iters", type=int, default=200, help="outer iterations per step")
+    ap.add_argument("--only-plain", action="store_true",
+                    help="time the single-robot workload only (no batched, adjoint or CPU legs; for profiling)")
     return ap.parse_args()
 
 
@@ -437,7 +439,8 @@ def main():
                     "d2h_bytes_per_step": 8 * 3 * m.n_verts},
             "gpu_launches": gpu_launches,
             "roofline": {"bound": "hbm", "kernel": {1: "k_pcg (streaming)", 2: "k_pcg_rr (register-resident)",
-                                                    3: "k_pcg_cluster"}
+                                                    3: "k_pcg_cluster", 4: "k_pcg_seg (segmented)",
+                                                    5: "k_pcg_df (dataflow, register-resident)"}
                          .get(stats.pcg_kernel, "k_pcg"),
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": recorded_traffic("k_pcg"),
@@ -452,6 +455,10 @@ def main():
                                      "max_springs": max(h["n_springs"] for h in hist),
                                      "final_springs": hist[-1]["n_springs"]}},
         }
+        if args.only_plain:
+            print(json.dumps(line))
+            sim.close()
+            return 0
         line["batched"] = bench_batched(stream, value)
         line["adjoint"] = bench_adjoint(stream)
         # ---- CPU baseline: the oracle on a bounded sample of the same workload ----

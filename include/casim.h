@@ -86,23 +86,29 @@ typedef struct {
   uint64_t wait_budget_cycles;  /* SM clock cycles a grid-barrier wait may spin
                                    before the kernel gives up with CASIM_E_TIMEOUT;
                                    0 selects the default (about 2 s)                 */
-  int32_t pcg_kernel;       /* PCG kernel: 0 auto (one robot: 2 if it fits, else 1;
-                               several robots: 4 if it fits, else 3, else 1);
+  int32_t pcg_kernel;       /* PCG kernel: 0 auto (one robot: MIXED 5 if it fits,
+                               else 2 if it fits, else 1; several robots: 4 if it
+                               fits, else 3, else 1);
                                1 streaming (whole grid, vectors in memory, any
                                size); 2 register-resident (whole grid, one row per
-                               thread); 3 cluster (one 16-CTA cluster per robot,
-                               vectors in shared memory, robots from a work
-                               queue); 4 segmented streaming (blocks assigned to
-                               robots, one CG per robot, shared grid barriers).
+                               thread, grid barriers); 3 cluster (one 16-CTA
+                               cluster per robot, vectors in shared memory, robots
+                               from a work queue); 4 segmented streaming (blocks
+                               assigned to robots, one CG per robot, shared grid
+                               barriers); 5 dataflow (MIXED only: register-resident
+                               without grid barriers; every shared value carries
+                               its CG epoch and readers wait for the rows they
+                               read).
                                A forced kernel that does not fit gives
                                CASIM_E_INVALID at upload                           */
   int32_t debug_flags;      /* test-only fault injection, 0 in normal use:
                                CASIM_DEBUG_BARRIER_NEVER_COMPLETES makes the PCG
-                               grid barrier (kernels 1 and 2; the cluster kernel
-                               uses the hardware cluster barrier) wait for one
-                               block more than it has,
-                               so every wait runs out of wait_budget_cycles and
-                               the step ends with CASIM_E_TIMEOUT               */
+                               grid barrier (kernels 1, 2 and 4) or the partial
+                               poll (kernel 5) wait for one block more than it
+                               has (the cluster kernel uses the hardware cluster
+                               barrier), so every wait runs out of
+                               wait_budget_cycles and the step ends with
+                               CASIM_E_TIMEOUT                                  */
 } casim_params;
 
 #define CASIM_DEBUG_BARRIER_NEVER_COMPLETES 1
@@ -122,7 +128,7 @@ typedef struct {
   int64_t total_pcg_iters;
   casim_iter_record last;   /* record of the most recent iteration                   */
   int32_t status;           /* device status code of the last casim_sync             */
-  int32_t pcg_kernel;       /* PCG kernel chosen at upload (1..4, see casim_params)   */
+  int32_t pcg_kernel;       /* PCG kernel chosen at upload (1..5, see casim_params)   */
 } casim_stats;
 
 /* Fills *p with the defaults: MIXED, self collision, k = 1, eps = 0.005,

@@ -79,7 +79,11 @@ struct casim_sim {
   int cap_items = 0, n_slices = 0, pcg_grid = 1, n_e_local = 0, n_e_spring = 0;
   bool pcg_rr = false;  // register-resident PCG (one row per thread)
   bool pcg_cl = false;  // cluster PCG (one cluster per robot, work queue)
-  int pcg_variant = 1;  // whole-grid kernel: 1 streaming, 2 register-resident
+  int pcg_variant = 1;  // whole-grid kernel: 1 streaming, 2 register-resident, 5 dataflow
+  unsigned long long *df_u = nullptr, *df_p = nullptr;  // dataflow PCG: epoch-tagged words
+  int *halo_ptr = nullptr, *halo_rows = nullptr, *sl_lcol = nullptr;  // dataflow PCG: block halos
+  std::vector<int> halo_ptr_h, halo_rows_h, sl_lcol_h;
+  int halo_max = 0;
   bool pcg_seg = false; // segmented streaming PCG (batches: blocks per robot)
   int seg_blocks = 0;
   std::vector<int> seg_h;  // 4 x seg_blocks: lo, hi, rb0, rb1
@@ -194,6 +198,12 @@ Dev<T> make_dev(casim_sim* sim) {
   d.w = (R4<T>*)sim->w;
   d.dx = (R4<T>*)sim->dx;
   d.partials = sim->partials;
+  d.df_u = sim->df_u;
+  d.df_p = sim->df_p;
+  d.halo_ptr = sim->halo_ptr;
+  d.halo_rows = sim->halo_rows;
+  d.sl_lcol = sim->sl_lcol;
+  d.halo_max = sim->halo_max;
   d.q_verts = sim->q_verts_d;
   d.qf_ptr = sim->qf_ptr;
   d.qf = sim->qf;
@@ -308,6 +318,13 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->dx = sim->dalloc<R4<T>>(n_free);
   sim->spring_c = sim->dalloc<R4<double>>(n_free);
   sim->partials = sim->dalloc<double>(2 * 4 * (size_t)std::max(sim->pcg_grid, 1));
+  if (sim->pcg_variant == 5) {
+    sim->df_u = sim->dalloc<unsigned long long>(4 * (size_t)std::max(n_free, 1));
+    sim->df_p = sim->dalloc<unsigned long long>(8 * ((size_t)sim->pcg_grid + 1));
+    sim->halo_ptr = sim->dalloc<int>(sim->halo_ptr_h.size());
+    sim->halo_rows = sim->dalloc<int>(std::max<size_t>(sim->halo_rows_h.size(), 1));
+    sim->sl_lcol = sim->dalloc<int>(std::max<size_t>(sim->sl_lcol_h.size(), 1));
+  }
   sim->q_verts_d = sim->dalloc<int>(n_q);
   sim->qf_ptr = sim->dalloc<int>(n_q + 1);
   sim->qf = sim->dalloc<int>(qf.size());
@@ -381,6 +398,16 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   if (!sl_col.empty()) {
     CK(cudaMemcpyAsync(sim->sl_col, sl_col.data(), sizeof(int) * sl_col.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(sim->sl_val, slv.data(), sizeof(T) * slv.size(), cudaMemcpyHostToDevice, st));
+  }
+  if (sim->pcg_variant == 5) {
+    CK(cudaMemcpyAsync(sim->halo_ptr, sim->halo_ptr_h.data(), sizeof(int) * sim->halo_ptr_h.size(),
+                       cudaMemcpyHostToDevice, st));
+    if (!sim->halo_rows_h.empty())
+      CK(cudaMemcpyAsync(sim->halo_rows, sim->halo_rows_h.data(), sizeof(int) * sim->halo_rows_h.size(),
+                         cudaMemcpyHostToDevice, st));
+    if (!sim->sl_lcol_h.empty())
+      CK(cudaMemcpyAsync(sim->sl_lcol, sim->sl_lcol_h.data(), sizeof(int) * sim->sl_lcol_h.size(),
+                         cudaMemcpyHostToDevice, st));
   }
   if (n_q) {
     CK(cudaMemcpyAsync(sim->q_verts_d, sim->q_verts.data(), sizeof(int) * n_q, cudaMemcpyHostToDevice, st));
@@ -604,7 +631,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.n_w_knots < 0 || (p.n_w_knots > 0 && !p.w_knots) || p.n_w_knots > 64) why = "w_knots";
   else if (!(p.cell_size > 0.0) || !std::isfinite(p.cell_size)) why = "cell_size";
   else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
-  else if (p.pcg_kernel < 0 || p.pcg_kernel > 4) why = "pcg_kernel";
+  else if (p.pcg_kernel < 0 || p.pcg_kernel > 5) why = "pcg_kernel";
   else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
@@ -1135,6 +1162,39 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   const bool fp64 = sim->params.precision == CASIM_FP64;
   const int rr_rows = fp64 ? pcg_rr_max_rows<double>() : pcg_rr_max_rows<float>();
   const bool rr_fits = max_width <= PCG_RR_MAXW && n_free <= rr_rows;
+  // dataflow PCG (FP32 vectors only): one row per thread, one block per SM.
+  // Block b owns rows [b R, (b + 1) R), R = PCG_DF_THREADS (whole slices); its
+  // halo is the sorted list of distinct columns its rows read, and every
+  // sliced-ELL entry also gets its column's index in that list.
+  bool df_fits = !fp64 && max_width <= PCG_RR_MAXW && n_free <= pcg_df_max_rows();
+  sim->halo_ptr_h.clear();
+  sim->halo_rows_h.clear();
+  sim->sl_lcol_h.clear();
+  sim->halo_max = 0;
+  if (df_fits) {
+    const int spb = PCG_DF_THREADS / 32;
+    const int nbk = (n_free + PCG_DF_THREADS - 1) / PCG_DF_THREADS;
+    sim->halo_ptr_h.assign(nbk + 1, 0);
+    sim->sl_lcol_h.assign(sl_col.size(), 0);
+    std::vector<int> cols;
+    for (int b = 0; b < nbk; ++b) {
+      const int s0 = b * spb, s1 = std::min(sim->n_slices, s0 + spb);
+      cols.clear();
+      for (int s = s0; s < s1; ++s)
+        for (int k = sl_ptr[s]; k < sl_ptr[s + 1]; ++k)
+          if (32 * s + (k - sl_ptr[s]) % 32 < n_free) cols.push_back(sl_col[k]);
+      std::sort(cols.begin(), cols.end());
+      cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      for (int s = s0; s < s1; ++s)
+        for (int k = sl_ptr[s]; k < sl_ptr[s + 1]; ++k)
+          if (32 * s + (k - sl_ptr[s]) % 32 < n_free)
+            sim->sl_lcol_h[k] = (int)(std::lower_bound(cols.begin(), cols.end(), sl_col[k]) - cols.begin());
+      sim->halo_rows_h.insert(sim->halo_rows_h.end(), cols.begin(), cols.end());
+      sim->halo_ptr_h[b + 1] = (int)sim->halo_rows_h.size();
+      sim->halo_max = std::max(sim->halo_max, (int)cols.size());
+    }
+    if ((size_t)sim->halo_max * 16 > PCG_DF_HALO_MAX_BYTES || !pcg_df_prepare(16 * sim->halo_max)) df_fits = false;
+  }
   // cluster PCG: every robot's rows must fit the cluster's shared memory
   int max_robot_rows = 0;
   for (int r = 0; r < sim->n_robots; ++r)
@@ -1145,7 +1205,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   if (need <= cap) max_clusters = fp64 ? pcg_cluster_max_clusters<double>(cap) : pcg_cluster_max_clusters<float>(cap);
   const bool cl_fits = need <= cap && max_clusters > 0;
   const int kern = sim->params.pcg_kernel;
-  if ((kern == 2 && !rr_fits) || (kern == 3 && !cl_fits))
+  if ((kern == 2 && !rr_fits) || (kern == 3 && !cl_fits) || (kern == 5 && !df_fits))
     return sim->fail(CASIM_E_INVALID, "requested PCG kernel does not fit this mesh (" + std::to_string(n_free) +
                                           " rows, width " + std::to_string(max_width) + ")");
   // auto: a single system runs fastest on the whole-grid register-resident
@@ -1194,12 +1254,15 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
     sim->pcg_grid = std::max(sim->pcg_grid, used);
   }
   sim->pcg_cl = !sim->pcg_seg && ((kern == 3) || (kern == 0 && cl_fits && (many || !rr_fits)));
-  sim->pcg_rr = !sim->pcg_cl && !sim->pcg_seg && ((kern == 2) || (kern == 0 && rr_fits));
-  sim->pcg_variant = sim->pcg_rr ? 2 : 1;
+  const bool df = !sim->pcg_cl && !sim->pcg_seg && ((kern == 5) || (kern == 0 && !many && df_fits));
+  sim->pcg_rr = !df && !sim->pcg_cl && !sim->pcg_seg && ((kern == 2) || (kern == 0 && rr_fits));
+  sim->pcg_variant = df ? 5 : sim->pcg_rr ? 2 : 1;
   sim->cl_rows_cap = cap;
   sim->pcg_clusters = std::max(1, std::min(max_clusters, sim->n_robots));
   if (sim->pcg_seg) {
     // partials buffer is sized by pcg_grid (already >= seg_blocks)
+  } else if (sim->pcg_variant == 5) {
+    sim->pcg_grid = std::max(1, (n_free + PCG_DF_THREADS - 1) / PCG_DF_THREADS);
   } else if (sim->pcg_rr) {
     sim->pcg_grid = std::max(1, (n_free + PCG_RR_THREADS - 1) / PCG_RR_THREADS);
   } else {

@@ -112,6 +112,12 @@ struct Dev {
   R4<T>* w;
   R4<T>* dx;             // PCG correction (streaming kernel)
   double* partials;      // 2 x 4 x pcg grid
+  unsigned long long* df_u;  // dataflow PCG: 2 x n_free x 2 epoch-tagged words of u
+  unsigned long long* df_p;  // dataflow PCG: 2 x (grid + 1) x 4 epoch-tagged partial words
+  const int* halo_ptr;   // dataflow PCG: per block, start of its halo in halo_rows
+  const int* halo_rows;  //   distinct rows each block's SpMV reads (sorted per block)
+  const int* sl_lcol;    //   per sliced-ELL entry: the column's index in its block's halo
+  int halo_max;          //   longest halo (rows)
   // collision
   const int* q_verts;    // n_q internal vertex ids (ascending)
   const int* qf_ptr;     // n_q + 1 incident boundary faces

@@ -19,6 +19,8 @@ static constexpr int PCG_RR_THREADS = 256;
 static constexpr int PCG_RR_MAXW = 16;   // widest sliced-ELL row kept in registers
 static constexpr int PCG_CL_THREADS = 1024;
 static constexpr int PCG_SEG_THREADS = 256;
+static constexpr int PCG_DF_THREADS = 384;
+static constexpr size_t PCG_DF_HALO_MAX_BYTES = 160 * 1024;  // halo words in shared memory
 static constexpr int PCG_CL_SIZE = 16;   // CTAs per cluster (non-portable size)
 
 template <typename T>
@@ -33,6 +35,8 @@ template <typename T>
 cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st);
 template <typename T>
 int pcg_rr_max_rows();
+int pcg_df_max_rows();
+bool pcg_df_prepare(int halo_bytes);
 template <typename T>
 int pcg_seg_max_blocks();
 template <typename T>

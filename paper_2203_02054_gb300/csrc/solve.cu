@@ -13,6 +13,7 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -331,12 +332,14 @@ struct DotAcc<double> {
 };
 
 // Block sums of NV per-thread values by fixed shuffle trees (within each warp,
-// then over the NW warp sums); the FP64 result is valid in lane 0 of warp 0.
+// then over the NW warp sums, padded with zeros to a power of two); the FP64
+// result is valid in lane 0 of warp 0.
 // Contains one __syncthreads; sh holds at least 32 * NV doubles.
 template <int NV, int NW, typename A>
 __device__ __forceinline__ void block_sums(A (&v)[NV], double* sh, double (&bs)[NV]) {
   static_assert(sizeof(A) == sizeof(double), "accumulator must fit a double slot");
-  static_assert(NW >= 1 && NW <= 32 && (NW & (NW - 1)) == 0, "warps per block must be a power of two");
+  static_assert(NW >= 1 && NW <= 32, "at most 32 warps per block");
+  constexpr int NW2 = NW <= 1 ? 1 : NW <= 2 ? 2 : NW <= 4 ? 4 : NW <= 8 ? 8 : NW <= 16 ? 16 : 32;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   A* sa = reinterpret_cast<A*>(sh);
 #pragma unroll
@@ -354,7 +357,7 @@ __device__ __forceinline__ void block_sums(A (&v)[NV], double* sh, double (&bs)[
     for (int k = 0; k < NV; ++k) {
       A t = lane < NW ? sa[k * 32 + lane] : acc_zero<A>();
 #pragma unroll
-      for (int o = NW >> 1; o > 0; o >>= 1) t = acc_add(t, shfl_down(t, o));
+      for (int o = NW2 >> 1; o > 0; o >>= 1) t = acc_add(t, shfl_down(t, o));
       bs[k] = acc_to_f64(t);
     }
   }
@@ -828,6 +831,402 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
     }
   }
   if (i == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, bb);
+}
+
+// ------------------------------------------------------- dataflow PCG (FP32)
+// Register-resident CG (one row per thread) with one grid-wide wait per
+// iteration instead of two.  The preconditioned residual u that neighbours
+// read is published as epoch-tagged words: each row as two 8-byte words, a
+// 16-bit epoch tag over 48 bits of payload (x, y, z in FP32).  Aligned 8-byte
+// accesses are single-copy atomic, so a word whose tag matches holds that
+// epoch's payload; a reader re-reads words that still carry an older tag
+// (bounded waits), so the SpMV waits only for the rows it reads and needs no
+// grid barrier.  Each block copies its halo (the distinct rows its SpMV
+// reads, listed at upload) into shared memory with mostly contiguous loads,
+// then multiplies from shared memory.  The reduction of (r.u, w.u, r.r) is
+// one arrival on the grid counter (relaxed: no fences) after the block has
+// stored its partials as tagged words; once the round completes, warp 0
+// reads the partials (re-reading any whose tag is not yet current) and sums
+// them in block order.  Words are double-buffered by epoch parity and zeroed
+// before each launch.  No block is ever more than one epoch ahead of a
+// reader of its words (it cannot pass a reduction before the reader has
+// arrived, after its last read of the older epoch), so a stale word is at
+// most two epochs old and its tag cannot match.  Sums and CG scalars are
+// formed as in the barrier kernels (block order, fixed trees), so results do
+// not depend on timing.
+__device__ __forceinline__ void st_v2_relaxed(unsigned long long* p, unsigned long long a, unsigned long long b) {
+  asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
+}
+__device__ __forceinline__ void ld_v2_relaxed(const unsigned long long* p, unsigned long long& a,
+                                              unsigned long long& b) {
+  asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(a), "=l"(b) : "l"(p));
+}
+
+// same load with the address base + 16 * idx formed inside the asm, so that
+// the compiler keeps one index register per row, not one 64-bit address
+__device__ __forceinline__ void ld_v2_relaxed_at(const unsigned long long* base, int idx, unsigned long long& a,
+                                                 unsigned long long& b) {
+  asm volatile(
+      "{\n\t.reg .u64 ad;\n\t"
+      "mad.wide.s32 ad, %2, 16, %3;\n\t"
+      "ld.relaxed.gpu.global.v2.u64 {%0, %1}, [ad];\n\t}"
+      : "=l"(a), "=l"(b)
+      : "r"(idx), "l"(base));
+}
+
+__device__ __forceinline__ unsigned long long df_tag(unsigned e) { return (unsigned long long)(e & 0xFFFFu) << 48; }
+__device__ __forceinline__ bool df_has(unsigned long long w, unsigned long long tag) {
+  return (w & 0xFFFF000000000000ull) == tag;
+}
+
+// u row: w0 = tag | x | y[31:16], w1 = tag | y[15:0] | z
+__device__ __forceinline__ void df_pack_u(unsigned long long tag, float x, float y, float z, unsigned long long& w0,
+                                          unsigned long long& w1) {
+  const unsigned bx = __float_as_uint(x), by = __float_as_uint(y), bz = __float_as_uint(z);
+  w0 = tag | ((unsigned long long)bx << 16) | (by >> 16);
+  w1 = tag | ((unsigned long long)(by & 0xFFFFu) << 32) | bz;
+}
+__device__ __forceinline__ void df_unpack_u(unsigned long long w0, unsigned long long w1, float& x, float& y,
+                                            float& z) {
+  x = __uint_as_float((unsigned)(w0 >> 16));
+  y = __uint_as_float((((unsigned)w0 & 0xFFFFu) << 16) | ((unsigned)(w1 >> 32) & 0xFFFFu));
+  z = __uint_as_float((unsigned)w1);
+}
+
+// three doubles (192 bits) as four 48-bit chunks under one tag each
+__device__ __forceinline__ void df_pack_3d(unsigned long long tag, const double (&v)[3], unsigned long long (&w)[4]) {
+  const unsigned long long b0 = __double_as_longlong(v[0]), b1 = __double_as_longlong(v[1]),
+                           b2 = __double_as_longlong(v[2]);
+  const unsigned long long m48 = 0xFFFFFFFFFFFFull;
+  w[0] = tag | (b0 >> 16);
+  w[1] = tag | ((b0 & 0xFFFFull) << 32) | (b1 >> 32);
+  w[2] = tag | ((b1 & 0xFFFFFFFFull) << 16) | (b2 >> 48);
+  w[3] = tag | (b2 & m48);
+}
+__device__ __forceinline__ void df_unpack_3d(const unsigned long long (&w)[4], double (&v)[3]) {
+  const unsigned long long m48 = 0xFFFFFFFFFFFFull;
+  const unsigned long long c0 = w[0] & m48, c1 = w[1] & m48, c2 = w[2] & m48, c3 = w[3] & m48;
+  v[0] = __longlong_as_double((long long)((c0 << 16) | (c1 >> 32)));
+  v[1] = __longlong_as_double((long long)(((c1 & 0xFFFFFFFFull) << 32) | (c2 >> 16)));
+  v[2] = __longlong_as_double((long long)(((c2 & 0xFFFFull) << 48) | c3));
+}
+
+// Pause between polls of words that are not yet current, so that spinning
+// readers do not crowd the L2 slices that the awaited stores go to.
+#ifndef CASIM_DF_BACKOFF_NS
+#define CASIM_DF_BACKOFF_NS 0
+#endif
+
+// Bounded polling: every 32nd poll checks the abort word and the clock budget
+// (on expiry records ST_TIMEOUT and raises abort).  Returns false to stop.
+struct DfWait {
+  long long t0 = 0;
+  unsigned n = 0;
+  __device__ __forceinline__ bool again(Ctrl* c, unsigned long long budget) {
+    if (CASIM_DF_BACKOFF_NS > 0) __nanosleep(CASIM_DF_BACKOFF_NS);
+    if ((++n & 31u) != 0) return true;
+    if (*(volatile int*)&c->abort) return false;
+    const long long now = clock64();
+    if (t0 == 0) {
+      t0 = now;
+      return true;
+    }
+    if ((unsigned long long)(now - t0) > budget) {
+      atomicExch(&c->abort, 1);
+      atomicOr(&c->status, ST_TIMEOUT);
+      return false;
+    }
+    return true;
+  }
+};
+
+static constexpr int DF_MAXQ = 5;  // partial slots per lane of warp 0: up to 160 blocks
+
+// Warp 0: lane 0 stores the block's sums under epoch e and arrives on the
+// grid counter (relaxed; the top-bit scheme of the barrier kernels, bounded
+// wait); once the round is complete every lane reads its blocks' slots
+// (lane, lane + 32, ...), re-reading any that do not yet carry epoch e, adds
+// them in block order, and a fixed shuffle tree gives tot in lane 0.  Returns
+// false (warp-uniform) when a wait gave up or another block aborted.
+__device__ __forceinline__ bool df_reduce(const Dev<float>& d, unsigned e, const double (&bs)[3],
+                                          double (&tot)[3]) {
+  const int lane = threadIdx.x & 31;
+  const int nb = gridDim.x;
+  unsigned long long* buf = d.df_p + (size_t)(e & 1u) * 4 * (size_t)nb;
+  const unsigned long long tag = df_tag(e);
+  int arrived = 1;
+  if (lane == 0) {
+    unsigned long long w[4];
+    df_pack_3d(tag, bs, w);
+    st_v2_relaxed(buf + 4 * (size_t)blockIdx.x, w[0], w[1]);
+    st_v2_relaxed(buf + 4 * (size_t)blockIdx.x + 2, w[2], w[3]);
+    const unsigned add = blockIdx.x == 0 ? (0x80000000u - ((unsigned)nb - 1u + d.bar_extra)) : 1u;
+    const unsigned old = atomicAdd(&d.ctrl->bar_count, add);
+    volatile unsigned* vc = &d.ctrl->bar_count;
+    DfWait wt;
+    while (((old ^ *vc) & 0x80000000u) == 0)
+      if (!wt.again(d.ctrl, d.wait_budget)) {
+        arrived = 0;
+        break;
+      }
+  }
+  if (!__shfl_sync(0xffffffffu, arrived, 0)) return false;
+  unsigned long long w[DF_MAXQ][4];
+#pragma unroll
+  for (int q = 0; q < DF_MAXQ; ++q) {
+    const int b = lane + 32 * q;
+    if (b < nb) {
+      ld_v2_relaxed(buf + 4 * (size_t)b, w[q][0], w[q][1]);
+      ld_v2_relaxed(buf + 4 * (size_t)b + 2, w[q][2], w[q][3]);
+    }
+  }
+  // slots whose store is not yet visible: re-read them all, then re-check
+  auto fresh = [&](int q) {
+    return df_has(w[q][0], tag) && df_has(w[q][1], tag) && df_has(w[q][2], tag) && df_has(w[q][3], tag);
+  };
+  unsigned stale = 0;
+#pragma unroll
+  for (int q = 0; q < DF_MAXQ; ++q)
+    if (lane + 32 * q < nb && !fresh(q)) stale |= 1u << q;
+  DfWait wt;
+  while (stale != 0 && wt.again(d.ctrl, d.wait_budget)) {
+#pragma unroll
+    for (int q = 0; q < DF_MAXQ; ++q)
+      if (stale & (1u << q)) {
+        const int b = lane + 32 * q;
+        ld_v2_relaxed(buf + 4 * (size_t)b, w[q][0], w[q][1]);
+        ld_v2_relaxed(buf + 4 * (size_t)b + 2, w[q][2], w[q][3]);
+      }
+#pragma unroll
+    for (int q = 0; q < DF_MAXQ; ++q)
+      if ((stale & (1u << q)) && fresh(q)) stale &= ~(1u << q);
+  }
+  if (!__all_sync(0xffffffffu, stale == 0)) return false;
+  double a[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int q = 0; q < DF_MAXQ; ++q) {
+    if (lane + 32 * q < nb) {
+      double v[3];
+      df_unpack_3d(w[q], v);
+      a[0] += v[0];
+      a[1] += v[1];
+      a[2] += v[2];
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    tot[k] = a[k];
+  }
+  return true;
+}
+
+template <int MAXW>
+__global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
+  constexpr int NW = PCG_DF_THREADS / 32;
+  __shared__ CgShared<float> cs;
+  __shared__ double sc[5];  // bb, rr, gamma, alpha, beta: used by lane 0 of warp 0 only
+  extern __shared__ unsigned long long halo[];  // 2 tagged words per halo row
+  const int lane = threadIdx.x & 31;
+  const bool w0 = threadIdx.x < 32;
+  const int n = d.n_free;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = i < n;
+  const size_t ustride = 2 * (size_t)n;  // words of one parity buffer of u
+  int lcol[MAXW];  // columns as indices into the block's halo
+  float val[MAXW];
+  int width = 0;
+  float dg = 1.0f;
+  if (act) {
+    const int sl = i >> 5, ln = i & 31;
+    const int base = d.sl_ptr[sl];
+    width = (d.sl_ptr[sl + 1] - base) >> 5;
+#pragma unroll
+    for (int j = 0; j < MAXW; ++j) {
+      lcol[j] = j < width ? d.sl_lcol[base + j * 32 + ln] : 0;
+      val[j] = j < width ? d.sl_val[base + j * 32 + ln] : 0.0f;
+    }
+    dg = d.diag[i];
+  }
+  auto store_u = [&](unsigned e, const float (&uu)[3]) {
+    unsigned long long a, b;
+    df_pack_u(df_tag(e), uu[0], uu[1], uu[2], a, b);
+    st_v2_relaxed(d.df_u + (size_t)(e & 1u) * ustride + 2 * (size_t)i, a, b);
+  };
+  const int h0 = d.halo_ptr[blockIdx.x], nh = d.halo_ptr[blockIdx.x + 1] - h0;
+  // A u for this row from the neighbours' u of epoch e.  Called by every
+  // thread of the block: the block copies its halo rows of epoch e into
+  // shared memory (re-reading rows whose words are not yet current), then
+  // each active row multiplies from shared memory.
+  auto spmv = [&](unsigned e, const float (&self)[3], float (&ax)[3]) {
+    const unsigned long long* buf = d.df_u + (size_t)(e & 1u) * ustride;
+    const unsigned long long tag = df_tag(e);
+    bool stale = false;
+#pragma unroll 4
+    for (int k = threadIdx.x; k < nh; k += PCG_DF_THREADS) {
+      unsigned long long w0, w1;
+      ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
+      halo[2 * k] = w0;
+      halo[2 * k + 1] = w1;
+      stale |= !(df_has(w0, tag) && df_has(w1, tag));
+    }
+    if (stale) {
+      DfWait wt;
+      for (int k = threadIdx.x; k < nh; k += PCG_DF_THREADS) {
+        unsigned long long w0 = halo[2 * k], w1 = halo[2 * k + 1];
+        while (!(df_has(w0, tag) && df_has(w1, tag))) {
+          if (!wt.again(d.ctrl, d.wait_budget)) break;
+          ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
+        }
+        halo[2 * k] = w0;
+        halo[2 * k + 1] = w1;
+      }
+      // a wait that gave up leaves the abort word raised: the next reduction
+      // cannot complete, so every block leaves at its next reduction
+    }
+    __syncthreads();
+    if (act) {
+      ax[0] = dg * self[0];
+      ax[1] = dg * self[1];
+      ax[2] = dg * self[2];
+#pragma unroll
+      for (int j = 0; j < MAXW; ++j) {
+        if (j < width) {
+          float vx, vy, vz;
+          df_unpack_u(halo[2 * lcol[j]], halo[2 * lcol[j] + 1], vx, vy, vz);
+          ax[0] += val[j] * vx;
+          ax[1] += val[j] * vy;
+          ax[2] += val[j] * vz;
+        }
+      }
+    }
+    __syncthreads();  // the halo is rewritten by the next call
+  };
+  unsigned ue = 0, re = 0;  // epochs of u and of the reductions (the same in every thread)
+  float r[3], u[3], w[3], p[3], s[3], dd[3] = {0.0f, 0.0f, 0.0f};
+  double a0[2] = {0.0, 0.0};
+  ++ue;
+  if (act) {
+    double rv[3];
+    residual_row_f64(d, i, dg, rv, a0);
+    for (int c = 0; c < 3; ++c) {
+      r[c] = (float)rv[c];
+      u[c] = r[c] / dg;
+    }
+    store_u(ue, u);
+  }
+  {
+    double bs2[2], t[3];
+    block_sums<2, NW>(a0, cs.sh, bs2);
+    ++re;
+    if (w0) {
+      const double bs[3] = {bs2[0], bs2[1], 0.0};
+      const bool ok = df_reduce(d, re, bs, t);
+      if (lane == 0) {
+        sc[0] = t[0];
+        sc[1] = t[1];
+        cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
+      }
+    }
+    __syncthreads();
+  }
+  if (cs.flag == CG_ABORT) return;
+  int it = 0;
+  if (cs.flag == CG_CONTINUE) {
+    DW a1[2] = {acc_zero<DW>(), acc_zero<DW>()};
+    spmv(ue, u, w);
+    if (act) {
+      a1[0] = dot3(r[0], r[1], r[2], u[0], u[1], u[2]);
+      a1[1] = dot3(w[0], w[1], w[2], u[0], u[1], u[2]);
+      for (int c = 0; c < 3; ++c) {
+        p[c] = u[c];
+        s[c] = w[c];
+      }
+    }
+    {
+      double bs2[2], t[3];
+      block_sums<2, NW>(a1, cs.sh, bs2);
+      ++re;
+      if (w0) {
+        const double bs[3] = {bs2[0], bs2[1], 0.0};
+        const bool ok = df_reduce(d, re, bs, t);
+        if (lane == 0) {
+          if (ok) {
+            sc[2] = t[0];
+            sc[3] = t[0] / t[1];
+            cs.ta = (float)sc[3];
+          }
+          cs.flag = ok ? CG_CONTINUE : CG_ABORT;
+        }
+      }
+      __syncthreads();
+    }
+    if (cs.flag == CG_ABORT) return;
+    float ta = cs.ta;
+    for (it = 1; it <= d.max_iter; ++it) {
+      ++ue;
+      if (act) {
+        for (int c = 0; c < 3; ++c) {
+          dd[c] += ta * p[c];
+          r[c] -= ta * s[c];
+          u[c] = r[c] / dg;
+        }
+        store_u(ue, u);
+      }
+      DW a2[3] = {acc_zero<DW>(), acc_zero<DW>(), acc_zero<DW>()};
+      spmv(ue, u, w);
+      if (act) {
+        a2[0] = dot3(r[0], r[1], r[2], u[0], u[1], u[2]);
+        a2[1] = dot3(w[0], w[1], w[2], u[0], u[1], u[2]);
+        a2[2] = dot3(r[0], r[1], r[2], r[0], r[1], r[2]);
+      }
+      {
+        double bs[3], t[3];
+        block_sums<3, NW>(a2, cs.sh, bs);
+        ++re;
+        if (w0) {
+          const bool ok = df_reduce(d, re, bs, t);
+          if (lane == 0) {
+            int f = CG_ABORT;
+            if (ok) {
+              double gamma = sc[2], alpha = sc[3], beta = sc[4], rr = sc[1];
+              f = cg_scalars(t, sc[0], d.tol2, gamma, alpha, beta, rr);
+              if (f == CG_NONFINITE && blockIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
+              sc[1] = rr;
+              sc[2] = gamma;
+              sc[3] = alpha;
+              sc[4] = beta;
+              cs.ta = (float)alpha;
+              cs.tb = (float)beta;
+            }
+            cs.flag = f;
+          }
+        }
+        __syncthreads();
+      }
+      const int f = cs.flag;
+      if (f == CG_ABORT) return;
+      if (f != CG_CONTINUE) break;
+      ta = cs.ta;
+      const float tb = cs.tb;
+      if (act)
+        for (int c = 0; c < 3; ++c) {
+          p[c] = u[c] + tb * p[c];
+          s[c] = w[c] + tb * s[c];
+        }
+    }
+    if (it > d.max_iter) {
+      it = d.max_iter;
+      if (i == 0) set_status(d.ctrl, ST_PCG_MAXIT);
+    }
+    if (act) {
+      R4<float> t = d.X[i];
+      t.x += dd[0]; t.y += dd[1]; t.z += dd[2];
+      d.X[i] = t;
+    }
+  }
+  if (i == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, sc[1], sc[0]);
 }
 
 // Segmented streaming variant for batches: block b works on a contiguous row
@@ -1333,13 +1732,26 @@ int pcg_rr_max_rows() {
   return sms * per * PCG_RR_THREADS;
 }
 
+bool pcg_df_prepare(int halo_bytes) {
+  return cudaFuncSetAttribute(k_pcg_df<PCG_RR_MAXW>, cudaFuncAttributeMaxDynamicSharedMemorySize, halo_bytes) ==
+         cudaSuccess;
+}
+
+int pcg_df_max_rows() {
+  int dev = 0, sms = 0, per = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_df<PCG_RR_MAXW>, PCG_DF_THREADS, 0);
+  const int blocks = std::min(sms * per, 32 * DF_MAXQ);
+  return blocks * PCG_DF_THREADS;
+}
+
 template <typename T>
 cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st) {
   if (d.n_free == 0) return cudaSuccess;
-  const bool rr = variant != 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(rr ? PCG_RR_THREADS : PCG_THREADS);
+  cfg.blockDim = dim3(variant == 5 ? PCG_DF_THREADS : variant == 2 ? PCG_RR_THREADS : PCG_THREADS);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -1347,6 +1759,19 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st) 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (variant == 5) {
+    if constexpr (std::is_same<T, float>::value) {
+      // epoch-tagged words start from zero in every launch
+      cudaError_t e = cudaMemsetAsync(d.df_u, 0, sizeof(unsigned long long) * 4 * (size_t)d.n_free, st);
+      if (e == cudaSuccess)
+        e = cudaMemsetAsync(d.df_p, 0, sizeof(unsigned long long) * 8 * (size_t)(grid + 1), st);
+      if (e != cudaSuccess) return e;
+      cfg.dynamicSmemBytes = 16 * (size_t)d.halo_max;
+      return cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW>, d);
+    } else {
+      return cudaErrorInvalidValue;
+    }
+  }
   if (variant == 2) return cudaLaunchKernelEx(&cfg, k_pcg_rr<T, PCG_RR_MAXW>, d);
   return cudaLaunchKernelEx(&cfg, k_pcg<T>, d);
 }

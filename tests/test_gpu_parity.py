@@ -277,17 +277,23 @@ def test_deterministic_and_checkpoint_resume():
         s.close()
 
 
-def test_pcg_cap_warning_and_timeout_status():
+def test_pcg_cap_warning():
     m = synth.config2_finger()
     sim = casim.Sim(m, pcg_max_iter=1)
     sim.step(1)
     assert sim.sync() == casim.CASIM_W_PCG_MAXIT
     sim.close()
-    # a barrier that waits for a block that does not exist must give up after
-    # its clock budget (~10 ms here) with a timeout status; the context stays
-    # usable afterwards
+
+
+@pytest.mark.parametrize("kernel", [2, 5])
+def test_pcg_wait_gives_up_with_timeout_status(kernel):
+    """A wait for a block that does not exist (the grid barrier of kernel 2,
+    the partial poll of kernel 5) must give up after its clock budget (~10 ms
+    here) with a timeout status; the context stays usable afterwards."""
+    m = synth.config2_finger()
     sim = casim.Sim(m, wait_budget_cycles=20_000_000, debug_flags=casim.CASIM_DEBUG_BARRIER_NEVER_COMPLETES,
-                    pcg_kernel=2)
+                    pcg_kernel=kernel)
+    assert sim.stats().pcg_kernel == kernel
     sim.step(1)
     with pytest.raises(casim.CasimError) as ei:
         sim.sync()
@@ -318,10 +324,11 @@ def test_host_validation_rejects_bad_input_before_launch():
     sim.close()
 
 
-@pytest.mark.parametrize("kernel", [1, 2, 3])
+@pytest.mark.parametrize("kernel", [1, 2, 3, 5])
 def test_both_pcg_kernels_match_oracle(kernel):
     m = synth.small_finger(nx=24, ny=4, nz=4, n_ch=4, seed=31, n_iters=8)
     sim = casim.Sim(m, pcg_kernel=kernel)
+    assert sim.stats().pcg_kernel == kernel
     sim.step(m.n_iters)
     assert sim.sync() == 0
     ref = loop.run_mesh(m)
