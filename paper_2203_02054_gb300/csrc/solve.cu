@@ -282,6 +282,20 @@ __device__ __forceinline__ DW dw_add(DW x, DW y) {
   return z;
 }
 
+// Sloppy double-word addition (Joldes, Muller, Popescu 2017, Algorithm 5):
+// 11 operations; for operands of the same sign the relative error is at most
+// 3u^2, otherwise the error is at most about u^2 (|x| + |y|), the same kind of
+// bound as an FP64 sum has.
+__device__ __forceinline__ DW dw_add_sloppy(DW x, DW y) {
+  float sh, sl;
+  two_sum_f(x.hi, y.hi, sh, sl);
+  const float v = __fadd_rn(x.lo, y.lo);
+  const float w = __fadd_rn(sl, v);
+  DW z;
+  fast_two_sum_f(sh, w, z.hi, z.lo);
+  return z;
+}
+
 __device__ __forceinline__ DW dot3(float a0, float a1, float a2, float b0, float b1, float b2) {
   float p = __fmul_rn(a0, b0);
   float e = __fmaf_rn(a0, b0, -p);
@@ -363,6 +377,36 @@ __device__ __forceinline__ void block_sums(A (&v)[NV], double* sh, double (&bs)[
   }
 }
 
+// Block sums of NV per-thread double words by fixed shuffle trees of sloppy
+// double-word additions; the double-word result is valid in lane 0 of warp 0.
+// Contains one __syncthreads; sh holds at least 32 * NV doubles.
+template <int NV, int NW>
+__device__ __forceinline__ void block_sums_dw(DW (&v)[NV], double* sh, DW (&bs)[NV]) {
+  static_assert(NW >= 1 && NW <= 32, "at most 32 warps per block");
+  constexpr int NW2 = NW <= 1 ? 1 : NW <= 2 ? 2 : NW <= 4 ? 4 : NW <= 8 ? 8 : NW <= 16 ? 16 : 32;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  DW* sa = reinterpret_cast<DW*>(sh);
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] = dw_add_sloppy(v[k], shfl_down(v[k], o));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) sa[k * 32 + wid] = v[k];
+  }
+  __syncthreads();
+  if (wid == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      DW t = lane < NW ? sa[k * 32 + lane] : DW{0.0f, 0.0f};
+#pragma unroll
+      for (int o = NW2 >> 1; o > 0; o >>= 1) t = dw_add_sloppy(t, shfl_down(t, o));
+      bs[k] = t;
+    }
+  }
+}
+
 // Called by all of warp 0 after block_sums.  Lane 0 stores the block's sums
 // as its partials, arrives and waits; the warp then adds the partials of
 // blocks [b0, b1) in block order: each lane its blocks in increasing order,
@@ -404,20 +448,31 @@ __device__ __forceinline__ bool warp0_reduce(const GridCtx& g, unsigned& epoch, 
 
 enum { CG_CONTINUE = 0, CG_DONE = 1, CG_NONFINITE = 2, CG_ABORT = 3 };
 
-// CG scalars after the reduction of (gamma_k, delta_k, rr) (lane 0 of warp 0).
+// CG scalars after the reduction of (gamma_k, delta_k, rr), by all of warp 0
+// (inputs read from lane 0, outputs in every lane).
 // alpha_k = gamma_k / (delta_k - beta_k gamma_k / alpha_{k-1}) with
 // beta_k = gamma_k / gamma_{k-1}, rearranged with q = gamma_{k-1} alpha_{k-1}
-// to alpha_k = gamma_k q / (delta_k q - gamma_k^2), so that one division lies
-// on the dependent path (beta_k's division runs beside it).
-__device__ __forceinline__ int cg_scalars(const double (&t)[3], double bb, double tol2, double& gamma, double& alpha,
-                                          double& beta, double& rr) {
-  const double gnew = t[0], delta = t[1];
-  rr = t[2];
+// to alpha_k = gamma_k q / (delta_k q - gamma_k^2); lanes 0 and 1 form
+// alpha_k's and beta_k's quotients in the same division, so one FP64
+// division lies on the dependent path.
+__device__ __forceinline__ int cg_scalars_warp(const double (&t)[3], double bb_l0, double tol2, double& gamma,
+                                               double& alpha, double& beta, double& rr) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const double gnew = __shfl_sync(full, t[0], 0), delta = __shfl_sync(full, t[1], 0);
+  const double bb = __shfl_sync(full, bb_l0, 0);
+  const double g = __shfl_sync(full, gamma, 0), a = __shfl_sync(full, alpha, 0);
+  rr = __shfl_sync(full, t[2], 0);
+  gamma = g;
+  alpha = a;
   if (!isfinite(gnew) || !isfinite(delta) || !isfinite(rr)) return CG_NONFINITE;
   if (rr <= tol2 * bb) return CG_DONE;
-  beta = gnew / gamma;
-  const double q = gamma * alpha;
-  alpha = (gnew * q) / (delta * q - gnew * gnew);
+  const double q = g * a;
+  const double num = lane == 1 ? gnew : gnew * q;
+  const double den = lane == 1 ? g : delta * q - gnew * gnew;
+  const double quo = num / den;
+  beta = __shfl_sync(full, quo, 1);
+  alpha = __shfl_sync(full, quo, 0);
   gamma = gnew;
   return CG_CONTINUE;
 }
@@ -625,10 +680,10 @@ __global__ void __launch_bounds__(PCG_THREADS, 1) k_pcg(Dev<T> d) {
         block_sums<3, NW>(a2, cs.sh, bs);
         if (w0) {
           const bool ok = warp0_reduce<3>(g, epoch, bs, 0, gridDim.x, t);
+          int f = CG_ABORT;
+          if (ok) f = cg_scalars_warp(t, bb, d.tol2, gamma, alpha, beta, rr);
           if (lane == 0) {
-            int f = CG_ABORT;
             if (ok) {
-              f = cg_scalars(t, bb, d.tol2, gamma, alpha, beta, rr);
               if (f == CG_NONFINITE && blockIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
               cs.ta = (T)alpha;
               cs.tb = (T)beta;
@@ -796,10 +851,10 @@ __global__ void __launch_bounds__(PCG_RR_THREADS, 2) k_pcg_rr(Dev<T> d) {
         block_sums<3, NW>(a2, cs.sh, bs);
         if (w0) {
           const bool ok = warp0_reduce<3>(g, epoch, bs, 0, gridDim.x, t);
+          int f = CG_ABORT;
+          if (ok) f = cg_scalars_warp(t, bb, d.tol2, gamma, alpha, beta, rr);
           if (lane == 0) {
-            int f = CG_ABORT;
             if (ok) {
-              f = cg_scalars(t, bb, d.tol2, gamma, alpha, beta, rr);
               if (f == CG_NONFINITE && blockIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
               cs.ta = (T)alpha;
               cs.tb = (T)beta;
@@ -943,13 +998,41 @@ struct DfWait {
 static constexpr int DF_MAXQ = 5;  // partial slots per lane of warp 0: up to 160 blocks
 
 // Warp 0: lane 0 stores the block's sums under epoch e and arrives on the
-// grid counter (relaxed; the top-bit scheme of the barrier kernels, bounded
-// wait); once the round is complete every lane reads its blocks' slots
-// (lane, lane + 32, ...), re-reading any that do not yet carry epoch e, adds
-// them in block order, and a fixed shuffle tree gives tot in lane 0.  Returns
-// false (warp-uniform) when a wait gave up or another block aborted.
-__device__ __forceinline__ bool df_reduce(const Dev<float>& d, unsigned e, const double (&bs)[3],
-                                          double (&tot)[3]) {
+// grid counter, then waits for the round to complete.  The arrival is a
+// fire-and-forget add: after round e (counted from 1 in each launch) the
+// counter's top bit equals e & 1, because the counter starts at zero and
+// every complete round adds 2^31 (block 0 adds 2^31 - (nblocks - 1), the
+// others 1), so the top bit flips exactly when a round's last arrival lands.
+// Once the round is complete every lane reads its blocks' slots (lane,
+// lane + 32, ...), re-reading any that do not yet carry epoch e, and adds them
+// in block order; a fixed shuffle tree gives tot in lane 0.  The sums are FP64
+// (S = double) or double words added on the FP32 pipes (S = DW; three DW
+// values fill the same four words).  Returns false (warp-uniform) when a wait
+// gave up or another block aborted.
+__device__ __forceinline__ void df_pack(unsigned long long tag, const double (&v)[3], unsigned long long (&w)[4]) {
+  df_pack_3d(tag, v, w);
+}
+__device__ __forceinline__ void df_pack(unsigned long long tag, const DW (&v)[3], unsigned long long (&w)[4]) {
+  double x[3];
+  for (int k = 0; k < 3; ++k)
+    x[k] = __longlong_as_double((long long)(((unsigned long long)__float_as_uint(v[k].hi) << 32) |
+                                            __float_as_uint(v[k].lo)));
+  df_pack_3d(tag, x, w);
+}
+__device__ __forceinline__ void df_unpack(const unsigned long long (&w)[4], double (&v)[3]) { df_unpack_3d(w, v); }
+__device__ __forceinline__ void df_unpack(const unsigned long long (&w)[4], DW (&v)[3]) {
+  double x[3];
+  df_unpack_3d(w, x);
+  for (int k = 0; k < 3; ++k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[k]);
+    v[k] = DW{__uint_as_float((unsigned)(b >> 32)), __uint_as_float((unsigned)b)};
+  }
+}
+__device__ __forceinline__ double df_add(double a, double b) { return a + b; }
+__device__ __forceinline__ DW df_add(DW a, DW b) { return dw_add_sloppy(a, b); }
+
+template <typename S>
+__device__ __forceinline__ bool df_reduce(const Dev<float>& d, unsigned e, const S (&bs)[3], S (&tot)[3]) {
   const int lane = threadIdx.x & 31;
   const int nb = gridDim.x;
   unsigned long long* buf = d.df_p + (size_t)(e & 1u) * 4 * (size_t)nb;
@@ -957,14 +1040,15 @@ __device__ __forceinline__ bool df_reduce(const Dev<float>& d, unsigned e, const
   int arrived = 1;
   if (lane == 0) {
     unsigned long long w[4];
-    df_pack_3d(tag, bs, w);
+    df_pack(tag, bs, w);
     st_v2_relaxed(buf + 4 * (size_t)blockIdx.x, w[0], w[1]);
     st_v2_relaxed(buf + 4 * (size_t)blockIdx.x + 2, w[2], w[3]);
     const unsigned add = blockIdx.x == 0 ? (0x80000000u - ((unsigned)nb - 1u + d.bar_extra)) : 1u;
-    const unsigned old = atomicAdd(&d.ctrl->bar_count, add);
+    atomicAdd(&d.ctrl->bar_count, add);  // result unused: issued as a reduction
+    const unsigned want = (e & 1u) << 31;
     volatile unsigned* vc = &d.ctrl->bar_count;
     DfWait wt;
-    while (((old ^ *vc) & 0x80000000u) == 0)
+    while ((*vc & 0x80000000u) != want)
       if (!wt.again(d.ctrl, d.wait_budget)) {
         arrived = 0;
         break;
@@ -1002,21 +1086,21 @@ __device__ __forceinline__ bool df_reduce(const Dev<float>& d, unsigned e, const
       if ((stale & (1u << q)) && fresh(q)) stale &= ~(1u << q);
   }
   if (!__all_sync(0xffffffffu, stale == 0)) return false;
-  double a[3] = {0.0, 0.0, 0.0};
+  S a[3] = {acc_zero<S>(), acc_zero<S>(), acc_zero<S>()};
 #pragma unroll
   for (int q = 0; q < DF_MAXQ; ++q) {
     if (lane + 32 * q < nb) {
-      double v[3];
-      df_unpack_3d(w[q], v);
-      a[0] += v[0];
-      a[1] += v[1];
-      a[2] += v[2];
+      S v[3];
+      df_unpack(w[q], v);
+      a[0] = df_add(a[0], v[0]);
+      a[1] = df_add(a[1], v[1]);
+      a[2] = df_add(a[2], v[2]);
     }
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a[k] += __shfl_down_sync(0xffffffffu, a[k], o);
+    for (int o = 16; o > 0; o >>= 1) a[k] = df_add(a[k], shfl_down(a[k], o));
     tot[k] = a[k];
   }
   return true;
@@ -1145,16 +1229,17 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       }
     }
     {
-      double bs2[2], t[3];
-      block_sums<2, NW>(a1, cs.sh, bs2);
+      DW bs2[2], t[3];
+      block_sums_dw<2, NW>(a1, cs.sh, bs2);
       ++re;
       if (w0) {
-        const double bs[3] = {bs2[0], bs2[1], 0.0};
+        const DW bs[3] = {bs2[0], bs2[1], DW{0.0f, 0.0f}};
         const bool ok = df_reduce(d, re, bs, t);
         if (lane == 0) {
           if (ok) {
-            sc[2] = t[0];
-            sc[3] = t[0] / t[1];
+            const double g = acc_to_f64(t[0]);
+            sc[2] = g;
+            sc[3] = g / acc_to_f64(t[1]);
             cs.ta = (float)sc[3];
           }
           cs.flag = ok ? CG_CONTINUE : CG_ABORT;
@@ -1182,16 +1267,19 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
         a2[2] = dot3(r[0], r[1], r[2], r[0], r[1], r[2]);
       }
       {
-        double bs[3], t[3];
-        block_sums<3, NW>(a2, cs.sh, bs);
+        DW bs[3], tw[3];
+        block_sums_dw<3, NW>(a2, cs.sh, bs);
         ++re;
         if (w0) {
-          const bool ok = df_reduce(d, re, bs, t);
+          const bool ok = df_reduce(d, re, bs, tw);
+          int f = CG_ABORT;
+          double gamma = sc[2], alpha = sc[3], beta = sc[4], rr = sc[1];
+          if (ok) {
+            const double t[3] = {acc_to_f64(tw[0]), acc_to_f64(tw[1]), acc_to_f64(tw[2])};
+            f = cg_scalars_warp(t, sc[0], d.tol2, gamma, alpha, beta, rr);
+          }
           if (lane == 0) {
-            int f = CG_ABORT;
             if (ok) {
-              double gamma = sc[2], alpha = sc[3], beta = sc[4], rr = sc[1];
-              f = cg_scalars(t, sc[0], d.tol2, gamma, alpha, beta, rr);
               if (f == CG_NONFINITE && blockIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
               sc[1] = rr;
               sc[2] = gamma;
@@ -1379,12 +1467,11 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
       block_sums<3, NW>(a2, cs.sh, bs);
       if (w0) {
         const bool ok = warp0_reduce<3>(g, epoch, bs, rb0, rb1, t);
+        int f = CG_ABORT;
+        if (ok) f = done ? CG_DONE : cg_scalars_warp(t, bb, d.tol2, gamma, alpha, beta, rr);
         if (lane == 0) {
-          int f = CG_ABORT;
           if (ok) {
-            f = CG_DONE;
             if (!done) {
-              f = cg_scalars(t, bb, d.tol2, gamma, alpha, beta, rr);
               if (f == CG_NONFINITE && b == rb0) set_status(d.ctrl, ST_NONFINITE);
               if (f != CG_CONTINUE) {
                 it_done = it;
