@@ -21,10 +21,13 @@ Geometric Computing"):
 * ``loop``      -- the inner while-loop of Algorithm 1 run for n iterations.
 * ``adjoint``   -- reverse-mode derivative of the unrolled loop w.r.t. the
                    chamber volume ratios.
+* ``remesh``    -- the remesh trigger of Sec. III-C (volume change and
+                   distortion of chamber elements) and Algorithm 1's outer
+                   loop of progressive actuation (without remeshing).
 
 Parity pins: every function is pinned by tests under ``tests/`` against
 closed forms, invariants, brute force or library routines; functions without
 such a pin say "parity unpinned" in their docstring.
 """
-from . import mesh, local, collision, springs, global_step, loop  # noqa: F401
+from . import mesh, local, collision, springs, global_step, loop, remesh  # noqa: F401
 # ``oracle.adjoint`` needs PyTorch and is imported on demand.
