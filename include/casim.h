@@ -322,6 +322,60 @@ int casim_contacts_noalloc(int32_t n_verts, const float* dev_xyz, int32_t n_tets
                            int32_t n_query, const int32_t* dev_query, double cell_size, int32_t max_pairs,
                            int32_t* dev_pair_count, int32_t* dev_pair_tet, void* cuda_stream);
 
+/* Remesh trigger (Sec. III-C; Algorithm 1, the check after the inner loop).
+   Remeshing itself is not part of this library; this reports which chamber
+   elements (tet_group >= 0) would trigger it.  For every chamber element,
+   F is the affine map taking the element's reference shape to its current
+   shape (F = D_cur D_ref^-1, D the edge matrix v1 - v0, v2 - v0, v3 - v0):
+     bit 1 (value 1): volume change  det F = Vol(cur) / Vol(ref) > alpha_max
+     bit 2 (value 2): distortion     largest singular value of F > d_max
+   (the paper's norm of the diagonal factor of F's SVD), evaluated in FP64 from
+   the current positions.  Body elements get 0.  The paper uses
+   alpha_max = d_max = 4.
+     ref_xyz             host, n_verts*3 doubles in the caller's vertex order:
+                         the reference shape (Algorithm 1 compares with the
+                         shape at the previous outer step); NULL = rest shape
+     flags_out           host, n_tets bytes, caller's tet order (written)
+     n_flagged           host, number of elements with any flag (may be NULL)
+     group_volume_ratio  host, n_groups doubles (may be NULL): per chamber
+                         group, the sum of current over the sum of reference
+                         element volumes
+   Synchronous: waits for the work queued on the simulation's stream.
+   Returns CASIM_E_INVALID for bad arguments (n_groups must equal 1 + the
+   largest group id when group_volume_ratio is given). */
+int casim_remesh_flags(casim_sim* sim, const double* ref_xyz, double alpha_max, double d_max,
+                       uint8_t* flags_out, int32_t* n_flagged, int32_t n_groups,
+                       double* group_volume_ratio);
+
+/* One outer step of casim_progressive. */
+typedef struct {
+  int32_t k;                       /* outer step, from 1                                   */
+  int32_t status;                  /* casim_sync of the step's inner loop (0 or a warning) */
+  int32_t n_volume;                /* chamber elements with bit 1 against the step's start */
+  int32_t n_distortion;            /* chamber elements with bit 2 against the step's start */
+  int32_t n_flagged;               /* chamber elements with either bit                     */
+  int32_t pad;
+  double applied_max;              /* largest volume ratio applied at this step             */
+  double chamber_volume_ratio_min; /* smallest per-group chamber volume ratio against rest  */
+  double chamber_volume_ratio_max; /* largest one                                          */
+} casim_outer_record;
+
+/* Progressive actuation: the outer loop of Algorithm 1 without the
+   remeshing step.  Outer step k = 1, 2, ... sets the volume ratios
+   a_g = min(alpha_target[g], k * alpha_step) (the paper's alpha_k = k alpha_max,
+   capped so that the last step applies exactly the target), runs n_inner
+   iterations of the loop from the current state (positions and springs carry
+   over), and records the remesh flags of the step against the shape it
+   started from and the chamber volume ratios against the rest shape.  It stops
+   after the step that applies every target, or after max_outer steps.
+     alpha_target   host, n_groups volume ratios (> 0)
+     records        host, room for max_outer records; *n_outer gets the count
+   Synchronous.  Leaves the targets' last applied ratios set.  Errors of the
+   inner loop are returned as by casim_sync. */
+int casim_progressive(casim_sim* sim, int32_t n_groups, const double* alpha_target, double alpha_step,
+                      int32_t n_inner, int32_t max_outer, double alpha_max, double d_max,
+                      casim_outer_record* records, int32_t* n_outer);
+
 void casim_destroy(casim_sim* sim);
 
 /* Message of the last failure on this handle (or of the last casim_create

@@ -42,8 +42,8 @@ EXPORTS = [
     "casim_backward", "casim_sync", "casim_get_positions",
     "casim_get_contacts", "casim_get_springs", "casim_set_springs", "casim_get_targets",
     "casim_get_history", "casim_get_stats", "casim_save_state", "casim_load_state",
-    "casim_get_sizes", "casim_get_phase_times", "casim_contacts_noalloc", "casim_destroy",
-    "casim_last_error",
+    "casim_get_sizes", "casim_get_phase_times", "casim_contacts_noalloc", "casim_remesh_flags",
+    "casim_progressive", "casim_destroy", "casim_last_error",
 ]
 
 
@@ -84,6 +84,20 @@ class casim_stats(ctypes.Structure):
         ("last", casim_iter_record),
         ("status", ctypes.c_int32),
         ("pcg_kernel", ctypes.c_int32),
+    ]
+
+
+class casim_outer_record(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int32),
+        ("status", ctypes.c_int32),
+        ("n_volume", ctypes.c_int32),
+        ("n_distortion", ctypes.c_int32),
+        ("n_flagged", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
+        ("applied_max", ctypes.c_double),
+        ("chamber_volume_ratio_min", ctypes.c_double),
+        ("chamber_volume_ratio_max", ctypes.c_double),
     ]
 
 
@@ -147,6 +161,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.casim_get_phase_times.argtypes = [_P, _D]
     L.casim_contacts_noalloc.argtypes = [ctypes.c_int32, _P, ctypes.c_int32, _P, ctypes.c_int32, _P,
                                          ctypes.c_double, ctypes.c_int32, _P, _P, _P]
+    L.casim_remesh_flags.argtypes = [_P, _D, ctypes.c_double, ctypes.c_double, _U8, _I32, ctypes.c_int32, _D]
+    L.casim_progressive.argtypes = [_P, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_double, ctypes.c_double, ctypes.POINTER(casim_outer_record), _I32]
     L.casim_destroy.argtypes = [_P]
     L.casim_destroy.restype = None
     L.casim_last_error.argtypes = [_P]
@@ -361,6 +378,32 @@ def casim_contacts_noalloc(n_verts: int, dev_xyz: int, n_tets: int, dev_tets: in
         int(max_pairs), _P(dev_pair_count), _P(dev_pair_tet), _P(stream or None))
 
 
+def casim_remesh_flags(sim, n_tets: int, n_groups: int, ref_xyz=None, alpha_max: float = 4.0, d_max: float = 4.0):
+    """(flags uint8 (n_tets,), n_flagged, group volume ratios (n_groups,))."""
+    flags = np.zeros(n_tets, np.uint8)
+    nf = np.zeros(1, np.int32)
+    gvr = np.zeros(max(n_groups, 1), np.float64)
+    ref = None
+    if ref_xyz is not None:
+        ref = np.ascontiguousarray(np.asarray(ref_xyz, dtype=np.float64).reshape(-1))
+    _check(load_library().casim_remesh_flags(sim, None if ref is None else _ptr(ref, ctypes.c_double), alpha_max,
+                                             d_max, _ptr(flags, ctypes.c_uint8), _ptr(nf, ctypes.c_int32), n_groups,
+                                             _ptr(gvr, ctypes.c_double) if n_groups else None), sim)
+    return flags, int(nf[0]), gvr[:n_groups]
+
+
+def casim_progressive(sim, alpha_target, alpha_step: float, n_inner: int, max_outer: int = 64,
+                      alpha_max: float = 4.0, d_max: float = 4.0):
+    """List of per-outer-step dicts (casim_outer_record fields)."""
+    a = np.ascontiguousarray(np.asarray(alpha_target, dtype=np.float64))
+    recs = (casim_outer_record * max_outer)()
+    n = np.zeros(1, np.int32)
+    _check(load_library().casim_progressive(sim, a.shape[0], _ptr(a, ctypes.c_double), alpha_step, n_inner,
+                                            max_outer, alpha_max, d_max, recs, _ptr(n, ctypes.c_int32)), sim)
+    names = [f[0] for f in casim_outer_record._fields_ if f[0] != "pad"]
+    return [{k: getattr(recs[i], k) for k in names} for i in range(int(n[0]))]
+
+
 def casim_destroy(sim):
     load_library().casim_destroy(sim)
 
@@ -422,6 +465,12 @@ class Sim:
 
     def step(self, n: int):
         casim_step(self.h, n)
+
+    def remesh_flags(self, ref=None, alpha_max=4.0, d_max=4.0):
+        return casim_remesh_flags(self.h, self.sizes["n_tets"], self.n_groups, ref, alpha_max, d_max)
+
+    def progressive(self, alpha_target, alpha_step, n_inner, max_outer=64, alpha_max=4.0, d_max=4.0):
+        return casim_progressive(self.h, alpha_target, alpha_step, n_inner, max_outer, alpha_max, d_max)
 
     def reset(self):
         casim_reset(self.h)

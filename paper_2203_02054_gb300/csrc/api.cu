@@ -101,6 +101,10 @@ struct casim_sim {
   int last_status = 0;
   double phase_ms[5] = {0, 0, 0, 0, 0};
   std::vector<double> alpha_h;  // current volume ratios (host copy, for the adjoint)
+  std::vector<double> rest_h;   // rest positions, internal order, FP64 (remesh trigger reference)
+  std::vector<int> group_h;     // group of every tet (caller's tet order)
+  double *rm_ref = nullptr, *rm_rest = nullptr, *rm_vols = nullptr;  // remesh trigger buffers (on first use)
+  unsigned char* rm_flags = nullptr;
   // adjoint: checkpoints of the last casim_forward_ckpt and reverse-pass buffers
   struct Adj {
     int n_iters = 0, every = 0, n_ckpt = 0, cap_ckpt = 0, cap_every = 0;
@@ -1004,6 +1008,10 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   std::vector<double> rest_int(3 * (size_t)n_v);
   for (int v = 0; v < n_v; ++v)
     for (int c = 0; c < 3; ++c) rest_int[3 * (size_t)sim->int_of_user[v] + c] = rest_xyz[3 * (size_t)v + c];
+  sim->rest_h = rest_int;
+  sim->group_h = group;
+  sim->rm_ref = sim->rm_rest = sim->rm_vols = nullptr;
+  sim->rm_flags = nullptr;
   sim->X_fixed.assign(3 * (size_t)(n_v - n_free), 0.0);
   for (int i = n_free; i < n_v; ++i)
     for (int c = 0; c < 3; ++c) sim->X_fixed[3 * (size_t)(i - n_free) + c] = rest_int[3 * (size_t)i + c];
@@ -1710,6 +1718,167 @@ int casim_get_sizes(casim_sim* sim, int32_t* n_verts, int32_t* n_tets, int32_t* 
 int casim_get_phase_times(casim_sim* sim, double* ms_out5) {
   if (!sim || !ms_out5) return CASIM_E_INVALID;
   for (int k = 0; k < 5; ++k) ms_out5[k] = sim->phase_ms[k];
+  return CASIM_OK;
+}
+
+// ---- remesh trigger and progressive actuation (Sec. III-C, Algorithm 1) ----
+}  // extern "C"
+
+namespace {
+
+// Flags and element volumes of every tet against the reference in sim->rm_ref
+// (internal order, FP64) or the rest shape; synchronous on the sim's stream.
+template <typename T>
+int remesh_eval_typed(casim_sim* sim, bool against_rest, double amax, double dmax, std::vector<uint8_t>& flags,
+                      std::vector<double>& vols) {
+  const Dev<T> d = make_dev<T>(sim);
+  launch_remesh_flags<T>(d, against_rest ? sim->rm_rest : sim->rm_ref, amax, dmax, sim->rm_flags, sim->rm_vols,
+                         sim->stream);
+  flags.resize(sim->n_t);
+  vols.resize(2 * (size_t)sim->n_t);
+  CK(cudaMemcpyAsync(flags.data(), sim->rm_flags, (size_t)sim->n_t, cudaMemcpyDeviceToHost, sim->stream));
+  CK(cudaMemcpyAsync(vols.data(), sim->rm_vols, sizeof(double) * 2 * sim->n_t, cudaMemcpyDeviceToHost, sim->stream));
+  CK(cudaStreamSynchronize(sim->stream));
+  return CASIM_OK;
+}
+
+int remesh_prepare(casim_sim* sim) {
+  if (!sim->rm_rest) {
+    sim->rm_ref = sim->dalloc<double>(3 * (size_t)sim->n_v);
+    sim->rm_rest = sim->dalloc<double>(3 * (size_t)sim->n_v);
+    sim->rm_vols = sim->dalloc<double>(2 * (size_t)std::max(sim->n_t, 1));
+    sim->rm_flags = sim->dalloc<unsigned char>(std::max(sim->n_t, 1));
+    if (!sim->rm_ref || !sim->rm_rest || !sim->rm_vols || !sim->rm_flags)
+      return sim->fail(CASIM_E_CUDA, "cudaMalloc failed");
+    CK(cudaMemcpyAsync(sim->rm_rest, sim->rest_h.data(), sizeof(double) * sim->rest_h.size(), cudaMemcpyHostToDevice,
+                       sim->stream));
+  }
+  return CASIM_OK;
+}
+
+int remesh_eval(casim_sim* sim, bool against_rest, double amax, double dmax, std::vector<uint8_t>& flags,
+                std::vector<double>& vols) {
+  return sim->params.precision == CASIM_FP64 ? remesh_eval_typed<double>(sim, against_rest, amax, dmax, flags, vols)
+                                             : remesh_eval_typed<float>(sim, against_rest, amax, dmax, flags, vols);
+}
+
+// per-group chamber volume ratios: sums of deformed over reference volumes, in tet order
+void group_volume_ratios(const casim_sim* sim, const std::vector<double>& vols, std::vector<double>& out) {
+  std::vector<double> num(sim->n_groups, 0.0), den(sim->n_groups, 0.0);
+  for (int e = 0; e < sim->n_t; ++e) {
+    const int g = sim->group_h[e];
+    if (g < 0) continue;
+    num[g] += vols[2 * (size_t)e];
+    den[g] += vols[2 * (size_t)e + 1];
+  }
+  out.assign(sim->n_groups, 0.0);
+  for (int g = 0; g < sim->n_groups; ++g) out[g] = den[g] != 0.0 ? num[g] / den[g] : 0.0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int casim_remesh_flags(casim_sim* sim, const double* ref_xyz, double alpha_max, double d_max, uint8_t* flags_out,
+                       int32_t* n_flagged, int32_t n_groups, double* group_volume_ratio) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  if (!flags_out) return sim->fail(CASIM_E_INVALID, "null flags_out");
+  if (!(alpha_max > 0.0) || !(d_max > 0.0) || !std::isfinite(alpha_max) || !std::isfinite(d_max))
+    return sim->fail(CASIM_E_INVALID, "alpha_max and d_max must be positive");
+  if (group_volume_ratio && n_groups != sim->n_groups)
+    return sim->fail(CASIM_E_INVALID, "n_groups must equal 1 + the largest group id");
+  int rc = remesh_prepare(sim);
+  if (rc) return rc;
+  if (ref_xyz) {
+    std::vector<double> ref(3 * (size_t)sim->n_v);
+    for (int v = 0; v < sim->n_v; ++v)
+      for (int c = 0; c < 3; ++c) {
+        const double x = ref_xyz[3 * (size_t)v + c];
+        if (!std::isfinite(x)) return sim->fail(CASIM_E_INVALID, "non-finite reference position");
+        ref[3 * (size_t)sim->int_of_user[v] + c] = x;
+      }
+    CK(cudaMemcpyAsync(sim->rm_ref, ref.data(), sizeof(double) * ref.size(), cudaMemcpyHostToDevice, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));  // ref is a local buffer
+  }
+  std::vector<uint8_t> flags;
+  std::vector<double> vols;
+  rc = remesh_eval(sim, ref_xyz == nullptr, alpha_max, d_max, flags, vols);
+  if (rc) return rc;
+  int count = 0;
+  for (int e = 0; e < sim->n_t; ++e) {
+    flags_out[e] = flags[e];
+    count += flags[e] != 0;
+  }
+  if (n_flagged) *n_flagged = count;
+  if (group_volume_ratio) {
+    std::vector<double> gvr;
+    group_volume_ratios(sim, vols, gvr);
+    std::copy(gvr.begin(), gvr.end(), group_volume_ratio);
+  }
+  return CASIM_OK;
+}
+
+int casim_progressive(casim_sim* sim, int32_t n_groups, const double* alpha_target, double alpha_step,
+                      int32_t n_inner, int32_t max_outer, double alpha_max, double d_max,
+                      casim_outer_record* records, int32_t* n_outer) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  if (n_groups != sim->n_groups) return sim->fail(CASIM_E_INVALID, "n_groups must equal 1 + the largest group id");
+  if (n_groups > 0 && !alpha_target) return sim->fail(CASIM_E_INVALID, "null alpha_target");
+  if (!(alpha_step > 0.0) || !std::isfinite(alpha_step))
+    return sim->fail(CASIM_E_INVALID, "alpha_step must be positive");
+  if (n_inner < 0 || max_outer < 1 || !records)
+    return sim->fail(CASIM_E_INVALID, "need n_inner >= 0, max_outer >= 1 and a records array");
+  if (!(alpha_max > 0.0) || !(d_max > 0.0)) return sim->fail(CASIM_E_INVALID, "alpha_max and d_max must be positive");
+  for (int g = 0; g < n_groups; ++g)
+    if (!(alpha_target[g] > 0.0) || !std::isfinite(alpha_target[g]))
+      return sim->fail(CASIM_E_INVALID, "volume ratio must be positive");
+  int rc = remesh_prepare(sim);
+  if (rc) return rc;
+  std::vector<double> applied(n_groups);
+  std::vector<uint8_t> flags;
+  std::vector<double> vols, gvr;
+  int done = 0;
+  for (int k = 1; k <= max_outer; ++k) {
+    bool last = true;
+    double amax_applied = 0.0;
+    for (int g = 0; g < n_groups; ++g) {
+      applied[g] = std::min(alpha_target[g], k * alpha_step);
+      last = last && applied[g] == alpha_target[g];
+      amax_applied = std::max(amax_applied, applied[g]);
+    }
+    if ((rc = casim_set_actuation(sim, n_groups, applied.data()))) return rc;
+    // the reference of this outer step's flags: the shape it starts from
+    if (sim->params.precision == CASIM_FP64)
+      launch_positions_f64<double>(make_dev<double>(sim), sim->n_v, sim->rm_ref, sim->stream);
+    else
+      launch_positions_f64<float>(make_dev<float>(sim), sim->n_v, sim->rm_ref, sim->stream);
+    if ((rc = casim_step(sim, n_inner))) return rc;
+    const int st = casim_sync(sim);
+    if (st < 0) return st;
+    if ((rc = remesh_eval(sim, false, alpha_max, d_max, flags, vols))) return rc;
+    casim_outer_record& r = records[done++];
+    r.k = k;
+    r.status = st;
+    r.n_volume = r.n_distortion = r.n_flagged = 0;
+    for (int e = 0; e < sim->n_t; ++e) {
+      r.n_volume += (flags[e] & 1) != 0;
+      r.n_distortion += (flags[e] & 2) != 0;
+      r.n_flagged += flags[e] != 0;
+    }
+    r.pad = 0;
+    r.applied_max = amax_applied;
+    if ((rc = remesh_eval(sim, true, alpha_max, d_max, flags, vols))) return rc;
+    group_volume_ratios(sim, vols, gvr);
+    r.chamber_volume_ratio_min = r.chamber_volume_ratio_max = gvr.empty() ? 0.0 : gvr[0];
+    for (double v : gvr) {
+      r.chamber_volume_ratio_min = std::min(r.chamber_volume_ratio_min, v);
+      r.chamber_volume_ratio_max = std::max(r.chamber_volume_ratio_max, v);
+    }
+    if (last) break;
+  }
+  if (n_outer) *n_outer = done;
   return CASIM_OK;
 }
 

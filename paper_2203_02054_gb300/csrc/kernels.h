@@ -54,6 +54,11 @@ void launch_gather_positions(const Dev<T>& d, const int* int_of_user, int n_user
                              cudaStream_t st);
 template <typename T>
 int pcg_max_grid();
+template <typename T>
+void launch_remesh_flags(const Dev<T>& d, const double* ref, double alpha_max, double d_max, unsigned char* flags,
+                         double* vols, cudaStream_t st);
+template <typename T>
+void launch_positions_f64(const Dev<T>& d, int n_v, double* out, cudaStream_t st);
 
 // Device view of one reverse step of the adjoint (iteration i of a segment).
 template <typename T>
