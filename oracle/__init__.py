@@ -24,10 +24,12 @@ Geometric Computing"):
 * ``remesh``    -- the remesh trigger of Sec. III-C (volume change and
                    distortion of chamber elements) and Algorithm 1's outer
                    loop of progressive actuation (without remeshing).
+* ``anderson``  -- Anderson acceleration of the loop (Sec. III-B) with an
+                   energy safeguard.
 
 Parity pins: every function is pinned by tests under ``tests/`` against
 closed forms, invariants, brute force or library routines; functions without
 such a pin say "parity unpinned" in their docstring.
 """
-from . import mesh, local, collision, springs, global_step, loop, remesh  # noqa: F401
+from . import mesh, local, collision, springs, global_step, loop, remesh, anderson  # noqa: F401
 # ``oracle.adjoint`` needs PyTorch and is imported on demand.
