@@ -376,6 +376,35 @@ int casim_progressive(casim_sim* sim, int32_t n_groups, const double* alpha_targ
                       int32_t n_inner, int32_t max_outer, double alpha_max, double d_max,
                       casim_outer_record* records, int32_t* n_outer);
 
+/* One step of casim_step_anderson. */
+typedef struct {
+  double e_prev;     /* Eq. 8 energy at x_k, the point the step came from (NaN without a proposal) */
+  double e_acc;      /* energy at the accelerated proposal                                         */
+  int32_t accepted;  /* 1: the proposal became x_{k+1}; 0: x_{k+1} = g_k                         */
+  int32_t proposed;  /* 1: a proposal was formed (history non-empty, solve succeeded)           */
+} casim_aa_record;
+
+#define CASIM_AA_MAX_M 16
+
+/* Anderson acceleration of the loop (Sec. III-B: the paper accelerates the
+   local-global iteration with the method of Peng et al. 2018).  Runs n_iters
+   iterations x_k -> g_k = G(x_k) of the loop (as casim_step) from the current
+   state and, with memory m (0 <= m <= CASIM_AA_MAX_M; 0 = plain loop), after
+   each one forms the proposal x_acc = g_k - dG theta, where dF, dG hold the
+   differences of the last m + 1 residuals f_j = g_j - x_j and images g_j, and
+   theta solves (dF^T dF + lambda I) theta = dF^T f_k, lambda = 1e-12
+   trace(dF^T dF) / m.  Safeguard (Peng et al.'s energy test): the proposal
+   becomes x_{k+1} only if its Eq. 8 energy is below that of x_k, both with the
+   local projections at the point and iteration k's spring targets;
+   otherwise x_{k+1} = g_k.
+   Each call starts with an empty history.
+     records     host, n_iters records (may be NULL)
+     n_accepted  host, number of accepted proposals (may be NULL)
+   Synchronous (waits for its work); the history records of casim_get_history
+   are those of the n_iters loop iterations.  Errors as casim_step. */
+int casim_step_anderson(casim_sim* sim, int32_t n_iters, int32_t m, casim_aa_record* records,
+                        int32_t* n_accepted);
+
 void casim_destroy(casim_sim* sim);
 
 /* Message of the last failure on this handle (or of the last casim_create

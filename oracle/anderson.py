@@ -14,11 +14,11 @@ through its normal equations with a Tikhonov term
 (dF^T dF + lambda I) theta = dF^T f_k, lambda = 1e-12 trace(dF^T dF) / m,
 and proposes x_acc = g_k - dG theta, dG = [g_{j+1} - g_j].
 
-Safeguard (reading of the paper's use of Peng et al.'s energy safeguard): the
-proposal is taken only if its energy does not exceed the plain iterate's,
-E(x_acc) <= E(g_k), both evaluated with the local projections at the point
-and the spring records of the iteration that produced g_k (so the two
-energies use the same springs); otherwise x_{k+1} = g_k.  The history keeps
+Safeguard (the energy test of Peng et al. 2018): the proposal is taken only
+if its energy is below that of the point it came from, E(x_acc) < E(x_k), both
+evaluated with the local projections at the point and the spring records of
+iteration k (the iteration that evaluated G(x_k), so the two energies use the
+same springs); otherwise x_{k+1} = g_k, the plain iterate.  The history keeps
 every evaluated pair whichever point is taken.  With m = 0 this is the plain
 loop.
 """
@@ -69,8 +69,8 @@ def energy(prep, X, st, alpha, knots, k_spring):
 
 @dataclass
 class AAStep:
-    e_plain: float      # E(g_k)
-    e_acc: float        # E(x_acc) (= e_plain when no proposal was formed)
+    e_prev: float       # E(x_k)
+    e_acc: float        # E(x_acc) (NaN when no proposal was formed)
     accepted: bool      # x_{k+1} = x_acc
 
 
@@ -91,9 +91,9 @@ def run_anderson(m_mesh, n_steps, m, X0=None, prep=None):
         F, Gs = F[-(m + 1):], Gs[-(m + 1):]
         if m > 0 and len(F) >= 2:
             xa = aa_proposal(F, Gs).reshape(g.shape)
-            ep = energy(prep, g, st, mm.alpha, mm.w_knots, mm.k_spring)
+            ep = energy(prep, x, st, mm.alpha, mm.w_knots, mm.k_spring)
             ea = energy(prep, xa, st, mm.alpha, mm.w_knots, mm.k_spring)
-            acc = ea <= ep
+            acc = ea < ep
             recs.append(AAStep(ep, ea, acc))
             x = xa if acc else g
         else:

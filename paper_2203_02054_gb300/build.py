@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcasim.so")
 
-SOURCES = ["api.cu", "collision.cu", "solve.cu", "adjoint.cu", "noalloc.cu", "remesh.cu"]
+SOURCES = ["api.cu", "collision.cu", "solve.cu", "adjoint.cu", "noalloc.cu", "remesh.cu", "anderson.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", CSRC, "-I", INCLUDE]

@@ -43,7 +43,7 @@ EXPORTS = [
     "casim_get_contacts", "casim_get_springs", "casim_set_springs", "casim_get_targets",
     "casim_get_history", "casim_get_stats", "casim_save_state", "casim_load_state",
     "casim_get_sizes", "casim_get_phase_times", "casim_contacts_noalloc", "casim_remesh_flags",
-    "casim_progressive", "casim_destroy", "casim_last_error",
+    "casim_progressive", "casim_step_anderson", "casim_destroy", "casim_last_error",
 ]
 
 
@@ -98,6 +98,15 @@ class casim_outer_record(ctypes.Structure):
         ("applied_max", ctypes.c_double),
         ("chamber_volume_ratio_min", ctypes.c_double),
         ("chamber_volume_ratio_max", ctypes.c_double),
+    ]
+
+
+class casim_aa_record(ctypes.Structure):
+    _fields_ = [
+        ("e_prev", ctypes.c_double),
+        ("e_acc", ctypes.c_double),
+        ("accepted", ctypes.c_int32),
+        ("proposed", ctypes.c_int32),
     ]
 
 
@@ -164,6 +173,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.casim_remesh_flags.argtypes = [_P, _D, ctypes.c_double, ctypes.c_double, _U8, _I32, ctypes.c_int32, _D]
     L.casim_progressive.argtypes = [_P, ctypes.c_int32, _D, ctypes.c_double, ctypes.c_int32, ctypes.c_int32,
                                     ctypes.c_double, ctypes.c_double, ctypes.POINTER(casim_outer_record), _I32]
+    L.casim_step_anderson.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(casim_aa_record), _I32]
     L.casim_destroy.argtypes = [_P]
     L.casim_destroy.restype = None
     L.casim_last_error.argtypes = [_P]
@@ -404,6 +414,15 @@ def casim_progressive(sim, alpha_target, alpha_step: float, n_inner: int, max_ou
     return [{k: getattr(recs[i], k) for k in names} for i in range(int(n[0]))]
 
 
+def casim_step_anderson(sim, n_iters: int, m: int):
+    """(list of per-iteration dicts (casim_aa_record fields), number of accepted proposals)."""
+    recs = (casim_aa_record * max(n_iters, 1))()
+    n = np.zeros(1, np.int32)
+    _check(load_library().casim_step_anderson(sim, n_iters, m, recs, _ptr(n, ctypes.c_int32)), sim)
+    names = [f[0] for f in casim_aa_record._fields_]
+    return [{k: getattr(recs[i], k) for k in names} for i in range(n_iters)], int(n[0])
+
+
 def casim_destroy(sim):
     load_library().casim_destroy(sim)
 
@@ -465,6 +484,9 @@ class Sim:
 
     def step(self, n: int):
         casim_step(self.h, n)
+
+    def step_anderson(self, n: int, m: int):
+        return casim_step_anderson(self.h, n, m)
 
     def remesh_flags(self, ref=None, alpha_max=4.0, d_max=4.0):
         return casim_remesh_flags(self.h, self.sizes["n_tets"], self.n_groups, ref, alpha_max, d_max)

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <numeric>
 #include <string>
@@ -35,6 +36,21 @@ size_t pow2_at_least(size_t n) {
 }
 
 }  // namespace
+
+// Device buffers of the Anderson-accelerated loop (allocated on first use,
+// for memory up to m_cap): positions x_k and the proposal (all vertices), the
+// residual and previous residual / image, the history rings dF, dG, and small
+// tables for the dot and combine kernels.
+struct AAState {
+  int m_cap = 0;
+  void *x = nullptr, *xa = nullptr, *f = nullptr, *fprev = nullptr, *gprev = nullptr;
+  std::vector<void*> dF, dG;
+  void** vec_tab = nullptr;
+  void** dg_tab = nullptr;
+  int* pairs = nullptr;
+  double* theta = nullptr;
+  double* partials = nullptr;
+};
 
 struct casim_sim {
   casim_params params{};
@@ -105,6 +121,7 @@ struct casim_sim {
   std::vector<int> group_h;     // group of every tet (caller's tet order)
   double *rm_ref = nullptr, *rm_rest = nullptr, *rm_vols = nullptr;  // remesh trigger buffers (on first use)
   unsigned char* rm_flags = nullptr;
+  AAState aa;                   // Anderson acceleration buffers (on first use)
   // adjoint: checkpoints of the last casim_forward_ckpt and reverse-pass buffers
   struct Adj {
     int n_iters = 0, every = 0, n_ckpt = 0, cap_ckpt = 0, cap_every = 0;
@@ -154,6 +171,9 @@ struct casim_sim {
     gexec = nullptr;
     for (void* q : allocs) cudaFree(q);
     allocs.clear();
+    rm_ref = rm_rest = rm_vols = nullptr;
+    rm_flags = nullptr;
+    aa = AAState{};
     graph_dirty = true;
   }
 };
@@ -1010,8 +1030,6 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
     for (int c = 0; c < 3; ++c) rest_int[3 * (size_t)sim->int_of_user[v] + c] = rest_xyz[3 * (size_t)v + c];
   sim->rest_h = rest_int;
   sim->group_h = group;
-  sim->rm_ref = sim->rm_rest = sim->rm_vols = nullptr;
-  sim->rm_flags = nullptr;
   sim->X_fixed.assign(3 * (size_t)(n_v - n_free), 0.0);
   for (int i = n_free; i < n_v; ++i)
     for (int c = 0; c < 3; ++c) sim->X_fixed[3 * (size_t)(i - n_free) + c] = rest_int[3 * (size_t)i + c];
@@ -1880,6 +1898,199 @@ int casim_progressive(casim_sim* sim, int32_t n_groups, const double* alpha_targ
   }
   if (n_outer) *n_outer = done;
   return CASIM_OK;
+}
+
+// ---- Anderson acceleration (Sec. III-B) ----
+}  // extern "C"
+
+namespace {
+
+int aa_prepare(casim_sim* sim, int m) {
+  AAState& A = sim->aa;
+  const size_t rs = 4 * (size_t)sim->rs;  // bytes of one R4<T>
+  const size_t nf = std::max(sim->n_free, 1), nv = std::max(sim->n_v, 1);
+  if (A.m_cap >= m && A.x) return CASIM_OK;
+  const int cap = std::max(m, 1);
+  A.x = sim->dalloc<unsigned char>(rs * nv);
+  A.xa = sim->dalloc<unsigned char>(rs * nv);
+  A.f = sim->dalloc<unsigned char>(rs * nf);
+  A.fprev = sim->dalloc<unsigned char>(rs * nf);
+  A.gprev = sim->dalloc<unsigned char>(rs * nf);
+  A.dF.assign(cap, nullptr);
+  A.dG.assign(cap, nullptr);
+  for (int j = 0; j < cap; ++j) {
+    A.dF[j] = sim->dalloc<unsigned char>(rs * nf);
+    A.dG[j] = sim->dalloc<unsigned char>(rs * nf);
+  }
+  const int max_pairs = cap * (cap + 1) / 2 + cap;
+  A.vec_tab = sim->dalloc<void*>(cap + 1);
+  A.dg_tab = sim->dalloc<void*>(cap);
+  A.pairs = sim->dalloc<int>(2 * max_pairs);
+  A.theta = sim->dalloc<double>(cap);
+  A.partials = sim->dalloc<double>((size_t)max_pairs * aa_dot_blocks(sim->n_free));
+  if (!A.x || !A.xa || !A.f || !A.fprev || !A.gprev || !A.vec_tab || !A.dg_tab || !A.pairs || !A.theta || !A.partials)
+    return sim->fail(CASIM_E_CUDA, "cudaMalloc failed");
+  for (int j = 0; j < cap; ++j)
+    if (!A.dF[j] || !A.dG[j]) return sim->fail(CASIM_E_CUDA, "cudaMalloc failed");
+  A.m_cap = cap;
+  return CASIM_OK;
+}
+
+// Eq. 8 energy at the positions in Xbuf (all vertices) with the local
+// projections there and the current spring targets: the local step's element
+// energies plus the spring energies, summed on the host in partial order.
+template <typename T>
+int aa_energy(casim_sim* sim, void* Xbuf, double& E) {
+  Dev<T> d = make_dev<T>(sim);
+  d.X = (R4<T>*)Xbuf;
+  d.stats = 1;
+  launch_local<T>(d, sim->stream);
+  launch_spring_energy<T>(d.X, d.spring_c, d.k_spring, sim->n_free, sim->e_partials + sim->n_e_local, sim->stream);
+  std::vector<double> parts(sim->n_e_local + sim->n_e_spring);
+  CK(cudaMemcpyAsync(parts.data(), sim->e_partials, sizeof(double) * parts.size(), cudaMemcpyDeviceToHost,
+                     sim->stream));
+  CK(cudaStreamSynchronize(sim->stream));
+  E = 0.0;
+  for (double p : parts) E += p;
+  return CASIM_OK;
+}
+
+// Cholesky solve of the small SPD system M theta = r (row-major n x n); false
+// if a pivot is not positive.
+bool small_spd_solve(std::vector<double> M, std::vector<double> r, int n, std::vector<double>& theta) {
+  for (int j = 0; j < n; ++j) {
+    double s = M[j * n + j];
+    for (int k = 0; k < j; ++k) s -= M[j * n + k] * M[j * n + k];
+    if (!(s > 0.0)) return false;
+    const double ljj = std::sqrt(s);
+    M[j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = M[i * n + j];
+      for (int k = 0; k < j; ++k) t -= M[i * n + k] * M[j * n + k];
+      M[i * n + j] = t / ljj;
+    }
+  }
+  for (int i = 0; i < n; ++i) {  // L y = r
+    double t = r[i];
+    for (int k = 0; k < i; ++k) t -= M[i * n + k] * r[k];
+    r[i] = t / M[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; --i) {  // L^T theta = y
+    double t = r[i];
+    for (int k = i + 1; k < n; ++k) t -= M[k * n + i] * r[k];
+    r[i] = t / M[i * n + i];
+  }
+  theta = r;
+  return true;
+}
+
+template <typename T>
+int step_anderson_typed(casim_sim* sim, int n_iters, int m, casim_aa_record* recs, int* n_accepted) {
+  AAState& A = sim->aa;
+  cudaStream_t st = sim->stream;
+  const int nf = sim->n_free;
+  const size_t row = sizeof(R4<T>);
+  CK(cudaMemcpyAsync(A.xa, sim->X, row * sim->n_v, cudaMemcpyDeviceToDevice, st));  // fixed rows of the proposal
+  int head = 0, n_hist = 0, have_prev = 0, accepted = 0;
+  for (int k = 0; k < n_iters; ++k) {
+    CK(cudaMemcpyAsync(A.x, sim->X, row * sim->n_v, cudaMemcpyDeviceToDevice, st));  // x_k (all vertices)
+    int rc = step_typed<T>(sim, 1);                                            // X = g_k = G(x_k)
+    if (rc) return rc;
+    const int slot = head;
+    launch_aa_update<T>((const R4<T>*)sim->X, (const R4<T>*)A.x, (R4<T>*)A.f, (R4<T>*)A.fprev, (R4<T>*)A.gprev,
+                        (R4<T>*)A.dF[slot], (R4<T>*)A.dG[slot], nf, have_prev, st);
+    if (have_prev && m > 0) {
+      head = (head + 1) % m;
+      n_hist = std::min(n_hist + 1, m);
+    }
+    have_prev = 1;
+    casim_aa_record r;
+    r.e_prev = r.e_acc = std::numeric_limits<double>::quiet_NaN();
+    r.accepted = 0;
+    r.proposed = 0;
+    if (m > 0 && n_hist > 0) {
+      // columns oldest first; vector table: dF columns, then f
+      const int h = n_hist;
+      std::vector<int> cols(h);
+      for (int j = 0; j < h; ++j) cols[j] = (head - h + j + m) % m;
+      std::vector<void*> vtab(h + 1), gtab(h);
+      for (int j = 0; j < h; ++j) {
+        vtab[j] = A.dF[cols[j]];
+        gtab[j] = A.dG[cols[j]];
+      }
+      vtab[h] = A.f;
+      std::vector<int> pairs;
+      for (int i = 0; i < h; ++i)
+        for (int j = i; j < h; ++j) {
+          pairs.push_back(i);
+          pairs.push_back(j);
+        }
+      for (int i = 0; i < h; ++i) {
+        pairs.push_back(i);
+        pairs.push_back(h);
+      }
+      const int np = (int)pairs.size() / 2, nb = aa_dot_blocks(nf);
+      CK(cudaMemcpyAsync(A.vec_tab, vtab.data(), sizeof(void*) * vtab.size(), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(A.pairs, pairs.data(), sizeof(int) * pairs.size(), cudaMemcpyHostToDevice, st));
+      launch_aa_dot<T>((const R4<T>* const*)A.vec_tab, A.pairs, np, nf, A.partials, st);
+      std::vector<double> parts((size_t)np * nb);
+      CK(cudaMemcpyAsync(parts.data(), A.partials, sizeof(double) * parts.size(), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      std::vector<double> dots(np, 0.0);
+      for (int p = 0; p < np; ++p)
+        for (int b = 0; b < nb; ++b) dots[p] += parts[(size_t)p * nb + b];
+      std::vector<double> M(h * h), rhs(h), theta;
+      int p = 0;
+      for (int i = 0; i < h; ++i)
+        for (int j = i; j < h; ++j, ++p) M[i * h + j] = M[j * h + i] = dots[p];
+      for (int i = 0; i < h; ++i, ++p) rhs[i] = dots[p];
+      double tr = 0.0;
+      for (int i = 0; i < h; ++i) tr += M[i * h + i];
+      for (int i = 0; i < h; ++i) M[i * h + i] += 1e-12 * tr / h;
+      if (tr > 0.0 && small_spd_solve(M, rhs, h, theta)) {
+        CK(cudaMemcpyAsync(A.dg_tab, gtab.data(), sizeof(void*) * gtab.size(), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(A.theta, theta.data(), sizeof(double) * h, cudaMemcpyHostToDevice, st));
+        launch_aa_combine<T>((const R4<T>*)sim->X, (const R4<T>* const*)A.dg_tab, A.theta, h, nf, (R4<T>*)A.xa, st);
+        // safeguard: the proposal must lower the energy of the point it came
+        // from (both with iteration k's springs); else x_{k+1} = g_k
+        double ep = 0.0, ea = 0.0;
+        if ((rc = aa_energy<T>(sim, A.x, ep))) return rc;
+        if ((rc = aa_energy<T>(sim, A.xa, ea))) return rc;
+        r.e_prev = ep;
+        r.e_acc = ea;
+        r.proposed = 1;
+        if (ea < ep) {
+          CK(cudaMemcpyAsync(sim->X, A.xa, row * nf, cudaMemcpyDeviceToDevice, st));
+          r.accepted = 1;
+          ++accepted;
+        }
+      }
+    }
+    if (recs) recs[k] = r;
+  }
+  CK(cudaStreamSynchronize(st));
+  if (n_accepted) *n_accepted = accepted;
+  return CASIM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int casim_step_anderson(casim_sim* sim, int32_t n_iters, int32_t m, casim_aa_record* records, int32_t* n_accepted) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
+  if (!sim->has_act) return sim->fail(CASIM_E_STATE, "no actuation set");
+  if (n_iters < 0 || m < 0 || m > CASIM_AA_MAX_M) return sim->fail(CASIM_E_INVALID, "need n_iters >= 0, 0 <= m <= 16");
+  if (n_iters == 0) {
+    if (n_accepted) *n_accepted = 0;
+    return CASIM_OK;
+  }
+  int rc = aa_prepare(sim, m);
+  if (rc) return rc;
+  sim->adj.valid = false;
+  return sim->params.precision == CASIM_FP64 ? step_anderson_typed<double>(sim, n_iters, m, records, n_accepted)
+                                             : step_anderson_typed<float>(sim, n_iters, m, records, n_accepted);
 }
 
 void casim_destroy(casim_sim* sim) {

@@ -59,6 +59,18 @@ void launch_remesh_flags(const Dev<T>& d, const double* ref, double alpha_max, d
                          double* vols, cudaStream_t st);
 template <typename T>
 void launch_positions_f64(const Dev<T>& d, int n_v, double* out, cudaStream_t st);
+int aa_dot_blocks(int n);
+template <typename T>
+void launch_aa_update(const R4<T>* g, const R4<T>* x, R4<T>* f, R4<T>* f_prev, R4<T>* g_prev, R4<T>* dF, R4<T>* dG,
+                      int n, int have_prev, cudaStream_t st);
+template <typename T>
+void launch_aa_dot(const R4<T>* const* vec, const int* pairs, int n_pairs, int n, double* partials, cudaStream_t st);
+template <typename T>
+void launch_aa_combine(const R4<T>* g, const R4<T>* const* dG, const double* theta, int m, int n, R4<T>* xa,
+                       cudaStream_t st);
+template <typename T>
+void launch_spring_energy(const R4<T>* X, const R4<double>* spring_c, double k_spring, int n, double* partials,
+                          cudaStream_t st);
 
 // Device view of one reverse step of the adjoint (iteration i of a segment).
 template <typename T>

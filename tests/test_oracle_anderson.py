@@ -1,7 +1,7 @@
 """Pins of the Anderson-accelerated loop (Sec. III-B): on a linear fixed-point
 map, AA with memory n terminates at the fixed point within n + 1 steps (its
 equivalence with GMRES, Walker and Ni 2011); memory 0 is the plain loop; the
-safeguard never takes a point of higher energy than the plain iterate; and on
+safeguard never takes a point of higher energy than the one it came from; and on
 a finger the accelerated loop shrinks the fixed-point residual faster."""
 import numpy as np
 
@@ -32,16 +32,16 @@ def test_memory_zero_is_the_plain_loop():
 
 
 def test_safeguard_and_acceleration():
-    m = synth.small_finger(nx=20, ny=4, nz=4, n_ch=4, seed=7, n_iters=30, precision=synth.PRECISION_FP64,
+    m = synth.small_finger(nx=20, ny=4, nz=4, n_ch=4, seed=7, n_iters=40, precision=synth.PRECISION_FP64,
                            collision=synth.COLLISION_OFF)
     prep = loop.prepare(m.rest, m.tets, m.group, m.fixed)
     res = {}
     for mem in (0, 5):
-        X, st, recs = anderson.run_anderson(m, 30, mem, prep=prep)
+        X, st, recs = anderson.run_anderson(m, 40, mem, prep=prep)
         for r in recs:
             if r.accepted:
-                assert r.e_acc <= r.e_plain
+                assert r.e_acc < r.e_prev
         g, *_ = loop.iterate(prep, X, st, m.alpha, np.zeros((0, 4)), m.w_knots, m.k_spring, m.eps, m.collision)
         res[mem] = (np.abs(g - X).max(), sum(r.accepted for r in recs))
     assert res[5][1] > 0
-    assert res[5][0] < 0.75 * res[0][0]
+    assert res[5][0] < 0.5 * res[0][0]
