@@ -328,6 +328,48 @@ def bench_adjoint(stream, n_iters=100, every=10):
             "grad_finite": bool(np.all(np.isfinite(grad))), "grad_norm": float(np.linalg.norm(grad))}
 
 
+def bench_anderson(stream, n_iters=200, mem=5):
+    """Anderson acceleration (memory 5, energy safeguard) against the plain
+    loop on the 51,840-tet finger: Eq. 8 energy per iteration, iterations to
+    come within 1e-2 / 1e-3 of the lower of the two runs' final energies, and
+    time per iteration (both timed around synchronous calls: the accelerated
+    loop synchronises every iteration)."""
+    import numpy as np
+
+    from paper_2203_02054_gb300 import casim, synth
+
+    m = synth.config2_finger()
+    res = {"workload": "finger 60x12x12 voxels, 8 chambers, 51,840 tets, self collision, %d iterations" % n_iters,
+           "n_tets": m.n_tets, "n_iters": n_iters, "memory": mem}
+    energies = {}
+    for mm in (0, mem):
+        sim = casim.Sim(m, stream=stream.cuda_stream)
+        casim.casim_step(sim.h, 2)
+        casim.casim_sync(sim.h)
+        casim.casim_reset(sim.h)
+        casim.casim_set_actuation(sim.h, m.alpha)
+        casim.casim_sync(sim.h)
+        t0 = time.perf_counter()
+        if mm == 0:
+            casim.casim_step(sim.h, n_iters)
+            acc = 0
+        else:
+            _recs, acc = casim.casim_step_anderson(sim.h, n_iters, mm)
+        casim.casim_sync(sim.h)
+        dt = time.perf_counter() - t0
+        E = np.array([h["energy"] for h in sim.history(cap=4096)][-n_iters:])
+        energies[mm] = E
+        key = "plain" if mm == 0 else "anderson"
+        res[key] = {"ms_per_iter": 1e3 * dt / n_iters, "accepted": acc, "final_energy": float(E[-1])}
+        sim.close()
+    e_min = min(float(energies[0].min()), float(energies[mem].min()))
+    for tol in (1e-2, 1e-3):
+        for mm, key in ((0, "plain"), (mem, "anderson")):
+            hit = np.nonzero(energies[mm] <= e_min * (1.0 + tol))[0]
+            res[key]["iters_to_%g" % tol] = int(hit[0]) + 1 if hit.size else None
+    return res
+
+
 # -------------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -461,6 +503,10 @@ def main():
             return 0
         line["batched"] = bench_batched(stream, value)
         line["adjoint"] = bench_adjoint(stream)
+        try:
+            line["anderson"] = bench_anderson(stream)
+        except Exception as e:  # a failure here must not cost the main line
+            line["anderson"] = {"error": "%s: %s" % (type(e).__name__, e)}
         # ---- CPU baseline: the oracle on a bounded sample of the same workload ----
         for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
             os.environ.setdefault(v, "1")
