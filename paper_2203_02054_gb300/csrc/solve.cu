@@ -966,19 +966,12 @@ __device__ __forceinline__ void df_unpack_3d(const unsigned long long (&w)[4], d
   v[2] = __longlong_as_double((long long)(((c2 & 0xFFFFull) << 48) | c3));
 }
 
-// Pause between polls of words that are not yet current, so that spinning
-// readers do not crowd the L2 slices that the awaited stores go to.
-#ifndef CASIM_DF_BACKOFF_NS
-#define CASIM_DF_BACKOFF_NS 0
-#endif
-
 // Bounded polling: every 32nd poll checks the abort word and the clock budget
 // (on expiry records ST_TIMEOUT and raises abort).  Returns false to stop.
 struct DfWait {
   long long t0 = 0;
   unsigned n = 0;
   __device__ __forceinline__ bool again(Ctrl* c, unsigned long long budget) {
-    if (CASIM_DF_BACKOFF_NS > 0) __nanosleep(CASIM_DF_BACKOFF_NS);
     if ((++n & 31u) != 0) return true;
     if (*(volatile int*)&c->abort) return false;
     const long long now = clock64();
