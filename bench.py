@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--iters", type=int, default=200, help="outer iterations per step")
     ap.add_argument("--only-plain", action="store_true",
                     help="time the single-robot workload only (no batched, adjoint or CPU legs; for profiling)")
+    ap.add_argument("--only-batched", type=int, default=0, metavar="N",
+                    help="run 2 warm-up and then N iterations of the 256-robot batch, print one line and exit "
+                         "(for profiling)")
     return ap.parse_args()
 
 
@@ -376,8 +379,31 @@ def bench_anderson(stream, n_iters=200, mem=5):
 
 
 # -------------------------------------------------------------------- GPU arm
+def run_only_batched(n_iters: int) -> int:
+    import torch
+
+    from paper_2203_02054_gb300 import casim, synth
+
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream(0)
+    batch = synth.config4_batch(n_iters=n_iters)
+    sim = casim.Sim(batch, stream=stream.cuda_stream, stats=0)
+    casim.casim_step(sim.h, 2)
+    casim.casim_sync(sim.h)
+    ms = _event_ms(stream, lambda: casim.casim_step(sim.h, n_iters))
+    status = casim.casim_sync(sim.h)
+    n_t = sum(m.n_tets for m in batch)
+    print(json.dumps({"workload": "256-robot batch, %d tets" % n_t, "n_iters": n_iters, "ms": ms,
+                      "ms_per_iter": ms / max(1, n_iters), "pcg_kernel": sim.stats().pcg_kernel,
+                      "device_status": status}))
+    sim.close()
+    return 0
+
+
 def main():
     args = parse()
+    if args.only_batched > 0:
+        return run_only_batched(args.only_batched)
     if args.impl == "reference":
         return run_reference(args)
     rank, world, local = dist_env()
