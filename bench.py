@@ -390,11 +390,17 @@ def run_only_batched(n_iters: int) -> int:
     sim = casim.Sim(batch, stream=stream.cuda_stream, stats=0)
     casim.casim_step(sim.h, 2)
     casim.casim_sync(sim.h)
+    st0 = casim.casim_get_stats(sim.h)
     ms = _event_ms(stream, lambda: casim.casim_step(sim.h, n_iters))
     status = casim.casim_sync(sim.h)
+    st1 = casim.casim_get_stats(sim.h)
+    hist = sim.history(cap=4096)[-n_iters:]
     n_t = sum(m.n_tets for m in batch)
+    k_max = sum(h["pcg_iters"] for h in hist) / max(1, len(hist))   # per launch: the slowest robot
+    k_mean = (st1.total_pcg_iters - st0.total_pcg_iters) / max(1, n_iters) / len(batch)
     print(json.dumps({"workload": "256-robot batch, %d tets" % n_t, "n_iters": n_iters, "ms": ms,
                       "ms_per_iter": ms / max(1, n_iters), "pcg_kernel": sim.stats().pcg_kernel,
+                      "k_pcg_max_per_launch": k_max, "k_pcg_mean_per_robot": k_mean,
                       "device_status": status}))
     sim.close()
     return 0
