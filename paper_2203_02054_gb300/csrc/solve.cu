@@ -1409,6 +1409,9 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
   bool first = true;
   int it = 1;
   for (;; ++it) {
+    // r.u and r.r of the new residual are formed in the update pass, so the
+    // SpMV pass does not read r again (same values, same order of rows)
+    A a_ru = acc_zero<A>(), a_rr = acc_zero<A>();
     if (!done) {
       for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
         const R4<T> ui = u[i], wi = w[i];
@@ -1434,25 +1437,25 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
         R4<T> un;
         un.x = ri.x / dg; un.y = ri.y / dg; un.z = ri.z / dg; un.w = T(0);
         u[i] = un;
+        a_ru = acc_add(a_ru, dot3(ri.x, ri.y, ri.z, un.x, un.y, un.z));
+        a_rr = acc_add(a_rr, dot3(ri.x, ri.y, ri.z, ri.x, ri.y, ri.z));
       }
     }
     if (!grid_barrier(g, epoch, &cs.ok)) return;
     // every block reads the same count: increments happen before this barrier
     const unsigned n_done = __ldcg(&d.ctrl->queue);
     if ((int)n_done >= d.n_robots || it > d.max_iter) break;
-    A a2[3] = {acc_zero<A>(), acc_zero<A>(), acc_zero<A>()};
+    A a2[3] = {a_ru, acc_zero<A>(), a_rr};
     if (!done) {
       for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
         const T dg = d.diag[i];
-        const R4<T> ui = u[i], ri = r[i];
+        const R4<T> ui = u[i];
         T ax, ay, az;
         spmv_row(d, i, u, dg, ui, ax, ay, az);
         R4<T> wi;
         wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
         w[i] = wi;
-        a2[0] = acc_add(a2[0], dot3(ri.x, ri.y, ri.z, ui.x, ui.y, ui.z));
         a2[1] = acc_add(a2[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
-        a2[2] = acc_add(a2[2], dot3(ri.x, ri.y, ri.z, ri.x, ri.y, ri.z));
       }
     }
     {
