@@ -6,10 +6,11 @@
 //   diagonal, -1/4 w per shared edge), b = sum_e w_e S_e^T P_e^T + k c - A_fx x_fixed,
 // the three coordinate columns sharing A.  They are solved together by
 // Jacobi-preconditioned conjugate gradients in the single-reduction form of
-// Chronopoulos and Gear (1989), inside one persistent cooperative kernel:
-// per iteration one grid barrier publishes the new preconditioned residual u
-// for the SpMV and one grid reduction produces (r.u, w.u, r.r) to FP64
-// accuracy.
+// Chronopoulos and Gear (1989), inside one persistent cooperative kernel.
+// Per iteration the neighbours' preconditioned residual u must be visible to
+// the SpMV and one grid reduction produces (r.u, w.u, r.r) to FP64 accuracy:
+// the barrier kernels publish u with a grid barrier, the dataflow kernel
+// (MIXED precision) with epoch-tagged words that readers wait for.
 #include <cooperative_groups.h>
 
 #include <algorithm>
