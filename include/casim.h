@@ -129,6 +129,12 @@ typedef struct {
   casim_iter_record last;   /* record of the most recent iteration                   */
   int32_t status;           /* device status code of the last casim_sync             */
   int32_t pcg_kernel;       /* PCG kernel chosen at upload (1..5, see casim_params)   */
+  int32_t status_bits;      /* OR of every device status word casim_sync has read
+                               since the mesh upload: 1 non-finite value, 2 wait
+                               timeout, 4 PCG iteration cap, 8 hash / pair
+                               overflow, 16 a vertex's pair list truncated at
+                               params.max_pairs_per_vertex                          */
+  int32_t pad;
 } casim_stats;
 
 /* Fills *p with the defaults: MIXED, self collision, k = 1, eps = 0.005,
@@ -311,10 +317,13 @@ int casim_get_phase_times(casim_sim* sim, double* ms_out5);
    CASIM_E_INVALID (null or misaligned pointer, id out of range, bad
    cell_size / max_pairs), CASIM_E_OVERFLOW (more pairs than max_pairs for
    some vertex, or more hash entries than the scratch holds),
-   CASIM_E_NONFINITE, CASIM_E_CUDA.
+   CASIM_E_NONFINITE, CASIM_E_CUDA.  Ids are checked on the device before
+   any position is read through them.  casim_last_error(NULL) on the calling
+   thread tells which check failed.
    Calls no cudaMalloc or cudaFree.  The first call on a device looks up the
    static array's device address (cudaGetSymbolAddress), so make that first
-   call outside any stream capture.  The call waits for its stream before it
+   call outside any stream capture.  The address is cached per device for the
+   life of the process and does not survive cudaDeviceReset.  The call waits for its stream before it
    returns.  Every call reuses the same array, which keeps the last call's
    contents (the call clears what must start at zero): calls whose GPU work
    overlaps, from several host threads or streams, race with each other. */
@@ -407,8 +416,10 @@ int casim_step_anderson(casim_sim* sim, int32_t n_iters, int32_t m, casim_aa_rec
 
 void casim_destroy(casim_sim* sim);
 
-/* Message of the last failure on this handle (or of the last casim_create
-   failure when sim is NULL).  Valid until the next call on the handle. */
+/* Message of the last failure on this handle.  With sim NULL: the message of
+   the last failure, on the calling host thread, of a call that takes no
+   handle (casim_create, casim_contacts_noalloc).  Valid until the next call
+   on the handle (or the next handle-free call on the thread). */
 const char* casim_last_error(const casim_sim* sim);
 
 #ifdef __cplusplus

@@ -84,6 +84,8 @@ class casim_stats(ctypes.Structure):
         ("last", casim_iter_record),
         ("status", ctypes.c_int32),
         ("pcg_kernel", ctypes.c_int32),
+        ("status_bits", ctypes.c_int32),
+        ("pad", ctypes.c_int32),
     ]
 
 

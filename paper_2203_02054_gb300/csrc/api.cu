@@ -37,6 +37,11 @@ size_t pow2_at_least(size_t n) {
 
 }  // namespace
 
+namespace casim {
+void set_handle_free_error(const char* msg) { g_create_error = msg ? msg : ""; }
+const char* handle_free_error() { return g_create_error.c_str(); }
+}  // namespace casim
+
 // Device buffers of the Anderson-accelerated loop (allocated on first use,
 // for memory up to m_cap): positions x_k and the proposal (all vertices), the
 // residual and previous residual / image, the history rings dF, dG, and small
@@ -115,6 +120,7 @@ struct casim_sim {
   bool no_graph = false;  // capture refused: launch the iteration eagerly
   long long iters = 0;
   int last_status = 0;
+  int status_bits = 0;  // OR of the device status words read by casim_sync
   double phase_ms[5] = {0, 0, 0, 0, 0};
   std::vector<double> alpha_h;  // current volume ratios (host copy, for the adjoint)
   std::vector<double> rest_h;   // rest positions, internal order, FP64 (remesh trigger reference)
@@ -1317,6 +1323,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
     CK(cudaMemcpy(sim->spheres_d, sim->spheres.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice));
   }
   sim->iters = 0;
+  sim->status_bits = 0;
   sim->has_mesh = true;
   sim->graph_dirty = true;
   if (sim->n_groups == 0) {
@@ -1472,6 +1479,7 @@ int casim_sync(casim_sim* sim) {
   int st = 0;
   CK(cudaMemcpy(&st, &sim->ctrl->status, sizeof(int), cudaMemcpyDeviceToHost));
   CK(cudaMemset(&sim->ctrl->status, 0, sizeof(int)));
+  sim->status_bits |= st;
   int rc = CASIM_OK;
   if (st & ST_TIMEOUT) rc = CASIM_E_TIMEOUT;
   else if (st & ST_NONFINITE) rc = CASIM_E_NONFINITE;
@@ -1625,6 +1633,7 @@ int casim_get_stats(casim_sim* sim, casim_stats* out) {
   out->total_pcg_iters = c.total_pcg;
   out->status = sim->last_status;
   out->pcg_kernel = sim->pcg_seg ? 4 : sim->pcg_cl ? 3 : sim->pcg_variant;
+  out->status_bits = sim->status_bits;
   if (c.iter > 0) {
     IterRec r;
     CK(cudaMemcpy(&r, sim->hist + ((c.iter - 1) % sim->hist_cap), sizeof(IterRec), cudaMemcpyDeviceToHost));

@@ -31,6 +31,7 @@ enum : int {
   ST_PCG_MAXIT = 4,
   ST_OVERFLOW = 8,
   ST_PAIRS_TRUNC = 16,   // a vertex had more self pairs than max_pairs_per_vertex
+  ST_BAD_INPUT = 32,     // an input id out of range (checked on the device before use)
 };
 
 struct IterRec {

@@ -99,6 +99,12 @@ void launch_adjoint_diag(const Dev<T>& d, const AdjDev<T>& a, cudaStream_t st);
 template <typename T>
 void launch_adjoint_flags(const Dev<T>& d, int* flag, cudaStream_t st);
 
+// Message of the last failure of a call that has no handle (casim_create,
+// casim_contacts_noalloc) on the calling host thread; casim_last_error(NULL)
+// returns it.
+void set_handle_free_error(const char* msg);
+const char* handle_free_error();
+
 int local_blocks(int n_t);
 int rhs_blocks(int n_free);
 int scan_tiles(int n);

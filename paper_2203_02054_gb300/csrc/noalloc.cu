@@ -26,7 +26,6 @@ constexpr int NA_MAX_TETS = 65536;
 constexpr int NA_MAX_QUERY = 16384;
 constexpr unsigned NA_HASH = 131072;  // power of two >= 2 * NA_MAX_TETS
 constexpr int NA_CAP_ITEMS = 16 * NA_MAX_TETS + 4096;
-constexpr int ST_BAD_INPUT = 16;      // a tet or query vertex id out of range
 
 // Byte offsets of the pieces inside the scratch array (each 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
@@ -49,10 +48,25 @@ static __device__ __align__(256) unsigned char g_scratch[SCRATCH_BYTES];
 
 // Device address of g_scratch per device, looked up once per device with that
 // device current.  In host code the name g_scratch is only a host-side stand-in
-// and must never be passed to a kernel.
+// and must never be passed to a kernel.  The cached address belongs to the
+// device's primary context: it does not survive cudaDeviceReset (the module is
+// loaded again in the new context).
 std::mutex g_mu;
 void* g_addr[64] = {nullptr};
-std::string g_err;
+
+// Control word and statistics record at the start of a call: zero, except the
+// bounding-box words, which start at the empty box (as a casim_step iteration
+// starts them) so that their atomic min / max reduce to the items' box.
+__global__ void k_init_ctrl(Ctrl* ctrl, IterRec* hist) {
+  if (threadIdx.x != 0) return;
+  Ctrl c{};
+  for (int j = 0; j < 3; ++j) {
+    c.box_lo[j] = 0x7FFFFFFFFFFFFFFFLL;
+    c.box_hi[j] = (long long)0x8000000000000000ULL;
+  }
+  *ctrl = c;
+  *hist = IterRec{};
+}
 
 __global__ void k_pack_and_check(const float* xyz, int n_verts, const int* tets, int n_tets, const int* query,
                                  int n_query, R4<float>* X, Ctrl* ctrl) {
@@ -68,10 +82,9 @@ __global__ void k_pack_and_check(const float* xyz, int n_verts, const int* tets,
   }
 }
 
-// Keeps the reason of the last rejection for a debugger; the return code is
-// the interface.
+// Records the reason of a rejection for casim_last_error(NULL) on this thread.
 int fail(int code, const std::string& msg) {
-  g_err = msg;
+  set_handle_free_error(msg.c_str());
   return code;
 }
 
@@ -114,9 +127,10 @@ extern "C" int casim_contacts_noalloc(int32_t n_verts, const float* dev_xyz, int
   Ctrl* ctrl = reinterpret_cast<Ctrl*>(base + OFF_CTRL);
   IterRec* hist = reinterpret_cast<IterRec*>(base + OFF_HIST);
   R4<float>* X = reinterpret_cast<R4<float>*>(base + OFF_X);
-  // the control word and the statistics record must start at zero
-  e = cudaMemsetAsync(base, 0, OFF_X, st);
-  if (e != cudaSuccess) return fail(CASIM_E_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
+  // the control word and the statistics record start from their initial values
+  k_init_ctrl<<<1, 32, 0, st>>>(ctrl, hist);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(CASIM_E_CUDA, std::string("control init: ") + cudaGetErrorString(e));
   int n_check = n_verts > 4 * n_tets ? n_verts : 4 * n_tets;
   if (n_query > n_check) n_check = n_query;
   k_pack_and_check<<<(n_check + 255) / 256, 256, 0, st>>>(dev_xyz, n_verts, dev_tets, n_tets, dev_query, n_query, X,
@@ -160,7 +174,9 @@ extern "C" int casim_contacts_noalloc(int32_t n_verts, const float* dev_xyz, int
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail(CASIM_E_CUDA, std::string("contact check: ") + cudaGetErrorString(e));
   if (status & ST_NONFINITE) return fail(CASIM_E_NONFINITE, "non-finite position");
-  if (status & (ST_OVERFLOW | ST_PAIRS_TRUNC))
-    return fail(CASIM_E_OVERFLOW, "more contacts or hash entries than the scratch holds");
+  if (status & ST_PAIRS_TRUNC)
+    return fail(CASIM_E_OVERFLOW, "a query vertex lies in more than max_pairs tets (the smallest ids are kept)");
+  if (status & ST_OVERFLOW)
+    return fail(CASIM_E_OVERFLOW, "more hash entries than the scratch holds (cell_size too small for the tets)");
   return CASIM_OK;
 }
