@@ -61,22 +61,37 @@ class SpringState:
                            self.bary.copy(), self.target.copy(), self.fallback.copy())
 
 
-def _ray_triangle(o, d, q0, q1, q2):
-    """Moller-Trumbore: (hit, t, beta1, beta2) of the ray o + t d against the
-    triangle q0 q1 q2, barycentrics inclusive, t > 0."""
+def _cross_rows(a, b):
+    """Row-wise cross products of (n, 3) arrays, written out component by
+    component (a_y b_z - a_z b_y, a_z b_x - a_x b_z, a_x b_y - a_y b_x)."""
+    return np.stack([a[..., 1] * b[..., 2] - a[..., 2] * b[..., 1],
+                     a[..., 2] * b[..., 0] - a[..., 0] * b[..., 2],
+                     a[..., 0] * b[..., 1] - a[..., 1] * b[..., 0]], axis=-1)
+
+
+def _dot_rows(a, b):
+    """Row-wise dot products a_x b_x + a_y b_y + a_z b_z, summed left to right."""
+    return a[..., 0] * b[..., 0] + a[..., 1] * b[..., 1] + a[..., 2] * b[..., 2]
+
+
+def _ray_triangles(o, d, q0, q1, q2):
+    """Moller-Trumbore (Moller and Trumbore 1997) for one ray o + t d against
+    many triangles (rows of q0, q1, q2): (hit, t, beta1, beta2) per triangle,
+    barycentrics inclusive, t > 0; a triangle parallel to the ray (det = 0)
+    is not hit."""
     e1 = q1 - q0
     e2 = q2 - q0
-    pv = np.cross(d, e2)
-    det = float(np.dot(e1, pv))
-    if det == 0.0:
-        return False, 0.0, 0.0, 0.0
-    inv = 1.0 / det
-    tv = o - q0
-    b1 = float(np.dot(tv, pv)) * inv
-    qv = np.cross(tv, e1)
-    b2 = float(np.dot(d, qv)) * inv
-    t = float(np.dot(e2, qv)) * inv
-    hit = (b1 >= 0.0) and (b2 >= 0.0) and (b1 + b2 <= 1.0) and (t > 0.0)
+    pv = _cross_rows(np.broadcast_to(d, e2.shape), e2)
+    det = _dot_rows(e1, pv)
+    ok = det != 0.0
+    inv = np.zeros_like(det)
+    inv[ok] = 1.0 / det[ok]
+    tv = o[None, :] - q0
+    b1 = _dot_rows(tv, pv) * inv
+    qv = _cross_rows(tv, e1)
+    b2 = _dot_rows(np.broadcast_to(d, qv.shape), qv) * inv
+    t = _dot_rows(e2, qv) * inv
+    hit = ok & (b1 >= 0.0) & (b2 >= 0.0) & (b1 + b2 <= 1.0) & (t > 0.0)
     return hit, t, b1, b2
 
 
@@ -134,25 +149,30 @@ def _face_unit_normal(X, face_verts):
 
 def ray_cast_target(X, v, nrm_v, faces, fnormals):
     """Self-collision correspondence of vertex v: (face id, b1, b2, fell back
-    to the closest point)."""
+    to the closest point).
+
+    Every exit face (not containing v, outward normal along the ray -n(v)) is
+    tested; among the hits the smallest t wins, then the lowest face id.  With
+    no hit, the closest point over all boundary faces not containing v wins
+    (smallest squared distance, then the lowest face id)."""
     d = -nrm_v
     o = X[v]
-    cand = np.nonzero((fnormals @ d > 0.0) & np.all(faces != v, axis=1))[0]
-    best = None
-    for f in cand:
-        hit, t, b1, b2 = _ray_triangle(o, d, X[faces[f, 0]], X[faces[f, 1]], X[faces[f, 2]])
-        if hit and (best is None or t < best[0]):
-            best = (t, int(f), b1, b2)
-    if best is not None:
-        return best[1], best[2], best[3], False
+    free = np.all(faces != v, axis=1)
+    cand = np.nonzero((fnormals @ d > 0.0) & free)[0]
+    if cand.size:
+        hit, t, b1, b2 = _ray_triangles(o, d, X[faces[cand, 0]], X[faces[cand, 1]], X[faces[cand, 2]])
+        if np.any(hit):
+            h = np.nonzero(hit)[0]
+            k = h[np.lexsort((cand[h], t[h]))[0]]
+            return int(cand[k]), float(b1[k]), float(b2[k]), False
     # no exit face hit: closest point over boundary faces not containing v
-    bestc = None
-    for f in np.nonzero(np.all(faces != v, axis=1))[0]:
+    best = None
+    for f in np.nonzero(free)[0]:
         x, b1, b2 = closest_point_triangle(o, X[faces[f, 0]], X[faces[f, 1]], X[faces[f, 2]])
         dd = float(np.dot(o - x, o - x))
-        if bestc is None or dd < bestc[0]:
-            bestc = (dd, int(f), b1, b2)
-    return bestc[1], bestc[2], bestc[3], True
+        if best is None or dd < best[0]:
+            best = (dd, int(f), b1, b2)
+    return best[1], best[2], best[3], True
 
 
 def _sphere_target(x, c, r, eps, nrm_v):

@@ -445,3 +445,108 @@ def test_slab_prefilter_equals_plain_all_pairs():
     a = collision.self_pairs(X, prep.tets, prep.query)
     b = collision.self_pairs(X, prep.tets, prep.query, n_slabs=1)
     assert np.array_equal(a, b) and a.shape[0] > 0
+
+
+# ------------------------------------------------- vertex normals (reading G18)
+def test_vertex_normal_is_area_weighted_closed_form():
+    """Corner vertex of the right-angle tet (0,0,0), (a,0,0), (0,b,0), (0,0,c)
+    with a, b, c unequal: its three boundary faces lie in the coordinate
+    planes with outward normals -z, -x, -y and areas ab/2, bc/2, ac/2, so the
+    normalised sum of the unnormalised face normals is -(bc, ac, ab)/|.|.
+    A uniform or angle weighting gives -(1, 1, 1)/sqrt(3) here (the three
+    face angles at the corner are all 90 degrees), and a missing
+    normalisation gives the wrong length."""
+    a, b, c = 1.0, 2.0, 4.0
+    X = np.array([[0.0, 0, 0], [a, 0, 0], [0, b, 0], [0, 0, c]])
+    tets = np.array([[0, 1, 2, 3]])
+    faces = mesh.boundary_faces(tets)
+    vn = mesh.vertex_normals(X, faces, 4)
+    expect = -np.array([b * c, a * c, a * b])
+    expect /= np.linalg.norm(expect)
+    assert np.allclose(vn[0], expect, rtol=0, atol=1e-15)
+    assert math.isclose(np.linalg.norm(vn[0]), 1.0, rel_tol=0, abs_tol=1e-15)
+    assert not np.allclose(vn[0], -np.ones(3) / math.sqrt(3.0), atol=1e-3)
+    # the ray from the corner along -n(v) runs along the normal of the
+    # opposite face x/a + y/b + z/c = 1 and hits it at the foot of the
+    # perpendicular from the origin: abc (bc, ac, ab) / (b^2c^2 + a^2c^2 + a^2b^2)
+    fn = mesh.face_normals(X, faces)
+    f, b1, b2, fb = springs.ray_cast_target(X, 0, vn[0], faces, fn)
+    assert not fb
+    assert sorted(faces[f].tolist()) == [1, 2, 3]
+    hit = (1 - b1 - b2) * X[faces[f, 0]] + b1 * X[faces[f, 1]] + b2 * X[faces[f, 2]]
+    den = (b * c) ** 2 + (a * c) ** 2 + (a * b) ** 2
+    foot = a * b * c * np.array([b * c, a * c, a * b]) / den
+    assert np.allclose(hit, foot, rtol=0, atol=1e-14)
+
+
+def test_vertex_normal_of_a_skewed_corner():
+    """A corner where two incident faces meet at 60 degrees with areas in the
+    ratio 1 : 3: a vertex at the origin of the tet (0,0,0), (1,0,0),
+    (cos60, sin60, 0) * 3, (0,0,1) has faces in the plane z = 0 (area 3/2 sin60,
+    outward -z), in the plane y = 0 (area 1/2, outward -y) and in the plane
+    through the z axis at 60 degrees (area 3/2, outward normal
+    (sin60, -cos60, 0)); the area-weighted normal is the normalised sum of
+    area * unit normal."""
+    s, co = math.sin(math.pi / 3), math.cos(math.pi / 3)
+    X = np.array([[0.0, 0, 0], [1, 0, 0], [3 * co, 3 * s, 0], [0, 0, 1]])
+    tets = np.array([[0, 1, 2, 3]])
+    faces = mesh.boundary_faces(tets)
+    vn = mesh.vertex_normals(X, faces, 4)
+    acc = 1.5 * s * np.array([0, 0, -1.0]) + 0.5 * np.array([0, -1.0, 0]) + 1.5 * np.array([-s, co, 0])
+    assert np.allclose(vn[0], acc / np.linalg.norm(acc), rtol=0, atol=1e-15)
+
+
+# ------------------------------------------ ray cast against a linear solve
+def _ray_tri_solve(o, d, q0, q1, q2):
+    """o + t d = q0 + b1 (q1 - q0) + b2 (q2 - q0) as a 3x3 linear system."""
+    M = np.stack([d, -(q1 - q0), -(q2 - q0)], axis=1)
+    t, b1, b2 = np.linalg.solve(M, q0 - o)
+    return t, b1, b2
+
+
+def test_ray_triangle_test_equals_linear_solve():
+    rng = np.random.default_rng(21)
+    o = rng.normal(size=3)
+    d = rng.normal(size=3)
+    q = rng.normal(size=(400, 3, 3)) * 2.0
+    hit, t, b1, b2 = springs._ray_triangles(o, d, q[:, 0], q[:, 1], q[:, 2])
+    n_hit = 0
+    for k in range(q.shape[0]):
+        ts, s1, s2 = _ray_tri_solve(o, d, *q[k])
+        margin = min(s1, s2, 1 - s1 - s2, ts)
+        if abs(margin) < 1e-9:
+            continue
+        assert bool(hit[k]) == (margin > 0), k
+        assert np.allclose([t[k], b1[k], b2[k]], [ts, s1, s2], rtol=1e-9, atol=1e-12)
+        n_hit += int(margin > 0)
+    assert n_hit > 10
+
+
+def test_ray_cast_target_equals_brute_force_on_a_penetrating_finger():
+    """Every self-pair vertex of a perturbed small finger: the first exit face
+    along -n(v) found by solving each face's 3x3 system one by one."""
+    m = synth.small_finger(nx=16, ny=4, nz=4, n_ch=3)
+    prep = loop.prepare(m.rest, m.tets, m.group, m.fixed)
+    X = synth.perturbed_positions(m, 0.35, seed=13)
+    pairs = collision.self_pairs(X, prep.tets, prep.query)
+    vn = mesh.vertex_normals(X, prep.faces, X.shape[0])
+    fn = mesh.face_normals(X, prep.faces)
+    checked = 0
+    for v in np.unique(pairs[:, 0]):
+        d = -vn[v]
+        best = None
+        for f in range(prep.faces.shape[0]):
+            fv = prep.faces[f]
+            if v in fv or float(fn[f] @ d) <= 0.0:
+                continue
+            t, s1, s2 = _ray_tri_solve(X[v], d, X[fv[0]], X[fv[1]], X[fv[2]])
+            if min(s1, s2, 1 - s1 - s2) >= -1e-12 and t > 0 and (best is None or t < best[0] - 1e-12):
+                best = (t, f, s1, s2)
+        f, b1, b2, fb = springs.ray_cast_target(X, v, vn[v], prep.faces, fn)
+        if best is None:
+            assert fb
+            continue
+        assert not fb and f == best[1], v
+        assert np.allclose([b1, b2], best[2:], atol=1e-9)
+        checked += 1
+    assert checked >= 5
