@@ -529,8 +529,11 @@ def main():
                                                "pcg": ph[4] / n_iters}},
             "clocks": clocks,
             "solver": {"k_pcg_mean_timed": stats.total_pcg_iters / max(1, stats.iterations),
+                       "device_status_bits": stats.status_bits,
+                       "pairs_truncated": bool(stats.status_bits & 16),
                        "last_step": {"max_self_pairs": max(h["n_self_pairs"] for h in hist),
                                      "max_obstacle_pairs": max(h["n_obstacle_pairs"] for h in hist),
+                                     "iters_with_obstacle_contact": sum(1 for h in hist if h["n_obstacle_pairs"]),
                                      "max_springs": max(h["n_springs"] for h in hist),
                                      "final_springs": hist[-1]["n_springs"]}},
         }

@@ -265,12 +265,23 @@ def _place_finger(rest, nx, ny, nz, h, theta, radius, root_z):
 def config3_gripper(seed=1003, n_iters=200) -> Mesh:
     """Three 60x12x12 fingers at 0/120/240 degrees (centre-line radius 8 cm)
     hanging 0.25 cm below a 40x40x4-voxel plate whose top is fixed, plus a
-    rigid sphere of radius 3 cm; 24 chamber ratios U(1.2,2.5); ~194k tets."""
+    rigid sphere of radius 3 cm in one finger's closing path; 24 chamber
+    ratios U(1.2,2.5); ~194k tets.  Draw order: ratios, object finger,
+    radial offset, depth."""
     rng = SplitMix64(seed)
     nx, ny, nz, n_ch, h = 60, 12, 12, 8, 0.5
     alpha = np.array([rng.uniform(1.2, 2.5) for _ in range(3 * n_ch)])
-    sphere = np.array([[rng.uniform(-1.0, 1.0), rng.uniform(-1.0, 1.0),
-                        -rng.uniform(12.0, 20.0), 3.0]])
+    # The sphere (the grasped object) sits in the closing path of a seeded
+    # finger f near the fingertips: centre at radius rho toward finger f, so
+    # that the sphere's surface lies within 0.25 cm inside that finger's inner
+    # face (radius 5 cm at rest; not touching), at depth 28-31 cm below the
+    # plate (the tips hang at 30.25 cm).  The finger curls onto it within the
+    # first tens of iterations.
+    f_obj = rng.randint(0, 2)
+    rho = 2.0 - rng.uniform(0.0, 0.25)
+    depth = rng.uniform(28.0, 31.0)
+    th = 2.0 * math.pi * f_obj / 3.0
+    sphere = np.array([[rho * math.cos(th), rho * math.sin(th), -depth, 3.0]])
     rests, tetss, groups, fixeds = [], [], [], []
     off = 0
     for f in range(3):

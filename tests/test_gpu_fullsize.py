@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from paper_2203_02054_gb300 import casim, synth
-from oracle import collision, loop, springs as osprings
+from oracle import collision, global_step, local, loop, springs as osprings
 
 pytestmark = pytest.mark.gpu
 POS_TOL = 1e-5
@@ -93,3 +93,112 @@ def test_gripper_full_run_properties():
         outs.append(X)
         sim.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+def _oracle_springs(prep, rec):
+    st = osprings.SpringState.empty(prep.query.shape[0])
+    assert np.array_equal(rec["verts"], prep.query)
+    st.active = rec["active"].copy()
+    st.kind = rec["kind"].astype(np.int8)
+    st.face = rec["face"].astype(np.int64)
+    st.bary = rec["bary"].copy()
+    st.target = rec["target"].copy()
+    return st
+
+
+def _oracle_global_with(prep, m, X, rec):
+    """The oracle's local and global steps from X with the spring set of
+    another update (active vertices and their targets) held as given."""
+    P, *_ = local.local_step(X, prep.tets, prep.T_c, prep.vol0, prep.group, m.alpha, m.w_knots)
+    act = rec["active"]
+    A, b = global_step.assemble(prep.tets, prep.omega, P, prep.n_verts, prep.query[act], rec["target"][act],
+                                m.k_spring)
+    return global_step.solve(A, b, X, prep.fixed)
+
+
+def _ray_t(X, v, nrm, face):
+    q0, q1, q2 = X[face[0]], X[face[1]], X[face[2]]
+    M = np.stack([-nrm, -(q1 - q0), -(q2 - q0)], axis=1)
+    return float(np.linalg.solve(M, q0 - X[v])[0])
+
+
+def _replay_along_trajectory(m, checkpoints):
+    """Runs the GPU loop from rest; at each checkpoint k it takes the GPU's
+    state (X_k and the spring records of iteration k-1), runs one more GPU
+    iteration and the oracle's iteration k from the same state, and compares:
+    pair sets bit for bit, obstacle vertices, spring decisions (a decision may
+    differ only where the oracle's release test is within 1e-5 cm of its
+    threshold), targets of equal decisions (1e-9; a different hit face only
+    where the two faces' ray parameters tie within 1e-9), and X_{k+1} within
+    1e-5 of the bounding-box diagonal against the oracle's solve with the
+    GPU's spring set (and against the oracle's own X_{k+1} when every
+    decision agrees)."""
+    from test_gpu_parity import _release_margin
+
+    prep = loop.prepare(m.rest, m.tets, m.group, m.fixed)
+    sim = casim.Sim(m)
+    done = 0
+    tol = POS_TOL * m.bbox_diag()
+    out = []
+    for k in checkpoints:
+        sim.step(k - done)
+        assert sim.sync() == 0
+        Xk = sim.positions()
+        st_prev = _oracle_springs(prep, sim.springs())
+        sim.step(1)
+        done = k + 1
+        assert sim.sync() == 0
+        pairs, obs = sim.contacts()
+        rec = sim.springs()
+        Xg = sim.positions()
+        Xn, stn, orec, ps, po = loop.iterate(prep, Xk, st_prev, m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps,
+                                             m.collision)
+        assert np.array_equal(pairs, ps), k
+        assert np.array_equal(obs, np.unique(po[:, 0]) if po.shape[0] else obs[:0]), k
+        diff = np.nonzero(rec["active"] != stn.active)[0]
+        for qi in diff:
+            assert st_prev.active[qi], (k, qi)
+            assert abs(_release_margin(Xk, prep, st_prev, qi, m.spheres, m.eps)) < 1e-5, (k, qi)
+        same = np.nonzero(rec["active"] & stn.active)[0]
+        assert np.array_equal(rec["kind"][same], stn.kind[same].astype(np.int32)), k
+        face_diff = same[rec["face"][same] != stn.face[same]]
+        vn = None
+        if face_diff.size:
+            from oracle import mesh as omesh
+
+            vn = omesh.vertex_normals(Xk, prep.faces, prep.n_verts)
+        for qi in face_diff:
+            v = prep.query[qi]
+            ta = _ray_t(Xk, v, -vn[v], prep.faces[rec["face"][qi]])
+            tb = _ray_t(Xk, v, -vn[v], prep.faces[stn.face[qi]])
+            assert abs(ta - tb) <= 1e-9 * max(1.0, abs(tb)), (k, qi, ta, tb)
+        eq = np.setdiff1d(same, face_diff)
+        assert np.abs(rec["target"][eq] - stn.target[eq]).max(initial=0.0) <= 1e-9, k
+        Xs = _oracle_global_with(prep, m, Xk, rec)
+        err_s = float(np.abs(Xg - Xs).max())
+        assert err_s <= tol, (k, err_s)
+        if diff.size == 0 and face_diff.size == 0:
+            assert float(np.abs(Xg - Xn).max()) <= tol, k
+        out.append(dict(k=k, pairs=int(ps.shape[0]), obstacle_pairs=int(po.shape[0]),
+                        springs=int(rec["active"].sum()), decision_ties=int(diff.size),
+                        face_ties=int(face_diff.size), err=err_s))
+    sim.close()
+    return out
+
+
+def test_gripper_mid_trajectory_replay_with_contacts():
+    """The benchmark workload (193,920 tets) at outer iterations 50, 100 and
+    199, with self and obstacle springs active."""
+    m = synth.config3_gripper()
+    res = _replay_along_trajectory(m, [50, 100, 199])
+    print(res)
+    assert all(r["pairs"] > 100 and r["springs"] > 100 for r in res)
+    assert res[-1]["obstacle_pairs"] > 0 and res[-2]["obstacle_pairs"] > 0
+
+
+def test_finger_mid_trajectory_replay_with_contacts():
+    """The 51,840-tet finger at outer iterations 50 and 99."""
+    m = synth.config2_finger()
+    res = _replay_along_trajectory(m, [50, 99])
+    print(res)
+    assert all(r["pairs"] > 100 and r["springs"] > 100 for r in res)
