@@ -17,6 +17,7 @@ shard); the value is the work of all ranks over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import math
 import hashlib
 import json
 import os
@@ -27,6 +28,12 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+
+# The CPU legs (the FP64 oracle) may use every host core: numpy's BLAS and
+# LAPACK read these before they load.
+NPROC = os.cpu_count() or 1
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, str(NPROC))
 
 METRIC = "tet-element iterations/sec at 200k tets"
 UNIT = "tet-iterations/s"
@@ -198,52 +205,90 @@ def aggregate(ms_local: float, units_local: float, pg=None, device=None):
 
 
 # ------------------------------------------------------------------ oracle arm
-def oracle_sample(m, prep=None):
-    """One outer iteration of the FP64 oracle from the rest shape; returns
-    (seconds, tet-iterations)."""
+CONTACT_SAMPLE = ("one outer iteration of the 193,920-tet gripper from a seeded contact-bearing state "
+                  "(rest + uniform noise of +-0.3 voxel edges on free vertices, seed 2203, FP32-rounded): "
+                  "brute-force exact collision check, spring creation by ray casts, local step, "
+                  "sparse LU global solve; FP64 numpy/scipy")
+
+
+def contact_state(m):
+    from paper_2203_02054_gb300 import synth
+    import numpy as np
+
+    return synth.perturbed_positions(m, 0.3, seed=2203, dtype=np.float32)
+
+
+def oracle_sample(m, prep=None, X0=None):
+    """One outer iteration of the FP64 oracle from X0 (default: the rest
+    shape) with no prior springs; returns (wall seconds, tet-iterations,
+    process CPU seconds, the iteration record)."""
     import numpy as np
 
     from oracle import loop, springs
 
     prep = prep or loop.prepare(m.rest, m.tets, m.group, m.fixed)
     st = springs.SpringState.empty(prep.query.shape[0])
+    X = np.array(m.rest if X0 is None else X0)
+    c0 = time.process_time()
     t0 = time.perf_counter()
-    loop.iterate(prep, np.array(m.rest), st, m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps, m.collision)
-    return time.perf_counter() - t0, m.n_tets
+    _x, _s, rec, _p, _o = loop.iterate(prep, X, st, m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps, m.collision)
+    return time.perf_counter() - t0, m.n_tets, time.process_time() - c0, rec
 
 
-def cpu_threads_used() -> int:
-    return 1
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline_record(value, wall, cpu, sample, extra=None):
+    """cores = the host threads the oracle actually kept busy (process CPU
+    time over wall time, rounded up), next to the cores it was allowed."""
+    busy = cpu / wall if wall > 0 else 1.0
+    rec = {"value": value, "unit": UNIT, "cores": max(1, int(math.ceil(busy - 0.05))), "kind": "oracle",
+           "sample": sample, "cores_allowed": NPROC, "cpu_busy_ratio": busy, "cpu_model": cpu_model(),
+           "blas_threads": os.environ.get("OPENBLAS_NUM_THREADS")}
+    if extra:
+        rec.update(extra)
+    return rec
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        os.environ.setdefault(v, "1")
     from paper_2203_02054_gb300 import synth
     from oracle import loop
 
     m = synth.config3_gripper()
     prep = loop.prepare(m.rest, m.tets, m.group, m.fixed)
+    X0 = contact_state(m)
     for _ in range(args.warmup):
-        oracle_sample(m, prep)
-    tot_t = 0.0
+        oracle_sample(m, prep, X0)
+    tot_t = tot_c = 0.0
     tot_u = 0
+    rec = None
     for _ in range(args.steps):
-        t, u = oracle_sample(m, prep)
+        t, u, c, rec = oracle_sample(m, prep, X0)
         tot_t += t
+        tot_c += c
         tot_u += u
     value = tot_u / tot_t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD, "n_tets": m.n_tets, "sample": "1 outer iteration per step"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
-                         "sample": "one outer iteration of the 193,920-tet gripper from rest per step "
-                                   "(brute-force exact collision check, springs, local step, sparse LU global solve)"},
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n_tets": m.n_tets,
+                                        "sample": "1 contact-bearing outer iteration per step"},
+        "cpu_baseline": cpu_baseline_record(value, tot_t, tot_c, CONTACT_SAMPLE,
+                                            {"self_pairs": rec.n_self_pairs, "springs": rec.n_springs}),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -547,13 +592,17 @@ def main():
             line["anderson"] = bench_anderson(stream)
         except Exception as e:  # a failure here must not cost the main line
             line["anderson"] = {"error": "%s: %s" % (type(e).__name__, e)}
-        # ---- CPU baseline: the oracle on a bounded sample of the same workload ----
-        for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-            os.environ.setdefault(v, "1")
-        t, u = oracle_sample(m)
-        line["cpu_baseline"] = {"value": u / t, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
-                                "sample": "one outer iteration of the 193,920-tet gripper from rest "
-                                          "(FP64 numpy/scipy, brute-force exact collision check)"}
+        # ---- CPU baseline: the oracle on bounded samples of the same workload ----
+        from oracle import loop as oloop
+
+        prep = oloop.prepare(m.rest, m.tets, m.group, m.fixed)
+        t_c, u_c, c_c, rec_c = oracle_sample(m, prep, contact_state(m))
+        t_r, u_r, c_r, _rec_r = oracle_sample(m, prep)
+        line["cpu_baseline"] = cpu_baseline_record(
+            u_c / t_c, t_c, c_c, CONTACT_SAMPLE,
+            {"self_pairs": rec_c.n_self_pairs, "springs": rec_c.n_springs,
+             "from_rest": {"value": u_r / t_r, "unit": UNIT, "cpu_busy_ratio": c_r / t_r,
+                           "sample": "one outer iteration from the rest shape (no contacts)"}})
         print(json.dumps(line))
     sim.close()
     if pg is not None:
