@@ -109,6 +109,13 @@ typedef struct {
                                barrier), so every wait runs out of
                                wait_budget_cycles and the step ends with
                                CASIM_E_TIMEOUT                                  */
+  int32_t pcg_precond;      /* preconditioner of the dataflow kernel (5): 0 auto =
+                               two-level (Jacobi plus an additive coarse
+                               correction over aggregates of 128 rows, Galerkin
+                               coarse matrix of the Laplacian, its inverse formed
+                               at upload); 1 Jacobi only.  Other kernels use
+                               Jacobi                                            */
+  int32_t pad_;
 } casim_params;
 
 #define CASIM_DEBUG_BARRIER_NEVER_COMPLETES 1
@@ -121,6 +128,16 @@ typedef struct {
   int32_t n_obstacle_pairs; /* |P_obs| found on X_i                                  */
   int32_t n_springs;        /* |V_col| after the spring update                       */
   int32_t pcg_iters;        /* PCG iterations of this outer iteration                */
+  /* Signatures of the iteration's discrete state (0 unless params.stats): the
+     sum mod 2^64 of a 64-bit mix of (tet id, interval of the w(eps) table its
+     strain fell in) over body tets, and of (boundary-vertex index, decision:
+     self spring kept from its record / obstacle spring / self spring cast in
+     this iteration, face or sphere id) over the springs after the update.  Two runs with
+     equal signatures at every iteration took the same discrete decisions
+     (with overwhelming probability), e.g. the two sides of a finite
+     difference. */
+  uint64_t knot_signature;
+  uint64_t spring_signature;
 } casim_iter_record;
 
 typedef struct {

@@ -63,6 +63,8 @@ class casim_params(ctypes.Structure):
         ("wait_budget_cycles", ctypes.c_uint64),
         ("pcg_kernel", ctypes.c_int32),
         ("debug_flags", ctypes.c_int32),
+        ("pcg_precond", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
     ]
 
 
@@ -74,6 +76,8 @@ class casim_iter_record(ctypes.Structure):
         ("n_obstacle_pairs", ctypes.c_int32),
         ("n_springs", ctypes.c_int32),
         ("pcg_iters", ctypes.c_int32),
+        ("knot_signature", ctypes.c_uint64),
+        ("spring_signature", ctypes.c_uint64),
     ]
 
 
@@ -350,7 +354,8 @@ def casim_get_history(sim, cap: int = 4096):
     n = ctypes.c_int32(0)
     _check(load_library().casim_get_history(sim, cap, arr, ctypes.byref(n)), sim)
     return [dict(energy=r.energy, pcg_rel_residual=r.pcg_rel_residual, n_self_pairs=r.n_self_pairs,
-                 n_obstacle_pairs=r.n_obstacle_pairs, n_springs=r.n_springs, pcg_iters=r.pcg_iters)
+                 n_obstacle_pairs=r.n_obstacle_pairs, n_springs=r.n_springs, pcg_iters=r.pcg_iters,
+                 knot_signature=r.knot_signature, spring_signature=r.spring_signature)
             for r in arr[:n.value]]
 
 
@@ -440,7 +445,7 @@ class Sim:
 
     def __init__(self, mesh, precision=None, collision=None, stream: int = 0, stats: int = 1,
                  pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0,
-                 pcg_kernel=0, debug_flags=0):
+                 pcg_kernel=0, debug_flags=0, pcg_precond=0):
         load_library()
         self.batch = None
         if isinstance(mesh, (list, tuple)):
@@ -463,6 +468,7 @@ class Sim:
         p.wait_budget_cycles = wait_budget_cycles
         p.pcg_kernel = pcg_kernel
         p.debug_flags = debug_flags
+        p.pcg_precond = pcg_precond
         self.params = p
         self.mesh = mesh
         self.h = casim_create(p, stream)

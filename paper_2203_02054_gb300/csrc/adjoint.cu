@@ -18,7 +18,9 @@
 // whose ray was cast this iteration, the barycentric weights of the ray-plane
 // hit x_v + t d, d = -n(v)/|n(v)|, through the vertex normal n(v) of the
 // incident boundary faces.  Barycentric adjoints of kept springs accumulate
-// across iterations until the iteration that cast them.
+// across iterations until the iteration that cast them.  Every sum is formed
+// in a fixed order (per-tet pullbacks by incidence, spring pullbacks by
+// emission slot), so the reverse pass is bitwise reproducible.
 #include "common.cuh"
 #include "kernels.h"
 #include "svd3.cuh"
@@ -44,11 +46,17 @@ __device__ __forceinline__ D3 posd(const R4<T>* X, int v) {
   return {(double)a.x, (double)a.y, (double)a.z};
 }
 
-__device__ __forceinline__ void atomic_add3(double* acc, int v, D3 a) {
-  atomicAdd(acc + 3 * (size_t)v, a.x);
-  atomicAdd(acc + 3 * (size_t)v + 1, a.y);
-  atomicAdd(acc + 3 * (size_t)v + 2, a.z);
-}
+// One spring's contributions go to consecutive slots starting at its base.
+struct Emit {
+  int* vert;
+  R4<double>* val;
+  size_t pos;
+  __device__ __forceinline__ void put(int v, D3 a) {
+    vert[pos] = v;
+    val[pos] = R4<double>{a.x, a.y, a.z, 0.0};
+    ++pos;
+  }
+};
 
 // slope of the piecewise-linear w(eps) table at eps (0 where clamped)
 __device__ __forceinline__ double w_and_slope(const double* k, int n, double eps, double& slope) {
@@ -308,6 +316,7 @@ __global__ void __launch_bounds__(128) k_adj_springs(Dev<T> d, AdjDev<T> a) {
     return;
   }
   const int v = d.q_verts[qi];
+  Emit em{a.em_vert, a.em_val, 4 * (size_t)qi + 3 * (size_t)d.qf_ptr[qi]};
   const R4<T> mv = a.mu[v];
   const D3 cb = (double)d.k_spring * d3(mv.x, mv.y, mv.z);
   const D3 x = posd(a.Xi, v);
@@ -320,7 +329,7 @@ __global__ void __launch_bounds__(128) k_adj_springs(Dev<T> d, AdjDev<T> a) {
     const double nu = normd(u);
     if (nu > 0.0) {
       const D3 uh = (1.0 / nu) * u;
-      atomic_add3(a.xbar_vert, v, ((r + eps) / nu) * (cb - dotd(uh, cb) * uh));
+      em.put(v, ((r + eps) / nu) * (cb - dotd(uh, cb) * uh));
     }
     a.betabar[2 * qi] = 0.0;
     a.betabar[2 * qi + 1] = 0.0;
@@ -372,11 +381,11 @@ __global__ void __launch_bounds__(128) k_adj_springs(Dev<T> d, AdjDev<T> a) {
       const D3 p0 = posd(a.Xi, gv.x), p1 = posd(a.Xi, gv.y), p2 = posd(a.Xi, gv.z);
       D3 r0, r1, r2;
       cross_vjp(p0, p1, p2, mb, r0, r1, r2);
-      atomic_add3(a.xbar_vert, gv.x, r0);
-      atomic_add3(a.xbar_vert, gv.y, r1);
-      atomic_add3(a.xbar_vert, gv.z, r2);
+      em.put(gv.x, r0);
+      em.put(gv.y, r1);
+      em.put(gv.z, r2);
     }
-    atomic_add3(a.xbar_vert, v, xb);
+    em.put(v, xb);
     bb1 = 0.0;
     bb2 = 0.0;
   } else if (a.sp_flag[qi] == 2) {
@@ -386,20 +395,56 @@ __global__ void __launch_bounds__(128) k_adj_springs(Dev<T> d, AdjDev<T> a) {
   }
   D3 c0, c1, c2;
   cross_vjp(q0, q1, q2, nb, c0, c1, c2);
-  atomic_add3(a.xbar_vert, fv.x, g0 + c0);
-  atomic_add3(a.xbar_vert, fv.y, g1 + c1);
-  atomic_add3(a.xbar_vert, fv.z, g2 + c2);
+  em.put(fv.x, g0 + c0);
+  em.put(fv.y, g1 + c1);
+  em.put(fv.z, g2 + c2);
   a.betabar[2 * qi] = bb1;
   a.betabar[2 * qi + 1] = bb2;
 }
 
-// g_v = sum over incident (tet, slot) of Xbar_tet + spring contributions; the
-// spring accumulator is cleared for the next iteration.
+// Grouping of the spring contributions by destination row (contributions to
+// fixed vertices are dropped: they have no row).
+__global__ void k_em_count(const int* __restrict__ em_vert, int n_slots, int n_free, int* cnt) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots) return;
+  const int u = em_vert[s];
+  if (u >= 0 && u < n_free) atomicAdd(&cnt[u], 1);
+}
+__global__ void k_em_fill(const int* __restrict__ em_vert, int n_slots, int n_free, const int* __restrict__ start,
+                          int* cur, int* list) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n_slots) return;
+  const int u = em_vert[s];
+  if (u >= 0 && u < n_free) list[start[u] + atomicAdd(&cur[u], 1)] = s;
+}
+
+// g_v = (spring contributions to v, added in slot order) + (sum over incident
+// (tet, slot) of Xbar_tet, in incidence order).  The fill order of a row's
+// slot list depends on timing, so each row sorts its list first (insertion
+// sort; a row receives a few tens of contributions at most); the result is
+// independent of the launch's timing.
 template <typename T>
 __global__ void __launch_bounds__(256) k_adj_gather(Dev<T> d, AdjDev<T> a) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= d.n_free) return;
-  double gx = a.xbar_vert[3 * (size_t)v], gy = a.xbar_vert[3 * (size_t)v + 1], gz = a.xbar_vert[3 * (size_t)v + 2];
+  int* L = a.em_list + a.em_start[v];
+  const int n = a.em_start[v + 1] - a.em_start[v];
+  for (int i = 1; i < n; ++i) {
+    const int key = L[i];
+    int j = i - 1;
+    while (j >= 0 && L[j] > key) {
+      L[j + 1] = L[j];
+      --j;
+    }
+    L[j + 1] = key;
+  }
+  double gx = 0.0, gy = 0.0, gz = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const R4<double> c = a.em_val[L[i]];
+    gx += c.x;
+    gy += c.y;
+    gz += c.z;
+  }
   for (int k = d.inc_ptr[v]; k < d.inc_ptr[v + 1]; ++k) {
     const R4<double> c = a.xbar_tet[d.inc[k]];
     gx += c.x;
@@ -407,16 +452,6 @@ __global__ void __launch_bounds__(256) k_adj_gather(Dev<T> d, AdjDev<T> a) {
     gz += c.z;
   }
   a.g[v] = R4<double>{gx, gy, gz, 0.0};
-  a.xbar_vert[3 * (size_t)v] = 0.0;
-  a.xbar_vert[3 * (size_t)v + 1] = 0.0;
-  a.xbar_vert[3 * (size_t)v + 2] = 0.0;
-}
-
-// The spring accumulator of fixed vertices is cleared too (they have no row).
-__global__ void k_adj_clear_fixed(double* acc, int n_free, int n_v) {
-  const int v = n_free + blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= n_v) return;
-  acc[3 * (size_t)v] = acc[3 * (size_t)v + 1] = acc[3 * (size_t)v + 2] = 0.0;
 }
 
 // diagonal of A_i = L + k diag(mask_i): the Laplacian diagonal first, then
@@ -463,10 +498,18 @@ void launch_adjoint_step(const Dev<T>& d, const AdjDev<T>& a, cudaStream_t st) {
   else
     k_adj_local<T, 6><<<nb, 128, 0, st>>>(d, a);
   if (a.n_groups > 0) k_adj_alpha_reduce<<<(a.n_groups + 63) / 64, 64, 0, st>>>(a.alpha_part, nb, a.n_groups, a.abar);
-  if (d.n_q > 0) k_adj_springs<T><<<(d.n_q + 127) / 128, 128, 0, st>>>(d, a);
+  cudaMemsetAsync(a.em_cnt, 0, sizeof(int) * ((size_t)d.n_free + 1), st);
+  cudaMemsetAsync(a.em_cur, 0, sizeof(int) * ((size_t)d.n_free + 1), st);
+  if (a.n_slots > 0) {
+    cudaMemsetAsync(a.em_vert, 0xff, sizeof(int) * (size_t)a.n_slots, st);
+    if (d.n_q > 0) k_adj_springs<T><<<(d.n_q + 127) / 128, 128, 0, st>>>(d, a);
+    k_em_count<<<(a.n_slots + 255) / 256, 256, 0, st>>>(a.em_vert, a.n_slots, d.n_free, a.em_cnt);
+  }
+  launch_scan_exclusive(a.em_cnt, a.em_start, d.n_free + 1, a.em_tiles, a.em_total, st);
+  if (a.n_slots > 0)
+    k_em_fill<<<(a.n_slots + 255) / 256, 256, 0, st>>>(a.em_vert, a.n_slots, d.n_free, a.em_start, a.em_cur,
+                                                        a.em_list);
   if (d.n_free > 0) k_adj_gather<T><<<(d.n_free + 255) / 256, 256, 0, st>>>(d, a);
-  if (d.n_v > d.n_free)
-    k_adj_clear_fixed<<<(d.n_v - d.n_free + 255) / 256, 256, 0, st>>>(a.xbar_vert, d.n_free, d.n_v);
 }
 
 template <typename T>

@@ -35,6 +35,68 @@ size_t pow2_at_least(size_t n) {
   return p;
 }
 
+// Recursive coordinate bisection of the vertices idx[0..n) by their rest
+// positions: split along the longest extent of the set's bounding box so that
+// the first part holds a multiple of RCB_LEAF vertices (about half), order
+// each part recursively; ties by vertex id, so the order is deterministic.
+constexpr int RCB_LEAF = 128;
+void rcb_order(const double* xyz, int* idx, int n) {
+  if (n <= RCB_LEAF) {
+    std::sort(idx, idx + n);
+    return;
+  }
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) {
+      lo[c] = std::min(lo[c], xyz[3 * (size_t)idx[i] + c]);
+      hi[c] = std::max(hi[c], xyz[3 * (size_t)idx[i] + c]);
+    }
+  int ax = 0;
+  for (int c = 1; c < 3; ++c)
+    if (hi[c] - lo[c] > hi[ax] - lo[ax]) ax = c;
+  const int nl = RCB_LEAF * ((n + 2 * RCB_LEAF - 1) / (2 * RCB_LEAF));
+  std::nth_element(idx, idx + nl, idx + n, [&](int a, int b) {
+    const double xa = xyz[3 * (size_t)a + ax], xb = xyz[3 * (size_t)b + ax];
+    return xa < xb || (xa == xb && a < b);
+  });
+  rcb_order(xyz, idx, nl);
+  rcb_order(xyz, idx + nl, n - nl);
+}
+
+// In-place inverse of the SPD n x n matrix A (row-major) by its Cholesky
+// factor L (A = L L^T, A^-1 = L^-T L^-1); false if a pivot is not positive.
+bool cholesky_inverse(std::vector<double>& A, int n) {
+  std::vector<double> L((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    double dsum = A[(size_t)j * n + j];
+    for (int k = 0; k < j; ++k) dsum -= L[(size_t)j * n + k] * L[(size_t)j * n + k];
+    if (!(dsum > 0.0)) return false;
+    const double ljj = std::sqrt(dsum);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      double t = A[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) t -= L[(size_t)i * n + k] * L[(size_t)j * n + k];
+      L[(size_t)i * n + j] = t / ljj;
+    }
+  }
+  // columns of L^-1 by forward substitution, then A^-1 = L^-T L^-1
+  std::vector<double> Li((size_t)n * n, 0.0);
+  for (int c = 0; c < n; ++c) {
+    for (int i = c; i < n; ++i) {
+      double t = i == c ? 1.0 : 0.0;
+      for (int k = c; k < i; ++k) t -= L[(size_t)i * n + k] * Li[(size_t)k * n + c];
+      Li[(size_t)i * n + c] = t / L[(size_t)i * n + i];
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j <= i; ++j) {
+      double t = 0.0;
+      for (int k = i; k < n; ++k) t += Li[(size_t)k * n + i] * Li[(size_t)k * n + j];
+      A[(size_t)i * n + j] = A[(size_t)j * n + i] = t;
+    }
+  return true;
+}
+
 }  // namespace
 
 namespace casim {
@@ -68,6 +130,7 @@ struct casim_sim {
   bool has_act = false;
   // host-side mesh
   int n_v = 0, n_t = 0, n_free = 0, n_q = 0, n_f = 0, n_groups = 0, n_spheres = 0;
+  int n_qf = 0;  // incidences (query vertex, boundary face)
   std::vector<int> int_of_user, user_of_int;
   std::vector<double> omega;
   std::vector<int> q_verts;  // internal ids
@@ -105,6 +168,9 @@ struct casim_sim {
   int *halo_ptr = nullptr, *halo_rows = nullptr, *sl_lcol = nullptr;  // dataflow PCG: block halos
   std::vector<int> halo_ptr_h, halo_rows_h, sl_lcol_h;
   int halo_max = 0;
+  std::vector<float> cg_ainv_h;  // dataflow PCG coarse correction: A_c^-1, row-major
+  int n_agg = 0;
+  float* cg_ainv = nullptr;
   bool pcg_seg = false; // segmented streaming PCG (batches: blocks per robot)
   int seg_blocks = 0;
   std::vector<int> seg_h;  // 4 x seg_blocks: lo, hi, rb0, rb1
@@ -141,7 +207,11 @@ struct casim_sim {
     void* mu = nullptr;
     R4<double>* g = nullptr;
     R4<double>* xbar_tet = nullptr;
-    double *xbar_vert = nullptr, *betabar = nullptr, *alpha_part = nullptr, *alpha_d = nullptr, *abar = nullptr;
+    double *betabar = nullptr, *alpha_part = nullptr, *alpha_d = nullptr, *abar = nullptr;
+    int *em_vert = nullptr, *em_cnt = nullptr, *em_start = nullptr, *em_cur = nullptr, *em_list = nullptr;
+    int *em_tiles = nullptr, *em_total = nullptr;
+    R4<double>* em_val = nullptr;
+    int n_slots = 0;
     void* finX = nullptr;     // final forward state, restored after the reverse pass
     int *fin_act = nullptr, *fin_kind = nullptr, *fin_face = nullptr;
     double *fin_bary = nullptr, *fin_tgt = nullptr;
@@ -234,6 +304,8 @@ Dev<T> make_dev(casim_sim* sim) {
   d.halo_rows = sim->halo_rows;
   d.sl_lcol = sim->sl_lcol;
   d.halo_max = sim->halo_max;
+  d.cg_ainv = sim->cg_ainv;
+  d.n_agg = sim->n_agg;
   d.q_verts = sim->q_verts_d;
   d.qf_ptr = sim->qf_ptr;
   d.qf = sim->qf;
@@ -350,7 +422,8 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->partials = sim->dalloc<double>(2 * 4 * (size_t)std::max(sim->pcg_grid, 1));
   if (sim->pcg_variant == 5) {
     sim->df_u = sim->dalloc<unsigned long long>(4 * (size_t)std::max(n_free, 1));
-    sim->df_p = sim->dalloc<unsigned long long>(8 * ((size_t)sim->pcg_grid + 1));
+    sim->df_p = sim->dalloc<unsigned long long>(2 * 16 * ((size_t)sim->pcg_grid + 1));
+    if (sim->n_agg > 0) sim->cg_ainv = sim->dalloc<float>((size_t)sim->n_agg * sim->n_agg);
     sim->halo_ptr = sim->dalloc<int>(sim->halo_ptr_h.size());
     sim->halo_rows = sim->dalloc<int>(std::max<size_t>(sim->halo_rows_h.size(), 1));
     sim->sl_lcol = sim->dalloc<int>(std::max<size_t>(sim->sl_lcol_h.size(), 1));
@@ -437,6 +510,9 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
                          cudaMemcpyHostToDevice, st));
     if (!sim->sl_lcol_h.empty())
       CK(cudaMemcpyAsync(sim->sl_lcol, sim->sl_lcol_h.data(), sizeof(int) * sim->sl_lcol_h.size(),
+                         cudaMemcpyHostToDevice, st));
+    if (sim->n_agg > 0)
+      CK(cudaMemcpyAsync(sim->cg_ainv, sim->cg_ainv_h.data(), sizeof(float) * sim->cg_ainv_h.size(),
                          cudaMemcpyHostToDevice, st));
   }
   if (n_q) {
@@ -663,6 +739,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
   else if (p.pcg_kernel < 0 || p.pcg_kernel > 5) why = "pcg_kernel";
   else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
+  else if (p.pcg_precond < 0 || p.pcg_precond > 1) why = "pcg_precond";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
       if (!(p.w_knots[2 * i + 2] > p.w_knots[2 * i])) why = "w_knots must be strictly ascending";
@@ -730,7 +807,16 @@ int adj_reserve(casim_sim* sim, int n_ckpt, int every) {
   A.mu = adj_alloc<R4<T>>(sim, nf);
   A.g = adj_alloc<R4<double>>(sim, nf);
   A.xbar_tet = adj_alloc<R4<double>>(sim, 4 * nt);
-  A.xbar_vert = adj_alloc<double>(sim, 3 * nv);
+  A.n_slots = 4 * sim->n_q + 3 * sim->n_qf;
+  const size_t ns = std::max(A.n_slots, 1);
+  A.em_vert = adj_alloc<int>(sim, ns);
+  A.em_val = adj_alloc<R4<double>>(sim, ns);
+  A.em_list = adj_alloc<int>(sim, ns);
+  A.em_cnt = adj_alloc<int>(sim, nf + 1);
+  A.em_start = adj_alloc<int>(sim, nf + 1);
+  A.em_cur = adj_alloc<int>(sim, nf + 1);
+  A.em_tiles = adj_alloc<int>(sim, scan_tiles((int)nf + 1) + 1);
+  A.em_total = adj_alloc<int>(sim, 1);
   A.betabar = adj_alloc<double>(sim, 2 * nq);
   A.alpha_part = adj_alloc<double>(sim, (size_t)local_blocks(sim->n_t) * ng);
   A.alpha_d = adj_alloc<double>(sim, ng);
@@ -817,7 +903,6 @@ int backward_typed(casim_sim* sim, const double* dL_dX, double* dL_dalpha) {
   CK(cudaMemcpyAsync(A.g, gh.data(), sizeof(R4<double>) * std::max(nf, 1), cudaMemcpyHostToDevice, st));
   CK(cudaMemsetAsync(A.abar, 0, sizeof(double) * std::max(ng, 1), st));
   CK(cudaMemsetAsync(A.betabar, 0, sizeof(double) * 2 * nq, st));
-  CK(cudaMemsetAsync(A.xbar_vert, 0, sizeof(double) * 3 * nv, st));
   if (ng) CK(cudaMemcpyAsync(A.alpha_d, sim->alpha_h.data(), sizeof(double) * ng, cudaMemcpyHostToDevice, st));
   // keep the history counters of the forward pass
   Ctrl saved;
@@ -859,7 +944,15 @@ int backward_typed(casim_sim* sim, const double* dL_dX, double* dL_dalpha) {
       a.sp_bary = A.seg_bary + j * 2 * nq;
       a.sp_flag = A.seg_flag + j * nq;
       a.xbar_tet = A.xbar_tet;
-      a.xbar_vert = A.xbar_vert;
+      a.em_vert = A.em_vert;
+      a.em_val = A.em_val;
+      a.em_cnt = A.em_cnt;
+      a.em_start = A.em_start;
+      a.em_cur = A.em_cur;
+      a.em_list = A.em_list;
+      a.em_tiles = A.em_tiles;
+      a.em_total = A.em_total;
+      a.n_slots = (sim->params.collision == 0 || sim->n_q == 0) ? 0 : A.n_slots;
       a.betabar = A.betabar;
       a.alpha_part = A.alpha_part;
       a.alpha = A.alpha_d;
@@ -996,14 +1089,26 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
         return sim->fail(CASIM_E_SINGULAR, "component of vertex " + std::to_string(v) + " has no fixed vertex");
     }
   }
-  // ---- internal numbering: free vertices first ----
+  // ---- internal numbering: free vertices first, robot by robot, each
+  // robot's free vertices in recursive-coordinate-bisection order of their
+  // rest positions (so that consecutive rows, and with them the PCG's thread
+  // blocks and coarse aggregates, are compact pieces of the body); then the
+  // fixed vertices in the caller's order ----
   sim->n_v = n_v;
   sim->n_t = n_t;
   sim->int_of_user.assign(n_v, -1);
   sim->user_of_int.assign(n_v, -1);
   int nf = 0;
-  for (int v = 0; v < n_v; ++v)
-    if (!fixed[v]) sim->int_of_user[v] = nf++;
+  {
+    std::vector<std::vector<int>> per_robot(n_robots);
+    for (int v = 0; v < n_v; ++v)
+      if (!fixed[v]) per_robot[std::max(0, robot_of_vert_user[v])].push_back(v);
+    for (int r = 0; r < n_robots; ++r) {
+      std::vector<int>& L = per_robot[r];
+      rcb_order(rest_xyz, L.data(), (int)L.size());
+      for (int v : L) sim->int_of_user[v] = nf++;
+    }
+  }
   sim->n_free = nf;
   int nx = nf;
   for (int v = 0; v < n_v; ++v)
@@ -1074,13 +1179,17 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   std::vector<char> on_surf(n_v, 0);
   for (int f = 0; f < sim->n_f; ++f)
     for (int k = 0; k < 3; ++k) on_surf[faces4[4 * f + k]] = 1;
+  // (listed in ascending caller vertex id, so that contacts and spring
+  // records come out in the caller's order)
   sim->q_verts.clear();
   std::vector<int> qidx(n_v, -1);
-  for (int i = 0; i < n_free; ++i)
-    if (on_surf[i]) {
+  for (int uv = 0; uv < n_v; ++uv) {
+    const int i = sim->int_of_user[uv];
+    if (i < n_free && on_surf[i]) {
       qidx[i] = (int)sim->q_verts.size();
       sim->q_verts.push_back(i);
     }
+  }
   sim->n_q = (int)sim->q_verts.size();
   std::vector<int> qf_ptr(sim->n_q + 1, 0), qf;
   for (int f = 0; f < sim->n_f; ++f)
@@ -1088,6 +1197,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
       if (qidx[faces4[4 * f + k]] >= 0) qf_ptr[qidx[faces4[4 * f + k]] + 1]++;
   for (int q = 0; q < sim->n_q; ++q) qf_ptr[q + 1] += qf_ptr[q];
   qf.assign(qf_ptr[sim->n_q], 0);
+  sim->n_qf = qf_ptr[sim->n_q];
   {
     std::vector<int> cur(qf_ptr.begin(), qf_ptr.end() - 1);
     for (int f = 0; f < sim->n_f; ++f)
@@ -1225,8 +1335,28 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
       sim->halo_ptr_h[b + 1] = (int)sim->halo_rows_h.size();
       sim->halo_max = std::max(sim->halo_max, (int)cols.size());
     }
-    if ((size_t)sim->halo_max * 16 > PCG_DF_HALO_MAX_BYTES || !pcg_df_prepare(16 * sim->halo_max)) df_fits = false;
+    if ((size_t)sim->halo_max * 16 > PCG_DF_HALO_MAX_BYTES) df_fits = false;
   }
+  // two-level preconditioner of the dataflow kernel: Galerkin coarse matrix
+  // A_c = Z^T L Z of the free-row Laplacian over aggregates of consecutive
+  // rows (a = row / R), inverted here in FP64 (Cholesky)
+  sim->n_agg = 0;
+  sim->cg_ainv_h.clear();
+  if (df_fits && n_robots == 1 && sim->params.pcg_precond == 0) {
+    const int R = pcg_df_agg_rows();
+    const int na = (n_free + R - 1) / R;
+    std::vector<double> Ac((size_t)na * na, 0.0);
+    for (int v = 0; v < n_free; ++v) {
+      const int a = v / R;
+      Ac[(size_t)a * na + a] += diagL[v];
+      for (const auto& e : rows_ff[v]) Ac[(size_t)a * na + e.first / R] += e.second;
+    }
+    if (cholesky_inverse(Ac, na)) {
+      sim->n_agg = na;
+      sim->cg_ainv_h.assign(Ac.begin(), Ac.end());
+    }
+  }
+  if (df_fits && !pcg_df_prepare(16 * sim->halo_max + (int)sizeof(float) * 3 * sim->n_agg)) df_fits = false;
   // cluster PCG: every robot's rows must fit the cluster's shared memory
   int max_robot_rows = 0;
   for (int r = 0; r < sim->n_robots; ++r)
@@ -1617,6 +1747,8 @@ int casim_get_history(casim_sim* sim, int32_t cap, casim_iter_record* out, int32
     out[j].n_obstacle_pairs = r.n_obstacle_pairs;
     out[j].n_springs = r.n_springs;
     out[j].pcg_iters = r.pcg_iters;
+    out[j].knot_signature = r.knot_sig;
+    out[j].spring_signature = r.spring_sig;
   }
   *n = (int32_t)m;
   return CASIM_OK;
@@ -1643,6 +1775,8 @@ int casim_get_stats(casim_sim* sim, casim_stats* out) {
     out->last.n_obstacle_pairs = r.n_obstacle_pairs;
     out->last.n_springs = r.n_springs;
     out->last.pcg_iters = r.pcg_iters;
+    out->last.knot_signature = r.knot_sig;
+    out->last.spring_signature = r.spring_sig;
   }
   return CASIM_OK;
 }

@@ -24,7 +24,7 @@
 
 namespace casim {
 
-static constexpr int MAX_CELLS_PER_ITEM = 512;
+static constexpr int MAX_CELLS_PER_ITEM = 4096;
 static constexpr int MAX_DDA_STEPS = 4096;
 
 template <typename T>
@@ -195,8 +195,10 @@ __global__ void k_scan_top(int* tile_sums, int n_tiles, int* total_out, Ctrl* ct
   }
   if (threadIdx.x == 0) {
     *total_out = carry;
-    ctrl->n_items = carry;
-    if (carry > cap) atomicOr(&ctrl->status, ST_OVERFLOW);
+    if (ctrl) {
+      ctrl->n_items = carry;
+      if (carry > cap) atomicOr(&ctrl->status, ST_OVERFLOW);
+    }
   }
 }
 
@@ -595,11 +597,19 @@ __device__ __forceinline__ V3 face_point(const Dev<T>& d, int f, double b1, doub
 static constexpr int SPRING_THREADS = 128;
 static constexpr int CAST_THREADS = 256;
 
+// Signature term of one spring record (see sig_mix): query index and the
+// decision code (0 a self spring kept from its record, 1 an obstacle spring,
+// 2 a self spring cast in this iteration) with the face or sphere id.
+__device__ __forceinline__ unsigned long long spring_term(int qi, int code, int face) {
+  return sig_mix((unsigned)qi, ((unsigned)code << 30) ^ (unsigned)(face + 1));
+}
+
 template <typename T>
 __global__ void __launch_bounds__(SPRING_THREADS) k_springs(Dev<T> d) {
   __shared__ int shi[32];
   const int qi = blockIdx.x * blockDim.x + threadIdx.x;
   int active_out = 0;
+  unsigned long long ssig = 0;
   if (qi < d.n_q) {
     const int v = d.q_verts[qi];
     const V3 x = pos(d, v);
@@ -679,8 +689,10 @@ __global__ void __launch_bounds__(SPRING_THREADS) k_springs(Dev<T> d) {
       d.sp.target[3 * qi + 2] = tgt.z;
       d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
       active_out = active;
+      if (active) ssig = spring_term(qi, kind, face);
     }
   }
+  if (d.stats) warp_add_u64(ssig, &(d.hist + (d.ctrl->iter % d.hist_cap))->spring_sig);
   const int ns = block_sum_int(active_out, shi);
   if (threadIdx.x == 0 && ns) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->n_springs, ns);
 }
@@ -725,6 +737,7 @@ __global__ void __launch_bounds__(CAST_THREADS) k_cast(Dev<T> d) {
       d.sp.target[3 * qi + 2] = tgt.z;
       d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
       active_out += active;
+      if (active && d.stats) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->spring_sig, spring_term(qi, 2, f));
     }
   }
   const int ns = block_sum_int(active_out, shi);
@@ -761,6 +774,14 @@ void launch_springs(const Dev<T>& d, cudaStream_t st) {
   k_cast<T><<<blocks, CAST_THREADS, 0, st>>>(d);
 }
 int scan_tiles(int n) { return (n + SCAN_TILE - 1) / SCAN_TILE; }
+
+void launch_scan_exclusive(const int* in, int* out, int n, int* tile_sums, int* total, cudaStream_t st) {
+  if (n <= 0) return;
+  const int n_tiles = scan_tiles(n);
+  k_scan_tiles<<<n_tiles, SCAN_THREADS, 0, st>>>(in, out, tile_sums, n);
+  k_scan_top<<<1, 1024, 0, st>>>(tile_sums, n_tiles, total, nullptr, 0);
+  k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, tile_sums, n);
+}
 
 template void launch_collision<float>(const Dev<float>&, const CollisionScratch&, cudaStream_t);
 template void launch_collision<double>(const Dev<double>&, const CollisionScratch&, cudaStream_t);

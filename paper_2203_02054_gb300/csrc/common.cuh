@@ -2,7 +2,9 @@
 //
 // Layout in HBM (per simulation, T = float in MIXED mode, double in FP64):
 //   vertices  X[n_v] as R4<T> (x, y, z, pad); internal order = free vertices
-//             first, then fixed ones, each in the caller's relative order;
+//             first (robot by robot, each robot's in recursive coordinate
+//             bisection order of the rest positions), then the fixed ones in
+//             the caller's relative order;
 //   elements  tet[n_t] int4 internal vertex ids (caller's tet order),
 //             Tc[3 n_t] rows x/y/z of the centered rest shape V N (Eq. 1),
 //             tinfo[n_t] (omega_e, Vol_e, |T_c|^2, group id as T),
@@ -41,7 +43,28 @@ struct IterRec {
   int n_obstacle_pairs;
   int n_springs;
   int pcg_iters;
+  unsigned long long knot_sig;    // sum over body tets of sig_mix(tet, w-table interval of its strain)
+  unsigned long long spring_sig;  // sum over active springs of sig_mix(query index, kind and face / sphere)
 };
+
+// Order-independent signatures of the discrete state of an iteration: a sum
+// (mod 2^64) of the SplitMix64 output function (Steele, Lea and Flood 2014)
+// applied to (index, state) pairs.  Equal signatures mean equal states with
+// overwhelming probability; the sum does not depend on the order of the adds.
+__host__ __device__ inline unsigned long long sig_mix(unsigned a, unsigned b) {
+  unsigned long long z = ((unsigned long long)a << 32 | b) + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+#ifdef __CUDACC__
+// Adds v (summed over the warp first) to *dst from lane 0; all lanes call it.
+__device__ inline void warp_add_u64(unsigned long long v, unsigned long long* dst) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0 && v) atomicAdd(dst, v);
+}
+#endif
 
 struct Ctrl {
   int status;            // ST_* bits
@@ -119,8 +142,10 @@ struct Dev {
   const int* halo_rows;  //   distinct rows each block's SpMV reads (sorted per block)
   const int* sl_lcol;    //   per sliced-ELL entry: the column's index in its block's halo
   int halo_max;          //   longest halo (rows)
+  const float* cg_ainv;  // dataflow PCG coarse correction: A_c^-1 (n_agg x n_agg, row-major)
+  int n_agg;             //   aggregates of 128 consecutive free rows; 0 = Jacobi only
   // collision
-  const int* q_verts;    // n_q internal vertex ids (ascending)
+  const int* q_verts;    // n_q internal vertex ids, in ascending caller id
   const int* qf_ptr;     // n_q + 1 incident boundary faces
   const int* qf;         // face ids
   const int4* faces;     // n_f (v0, v1, v2, owning tet)

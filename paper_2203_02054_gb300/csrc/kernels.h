@@ -36,7 +36,8 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st);
 template <typename T>
 int pcg_rr_max_rows();
 int pcg_df_max_rows();
-bool pcg_df_prepare(int halo_bytes);
+bool pcg_df_prepare(int smem_bytes);
+int pcg_df_agg_rows();
 template <typename T>
 int pcg_seg_max_blocks();
 template <typename T>
@@ -83,7 +84,20 @@ struct AdjDev {
   const double* sp_bary;  // 2 n_q
   const int* sp_flag;     // self spring cast in iteration i: 1 by a ray hit, 2 by the closest point
   R4<double>* xbar_tet;   // 4 n_t per-tet pullbacks
-  double* xbar_vert;      // 3 n_v spring pullbacks (FP64 atomics)
+  // Spring pullbacks, gathered deterministically: spring qi writes its
+  // contributions to the slots [4 qi + 3 qf_ptr[qi], ...) (destination vertex
+  // and value; at most 4 + 3 x its incident boundary faces), then the slots
+  // are grouped by destination (count, scan, fill) and every vertex adds its
+  // contributions in slot order.
+  int* em_vert;           // n_slots destination vertex, -1 = unused
+  R4<double>* em_val;     // n_slots contributions
+  int* em_cnt;            // n_free + 1 counts per destination
+  int* em_start;          // n_free + 1 exclusive offsets
+  int* em_cur;            // n_free fill cursors
+  int* em_list;           // n_slots slot ids grouped by destination
+  int* em_tiles;          // scan tiles
+  int* em_total;          // 1
+  int n_slots;
   double* betabar;        // 2 n_q barycentric adjoints of kept springs
   double* alpha_part;     // local blocks x n_groups
   const double* alpha;    // n_groups
@@ -104,6 +118,8 @@ void launch_adjoint_flags(const Dev<T>& d, int* flag, cudaStream_t st);
 // returns it.
 void set_handle_free_error(const char* msg);
 const char* handle_free_error();
+
+void launch_scan_exclusive(const int* in, int* out, int n, int* tile_sums, int* total, cudaStream_t st);
 
 int local_blocks(int n_t);
 int rhs_blocks(int n_free);

@@ -30,16 +30,20 @@ __device__ __forceinline__ float cbrt_t<float>(float x) { return cbrtf(x); }
 template <>
 __device__ __forceinline__ double cbrt_t<double>(double x) { return cbrt(x); }
 
-__device__ __forceinline__ double w_table(const double* knots, int n, double eps) {
-  // piecewise linear through (eps_i, w_i), clamped at both ends
+__device__ __forceinline__ double w_table(const double* knots, int n, double eps, int& seg) {
+  // piecewise linear through (eps_i, w_i), clamped at both ends; seg = the
+  // interval used (0 below the first knot, i + 1 for [eps_i, eps_i+1), n above)
+  seg = 0;
   if (eps <= knots[0]) return knots[1];
   for (int i = 0; i + 1 < n; ++i) {
     const double x0 = knots[2 * i], x1 = knots[2 * i + 2];
     if (eps < x1) {
       const double y0 = knots[2 * i + 1], y1 = knots[2 * i + 3];
+      seg = i + 1;
       return y0 + (eps - x0) * (y1 - y0) / (x1 - x0);
     }
   }
+  seg = n;
   return knots[2 * n - 1];
 }
 
@@ -48,6 +52,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local(Dev<T> d) {
   __shared__ double shd[32];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   double en = 0.0;
+  unsigned long long ksig = 0;
   if (e < d.n_t) {
     const int4 t = d.tet[e];
     const R4<T> x0 = d.X[t.x], x1 = d.X[t.y], x2 = d.X[t.z], x3 = d.X[t.w];
@@ -94,7 +99,9 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local(Dev<T> d) {
           mis += q * q;
         }
       const double strain = sqrt((double)mis / (double)tt);
-      const T w = (T)w_table(d.knots, d.n_knots, strain);
+      int seg;
+      const T w = (T)w_table(d.knots, d.n_knots, strain, seg);
+      if (d.stats) ksig = sig_mix((unsigned)e, (unsigned)seg);
       T B[3][4];
       for (int i = 0; i < 3; ++i)
         for (int k = 0; k < 4; ++k) B[i][k] = (T(1) - w) * Xc[i][k] + w * RT[i][k];
@@ -125,6 +132,7 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local(Dev<T> d) {
       out[k] = c;
     }
   }
+  if (d.stats) warp_add_u64(ksig, &(d.hist + (d.ctrl->iter % d.hist_cap))->knot_sig);
   const double s = block_sum(en, shd);
   if (threadIdx.x == 0) d.e_partials[blockIdx.x] = s;
 }
@@ -1100,12 +1108,221 @@ __device__ __forceinline__ bool df_reduce(const Dev<float>& d, unsigned e, const
   return true;
 }
 
-template <int MAXW>
+
+// ---- two-level preconditioner of the dataflow kernel ----------------------
+// M^-1 = D^-1 + Z A_c^-1 Z^T: Jacobi plus an additive coarse correction over
+// aggregates of DF_AGG_ROWS consecutive rows (compact pieces of the body: the
+// free rows are numbered by recursive coordinate bisection), Z the 0/1
+// aggregation matrix and A_c = Z^T L Z the Galerkin coarse matrix of the
+// spring-free Laplacian (both SPD, so M is SPD: A + k diag(mask) >= L only
+// makes the coarse part an approximation).  A_c^-1 is formed once at upload.
+// Per CG iteration every block needs g_i = (A_c^-1 Z^T v)_{a_i} for its own
+// aggregates a_i and v = r_{k+1}, before r_{k+1}'s SpMV.  With
+// r_{k+1} = r_k - alpha_k s_k and s_k = w_k + beta_k s_{k-1} (w = A u),
+// g(r_{k+1}) = g(r_k) - alpha_k g(s_k) and g(s_k) = g(w_k) + beta_k g(s_{k-1}):
+// every block adds its aggregates' sums of w_k and r_k to the slot it
+// publishes in the reduction it already makes, so g(r_k) and g(w_k) are
+// formed fresh from that round's sums (only g(s) is carried, like s itself),
+// and the coarse correction costs no extra grid-wide wait.
+static constexpr int DF_AGG_ROWS = 128;
+static constexpr int DF_AGG = PCG_DF_THREADS / DF_AGG_ROWS;  // aggregates per block
+static constexpr int DF_SLOT_C = 4 + 4 * DF_AGG;             // slot words with the aggregate sums
+
+// All threads: per-warp sums of w and r over the warp's rows (fixed shuffle
+// trees), stored by lane 0 in sz[warp]; call before block_sums*, whose
+// __syncthreads publishes them.
+__device__ __forceinline__ void agg_warp_sums(const float (&w)[3], const float (&r)[3], float (*sz)[6]) {
+  float a[6] = {w[0], w[1], w[2], r[0], r[1], r[2]};
+#pragma unroll
+  for (int c = 0; c < 6; ++c)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[c] = __fadd_rn(a[c], __shfl_down_sync(0xffffffffu, a[c], o));
+  if ((threadIdx.x & 31) == 0)
+#pragma unroll
+    for (int c = 0; c < 6; ++c) sz[threadIdx.x >> 5][c] = a[c];
+}
+
+// Warp 0: lane 0 stores the block's sums bs and its aggregates' sums (warps
+// 4k..4k+3 of aggregate k, added in order) as one slot of epoch e, arrives on
+// the grid counter and waits for the round to complete.  Returns false
+// (warp-uniform) when the wait gave up or another block aborted.
+template <typename S>
+__device__ __forceinline__ bool df_publish_c(const Dev<float>& d, unsigned e, const S (&bs)[3],
+                                             const float (*sz)[6]) {
+  const int lane = threadIdx.x & 31;
+  const int nb = gridDim.x;
+  unsigned long long* buf = d.df_p + (size_t)(e & 1u) * DF_SLOT_C * (size_t)nb;
+  const unsigned long long tag = df_tag(e);
+  int arrived = 1;
+  if (lane == 0) {
+    unsigned long long w[4];
+    df_pack(tag, bs, w);
+    unsigned long long* slot = buf + DF_SLOT_C * (size_t)blockIdx.x;
+    st_v2_relaxed(slot, w[0], w[1]);
+    st_v2_relaxed(slot + 2, w[2], w[3]);
+    constexpr int WPA = DF_AGG_ROWS / 32;
+#pragma unroll
+    for (int k = 0; k < DF_AGG; ++k) {
+      float z[6];
+#pragma unroll
+      for (int c = 0; c < 6; ++c) {
+        float t = sz[WPA * k][c];
+#pragma unroll
+        for (int q = 1; q < WPA; ++q) t = __fadd_rn(t, sz[WPA * k + q][c]);
+        z[c] = t;
+      }
+      unsigned long long a, b;
+      df_pack_u(tag, z[0], z[1], z[2], a, b);
+      st_v2_relaxed(slot + 4 + 4 * k, a, b);
+      df_pack_u(tag, z[3], z[4], z[5], a, b);
+      st_v2_relaxed(slot + 6 + 4 * k, a, b);
+    }
+    const unsigned add = blockIdx.x == 0 ? (0x80000000u - ((unsigned)nb - 1u + d.bar_extra)) : 1u;
+    atomicAdd(&d.ctrl->bar_count, add);
+    const unsigned want = (e & 1u) << 31;
+    volatile unsigned* vc = &d.ctrl->bar_count;
+    DfWait wt;
+    while ((*vc & 0x80000000u) != want)
+      if (!wt.again(d.ctrl, d.wait_budget)) {
+        arrived = 0;
+        break;
+      }
+  }
+  return __shfl_sync(0xffffffffu, arrived, 0) != 0;
+}
+
+// Warp 0 after the round: the dot sums of all slots of epoch e, each lane its
+// slots (lane, lane + 32, ...) in block order, then a fixed shuffle tree;
+// tot is valid in lane 0.  Re-reads slots whose words are not yet current.
+template <typename S>
+__device__ __forceinline__ bool df_gather_dots_c(const Dev<float>& d, unsigned e, S (&tot)[3]) {
+  const int lane = threadIdx.x & 31;
+  const int nb = gridDim.x;
+  const unsigned long long* buf = d.df_p + (size_t)(e & 1u) * DF_SLOT_C * (size_t)nb;
+  const unsigned long long tag = df_tag(e);
+  unsigned long long w[DF_MAXQ][4];
+#pragma unroll
+  for (int q = 0; q < DF_MAXQ; ++q) {
+    const int b = lane + 32 * q;
+    if (b < nb) {
+      ld_v2_relaxed(buf + DF_SLOT_C * (size_t)b, w[q][0], w[q][1]);
+      ld_v2_relaxed(buf + DF_SLOT_C * (size_t)b + 2, w[q][2], w[q][3]);
+    }
+  }
+  auto fresh = [&](int q) {
+    return df_has(w[q][0], tag) && df_has(w[q][1], tag) && df_has(w[q][2], tag) && df_has(w[q][3], tag);
+  };
+  unsigned stale = 0;
+#pragma unroll
+  for (int q = 0; q < DF_MAXQ; ++q)
+    if (lane + 32 * q < nb && !fresh(q)) stale |= 1u << q;
+  DfWait wt;
+  while (stale != 0 && wt.again(d.ctrl, d.wait_budget)) {
+#pragma unroll
+    for (int q = 0; q < DF_MAXQ; ++q)
+      if (stale & (1u << q)) {
+        const int b = lane + 32 * q;
+        ld_v2_relaxed(buf + DF_SLOT_C * (size_t)b, w[q][0], w[q][1]);
+        ld_v2_relaxed(buf + DF_SLOT_C * (size_t)b + 2, w[q][2], w[q][3]);
+      }
+#pragma unroll
+    for (int q = 0; q < DF_MAXQ; ++q)
+      if ((stale & (1u << q)) && fresh(q)) stale &= ~(1u << q);
+  }
+  if (!__all_sync(0xffffffffu, stale == 0)) return false;
+  S a[3] = {acc_zero<S>(), acc_zero<S>(), acc_zero<S>()};
+#pragma unroll
+  for (int q = 0; q < DF_MAXQ; ++q) {
+    if (lane + 32 * q < nb) {
+      S v[3];
+      df_unpack(w[q], v);
+      a[0] = df_add(a[0], v[0]);
+      a[1] = df_add(a[1], v[1]);
+      a[2] = df_add(a[2], v[2]);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[k] = df_add(a[k], shfl_down(a[k], o));
+    tot[k] = a[k];
+  }
+  return true;
+}
+
+// Warps 1..5 after the round (threads 32..191, one slot each): thread t reads
+// slot t's aggregate sums of w and r and forms its part of
+// g_i = sum_j Ainv[i][j] z_j for the block's aggregates i (ainv: DF_AGG rows
+// of A_c^-1 in shared memory); the parts are added by fixed trees (warp
+// shuffles, then the five warp totals in order) into g[0] (from w) and g[1]
+// (from r).  Uses named barrier 1 (160 threads).
+__device__ __forceinline__ void df_gather_coarse(const Dev<float>& d, unsigned e, const float* ainv,
+                                                 float (*part)[6 * DF_AGG], float (*g)[DF_AGG][3]) {
+  const int t = (int)threadIdx.x - 32;
+  const int nb = gridDim.x;
+  float c[DF_AGG][6];
+#pragma unroll
+  for (int i = 0; i < DF_AGG; ++i)
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc) c[i][cc] = 0.0f;
+  if (t < nb) {
+    const unsigned long long* slot = d.df_p + (size_t)(e & 1u) * DF_SLOT_C * (size_t)nb + DF_SLOT_C * (size_t)t + 4;
+    const unsigned long long tag = df_tag(e);
+    unsigned long long w[4 * DF_AGG];
+#pragma unroll
+    for (int k = 0; k < 2 * DF_AGG; ++k) ld_v2_relaxed(slot + 2 * k, w[2 * k], w[2 * k + 1]);
+    DfWait wt;
+    for (;;) {
+      bool ok = true;
+#pragma unroll
+      for (int k = 0; k < 4 * DF_AGG; ++k) ok = ok && df_has(w[k], tag);
+      if (ok || !wt.again(d.ctrl, d.wait_budget)) break;
+#pragma unroll
+      for (int k = 0; k < 2 * DF_AGG; ++k) ld_v2_relaxed(slot + 2 * k, w[2 * k], w[2 * k + 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < DF_AGG; ++k) {
+      const int j = DF_AGG * t + k;
+      if (j >= d.n_agg) break;
+      float z[6];
+      df_unpack_u(w[4 * k], w[4 * k + 1], z[0], z[1], z[2]);
+      df_unpack_u(w[4 * k + 2], w[4 * k + 3], z[3], z[4], z[5]);
+#pragma unroll
+      for (int i = 0; i < DF_AGG; ++i) {
+        const float a = ainv[i * d.n_agg + j];
+#pragma unroll
+        for (int cc = 0; cc < 6; ++cc) c[i][cc] = __fmaf_rn(a, z[cc], c[i][cc]);
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < DF_AGG; ++i)
+#pragma unroll
+    for (int cc = 0; cc < 6; ++cc)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c[i][cc] = __fadd_rn(c[i][cc], __shfl_down_sync(0xffffffffu, c[i][cc], o));
+  const int wq = t >> 5;
+  if ((t & 31) == 0)
+#pragma unroll
+    for (int i = 0; i < DF_AGG; ++i)
+#pragma unroll
+      for (int cc = 0; cc < 6; ++cc) part[wq][6 * i + cc] = c[i][cc];
+  asm volatile("bar.sync 1, 160;" ::: "memory");
+  if (t < 6 * DF_AGG) {
+    float s = part[0][t];
+#pragma unroll
+    for (int q = 1; q < 5; ++q) s = __fadd_rn(s, part[q][t]);
+    const int i = t / 6, cc = t % 6;
+    g[cc / 3][i][cc % 3] = s;
+  }
+}
+
+template <int MAXW, bool COARSE>
 __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   constexpr int NW = PCG_DF_THREADS / 32;
   __shared__ CgShared<float> cs;
   __shared__ double sc[5];  // bb, rr, gamma, alpha, beta: used by lane 0 of warp 0 only
-  extern __shared__ unsigned long long halo[];  // 2 tagged words per halo row
+  extern __shared__ unsigned long long halo[];  // 2 tagged words per halo row (+ coarse rows)
   const int lane = threadIdx.x & 31;
   const bool w0 = threadIdx.x < 32;
   const int n = d.n_free;
@@ -1126,6 +1343,21 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       val[j] = j < width ? d.sl_val[base + j * 32 + ln] : 0.0f;
     }
     dg = d.diag[i];
+  }
+  // coarse correction state (COARSE only): per-warp aggregate sums, the
+  // parts of warps 1..5, the block's g values, this block's rows of A_c^-1
+  __shared__ float s_zw[COARSE ? NW : 1][6];
+  __shared__ float s_part[COARSE ? 5 : 1][6 * DF_AGG];
+  __shared__ float s_g[2][DF_AGG][3];  // g(w), g(r) of the block's aggregates
+  __shared__ int s_ok;
+  float* ainv = reinterpret_cast<float*>(halo + 2 * (size_t)d.halo_max);
+  const int ia = (int)threadIdx.x / DF_AGG_ROWS;  // this row's aggregate within the block
+  if constexpr (COARSE) {
+    for (int k = threadIdx.x; k < DF_AGG * d.n_agg; k += PCG_DF_THREADS) {
+      const int r = k / d.n_agg, j = k - r * d.n_agg;
+      const int a = DF_AGG * (int)blockIdx.x + r;
+      ainv[k] = a < d.n_agg ? d.cg_ainv[(size_t)a * d.n_agg + j] : 0.0f;
+    }
   }
   auto store_u = [&](unsigned e, const float (&uu)[3]) {
     unsigned long long a, b;
@@ -1152,7 +1384,9 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
     if (stale) {
       DfWait wt;
       for (int k = threadIdx.x; k < nh; k += PCG_DF_THREADS) {
-        unsigned long long w0 = halo[2 * k], w1 = halo[2 * k + 1];
+        unsigned long long w0, w1;
+        w0 = halo[2 * k];
+        w1 = halo[2 * k + 1];
         while (!(df_has(w0, tag) && df_has(w1, tag))) {
           if (!wt.again(d.ctrl, d.wait_budget)) break;
           ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
@@ -1181,8 +1415,29 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
     }
     __syncthreads();  // the halo is rewritten by the next call
   };
+  // COARSE: the reduction of epoch e with the aggregate sums of zv.  Warp 0
+  // publishes the slot and waits for the round; after a block-wide barrier
+  // warp 0 sums the dot words (dots(), which also sets cs.flag) while warps
+  // 1..5 form the block's coarse values g (into s_g); a second barrier
+  // publishes both.  Returns false (block-uniform) when the round was not
+  // completed.
+  auto reduce_c = [&](unsigned e, const auto (&bs)[3], auto dots) -> bool {
+    if (w0) {
+      const bool ok = df_publish_c(d, e, bs, s_zw);
+      if (lane == 0) s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) return false;
+    if (w0)
+      dots();
+    else if (threadIdx.x < 32 * 6)
+      df_gather_coarse(d, e, ainv, s_part, s_g);
+    __syncthreads();
+    return true;
+  };
   unsigned ue = 0, re = 0;  // epochs of u and of the reductions (the same in every thread)
-  float r[3], u[3], w[3], p[3], s[3], dd[3] = {0.0f, 0.0f, 0.0f};
+  float r[3] = {0.0f, 0.0f, 0.0f}, u[3], w[3] = {0.0f, 0.0f, 0.0f}, p[3], s[3], dd[3] = {0.0f, 0.0f, 0.0f};
+  float gr[3] = {0.0f, 0.0f, 0.0f}, gs[3] = {0.0f, 0.0f, 0.0f};  // g(r), g(s) of this row's aggregate
   double a0[2] = {0.0, 0.0};
   ++ue;
   if (act) {
@@ -1192,27 +1447,48 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       r[c] = (float)rv[c];
       u[c] = r[c] / dg;
     }
-    store_u(ue, u);
+    if constexpr (!COARSE) store_u(ue, u);
   }
   {
     double bs2[2], t[3];
+    if constexpr (COARSE) agg_warp_sums(w, r, s_zw);  // w is zero here
     block_sums<2, NW>(a0, cs.sh, bs2);
     ++re;
-    if (w0) {
-      const double bs[3] = {bs2[0], bs2[1], 0.0};
-      const bool ok = df_reduce(d, re, bs, t);
-      if (lane == 0) {
-        sc[0] = t[0];
-        sc[1] = t[1];
-        cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
+    if constexpr (!COARSE) {
+      if (w0) {
+        const double bs[3] = {bs2[0], bs2[1], 0.0};
+        const bool ok = df_reduce(d, re, bs, t);
+        if (lane == 0) {
+          sc[0] = t[0];
+          sc[1] = t[1];
+          cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
+        }
       }
+      __syncthreads();
+    } else {
+      const double bs[3] = {bs2[0], bs2[1], 0.0};
+      if (!reduce_c(re, bs, [&] {
+            const bool ok = df_gather_dots_c(d, re, t);
+            if (lane == 0) {
+              sc[0] = t[0];
+              sc[1] = t[1];
+              cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
+            }
+          }))
+        return;
+      for (int c = 0; c < 3; ++c) gr[c] = s_g[1][ia][c];
     }
-    __syncthreads();
   }
   if (cs.flag == CG_ABORT) return;
   int it = 0;
   if (cs.flag == CG_CONTINUE) {
     DW a1[2] = {acc_zero<DW>(), acc_zero<DW>()};
+    if constexpr (COARSE) {
+      if (act) {
+        for (int c = 0; c < 3; ++c) u[c] = r[c] / dg + gr[c];
+        store_u(ue, u);
+      }
+    }
     spmv(ue, u, w);
     if (act) {
       a1[0] = dot3(r[0], r[1], r[2], u[0], u[1], u[2]);
@@ -1223,12 +1499,12 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       }
     }
     {
-      DW bs2[2], t[3];
+      DW bs2[2], t[3] = {};
+      if constexpr (COARSE) agg_warp_sums(w, r, s_zw);
       block_sums_dw<2, NW>(a1, cs.sh, bs2);
       ++re;
-      if (w0) {
-        const DW bs[3] = {bs2[0], bs2[1], DW{0.0f, 0.0f}};
-        const bool ok = df_reduce(d, re, bs, t);
+      const DW bs[3] = {bs2[0], bs2[1], DW{0.0f, 0.0f}};
+      auto first_scalars = [&](bool ok) {
         if (lane == 0) {
           if (ok) {
             const double g = acc_to_f64(t[0]);
@@ -1238,18 +1514,30 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
           }
           cs.flag = ok ? CG_CONTINUE : CG_ABORT;
         }
+      };
+      if constexpr (!COARSE) {
+        if (w0) first_scalars(df_reduce(d, re, bs, t));
+        __syncthreads();
+      } else {
+        if (!reduce_c(re, bs, [&] { first_scalars(df_gather_dots_c(d, re, t)); })) return;
+        for (int c = 0; c < 3; ++c) {
+          gs[c] = s_g[0][ia][c];  // s_0 = w_0
+          gr[c] = s_g[1][ia][c];
+        }
       }
-      __syncthreads();
     }
     if (cs.flag == CG_ABORT) return;
     float ta = cs.ta;
     for (it = 1; it <= d.max_iter; ++it) {
       ++ue;
+      if constexpr (COARSE)
+        for (int c = 0; c < 3; ++c) gr[c] -= ta * gs[c];
       if (act) {
         for (int c = 0; c < 3; ++c) {
           dd[c] += ta * p[c];
           r[c] -= ta * s[c];
           u[c] = r[c] / dg;
+          if constexpr (COARSE) u[c] += gr[c];
         }
         store_u(ue, u);
       }
@@ -1261,11 +1549,11 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
         a2[2] = dot3(r[0], r[1], r[2], r[0], r[1], r[2]);
       }
       {
-        DW bs[3], tw[3];
+        DW bs[3], tw[3] = {};
+        if constexpr (COARSE) agg_warp_sums(w, r, s_zw);
         block_sums_dw<3, NW>(a2, cs.sh, bs);
         ++re;
-        if (w0) {
-          const bool ok = df_reduce(d, re, bs, tw);
+        auto scalars = [&](bool ok) {
           int f = CG_ABORT;
           double gamma = sc[2], alpha = sc[3], beta = sc[4], rr = sc[1];
           if (ok) {
@@ -1284,14 +1572,24 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
             }
             cs.flag = f;
           }
+        };
+        if constexpr (!COARSE) {
+          if (w0) scalars(df_reduce(d, re, bs, tw));
+          __syncthreads();
+        } else {
+          if (!reduce_c(re, bs, [&] { scalars(df_gather_dots_c(d, re, tw)); })) return;
         }
-        __syncthreads();
       }
       const int f = cs.flag;
       if (f == CG_ABORT) return;
       if (f != CG_CONTINUE) break;
       ta = cs.ta;
       const float tb = cs.tb;
+      if constexpr (COARSE)
+        for (int c = 0; c < 3; ++c) {
+          gs[c] = s_g[0][ia][c] + tb * gs[c];  // g(s_k) = g(w_k) + beta_k g(s_k-1)
+          gr[c] = s_g[1][ia][c];               // g(r_k), fresh from this round's sums
+        }
       if (act)
         for (int c = 0; c < 3; ++c) {
           p[c] = u[c] + tb * p[c];
@@ -1766,6 +2064,8 @@ __global__ void k_finalize(Dev<T> d) {
     nx->n_obstacle_pairs = 0;
     nx->n_springs = 0;
     nx->pcg_iters = 0;
+    nx->knot_sig = 0;
+    nx->spring_sig = 0;
   }
 }
 
@@ -1816,16 +2116,20 @@ int pcg_rr_max_rows() {
   return sms * per * PCG_RR_THREADS;
 }
 
-bool pcg_df_prepare(int halo_bytes) {
-  return cudaFuncSetAttribute(k_pcg_df<PCG_RR_MAXW>, cudaFuncAttributeMaxDynamicSharedMemorySize, halo_bytes) ==
-         cudaSuccess;
+bool pcg_df_prepare(int smem_bytes) {
+  return cudaFuncSetAttribute(k_pcg_df<PCG_RR_MAXW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_bytes) == cudaSuccess &&
+         cudaFuncSetAttribute(k_pcg_df<PCG_RR_MAXW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              smem_bytes) == cudaSuccess;
 }
+
+int pcg_df_agg_rows() { return DF_AGG_ROWS; }
 
 int pcg_df_max_rows() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_df<PCG_RR_MAXW>, PCG_DF_THREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_df<PCG_RR_MAXW, true>, PCG_DF_THREADS, 0);
   const int blocks = std::min(sms * per, 32 * DF_MAXQ);
   return blocks * PCG_DF_THREADS;
 }
@@ -1848,10 +2152,14 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st) 
       // epoch-tagged words start from zero in every launch
       cudaError_t e = cudaMemsetAsync(d.df_u, 0, sizeof(unsigned long long) * 4 * (size_t)d.n_free, st);
       if (e == cudaSuccess)
-        e = cudaMemsetAsync(d.df_p, 0, sizeof(unsigned long long) * 8 * (size_t)(grid + 1), st);
+        e = cudaMemsetAsync(d.df_p, 0, sizeof(unsigned long long) * 2 * DF_SLOT_C * (size_t)(grid + 1), st);
       if (e != cudaSuccess) return e;
       cfg.dynamicSmemBytes = 16 * (size_t)d.halo_max;
-      return cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW>, d);
+      if (d.n_agg > 0) {
+        cfg.dynamicSmemBytes += sizeof(float) * DF_AGG * (size_t)d.n_agg;
+        return cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW, true>, d);
+      }
+      return cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW, false>, d);
     } else {
       return cudaErrorInvalidValue;
     }

@@ -1,7 +1,8 @@
 """Adjoint (reverse pass of the unrolled loop) on the GPU: dL/dalpha for a
 loss on tip-vertex positions, against the oracle's FP64 adjoint and against
-central finite differences of the GPU's own FP64 forward pass (h = 1e-4,
-only where the spring decisions at alpha +- h are identical)."""
+central finite differences of the GPU's own FP64 forward pass, with every
+group classified by whether a spring decision or a w(eps) interval changes
+within +-h."""
 import numpy as np
 import pytest
 
@@ -68,18 +69,16 @@ def test_gpu_adjoint_mixed_close_to_fp64():
     assert np.allclose(g32, g64, rtol=2e-3, atol=2e-3 * np.abs(g64).max())
 
 
-def _decisions(sim, n_iters):
-    """Spring decisions of the last run: springs per iteration and the final
-    records (pair counts are left out: a vertex already in contact may gain or
-    lose a second pair without changing any spring)."""
-    sp = sim.springs()
-    hist = sim.history()
-    return ([h["n_springs"] for h in hist][-n_iters:], sp["active"].tolist(), sp["kind"].tolist(),
-            sp["face"].tolist())
+def _signatures(sim, n_iters):
+    """Per-iteration signatures of the discrete state of the last run: the
+    spring records after each update and the w(eps) interval of every body
+    tet (casim_iter_record.spring_signature / knot_signature)."""
+    hist = sim.history()[-n_iters:]
+    return [h["spring_signature"] for h in hist], [h["knot_signature"] for h in hist]
 
 
 def _fd(sim, m, tips, targets, gi, h, n_iters):
-    vals, decs = [], []
+    vals, sigs = [], []
     for sgn in (1.0, -1.0):
         a = m.alpha.copy()
         a[gi] += sgn * h
@@ -89,52 +88,111 @@ def _fd(sim, m, tips, targets, gi, h, n_iters):
         assert sim.sync() == 0
         X = sim.positions()
         vals.append(float(np.sum((X[tips] - targets) ** 2)))
-        decs.append(_decisions(sim, n_iters))
-    return (vals[0] - vals[1]) / (2 * h), decs
+        sigs.append(_signatures(sim, n_iters))
+    return (vals[0] - vals[1]) / (2 * h), sigs
 
 
-@pytest.mark.parametrize("n_iters,h,need", [(8, 1e-4, 3), (20, 1e-6, 8)])
-def test_gpu_adjoint_central_differences_on_20k_copy(n_iters, h, need):
+@pytest.mark.parametrize("n_iters,h", [(100, 1e-4), (100, 1e-6), (8, 1e-4)])
+def test_gpu_adjoint_central_differences_on_20k_copy(n_iters, h):
     """The 20,736-tet copy of the adjoint workload (96x6x6 voxels, 16
-    chambers), FP64 forward, checkpoints every 5.  A group is compared only
-    where the spring decisions at alpha +- h equal those at alpha (over 20
-    iterations some release test lies within h's reach for most groups, so the
-    h = 1e-4 check runs 8 iterations).  The strain table w(eps) is piecewise
-    linear, so a difference with h = 1e-4 may also straddle a knot crossing of
-    some body tet: most eligible groups must agree within 1e-4, all within
-    1e-3; with h = 1e-6 every eligible group must agree within 1e-4."""
+    chambers), FP64 forward with checkpoints every 10, against central
+    differences of the same forward at alpha_g +- h.
+
+    Each group is classified by the discrete state of the two perturbed runs
+    against the unperturbed one, iteration by iteration: a spring decision
+    differs (a spring created, released or re-targeted to another face: the
+    loss jumps, so the difference quotient measures the jump, not the
+    derivative), or only the w(eps) interval of some body tet differs (a knot
+    of the piecewise-linear table lies within +-h: the loss has a kink there),
+    or neither.  Groups with neither must agree within 1e-4 relative; groups
+    with only knot crossings are reported and held to 1e-3; groups with a
+    spring decision change are reported only."""
     m = synth.config5_adjoint(nx=96, ny=6, nz=6, n_ch=16, n_iters=n_iters)
     m.precision = synth.PRECISION_FP64
     tips, targets = m.tip_verts, m.tip_targets
     sim = casim.Sim(m)
-    L, g, _ = _gpu_grad(sim, m, tips, targets, n_iters, 5)
+    L, g, _ = _gpu_grad(sim, m, tips, targets, n_iters, 10)
     casim.casim_set_actuation(sim.h, m.alpha)
     sim.reset()
     sim.step(n_iters)
-    sim.sync()
-    base = _decisions(sim, n_iters)
-    checked = 0
-    close = 0
+    assert sim.sync() == 0
+    base_s, base_k = _signatures(sim, n_iters)
+    report = []
     for gi in range(m.n_groups):
-        fd, decs = _fd(sim, m, tips, targets, gi, h, n_iters)
-        if decs[0] == base and decs[1] == base:
-            rel = abs(g[gi] - fd) / abs(fd)
-            assert rel <= (1e-4 if h < 1e-5 else 1e-3), (gi, g[gi], fd)
-            close += rel <= 1e-4
-            checked += 1
-    assert checked >= need, checked
-    assert close >= max(need, (3 * checked) // 4), (close, checked)
+        fd, sigs = _fd(sim, m, tips, targets, gi, h, n_iters)
+        spring_change = any(s != base_s for s, _k in sigs)
+        knot_change = any(k != base_k for _s, k in sigs)
+        rel = abs(g[gi] - fd) / abs(fd)
+        kind = "spring" if spring_change else ("knot" if knot_change else "clean")
+        report.append((gi, kind, rel))
+    sim.close()
+    print("h=%g n=%d: %s" % (h, n_iters, ", ".join("%d:%s:%.1e" % r for r in report)))
+    clean = [r for r in report if r[1] == "clean"]
+    knot = [r for r in report if r[1] == "knot"]
+    for gi, kind, rel in clean:
+        assert rel <= 1e-4, (gi, kind, rel)
+    for gi, kind, rel in knot:
+        assert rel <= 1e-3, (gi, kind, rel)
+    # with h = 1e-6 every group keeps its decisions; with h = 1e-4 over 100
+    # iterations most groups see a spring decision change within +-h
+    assert len(clean) + len(knot) >= (8 if h < 1e-5 else (1 if n_iters > 20 else 3)), report
+
+
+def _sig_mix(a, b):
+    """SplitMix64's output function on the 64-bit word (a << 32 | b) plus the
+    golden-ratio increment (Steele, Lea and Flood 2014)."""
+    M = (1 << 64) - 1
+    z = (((a << 32) | b) + 0x9E3779B97F4A7C15) & M
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M
+    return z ^ (z >> 31)
+
+
+def test_signatures_deterministic_and_equal_to_their_definition():
+    """Two identical runs give equal signatures at every iteration, and the
+    spring signature of the last iteration equals its definition evaluated on
+    the host from the spring records and the contacts of the last check (sum
+    mod 2^64 over active springs of the mix of (index, code << 30 xor
+    (face + 1)), code 1 for an obstacle spring, 2 for a self spring whose
+    vertex was in a pair (cast in that iteration), 0 for a kept one))."""
+    m = synth.small_finger(nx=20, ny=4, nz=4, n_ch=4, n_iters=6)
+    X0 = synth.perturbed_positions(m, 0.3, seed=3, dtype=np.float32)
+    sim = casim.Sim(m)
+    runs = []
+    for _ in range(2):
+        sim.set_positions(X0)
+        sim.reset()
+        sim.step(6)
+        assert sim.sync() == 0
+        runs.append(_signatures(sim, 6))
+    assert runs[0] == runs[1]
+    assert all(k != 0 for k in runs[0][1])
+    sp = sim.springs()
+    in_pair = set(sim.contacts()[0][:, 0].tolist())
+    expect = 0
+    for qi in np.nonzero(sp["active"])[0]:
+        code = 1 if sp["kind"][qi] == 1 else (2 if int(sp["verts"][qi]) in in_pair else 0)
+        expect = (expect + _sig_mix(int(qi), ((code << 30) ^ (int(sp["face"][qi]) + 1)) & 0xFFFFFFFF)) \
+            & ((1 << 64) - 1)
+    assert sp["active"].sum() > 0
+    assert runs[1][0][-1] == expect
     sim.close()
 
 
-def test_gpu_adjoint_matches_oracle_adjoint_on_20k_copy():
-    m = synth.config5_adjoint(nx=96, ny=6, nz=6, n_ch=16, n_iters=6)
+@pytest.mark.parametrize("n_iters,every", [(6, 3), (100, 10)])
+def test_gpu_adjoint_matches_oracle_adjoint_on_20k_copy(n_iters, every):
+    """The 20,736-tet copy at the adjoint workload's horizon (100 unrolled
+    iterations, checkpoints every 10) and at a short one: FP64 GPU forward and
+    reverse pass against the oracle's FP64 autograd adjoint."""
+    m = synth.config5_adjoint(nx=96, ny=6, nz=6, n_ch=16, n_iters=n_iters)
     m.precision = synth.PRECISION_FP64
     tips, targets = m.tip_verts, m.tip_targets
     sim = casim.Sim(m)
-    L, g, X = _gpu_grad(sim, m, tips, targets, 6, 3)
+    L, g, X = _gpu_grad(sim, m, tips, targets, n_iters, every)
     sim.close()
-    Lo, go, Xo, _ = oadj.loss_and_grad(m, 6, tips, targets)
+    Lo, go, Xo, _ = oadj.loss_and_grad(m, n_iters, tips, targets)
+    print("n=%d: |X - Xo| %.2e, |g - go| / |go| %.2e, |g| %.3e" % (
+        n_iters, np.abs(X - Xo).max(), np.abs(g - go).max() / np.abs(go).max(), np.abs(go).max()))
     assert np.abs(X - Xo).max() < 1e-8
     assert np.allclose(g, go, rtol=1e-6, atol=1e-8 * np.abs(go).max()), np.abs(g - go).max()
 
