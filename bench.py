@@ -564,7 +564,8 @@ def main():
             "gpu_launches": gpu_launches,
             "roofline": {"bound": "hbm", "kernel": {1: "k_pcg (streaming)", 2: "k_pcg_rr (register-resident)",
                                                     3: "k_pcg_cluster", 4: "k_pcg_seg (segmented)",
-                                                    5: "k_pcg_df (dataflow, register-resident)"}
+                                                    5: "k_pcg_df (dataflow, register-resident, two-level "
+                                                       "preconditioner)"}
                          .get(stats.pcg_kernel, "k_pcg"),
                          "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                          "peak_kind": peak_kind, "traffic": recorded_traffic("k_pcg"),
