@@ -423,6 +423,35 @@ def bench_anderson(stream, n_iters=200, mem=5):
     return res
 
 
+def bench_broad_phase(stream):
+    """The two broad phases on the finger (51,840 tets, 100 iterations) and
+    the gripper (193,920 tets, 200 iterations): CUDA-event phase split of the
+    collision check and spring update per outer iteration, and the whole
+    loop's time per outer iteration (graph replay), for the per-iteration
+    spatial hash (0) and the AABB trees refitted every iteration (1)."""
+    from paper_2203_02054_gb300 import casim, synth
+
+    out = {}
+    for name, m in (("finger_51840", synth.config2_finger()), ("gripper_193920", synth.config3_gripper())):
+        rec = {}
+        for broad in (0, 1):
+            sim = casim.Sim(m, stream=stream.cuda_stream, stats=0, broad_phase=broad)
+            casim.casim_step(sim.h, 3)
+            casim.casim_sync(sim.h)
+            ms = _event_ms(stream, lambda: (casim.casim_reset(sim.h), casim.casim_step(sim.h, m.n_iters)))
+            sim.close()
+            prof = casim.Sim(m, stream=stream.cuda_stream, stats=2, broad_phase=broad)
+            prof.step(m.n_iters)
+            prof.sync()
+            ph = casim.casim_get_phase_times(prof.h) / m.n_iters
+            prof.close()
+            rec["hash" if broad == 0 else "aabb_tree"] = {
+                "ms_per_iter": ms / m.n_iters, "collision_ms_per_iter": float(ph[0]),
+                "springs_ms_per_iter": float(ph[1])}
+        out[name] = rec
+    return out
+
+
 # -------------------------------------------------------------------- GPU arm
 def run_only_batched(n_iters: int) -> int:
     import torch
@@ -589,6 +618,10 @@ def main():
             return 0
         line["batched"] = bench_batched(stream, value)
         line["adjoint"] = bench_adjoint(stream)
+        try:
+            line["broad_phase"] = bench_broad_phase(stream)
+        except Exception as e:  # a failure here must not cost the main line
+            line["broad_phase"] = {"error": "%s: %s" % (type(e).__name__, e)}
         try:
             line["anderson"] = bench_anderson(stream)
         except Exception as e:  # a failure here must not cost the main line

@@ -115,7 +115,12 @@ typedef struct {
                                coarse matrix of the Laplacian, its inverse formed
                                at upload); 1 Jacobi only.  Other kernels use
                                Jacobi                                            */
-  int32_t pad_;
+  int32_t broad_phase;      /* collision broad phase: 0 spatial hash rebuilt every
+                               iteration; 1 AABB trees (Sec. II-B) over the tets
+                               and the boundary faces, built once at upload (median
+                               split of the rest centroids) and refitted every
+                               iteration.  Both give the same contact pairs and
+                               spring targets (exact leaf tests, same tie rules) */
 } casim_params;
 
 #define CASIM_DEBUG_BARRIER_NEVER_COMPLETES 1
@@ -131,8 +136,9 @@ typedef struct {
   /* Signatures of the iteration's discrete state (0 unless params.stats): the
      sum mod 2^64 of a 64-bit mix of (tet id, interval of the w(eps) table its
      strain fell in) over body tets, and of (boundary-vertex index, decision:
-     self spring kept from its record / obstacle spring / self spring cast in
-     this iteration, face or sphere id) over the springs after the update.  Two runs with
+     0 self spring kept from its record / 1 sphere spring / 2 tetrahedral-
+     obstacle spring / 3 self spring cast in this iteration, face, sphere or
+     obstacle face id) over the springs after the update.  Two runs with
      equal signatures at every iteration took the same discrete decisions
      (with overwhelming probability), e.g. the two sides of a finite
      difference. */
@@ -206,6 +212,27 @@ int casim_set_actuation(casim_sim* sim, int32_t n_groups, const double* alpha);
 
 /* Rigid obstacle spheres O_obs (Eq. 4): host, n*4 doubles (cx, cy, cz, r). */
 int casim_set_spheres(casim_sim* sim, int32_t n, const double* cxyzr);
+
+/* Rigid tetrahedral obstacle O_obs (Sec. II-B, Eq. 4): the paper builds AABB
+   trees over the robot and over the obstacle, with one tetrahedron per leaf.
+   A non-fixed robot boundary vertex strictly inside an obstacle tetrahedron
+   (exact signs) is in contact with the obstacle; its spring (kind 2 in the
+   spring records) targets the closest point of the obstacle's boundary,
+   offset by eps along that face's outward normal (Sec. II-C), and is released
+   like a self spring once the vertex is more than eps outside the stored face
+   point.  When a vertex is also inside a sphere, the obstacle whose signed
+   surface distance is smallest wins (spheres on ties).  Requires collision
+   mode CASIM_COLLISION_SELF_OBSTACLE to take effect.
+     n_verts, xyz   host, n_verts*3 doubles (rounded to the working precision)
+     n_tets, tets   host, n_tets*4 int32, positively oriented; 0 removes the
+                    obstacle
+   The obstacle's AABB trees (tets and boundary faces) are built and fitted
+   here; it never moves.  Copies its inputs; replaces any previous obstacle;
+   must follow casim_upload_mesh (an upload removes the obstacle).
+   Errors: CASIM_E_STATE before an upload, CASIM_E_INVALID for ids out of
+   range, non-positive volumes or non-finite positions, CASIM_E_CUDA. */
+int casim_set_obstacle_mesh(casim_sim* sim, int32_t n_verts, const double* xyz, int32_t n_tets,
+                            const int32_t* tets);
 
 /* Overwrites all vertex positions (host, n_verts*3 doubles, caller order).
    In MIXED mode the values are rounded to FP32. */

@@ -46,11 +46,20 @@ class IterDecisions:
     """Discrete state of one iteration, recorded by the numpy forward pass."""
 
     active: np.ndarray      # (n_q,) bool, springs after the update
-    kind: np.ndarray        # (n_q,) 0 self, 1 obstacle
+    kind: np.ndarray        # (n_q,) 0 self, 1 sphere obstacle, 2 tetrahedral obstacle
     face: np.ndarray        # (n_q,) face id or sphere id
     bary: np.ndarray        # (n_q, 2)
     recast: np.ndarray      # (n_q,) bool: self spring cast this iteration (vertex in a pair) by a ray hit
     cast: np.ndarray = None  # (n_q,) bool: self spring cast this iteration (ray hit or closest point)
+
+
+def _obstacle_of(m):
+    """The generator mesh's tetrahedral obstacle, if it has one."""
+    if getattr(m, "obstacle_X", None) is None:
+        return None
+    from . import obstacle
+
+    return obstacle.prepare(m.obstacle_X, m.obstacle_tets)
 
 
 def record_forward(m, n_iters, prep=None):
@@ -59,8 +68,12 @@ def record_forward(m, n_iters, prep=None):
     X = m.rest.copy()
     st = springs.SpringState.empty(prep.query.shape[0])
     dec: List[IterDecisions] = []
+    obs = _obstacle_of(m)
     for _ in range(n_iters):
-        Xn, st, rec, ps, po = loop.iterate(prep, X, st, m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps, m.collision)
+        Xn, st, rec, ps, po = loop.iterate(prep, X, st, m.alpha, m.spheres, m.w_knots, m.k_spring, m.eps, m.collision,
+                                           obs)
+        if isinstance(po, tuple):
+            po = np.concatenate(po)
         in_self = np.isin(prep.query, ps[:, 0]) if ps.shape[0] else np.zeros(prep.query.shape[0], bool)
         in_obs = np.isin(prep.query, po[:, 0]) if po.shape[0] else np.zeros(prep.query.shape[0], bool)
         cast = st.active & (st.kind == springs.KIND_SELF) & in_self & ~in_obs
@@ -135,7 +148,7 @@ def _bary(b, q0, q1, q2):
     return torch.stack([(d22 * r1 - d12 * r2) / den, (d11 * r2 - d12 * r1) / den])
 
 
-def _spring_targets(X, prep, dec: IterDecisions, spheres, eps, bary_t):
+def _spring_targets(X, prep, dec: IterDecisions, spheres, eps, bary_t, obs=None):
     """Targets c_v (n_active, 3) and their vertex ids, for the fixed decisions.
 
     ``bary_t`` maps a query index to the barycentric weights (a tensor) of its
@@ -155,6 +168,13 @@ def _spring_targets(X, prep, dec: IterDecisions, spheres, eps, bary_t):
     for qi in act.tolist():
         v = int(q[qi])
         x = X[v]
+        if dec.kind[qi] == springs.KIND_MESH_OBSTACLE:
+            # a point of the rigid tetrahedral obstacle: constant
+            from . import obstacle
+
+            b1, b2 = dec.bary[qi]
+            out.append(torch.from_numpy(obstacle.target(obs, int(dec.face[qi]), float(b1), float(b2), eps)))
+            continue
         if dec.kind[qi] == springs.KIND_OBSTACLE:
             c = torch.from_numpy(spheres[dec.face[qi], :3])
             r = float(spheres[dec.face[qi], 3])
@@ -183,6 +203,7 @@ def _spring_targets(X, prep, dec: IterDecisions, spheres, eps, bary_t):
 def loss_and_grad(m, n_iters, loss_verts, targets, prep=None):
     """FP64 loss and dL/dalpha of the unrolled loop (decisions from numpy)."""
     X_np, dec, prep = record_forward(m, n_iters, prep)
+    obs = _obstacle_of(m)
     tets = torch.from_numpy(prep.tets)
     T_c = torch.from_numpy(prep.T_c)
     vol0 = torch.from_numpy(prep.vol0)
@@ -200,7 +221,7 @@ def loss_and_grad(m, n_iters, loss_verts, targets, prep=None):
         for qi in list(bary_t):
             if not dec[it].active[qi] or dec[it].kind[qi] != springs.KIND_SELF:
                 del bary_t[qi]
-        c, sv = _spring_targets(X, prep, dec[it], m.spheres, m.eps, bary_t)
+        c, sv = _spring_targets(X, prep, dec[it], m.spheres, m.eps, bary_t, obs)
         om = torch.from_numpy(omega)[:, None, None]
         bw = (om * P).transpose(1, 2)             # (n_t, 4, 3)
         b = torch.zeros((n_v, 3), dtype=torch.float64).index_add(0, tets.reshape(-1), bw.reshape(-1, 3))
@@ -228,6 +249,6 @@ def loss_numpy(m, n_iters, loss_verts, targets, alpha=None, prep=None):
     """The same loss evaluated by the numpy oracle's forward pass."""
     a = m.alpha if alpha is None else alpha
     r = loop.run(m.rest, m.tets, m.group, m.fixed, a, n_iters, spheres=m.spheres, knots=m.w_knots, k=m.k_spring,
-                 eps=m.eps, collision_mode=m.collision, prep=prep)
+                 eps=m.eps, collision_mode=m.collision, prep=prep, obstacle=_obstacle_of(m))
     d = r.X[loss_verts] - targets
     return float(np.sum(d * d)), r

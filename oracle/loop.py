@@ -63,10 +63,11 @@ class RunResult:
     sphere_pairs: Optional[np.ndarray] = None
 
 
-def iterate(prep: Prepared, X, st, alpha, spheres, knots, k, eps, collision_mode):
+def iterate(prep: Prepared, X, st, alpha, spheres, knots, k, eps, collision_mode, obstacle=None):
     """One outer iteration from X_i (and the spring records of iteration i-1).
 
-    Returns X_{i+1}, the updated springs, the iteration record and the pairs."""
+    Returns X_{i+1}, the updated springs, the iteration record and the pairs
+    (self pairs; sphere pairs followed by tetrahedral-obstacle pairs)."""
     if collision_mode >= 1:
         sp_self = collision.self_pairs(X, prep.tets, prep.query)
     else:
@@ -75,21 +76,30 @@ def iterate(prep: Prepared, X, st, alpha, spheres, knots, k, eps, collision_mode
         sp_obs = collision.sphere_pairs(X, prep.query, spheres)
     else:
         sp_obs = np.zeros((0, 2), np.int64)
+    sp_mesh = None
+    if collision_mode >= 2 and obstacle is not None:
+        from . import obstacle as obst
+
+        sp_mesh = obst.pairs(X, prep.query, obstacle)
     if collision_mode >= 1:
         vn = mesh.vertex_normals(X, prep.faces, prep.n_verts)
-        st = springs.update_springs(X, prep.query, st, sp_self, sp_obs, spheres, prep.faces, vn, eps)
+        st = springs.update_springs(X, prep.query, st, sp_self, sp_obs, spheres, prep.faces, vn, eps,
+                                    obstacle, sp_mesh)
     P, _R, _eps, _w = local.local_step(X, prep.tets, prep.T_c, prep.vol0, prep.group, alpha, knots)
     sv = prep.query[st.active]
     stg = st.target[st.active]
     energy = local.elastic_energy(X, prep.tets, P, prep.omega) + springs.spring_energy(X, prep.query, st, k)
     A, b = global_step.assemble(prep.tets, prep.omega, P, prep.n_verts, sv, stg, k)
     Xn = global_step.solve(A, b, X, prep.fixed)
-    rec = IterRecord(energy, int(sp_self.shape[0]), int(sp_obs.shape[0]), int(st.active.sum()))
+    n_obs = int(sp_obs.shape[0]) + (0 if sp_mesh is None else int(sp_mesh.shape[0]))
+    rec = IterRecord(energy, int(sp_self.shape[0]), n_obs, int(st.active.sum()))
+    if sp_mesh is not None:
+        sp_obs = (sp_obs, sp_mesh)
     return Xn, st, rec, sp_self, sp_obs
 
 
 def run(rest, tets, group, fixed, alpha, n_iters, spheres=None, knots=((0.0, 1.0),), k=1.0,
-        eps=0.005, collision_mode=1, X0=None, springs0=None, prep=None) -> RunResult:
+        eps=0.005, collision_mode=1, X0=None, springs0=None, prep=None, obstacle=None) -> RunResult:
     """Run ``n_iters`` iterations from X0 (default: rest) and springs0."""
     prep = prep or prepare(rest, tets, group, fixed)
     spheres = np.zeros((0, 4)) if spheres is None else np.asarray(spheres, dtype=np.float64)
@@ -97,7 +107,7 @@ def run(rest, tets, group, fixed, alpha, n_iters, spheres=None, knots=((0.0, 1.0
     st = springs0.copy() if springs0 is not None else springs.SpringState.empty(prep.query.shape[0])
     res = RunResult(X, st)
     for _ in range(n_iters):
-        X, st, rec, ps, po = iterate(prep, X, st, alpha, spheres, knots, k, eps, collision_mode)
+        X, st, rec, ps, po = iterate(prep, X, st, alpha, spheres, knots, k, eps, collision_mode, obstacle)
         res.history.append(rec)
         res.self_pairs, res.sphere_pairs = ps, po
     res.X, res.springs = X, st
@@ -105,7 +115,13 @@ def run(rest, tets, group, fixed, alpha, n_iters, spheres=None, knots=((0.0, 1.0
 
 
 def run_mesh(m, n_iters=None, X0=None, springs0=None, prep=None, knots=None) -> RunResult:
-    """Convenience wrapper for a generator ``Mesh``."""
+    """Convenience wrapper for a generator ``Mesh`` (its tetrahedral obstacle
+    included when it has one)."""
+    obstacle = None
+    if getattr(m, "obstacle_X", None) is not None:
+        from . import obstacle as obst
+
+        obstacle = obst.prepare(m.obstacle_X, m.obstacle_tets)
     return run(m.rest, m.tets, m.group, m.fixed, m.alpha, m.n_iters if n_iters is None else n_iters,
                spheres=m.spheres, knots=m.w_knots if knots is None else knots, k=m.k_spring,
-               eps=m.eps, collision_mode=m.collision, X0=X0, springs0=springs0, prep=prep)
+               eps=m.eps, collision_mode=m.collision, X0=X0, springs0=springs0, prep=prep, obstacle=obstacle)

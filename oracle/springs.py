@@ -19,6 +19,12 @@ energy k |v - v_c|^2 (Eq. 5).  Per iteration, after detection:
   point over boundary faces not containing v is used.  The stored record is
   (face f, barycentrics beta1, beta2) and v_c = b + eps n_f, b the hit point
   and n_f the unit face normal.
+* v inside the tetrahedral obstacle (``oracle.obstacle``): a spring to the
+  closest point of the obstacle's boundary offset by eps along that face's
+  outward normal (Sec. II-C), record (face, beta1, beta2).  When v is inside
+  spheres and the mesh obstacle, the obstacle whose signed surface distance
+  is smallest wins (|x_v - c_j| - r_j for a sphere, minus the distance to the
+  boundary for the mesh; spheres first on ties).
 * else an existing spring is released or kept by the paper's release
   condition (v outside the obstacle and its normal distance to the contact
   surface above eps), read as: obstacle spring released iff
@@ -33,7 +39,8 @@ from dataclasses import dataclass
 import numpy as np
 
 KIND_SELF = 0
-KIND_OBSTACLE = 1
+KIND_OBSTACLE = 1       # sphere obstacle: face = sphere id
+KIND_MESH_OBSTACLE = 2  # tetrahedral obstacle: face = obstacle boundary face id, bary on it
 
 
 @dataclass
@@ -183,29 +190,50 @@ def _sphere_target(x, c, r, eps, nrm_v):
 
 
 def update_springs(X, query, prev: SpringState, self_pairs, sphere_pairs, spheres,
-                   faces, vnormals, eps) -> SpringState:
+                   faces, vnormals, eps, obstacle=None, obstacle_pairs=None) -> SpringState:
     """One spring update (create, re-target or release) for every query vertex."""
+    from . import obstacle as obst
+
     st = prev.copy()
     st.fallback[:] = False
     fn = np.cross(X[faces[:, 1]] - X[faces[:, 0]], X[faces[:, 2]] - X[faces[:, 0]])
     in_self = np.zeros(query.shape[0], bool)
+    in_mesh = np.zeros(query.shape[0], bool)
     pos = {int(v): i for i, v in enumerate(query)}
     for v, _e in self_pairs:
         in_self[pos[int(v)]] = True
+    if obstacle_pairs is not None:
+        for v, _e in obstacle_pairs:
+            in_mesh[pos[int(v)]] = True
     obs_hits = {}
     for v, j in sphere_pairs:
         obs_hits.setdefault(pos[int(v)], []).append(int(j))
     for i, v in enumerate(query):
         x = X[v]
+        sphere = None
         if i in obs_hits:
             js = obs_hits[i]
             dists = [float(np.linalg.norm(x - spheres[j, :3])) - float(spheres[j, 3]) for j in js]
-            j = js[int(np.argmin(dists))]
+            k = int(np.argmin(dists))
+            sphere = (js[k], dists[k])
+        mesh_hit = None
+        if in_mesh[i]:
+            f, b1, b2, d2 = obst.closest_boundary_point(x, obstacle)
+            mesh_hit = (f, b1, b2, -float(np.sqrt(d2)))
+        if sphere is not None and (mesh_hit is None or sphere[1] <= mesh_hit[3]):
+            j = sphere[0]
             st.active[i] = True
             st.kind[i] = KIND_OBSTACLE
             st.face[i] = j
             st.bary[i] = 0.0
             st.target[i] = _sphere_target(x, spheres[j, :3], float(spheres[j, 3]), eps, vnormals[v])
+        elif mesh_hit is not None:
+            f, b1, b2, _d = mesh_hit
+            st.active[i] = True
+            st.kind[i] = KIND_MESH_OBSTACLE
+            st.face[i] = f
+            st.bary[i] = (b1, b2)
+            st.target[i] = obst.target(obstacle, f, b1, b2, eps)
         elif in_self[i]:
             f, b1, b2, fb = ray_cast_target(X, v, vnormals[v], faces, fn)
             st.fallback[i] = fb
@@ -223,6 +251,13 @@ def update_springs(X, query, prev: SpringState, self_pairs, sphere_pairs, sphere
                     st.active[i] = False
                 else:
                     st.target[i] = _sphere_target(x, c, r, eps, vnormals[v])
+            elif st.kind[i] == KIND_MESH_OBSTACLE:
+                f = int(st.face[i])
+                b1, b2 = st.bary[i]
+                if obst.released(x, obstacle, f, b1, b2, eps):
+                    st.active[i] = False
+                else:
+                    st.target[i] = obst.target(obstacle, f, b1, b2, eps)
             else:
                 f = int(st.face[i])
                 b = _face_point(X, faces[f], st.bary[i, 0], st.bary[i, 1])

@@ -38,7 +38,7 @@ CASIM_DEBUG_BARRIER_NEVER_COMPLETES = 1
 
 EXPORTS = [
     "casim_default_params", "casim_create", "casim_upload_mesh", "casim_upload_batch", "casim_set_actuation",
-    "casim_set_spheres", "casim_set_positions", "casim_reset", "casim_step", "casim_forward_ckpt",
+    "casim_set_spheres", "casim_set_obstacle_mesh", "casim_set_positions", "casim_reset", "casim_step", "casim_forward_ckpt",
     "casim_backward", "casim_sync", "casim_get_positions",
     "casim_get_contacts", "casim_get_springs", "casim_set_springs", "casim_get_targets",
     "casim_get_history", "casim_get_stats", "casim_save_state", "casim_load_state",
@@ -64,7 +64,7 @@ class casim_params(ctypes.Structure):
         ("pcg_kernel", ctypes.c_int32),
         ("debug_flags", ctypes.c_int32),
         ("pcg_precond", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("broad_phase", ctypes.c_int32),
     ]
 
 
@@ -157,6 +157,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     L.casim_upload_batch.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(casim_mesh_desc)]
     L.casim_set_actuation.argtypes = [_P, ctypes.c_int32, _D]
     L.casim_set_spheres.argtypes = [_P, ctypes.c_int32, _D]
+    L.casim_set_obstacle_mesh.argtypes = [_P, ctypes.c_int32, _D, ctypes.c_int32, _I32]
     L.casim_set_positions.argtypes = [_P, _D]
     L.casim_reset.argtypes = [_P]
     L.casim_step.argtypes = [_P, ctypes.c_int32]
@@ -254,6 +255,13 @@ def casim_set_actuation(sim, alpha):
 def casim_set_spheres(sim, spheres):
     s = np.ascontiguousarray(np.asarray(spheres, dtype=np.float64).reshape(-1, 4))
     return _check(load_library().casim_set_spheres(sim, s.shape[0], _ptr(s, ctypes.c_double)), sim)
+
+
+def casim_set_obstacle_mesh(sim, xyz, tets):
+    x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3))
+    t = np.ascontiguousarray(np.asarray(tets, dtype=np.int32).reshape(-1, 4))
+    return _check(load_library().casim_set_obstacle_mesh(sim, x.shape[0], _ptr(x, ctypes.c_double), t.shape[0],
+                                                         _ptr(t, ctypes.c_int32)), sim)
 
 
 def casim_set_positions(sim, xyz):
@@ -445,7 +453,7 @@ class Sim:
 
     def __init__(self, mesh, precision=None, collision=None, stream: int = 0, stats: int = 1,
                  pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0,
-                 pcg_kernel=0, debug_flags=0, pcg_precond=0):
+                 pcg_kernel=0, debug_flags=0, pcg_precond=0, broad_phase=0):
         load_library()
         self.batch = None
         if isinstance(mesh, (list, tuple)):
@@ -469,6 +477,7 @@ class Sim:
         p.pcg_kernel = pcg_kernel
         p.debug_flags = debug_flags
         p.pcg_precond = pcg_precond
+        p.broad_phase = broad_phase
         self.params = p
         self.mesh = mesh
         self.h = casim_create(p, stream)
@@ -483,6 +492,8 @@ class Sim:
                 casim_set_actuation(self.h, alpha)
             if mesh.spheres is not None and len(mesh.spheres):
                 casim_set_spheres(self.h, mesh.spheres)
+            if getattr(mesh, "obstacle_X", None) is not None:
+                casim_set_obstacle_mesh(self.h, mesh.obstacle_X, mesh.obstacle_tets)
         except Exception:
             casim_destroy(self.h)
             self.h = None

@@ -315,6 +315,13 @@ __global__ void __launch_bounds__(128) k_adj_springs(Dev<T> d, AdjDev<T> a) {
     a.betabar[2 * qi + 1] = 0.0;
     return;
   }
+  if (a.sp_kind[qi] == 2) {
+    // tetrahedral-obstacle spring: the target is a point of the rigid
+    // obstacle, held constant (its weights are not differentiated)
+    a.betabar[2 * qi] = 0.0;
+    a.betabar[2 * qi + 1] = 0.0;
+    return;
+  }
   const int v = d.q_verts[qi];
   Emit em{a.em_vert, a.em_val, 4 * (size_t)qi + 3 * (size_t)d.qf_ptr[qi]};
   const R4<T> mv = a.mu[v];

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <functional>
 #include <limits>
 #include <new>
 #include <numeric>
@@ -61,6 +62,81 @@ void rcb_order(const double* xyz, int* idx, int n) {
   });
   rcb_order(xyz, idx, nl);
   rcb_order(xyz, idx + nl, n - nl);
+}
+
+// AABB tree over n primitives with centroids cen (3 per primitive): median
+// split along the longest extent of the centroids' box (ties by primitive
+// id), built once (Sec. II-B keeps the tree and refits its boxes).  Internal
+// nodes in preorder, node 0 the root; child codes >= 0 internal, < 0 leaf
+// ~prim; parent[i] of internal node i, parent[n - 1 + p] of leaf p.
+struct BvhHost {
+  std::vector<int2> child;
+  std::vector<int> parent;
+};
+void bvh_build(const std::vector<double>& cen, int n, BvhHost& out) {
+  out.child.assign(std::max(n - 1, 0), make_int2(0, 0));
+  out.parent.assign(std::max(2 * n - 1, 0), -1);
+  if (n < 2) return;
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  int next = 0;
+  std::function<int(int, int, int)> build = [&](int a, int b, int par) -> int {
+    if (b - a == 1) {
+      out.parent[n - 1 + idx[a]] = par;
+      return ~idx[a];
+    }
+    const int node = next++;
+    out.parent[node] = par;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int i = a; i < b; ++i)
+      for (int c = 0; c < 3; ++c) {
+        lo[c] = std::min(lo[c], cen[3 * (size_t)idx[i] + c]);
+        hi[c] = std::max(hi[c], cen[3 * (size_t)idx[i] + c]);
+      }
+    int ax = 0;
+    for (int c = 1; c < 3; ++c)
+      if (hi[c] - lo[c] > hi[ax] - lo[ax]) ax = c;
+    const int m = a + (b - a) / 2;
+    std::nth_element(idx.begin() + a, idx.begin() + m, idx.begin() + b, [&](int p, int q) {
+      const double xp = cen[3 * (size_t)p + ax], xq = cen[3 * (size_t)q + ax];
+      return xp < xq || (xp == xq && p < q);
+    });
+    const int l = build(a, m, node);
+    const int r = build(m, b, node);
+    out.child[node] = make_int2(l, r);
+    return node;
+  };
+  build(0, n, -1);
+}
+
+// Boundary faces of a tet mesh: faces of exactly one tet, oriented outward
+// (face k of a tet is opposite its local vertex k), ordered by (tet, k), as
+// (v0, v1, v2, owning tet).
+void boundary_faces4(const int32_t* tets, int n_t, std::vector<int>& faces4) {
+  faces4.clear();
+  std::vector<std::array<int, 4>> keys(4 * (size_t)n_t);
+  for (int e = 0; e < n_t; ++e)
+    for (int k = 0; k < 4; ++k) {
+      int t3[3] = {tets[4 * e + kTetFace[k][0]], tets[4 * e + kTetFace[k][1]], tets[4 * e + kTetFace[k][2]]};
+      std::sort(t3, t3 + 3);
+      keys[4 * (size_t)e + k] = {t3[0], t3[1], t3[2], 4 * e + k};
+    }
+  std::sort(keys.begin(), keys.end());
+  std::vector<char> once(4 * (size_t)n_t, 0);
+  for (size_t i = 0; i < keys.size();) {
+    size_t j = i + 1;
+    while (j < keys.size() && keys[j][0] == keys[i][0] && keys[j][1] == keys[i][1] && keys[j][2] == keys[i][2]) ++j;
+    if (j - i == 1) once[keys[i][3]] = 1;
+    i = j;
+  }
+  for (int id = 0; id < 4 * n_t; ++id)
+    if (once[id]) {
+      const int e = id / 4, k = id % 4;
+      faces4.push_back(tets[4 * e + kTetFace[k][0]]);
+      faces4.push_back(tets[4 * e + kTetFace[k][1]]);
+      faces4.push_back(tets[4 * e + kTetFace[k][2]]);
+      faces4.push_back(e);
+    }
 }
 
 // In-place inverse of the SPD n x n matrix A (row-major) by its Cholesky
@@ -176,6 +252,25 @@ struct casim_sim {
   std::vector<int> seg_h;  // 4 x seg_blocks: lo, hi, rb0, rb1
   int* seg_d = nullptr;
   int pcg_clusters = 0, cl_rows_cap = 0, n_robots = 1;
+  // AABB trees (broad phase 1) of the robot's tets and boundary faces
+  BvhHost bvh_t_h, bvh_f_h;
+  BvhDev bt{}, bf{};
+  int* obs_mesh = nullptr;  // n_q
+  // rigid tetrahedral obstacle (its own allocations, replaced as a whole)
+  std::vector<void*> obs_allocs;
+  BvhDev ot{}, of{};
+  void* OX = nullptr;
+  int4* oface = nullptr;
+  int n_ov = 0, n_ot = 0, n_of = 0;
+  void free_obstacle() {
+    for (void* q : obs_allocs) cudaFree(q);
+    obs_allocs.clear();
+    ot = BvhDev{};
+    of = BvhDev{};
+    OX = nullptr;
+    oface = nullptr;
+    n_ov = n_ot = n_of = 0;
+  }
   int* robot_row = nullptr;
   std::vector<int> robot_row_h;
   std::vector<int> robot_of_vert_h, robot_of_tet_h, robot_of_face_h;
@@ -243,6 +338,9 @@ struct casim_sim {
   }
   void free_all() {
     free_adj();
+    free_obstacle();
+    bt = BvhDev{};
+    bf = BvhDev{};
     if (gexec) cudaGraphExecDestroy(gexec);
     gexec = nullptr;
     for (void* q : allocs) cudaFree(q);
@@ -326,6 +424,15 @@ Dev<T> make_dev(casim_sim* sim) {
   d.cast_list = sim->cast_list;
   d.cast_nrm = sim->cast_nrm;
   d.spring_c = (R4<double>*)sim->spring_c;
+  d.broad = sim->params.broad_phase;
+  d.bt = sim->bt;
+  d.bf = sim->bf;
+  d.ot = sim->ot;
+  d.of = sim->of;
+  d.OX = (const R4<T>*)sim->OX;
+  d.oface = sim->oface;
+  d.n_of = sim->n_of;
+  d.obs_mesh = sim->obs_mesh;
   d.k_spring = sim->params.k_spring;
   d.eps = sim->params.eps;
   d.cell = sim->params.cell_size;
@@ -443,6 +550,19 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->pair_count = sim->dalloc<int>(n_q);
   sim->pair_tet = sim->dalloc<int>((size_t)n_q * sim->params.max_pairs_per_vertex);
   sim->obs_sphere = sim->dalloc<int>(n_q);
+  sim->obs_mesh = sim->dalloc<int>(n_q);
+  auto alloc_bvh = [&](const BvhHost& h, int n, int nv, const int4* prim, BvhDev& b) {
+    b = BvhDev{};
+    if (sim->params.broad_phase != 1 || n <= 0) return;
+    b.n = n;
+    b.nv = nv;
+    b.prim = prim;
+    b.child = sim->dalloc<int2>(std::max(n - 1, 1));
+    b.parent = sim->dalloc<int>(2 * (size_t)n);
+    b.lo = sim->dalloc<float4>(std::max(n - 1, 1));
+    b.hi = sim->dalloc<float4>(std::max(n - 1, 1));
+    b.flag = sim->dalloc<int>(std::max(n - 1, 1));
+  };
   sim->sp.active = sim->dalloc<int>(n_q);
   sim->sp.kind = sim->dalloc<int>(n_q);
   sim->sp.face = sim->dalloc<int>(n_q);
@@ -466,6 +586,8 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->n_e_local = local_blocks(n_t);
   sim->n_e_spring = rhs_blocks(n_free);
   sim->e_partials = sim->dalloc<double>(sim->n_e_local + sim->n_e_spring + 1);
+  alloc_bvh(sim->bvh_t_h, n_t, 4, sim->tet, sim->bt);
+  alloc_bvh(sim->bvh_f_h, n_f, 3, sim->faces, sim->bf);
   for (void* q : sim->allocs)
     if (!q) return sim->fail(CASIM_E_CUDA, "cudaMalloc failed");
   if (!sim->X || !sim->items || !sim->P || !sim->e_partials || !sim->hist)
@@ -540,6 +662,16 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   CK(cudaMemsetAsync(sim->sp.fallback, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->pair_count, 0, sizeof(int) * std::max(n_q, 1), st));
   CK(cudaMemsetAsync(sim->obs_sphere, 0xff, sizeof(int) * std::max(n_q, 1), st));
+  CK(cudaMemsetAsync(sim->obs_mesh, 0, sizeof(int) * std::max(n_q, 1), st));
+  for (auto pr : {std::make_pair(&sim->bvh_t_h, &sim->bt), std::make_pair(&sim->bvh_f_h, &sim->bf)}) {
+    const BvhHost& h = *pr.first;
+    BvhDev& b = *pr.second;
+    if (b.n >= 2) {
+      CK(cudaMemcpyAsync((void*)b.child, h.child.data(), sizeof(int2) * h.child.size(), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync((void*)b.parent, h.parent.data(), sizeof(int) * h.parent.size(), cudaMemcpyHostToDevice,
+                         st));
+    }
+  }
   {
     Ctrl c0{};
     for (int j = 0; j < 3; ++j) {
@@ -740,6 +872,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.pcg_kernel < 0 || p.pcg_kernel > 5) why = "pcg_kernel";
   else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
   else if (p.pcg_precond < 0 || p.pcg_precond > 1) why = "pcg_precond";
+  else if (p.broad_phase < 0 || p.broad_phase > 1) why = "broad_phase";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
       if (!(p.w_knots[2 * i + 2] > p.w_knots[2 * i])) why = "w_knots must be strictly ascending";
@@ -1146,32 +1279,9 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
     for (int c = 0; c < 3; ++c) sim->X_fixed[3 * (size_t)(i - n_free) + c] = rest_int[3 * (size_t)i + c];
   // ---- boundary faces: faces of exactly one tet, ordered by (tet, k) ----
   std::vector<int> faces4;
-  {
-    std::vector<std::array<int, 4>> keys(4 * (size_t)n_t);  // sorted triple + index
-    for (int e = 0; e < n_t; ++e)
-      for (int k = 0; k < 4; ++k) {
-        int a = tets[4 * e + kTetFace[k][0]], b = tets[4 * e + kTetFace[k][1]], c = tets[4 * e + kTetFace[k][2]];
-        int t3[3] = {a, b, c};
-        std::sort(t3, t3 + 3);
-        keys[4 * (size_t)e + k] = {t3[0], t3[1], t3[2], 4 * e + k};
-      }
-    std::sort(keys.begin(), keys.end());
-    std::vector<char> once(4 * (size_t)n_t, 0);
-    for (size_t i = 0; i < keys.size();) {
-      size_t j = i + 1;
-      while (j < keys.size() && keys[j][0] == keys[i][0] && keys[j][1] == keys[i][1] && keys[j][2] == keys[i][2]) ++j;
-      if (j - i == 1) once[keys[i][3]] = 1;
-      i = j;
-    }
-    for (int idx = 0; idx < 4 * n_t; ++idx)
-      if (once[idx]) {
-        const int e = idx / 4, k = idx % 4;
-        faces4.push_back(tets_int[4 * e + kTetFace[k][0]]);
-        faces4.push_back(tets_int[4 * e + kTetFace[k][1]]);
-        faces4.push_back(tets_int[4 * e + kTetFace[k][2]]);
-        faces4.push_back(e);
-      }
-  }
+  boundary_faces4(tets, n_t, faces4);
+  for (size_t i = 0; i < faces4.size(); i += 4)
+    for (int k = 0; k < 3; ++k) faces4[i + k] = sim->int_of_user[faces4[i + k]];
   sim->n_f = (int)(faces4.size() / 4);
   sim->robot_of_face_h.resize(sim->n_f);
   for (int f = 0; f < sim->n_f; ++f) sim->robot_of_face_h[f] = robot_of_tet[faces4[4 * f + 3]];
@@ -1293,6 +1403,27 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
         }
       }
     }
+  }
+  // ---- AABB trees of the tets and boundary faces (broad phase 1) ----
+  sim->bvh_t_h = BvhHost{};
+  sim->bvh_f_h = BvhHost{};
+  if (sim->params.broad_phase == 1) {
+    std::vector<double> cen(3 * (size_t)n_t);
+    for (int e = 0; e < n_t; ++e)
+      for (int c = 0; c < 3; ++c) {
+        double a = 0.0;
+        for (int k = 0; k < 4; ++k) a += rest_int[3 * (size_t)tets_int[4 * e + k] + c];
+        cen[3 * (size_t)e + c] = 0.25 * a;
+      }
+    bvh_build(cen, n_t, sim->bvh_t_h);
+    cen.assign(3 * (size_t)sim->n_f, 0.0);
+    for (int f = 0; f < sim->n_f; ++f)
+      for (int c = 0; c < 3; ++c) {
+        double a = 0.0;
+        for (int k = 0; k < 3; ++k) a += rest_int[3 * (size_t)faces4[4 * f + k] + c];
+        cen[3 * (size_t)f + c] = a / 3.0;
+      }
+    bvh_build(cen, sim->n_f, sim->bvh_f_h);
   }
   // ---- spatial hash sizes ----
   sim->H_t = (unsigned)pow2_at_least(2 * (size_t)n_t);
@@ -1551,6 +1682,130 @@ int casim_set_spheres(casim_sim* sim, int32_t n, const double* cxyzr) {
   return CASIM_OK;
 }
 
+}  // extern "C"
+
+namespace {
+template <typename T>
+int set_obstacle_typed(casim_sim* sim, int32_t n_verts, const double* xyz, int32_t n_tets, const int32_t* tets) {
+  sim->free_obstacle();
+  if (n_tets == 0) {
+    sim->graph_dirty = true;
+    return CASIM_OK;
+  }
+  std::vector<int> faces4;
+  boundary_faces4(tets, n_tets, faces4);
+  const int n_of = (int)(faces4.size() / 4);
+  BvhHost ht, hf;
+  std::vector<double> cen(3 * (size_t)n_tets);
+  for (int e = 0; e < n_tets; ++e)
+    for (int c = 0; c < 3; ++c) {
+      double a = 0.0;
+      for (int k = 0; k < 4; ++k) a += xyz[3 * (size_t)tets[4 * e + k] + c];
+      cen[3 * (size_t)e + c] = 0.25 * a;
+    }
+  bvh_build(cen, n_tets, ht);
+  cen.assign(3 * (size_t)n_of, 0.0);
+  for (int f = 0; f < n_of; ++f)
+    for (int c = 0; c < 3; ++c) {
+      double a = 0.0;
+      for (int k = 0; k < 3; ++k) a += xyz[3 * (size_t)faces4[4 * f + k] + c];
+      cen[3 * (size_t)f + c] = a / 3.0;
+    }
+  bvh_build(cen, n_of, hf);
+  auto oalloc = [&](size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) return nullptr;
+    sim->obs_allocs.push_back(q);
+    return q;
+  };
+  std::vector<R4<T>> Xh(n_verts);
+  for (int i = 0; i < n_verts; ++i)
+    Xh[i] = R4<T>{(T)xyz[3 * (size_t)i], (T)xyz[3 * (size_t)i + 1], (T)xyz[3 * (size_t)i + 2], T(0)};
+  std::vector<int4> th(n_tets), fh(n_of);
+  for (int e = 0; e < n_tets; ++e) th[e] = make_int4(tets[4 * e], tets[4 * e + 1], tets[4 * e + 2], tets[4 * e + 3]);
+  for (int f = 0; f < n_of; ++f)
+    fh[f] = make_int4(faces4[4 * f], faces4[4 * f + 1], faces4[4 * f + 2], faces4[4 * f + 3]);
+  void* OX = oalloc(sizeof(R4<T>) * n_verts);
+  int4* otet = (int4*)oalloc(sizeof(int4) * n_tets);
+  int4* oface = (int4*)oalloc(sizeof(int4) * std::max(n_of, 1));
+  auto mk = [&](const BvhHost& h, int n, int nv, const int4* prim, BvhDev& b) -> bool {
+    b = BvhDev{};
+    b.n = n;
+    b.nv = nv;
+    b.prim = prim;
+    if (n < 2) return true;
+    b.child = (int2*)oalloc(sizeof(int2) * (n - 1));
+    b.parent = (int*)oalloc(sizeof(int) * (2 * (size_t)n - 1));
+    b.lo = (float4*)oalloc(sizeof(float4) * (n - 1));
+    b.hi = (float4*)oalloc(sizeof(float4) * (n - 1));
+    b.flag = (int*)oalloc(sizeof(int) * (n - 1));
+    return b.child && b.parent && b.lo && b.hi && b.flag;
+  };
+  bool ok = OX && otet && oface && mk(ht, n_tets, 4, otet, sim->ot) && mk(hf, n_of, 3, oface, sim->of);
+  if (!ok) {
+    sim->free_obstacle();
+    return sim->fail(CASIM_E_CUDA, "cudaMalloc failed (obstacle)");
+  }
+  cudaStream_t st = sim->stream;
+  CK(cudaMemcpyAsync(OX, Xh.data(), sizeof(R4<T>) * n_verts, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(otet, th.data(), sizeof(int4) * n_tets, cudaMemcpyHostToDevice, st));
+  if (n_of) CK(cudaMemcpyAsync(oface, fh.data(), sizeof(int4) * n_of, cudaMemcpyHostToDevice, st));
+  for (auto pr : {std::make_pair(&ht, &sim->ot), std::make_pair(&hf, &sim->of)}) {
+    const BvhHost& h = *pr.first;
+    BvhDev& b = *pr.second;
+    if (b.n >= 2) {
+      CK(cudaMemcpyAsync((void*)b.child, h.child.data(), sizeof(int2) * h.child.size(), cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync((void*)b.parent, h.parent.data(), sizeof(int) * h.parent.size(), cudaMemcpyHostToDevice,
+                         st));
+    }
+  }
+  // the obstacle does not move: its boxes are fitted once
+  launch_bvh_refit<T>(sim->ot, (const R4<T>*)OX, st);
+  launch_bvh_refit<T>(sim->of, (const R4<T>*)OX, st);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(st));
+  sim->OX = OX;
+  sim->oface = oface;
+  sim->n_ov = n_verts;
+  sim->n_ot = n_tets;
+  sim->n_of = n_of;
+  sim->graph_dirty = true;
+  return CASIM_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int casim_set_obstacle_mesh(casim_sim* sim, int32_t n_verts, const double* xyz, int32_t n_tets,
+                            const int32_t* tets) {
+  if (!sim) return CASIM_E_INVALID;
+  if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "upload the robot mesh first");
+  if (n_tets < 0 || n_verts < 0 || (n_tets > 0 && (!xyz || !tets || n_verts < 4)))
+    return sim->fail(CASIM_E_INVALID, "obstacle: bad sizes or null pointer");
+  for (long long i = 0; i < 3LL * n_verts; ++i)
+    if (!std::isfinite(xyz[i])) return sim->fail(CASIM_E_INVALID, "obstacle: non-finite position");
+  for (int e = 0; e < n_tets; ++e) {
+    for (int k = 0; k < 4; ++k)
+      if (tets[4 * e + k] < 0 || tets[4 * e + k] >= n_verts)
+        return sim->fail(CASIM_E_INVALID, "obstacle: vertex id out of range at tet " + std::to_string(e));
+    double V[4][3];
+    for (int k = 0; k < 4; ++k)
+      for (int c = 0; c < 3; ++c) V[k][c] = xyz[3 * (size_t)tets[4 * e + k] + c];
+    const double a[3] = {V[1][0] - V[0][0], V[1][1] - V[0][1], V[1][2] - V[0][2]};
+    const double b[3] = {V[2][0] - V[0][0], V[2][1] - V[0][1], V[2][2] - V[0][2]};
+    const double c[3] = {V[3][0] - V[0][0], V[3][1] - V[0][1], V[3][2] - V[0][2]};
+    const double vol = a[0] * (b[1] * c[2] - b[2] * c[1]) - a[1] * (b[0] * c[2] - b[2] * c[0]) +
+                       a[2] * (b[0] * c[1] - b[1] * c[0]);
+    if (!(vol > 0.0)) return sim->fail(CASIM_E_INVALID, "obstacle: non-positive volume at tet " + std::to_string(e));
+  }
+  return sim->params.precision == CASIM_FP64 ? set_obstacle_typed<double>(sim, n_verts, xyz, n_tets, tets)
+                                             : set_obstacle_typed<float>(sim, n_verts, xyz, n_tets, tets);
+}
+
+}  // extern "C"
+
+extern "C" {
+
 int casim_set_positions(casim_sim* sim, const double* xyz) {
   if (!sim) return CASIM_E_INVALID;
   sim->adj.valid = false;
@@ -1632,12 +1887,14 @@ int casim_get_contacts(casim_sim* sim, int32_t* pairs, int64_t* n_pairs, int32_t
   if (!sim || !n_pairs || !n_obst) return CASIM_E_INVALID;
   if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
   const int n_q = sim->n_q, mp = sim->params.max_pairs_per_vertex;
-  std::vector<int> cnt(std::max(n_q, 1)), pt((size_t)std::max(n_q, 1) * mp), obs(std::max(n_q, 1));
+  std::vector<int> cnt(std::max(n_q, 1)), pt((size_t)std::max(n_q, 1) * mp), obs(std::max(n_q, 1)),
+      obm(std::max(n_q, 1));
   CK(cudaStreamSynchronize(sim->stream));
   if (n_q) {
     CK(cudaMemcpy(cnt.data(), sim->pair_count, sizeof(int) * n_q, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(pt.data(), sim->pair_tet, sizeof(int) * (size_t)n_q * mp, cudaMemcpyDeviceToHost));
     CK(cudaMemcpy(obs.data(), sim->obs_sphere, sizeof(int) * n_q, cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(obm.data(), sim->obs_mesh, sizeof(int) * n_q, cudaMemcpyDeviceToHost));
   }
   const int64_t cap_p = *n_pairs, cap_o = *n_obst;
   int64_t np = 0, no = 0;
@@ -1651,7 +1908,7 @@ int casim_get_contacts(casim_sim* sim, int32_t* pairs, int64_t* n_pairs, int32_t
       }
       ++np;
     }
-    if (obs[q] >= 0) {
+    if (obs[q] >= 0 || obm[q] > 0) {
       if (obstacle_verts && no < cap_o) obstacle_verts[no] = uv;
       ++no;
     }
@@ -1709,7 +1966,8 @@ int casim_set_springs(casim_sim* sim, int64_t n, const int32_t* verts, const uin
     a[q] = active[q] ? 1 : 0;
     k[q] = kind[q];
     f[q] = face[q];
-    if (a[q] && (k[q] < 0 || k[q] > 1)) return sim->fail(CASIM_E_INVALID, "spring kind");
+    if (a[q] && (k[q] < 0 || k[q] > 2)) return sim->fail(CASIM_E_INVALID, "spring kind");
+    if (a[q] && k[q] == 2 && (f[q] < 0 || f[q] >= sim->n_of)) return sim->fail(CASIM_E_INVALID, "obstacle face id");
     if (a[q] && k[q] == 0 && (f[q] < 0 || f[q] >= sim->n_f)) return sim->fail(CASIM_E_INVALID, "spring face id");
     if (a[q] && k[q] == 1 && (f[q] < 0 || f[q] >= sim->n_spheres)) return sim->fail(CASIM_E_INVALID, "spring sphere id");
   }

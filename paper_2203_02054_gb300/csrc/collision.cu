@@ -18,6 +18,7 @@
 // per casting vertex.  All spring geometry is evaluated in FP64.
 #include <algorithm>
 
+#include "bvh.cuh"
 #include "common.cuh"
 #include "kernels.h"
 #include "predicates.cuh"
@@ -229,8 +230,8 @@ __device__ __forceinline__ T max4(T a, T b, T c, T e) {
 // p strictly inside tet t, evaluated in the positions' own precision (the
 // box reject compares exactly; the orientation signs are exact).
 template <typename T>
-__device__ __forceinline__ bool strictly_inside(const Dev<T>& d, T px, T py, T pz, int4 t) {
-  const R4<T> a = d.X[t.x], b = d.X[t.y], c = d.X[t.z], e = d.X[t.w];
+__device__ __forceinline__ bool strictly_inside_at(const R4<T>* X, T px, T py, T pz, int4 t) {
+  const R4<T> a = X[t.x], b = X[t.y], c = X[t.z], e = X[t.w];
   if (px < min4(a.x, b.x, c.x, e.x) || px > max4(a.x, b.x, c.x, e.x)) return false;
   if (py < min4(a.y, b.y, c.y, e.y) || py > max4(a.y, b.y, c.y, e.y)) return false;
   if (pz < min4(a.z, b.z, c.z, e.z) || pz > max4(a.z, b.z, c.z, e.z)) return false;
@@ -240,6 +241,43 @@ __device__ __forceinline__ bool strictly_inside(const Dev<T>& d, T px, T py, T p
   if (orient_t(a.x, a.y, a.z, b.x, b.y, b.z, px, py, pz, e.x, e.y, e.z) <= 0) return false;
   if (orient_t(a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z, px, py, pz) <= 0) return false;
   return true;
+}
+template <typename T>
+__device__ __forceinline__ bool strictly_inside(const Dev<T>& d, T px, T py, T pz, int4 t) {
+  return strictly_inside_at(d.X, px, py, pz, t);
+}
+
+// Obstacle tests of one query point (Eq. 4): the sphere whose signed surface
+// distance |x - c_j| - r_j is smallest among those strictly containing it
+// (ties: lowest j), how many spheres contain it, and how many tetrahedra of
+// the rigid tetrahedral obstacle strictly contain it (exact signs, AABB tree
+// of the obstacle).  Spheres use the fixed FP64 evaluation order.
+template <typename T>
+__device__ __forceinline__ void obstacle_tests(const Dev<T>& d, T px, T py, T pz, int& best, int& n_sph,
+                                               int& n_mesh) {
+  best = -1;
+  n_sph = 0;
+  n_mesh = 0;
+  if (d.collision < 2) return;
+  double bestd = 0.0;
+  for (int j = 0; j < d.n_spheres; ++j) {
+    const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
+    const double r = d.spheres[4 * j + 3];
+    const double dx = __dsub_rn((double)px, cx), dy = __dsub_rn((double)py, cy), dz = __dsub_rn((double)pz, cz);
+    const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    if (d2 < __dmul_rn(r, r)) {
+      ++n_sph;
+      const double dist = sqrt(d2) - r;
+      if (best < 0 || dist < bestd) {
+        best = j;
+        bestd = dist;
+      }
+    }
+  }
+  if (d.ot.n > 0)
+    bvh_point_query(d.ot, (double)px, (double)py, (double)pz, [&](int e) {
+      if (strictly_inside_at(d.OX, px, py, pz, d.ot.prim[e])) ++n_mesh;
+    });
 }
 
 // One warp per query vertex: the lanes test the candidates of the vertex's
@@ -304,30 +342,114 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
         }
       }
     }
-    int best = -1;
     if (lane == 0) {
       if (over) set_status(d.ctrl, ST_PAIRS_TRUNC);
       d.pair_count[qi] = cnt;
       n_self = cnt;
-      if (d.collision >= 2) {
-        double bestd = 0.0;
-        for (int j = 0; j < d.n_spheres; ++j) {
-          const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
-          const double r = d.spheres[4 * j + 3];
-          const double dx = __dsub_rn((double)px, cx), dy = __dsub_rn((double)py, cy), dz = __dsub_rn((double)pz, cz);
-          const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-          if (d2 < __dmul_rn(r, r)) {
-            ++n_obs;
-            const double dist = sqrt(d2) - r;
-            if (best < 0 || dist < bestd) {
-              best = j;
-              bestd = dist;
-            }
-          }
-        }
-      }
+      int best, n_sph, n_mesh;
+      obstacle_tests(d, px, py, pz, best, n_sph, n_mesh);
+      n_obs = n_sph + n_mesh;
       d.obs_sphere[qi] = best;
+      if (d.obs_mesh) d.obs_mesh[qi] = n_mesh;
     }
+  }
+  const int s1 = block_sum_int(n_self, shi);
+  const int s2 = block_sum_int(n_obs, shi);
+  if (threadIdx.x == 0 && (s1 | s2)) {
+    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
+    atomicAdd(&rec->n_self_pairs, s1);
+    atomicAdd(&rec->n_obstacle_pairs, s2);
+  }
+}
+
+// ---- AABB trees: refit and point queries ----
+// Refit after the positions moved (the tree's structure is kept, Sec. II-B):
+// one thread per leaf computes its box and climbs; at every internal node the
+// first of the two arriving threads stops, the second forms the union of the
+// two children's boxes (the sibling's box was written before its arrival,
+// fenced) and continues toward the root.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bvh_refit(BvhDev b, const R4<T>* __restrict__ X) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= b.n || b.n < 2) return;
+  float4 lo, hi;
+  prim_box(b, X, p, lo, hi);
+  int me = ~p;
+  int node = b.parent[b.n - 1 + p];
+  while (node >= 0) {
+    __threadfence();
+    if (atomicAdd(&b.flag[node], 1) == 0) return;
+    __threadfence();
+    const int2 c = b.child[node];
+    const int other = c.x == me ? c.y : c.x;
+    float4 olo, ohi;
+    if (other < 0) {
+      prim_box(b, X, ~other, olo, ohi);
+    } else {
+      olo = __ldcg(&b.lo[other]);
+      ohi = __ldcg(&b.hi[other]);
+    }
+    lo = make_float4(fminf(lo.x, olo.x), fminf(lo.y, olo.y), fminf(lo.z, olo.z), 0.0f);
+    hi = make_float4(fmaxf(hi.x, ohi.x), fmaxf(hi.y, ohi.y), fmaxf(hi.z, ohi.z), 0.0f);
+    __stcg(&b.lo[node], lo);
+    __stcg(&b.hi[node], hi);
+    me = node;
+    node = b.parent[node];
+  }
+}
+
+// Narrow phase over the robot's AABB tree (broad phase 1): one thread per
+// query vertex descends through the boxes containing it and tests the tets
+// at the leaves exactly; the pair list is the same sorted, duplicate-free
+// list as the hash path's (at most max_pairs, the smallest tet ids).
+static constexpr int NARROW_BVH_THREADS = 128;
+
+template <typename T>
+__global__ void __launch_bounds__(NARROW_BVH_THREADS) k_narrow_bvh(Dev<T> d) {
+  __shared__ int shi[32];
+  const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+  int n_self = 0, n_obs = 0;
+  if (qi < d.n_q) {
+    const int v = d.q_verts[qi];
+    const R4<T> pv = d.X[v];
+    const T px = pv.x, py = pv.y, pz = pv.z;
+    int cnt = 0;
+    bool over = false;
+    int* out = d.pair_tet + (size_t)qi * d.max_pairs;
+    const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
+    if (d.collision >= 1 && isfinite(px) && isfinite(py) && isfinite(pz)) {
+      bvh_point_query(d.bt, (double)px, (double)py, (double)pz, [&](int e) {
+        const int4 t = d.tet[e];
+        if (d.robot_of_tet && d.robot_of_tet[e] != rv) return;
+        if (t.x == v || t.y == v || t.z == v || t.w == v) return;
+        if (!strictly_inside(d, px, py, pz, t)) return;
+        int pos = 0;
+        while (pos < cnt && out[pos] < e) ++pos;
+        if (pos < cnt && out[pos] == e) return;
+        if (cnt == d.max_pairs) {
+          over = true;
+          if (pos == cnt) return;
+          --cnt;
+        }
+        for (int j = cnt; j > pos; --j) out[j] = out[j - 1];
+        out[pos] = e;
+        ++cnt;
+      });
+    }
+    if (over) set_status(d.ctrl, ST_PAIRS_TRUNC);
+    d.pair_count[qi] = cnt;
+    n_self = cnt;
+    int best, n_sph, n_mesh;
+    if (isfinite(px) && isfinite(py) && isfinite(pz)) {
+      obstacle_tests(d, px, py, pz, best, n_sph, n_mesh);
+    } else {
+      best = -1;
+      n_sph = n_mesh = 0;
+      set_status(d.ctrl, ST_NONFINITE);
+    }
+    n_obs = n_sph + n_mesh;
+    d.obs_sphere[qi] = best;
+    if (d.obs_mesh) d.obs_mesh[qi] = n_mesh;
   }
   const int s1 = block_sum_int(n_self, shi);
   const int s2 = block_sum_int(n_obs, shi);
@@ -591,6 +713,51 @@ __device__ __forceinline__ V3 face_point(const Dev<T>& d, int f, double b1, doub
   return add(add(scl(1.0 - b1 - b2, q0), scl(b1, q1)), scl(b2, q2));
 }
 
+// Point and unit outward normal of boundary face f of the tetrahedral
+// obstacle at barycentrics (b1, b2).
+template <typename T>
+__device__ __forceinline__ V3 obstacle_face_point(const Dev<T>& d, int f, double b1, double b2, V3& nunit) {
+  const int4 fv = d.oface[f];
+  const R4<T> a = d.OX[fv.x], b = d.OX[fv.y], c = d.OX[fv.z];
+  const V3 q0 = {(double)a.x, (double)a.y, (double)a.z}, q1 = {(double)b.x, (double)b.y, (double)b.z},
+           q2 = {(double)c.x, (double)c.y, (double)c.z};
+  const V3 n = cross(sub(q1, q0), sub(q2, q0));
+  nunit = scl(1.0 / norm(n), n);
+  return add(add(scl(1.0 - b1 - b2, q0), scl(b1, q1)), scl(b2, q2));
+}
+
+// Closest point of the tetrahedral obstacle's boundary to x (Sec. II-C,
+// robot-obstacle response): the face with the smallest squared distance,
+// ties to the lowest face id, found through the obstacle's face tree.
+template <typename T>
+__device__ __forceinline__ int obstacle_closest(const Dev<T>& d, V3 x, double& b1, double& b2, double& d2) {
+  int bf = -1;
+  double bd = INFINITY, c1 = 0.0, c2 = 0.0;
+  bvh_nearest(
+      d.of, x.x, x.y, x.z,
+      [&](int f) {
+        const int4 fv = d.oface[f];
+        const R4<T> a = d.OX[fv.x], b = d.OX[fv.y], c = d.OX[fv.z];
+        const V3 q0 = {(double)a.x, (double)a.y, (double)a.z}, q1 = {(double)b.x, (double)b.y, (double)b.z},
+                 q2 = {(double)c.x, (double)c.y, (double)c.z};
+        double e1, e2;
+        const V3 p = closest_tri(x, q0, q1, q2, e1, e2);
+        const V3 dd = sub(x, p);
+        const double dist2 = dot(dd, dd);
+        if (bf < 0 || dist2 < bd || (dist2 == bd && f < bf)) {
+          bf = f;
+          bd = dist2;
+          c1 = e1;
+          c2 = e2;
+        }
+      },
+      [&]() { return bd; });
+  b1 = c1;
+  b2 = c2;
+  d2 = bd;
+  return bf;
+}
+
 // Spring update, one thread per query vertex.  A vertex in a self pair (and
 // in no obstacle pair) needs a ray cast: it is appended to the cast list with
 // its unit normal and finished by k_cast; every other vertex is finished here.
@@ -598,8 +765,9 @@ static constexpr int SPRING_THREADS = 128;
 static constexpr int CAST_THREADS = 256;
 
 // Signature term of one spring record (see sig_mix): query index and the
-// decision code (0 a self spring kept from its record, 1 an obstacle spring,
-// 2 a self spring cast in this iteration) with the face or sphere id.
+// decision code (0 a self spring kept from its record, 1 a sphere spring, 2 a
+// tetrahedral-obstacle spring, 3 a self spring cast in this iteration) with
+// the face, sphere or obstacle face id.
 __device__ __forceinline__ unsigned long long spring_term(int qi, int code, int face) {
   return sig_mix((unsigned)qi, ((unsigned)code << 30) ^ (unsigned)(face + 1));
 }
@@ -628,9 +796,23 @@ __global__ void __launch_bounds__(SPRING_THREADS) k_springs(Dev<T> d) {
     int face = d.sp.face[qi];
     double b1 = d.sp.bary[2 * qi], b2 = d.sp.bary[2 * qi + 1];
     V3 tgt = {0.0, 0.0, 0.0};
-    const int js = d.obs_sphere[qi];
+    int js = d.obs_sphere[qi];
     const double eps = d.eps;
     bool deferred = false;
+    // inside the tetrahedral obstacle: its closest boundary point, unless a
+    // containing sphere's surface is at least as near (signed distances
+    // |x - c| - r and minus the distance to the obstacle's boundary)
+    int mf = -1;
+    double m1 = 0.0, m2 = 0.0;
+    if (d.obs_mesh && d.obs_mesh[qi] > 0) {
+      double md2;
+      mf = obstacle_closest(d, x, m1, m2, md2);
+      if (js >= 0 && mf >= 0) {
+        const V3 c = {d.spheres[4 * js], d.spheres[4 * js + 1], d.spheres[4 * js + 2]};
+        if (!(norm(sub(x, c)) - d.spheres[4 * js + 3] <= -sqrt(md2))) js = -1;
+        else mf = -1;
+      }
+    }
     if (js >= 0) {
       const V3 c = {d.spheres[4 * js], d.spheres[4 * js + 1], d.spheres[4 * js + 2]};
       const double r = d.spheres[4 * js + 3];
@@ -642,6 +824,15 @@ __global__ void __launch_bounds__(SPRING_THREADS) k_springs(Dev<T> d) {
       face = js;
       b1 = b2 = 0.0;
       tgt = add(c, scl(r + eps, u));
+    } else if (mf >= 0) {
+      V3 nf;
+      const V3 bp = obstacle_face_point(d, mf, m1, m2, nf);
+      active = 1;
+      kind = 2;
+      face = mf;
+      b1 = m1;
+      b2 = m2;
+      tgt = add(bp, scl(eps, nf));
     } else if (d.pair_count[qi] > 0) {
       deferred = true;
       const int slot = atomicAdd(&d.ctrl->n_cast, 1);  // < n_q: each vertex enters once
@@ -660,6 +851,14 @@ __global__ void __launch_bounds__(SPRING_THREADS) k_springs(Dev<T> d) {
         } else {
           u = nu == 0.0 ? scl(-1.0, n) : scl(1.0 / nu, u);
           tgt = add(c, scl(r + eps, u));
+        }
+      } else if (kind == 2) {
+        V3 nf;
+        const V3 bp = obstacle_face_point(d, face, b1, b2, nf);
+        if (dot(nf, sub(x, bp)) > eps) {
+          active = 0;
+        } else {
+          tgt = add(bp, scl(eps, nf));
         }
       } else {
         V3 nf;
@@ -737,8 +936,96 @@ __global__ void __launch_bounds__(CAST_THREADS) k_cast(Dev<T> d) {
       d.sp.target[3 * qi + 2] = tgt.z;
       d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
       active_out += active;
-      if (active && d.stats) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->spring_sig, spring_term(qi, 2, f));
+      if (active && d.stats) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->spring_sig, spring_term(qi, 3, f));
     }
+  }
+  const int ns = block_sum_int(active_out, shi);
+  if (threadIdx.x == 0 && ns) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->n_springs, ns);
+}
+
+// Self springs of the listed vertices with the robot's face tree (broad
+// phase 1): one thread per casting vertex finds the first exit face along
+// -n(v) (smallest t, then the lowest face id; the tree prunes boxes entered
+// beyond the best hit), else the closest point over the boundary faces not
+// containing v (smallest squared distance, then the lowest face id).
+template <typename T>
+__global__ void __launch_bounds__(CAST_THREADS) k_cast_bvh(Dev<T> d) {
+  __shared__ int shi[32];
+  const int n_cast = d.ctrl->n_cast;
+  int active_out = 0;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_cast; j += gridDim.x * blockDim.x) {
+    const int qi = d.cast_list[j];
+    const int v = d.q_verts[qi];
+    const V3 x = pos(d, v);
+    const V3 dir = {-d.cast_nrm[3 * qi], -d.cast_nrm[3 * qi + 1], -d.cast_nrm[3 * qi + 2]};
+    const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
+    int bf = -1, fell_back = 0;
+    double bt = INFINITY, b1 = 0.0, b2 = 0.0;
+    const double o[3] = {x.x, x.y, x.z}, dv[3] = {dir.x, dir.y, dir.z};
+    bvh_ray(
+        d.bf, o, dv,
+        [&](int f) {
+          if (d.robot_of_face && d.robot_of_face[f] != rv) return;
+          V3 q0, q1, q2;
+          int4 fv;
+          face_verts(d, f, q0, q1, q2, fv);
+          if (fv.x == v || fv.y == v || fv.z == v) return;
+          if (!(dot(dir, cross(sub(q1, q0), sub(q2, q0))) > 0.0)) return;
+          double t, e1, e2;
+          if (!ray_tri(x, dir, q0, q1, q2, t, e1, e2)) return;
+          if (bf < 0 || t < bt || (t == bt && f < bf)) {
+            bf = f;
+            bt = t;
+            b1 = e1;
+            b2 = e2;
+          }
+        },
+        [&]() { return bt; });
+    if (bf < 0) {
+      fell_back = 1;
+      double bd = INFINITY;
+      bvh_nearest(
+          d.bf, x.x, x.y, x.z,
+          [&](int f) {
+            if (d.robot_of_face && d.robot_of_face[f] != rv) return;
+            V3 q0, q1, q2;
+            int4 fv;
+            face_verts(d, f, q0, q1, q2, fv);
+            if (fv.x == v || fv.y == v || fv.z == v) return;
+            double e1, e2;
+            const V3 p = closest_tri(x, q0, q1, q2, e1, e2);
+            const V3 dd = sub(x, p);
+            const double dist2 = dot(dd, dd);
+            if (bf < 0 || dist2 < bd || (dist2 == bd && f < bf)) {
+              bf = f;
+              bd = dist2;
+              b1 = e1;
+              b2 = e2;
+            }
+          },
+          [&]() { return bd; });
+    }
+    V3 tgt = {0.0, 0.0, 0.0};
+    if (bf >= 0) {
+      V3 nf;
+      const V3 bp = face_point(d, bf, b1, b2, nf);
+      tgt = add(bp, scl(d.eps, nf));
+    } else {
+      b1 = b2 = 0.0;
+    }
+    const int active = bf >= 0;
+    d.sp.active[qi] = active;
+    d.sp.fallback[qi] = fell_back;
+    d.sp.kind[qi] = 0;
+    d.sp.face[qi] = bf;
+    d.sp.bary[2 * qi] = b1;
+    d.sp.bary[2 * qi + 1] = b2;
+    d.sp.target[3 * qi] = tgt.x;
+    d.sp.target[3 * qi + 1] = tgt.y;
+    d.sp.target[3 * qi + 2] = tgt.z;
+    d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
+    active_out += active;
+    if (active && d.stats) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->spring_sig, spring_term(qi, 3, bf));
   }
   const int ns = block_sum_int(active_out, shi);
   if (threadIdx.x == 0 && ns) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->n_springs, ns);
@@ -746,7 +1033,22 @@ __global__ void __launch_bounds__(CAST_THREADS) k_cast(Dev<T> d) {
 
 // ---- launchers ----
 template <typename T>
+void launch_bvh_refit(const BvhDev& b, const R4<T>* X, cudaStream_t st) {
+  if (b.n < 2) return;
+  cudaMemsetAsync(b.flag, 0, sizeof(int) * (size_t)(b.n - 1), st);
+  k_bvh_refit<T><<<(b.n + 255) / 256, 256, 0, st>>>(b, X);
+}
+
+template <typename T>
 void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t st) {
+  if (d.broad == 1) {
+    // AABB trees: refit the tet and face trees to this iteration's positions
+    launch_bvh_refit<T>(d.bt, d.X, st);
+    launch_bvh_refit<T>(d.bf, d.X, st);
+    if (d.n_q > 0)
+      k_narrow_bvh<T><<<(d.n_q + NARROW_BVH_THREADS - 1) / NARROW_BVH_THREADS, NARROW_BVH_THREADS, 0, st>>>(d);
+    return;
+  }
   const int n_items = d.n_t + d.n_f;
   const int H = (int)(d.H_t + d.H_f);
   cudaMemsetAsync(d.cell_count, 0, sizeof(int) * (size_t)(H + 1), st);
@@ -769,6 +1071,10 @@ void launch_springs(const Dev<T>& d, cudaStream_t st) {
   if (d.n_q <= 0) return;
   k_springs<T><<<(d.n_q + SPRING_THREADS - 1) / SPRING_THREADS, SPRING_THREADS, 0, st>>>(d);
   // enough warps for one pass over a list of up to 8,192 casts
+  if (d.broad == 1) {
+    k_cast_bvh<T><<<std::min((d.n_q + CAST_THREADS - 1) / CAST_THREADS, 1024), CAST_THREADS, 0, st>>>(d);
+    return;
+  }
   const int per_block = CAST_THREADS / 32;
   const int blocks = std::min((d.n_q + per_block - 1) / per_block, 1024);
   k_cast<T><<<blocks, CAST_THREADS, 0, st>>>(d);
@@ -783,6 +1089,8 @@ void launch_scan_exclusive(const int* in, int* out, int n, int* tile_sums, int* 
   k_scan_add<<<(n + 255) / 256, 256, 0, st>>>(out, tile_sums, n);
 }
 
+template void launch_bvh_refit<float>(const BvhDev&, const R4<float>*, cudaStream_t);
+template void launch_bvh_refit<double>(const BvhDev&, const R4<double>*, cudaStream_t);
 template void launch_collision<float>(const Dev<float>&, const CollisionScratch&, cudaStream_t);
 template void launch_collision<double>(const Dev<double>&, const CollisionScratch&, cudaStream_t);
 template void launch_springs<float>(const Dev<float>&, cudaStream_t);

@@ -98,10 +98,22 @@ __host__ __device__ inline double order_decode(long long c) {
   return u.d;
 }
 
+// One AABB tree (layout in bvh.cuh): n primitives, n - 1 internal nodes.
+struct BvhDev {
+  int n;               // primitives; 0 = no tree
+  int nv;              // vertices per primitive: 4 (tets) or 3 (faces)
+  const int2* child;   // n - 1
+  const int* parent;   // 2 n - 1
+  float4* lo;          // n - 1 internal boxes
+  float4* hi;
+  int* flag;           // n - 1 refit arrival counters (zeroed before each refit)
+  const int4* prim;    // primitive vertex ids
+};
+
 struct SpringDev {
   int* active;           // n_q
-  int* kind;             // n_q: 0 self, 1 obstacle
-  int* face;             // n_q: face id / sphere id / -1
+  int* kind;             // n_q: 0 self, 1 sphere obstacle, 2 tetrahedral obstacle
+  int* face;             // n_q: face id / sphere id / obstacle face id / -1
   double* bary;          // 2 n_q
   double* target;        // 3 n_q
   int* fallback;         // n_q: 1 if this update's self target is a closest point
@@ -164,6 +176,14 @@ struct Dev {
   int* cast_list;        // n_q: query indices whose spring needs a ray cast
   double* cast_nrm;      // 3 n_q: unit vertex normal of each listed query vertex
   R4<double>* spring_c;  // n_free: (c, mask), FP64
+  // AABB trees (broad phase 1) and the rigid tetrahedral obstacle
+  int broad;             // 0 spatial hash, 1 AABB trees refitted every iteration
+  BvhDev bt, bf;         // robot tets, robot boundary faces
+  BvhDev ot, of;         // obstacle tets, obstacle boundary faces (static)
+  const R4<T>* OX;       // obstacle positions (the working precision)
+  const int4* oface;     // obstacle boundary faces (v0, v1, v2, owning tet)
+  int n_of;
+  int* obs_mesh;         // n_q: obstacle tets strictly containing the vertex
   // parameters
   double k_spring, eps, cell, inv_cell, tol2;
   int max_iter, collision, stats;

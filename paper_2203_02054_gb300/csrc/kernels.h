@@ -28,6 +28,8 @@ void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t 
 template <typename T>
 void launch_springs(const Dev<T>& d, cudaStream_t st);
 template <typename T>
+void launch_bvh_refit(const BvhDev& b, const R4<T>* X, cudaStream_t st);
+template <typename T>
 void launch_local(const Dev<T>& d, cudaStream_t st);
 template <typename T>
 void launch_rhs(const Dev<T>& d, cudaStream_t st);

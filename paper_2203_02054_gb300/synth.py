@@ -101,6 +101,8 @@ class Mesh:
     w_knots: tuple = SOFT_W_KNOTS
     tip_verts: Optional[np.ndarray] = None     # (m,) int32 loss vertices
     tip_targets: Optional[np.ndarray] = None   # (m, 3) float64
+    obstacle_X: Optional[np.ndarray] = None    # (n_o, 3) rigid tetrahedral obstacle positions
+    obstacle_tets: Optional[np.ndarray] = None # (m_o, 4) int32, positively oriented
 
     @property
     def n_verts(self) -> int:
@@ -350,6 +352,17 @@ def small_finger(nx=20, ny=4, nz=4, n_ch=4, seed=7, lo=1.5, hi=2.5, n_iters=30,
     m.precision = precision
     m.collision = collision
     return m
+
+
+def box_obstacle(nx, ny, nz, h, origin, dtype=np.float64):
+    """A rigid box obstacle: an nx x ny x nz block of voxels of edge h, split
+    into Kuhn tets, translated to ``origin``; optionally rounded to float32 so
+    that a MIXED-precision consumer sees the identical coordinates."""
+    rest, tets, _g, _f = _voxel_kuhn(nx, ny, nz, h)
+    X = rest + np.asarray(origin, dtype=np.float64)[None, :]
+    if dtype == np.float32:
+        X = X.astype(np.float32).astype(np.float64)
+    return X, tets
 
 
 def perturbed_positions(mesh: Mesh, amplitude: float, seed: int, dtype=np.float64) -> np.ndarray:

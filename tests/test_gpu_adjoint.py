@@ -153,8 +153,8 @@ def test_signatures_deterministic_and_equal_to_their_definition():
     spring signature of the last iteration equals its definition evaluated on
     the host from the spring records and the contacts of the last check (sum
     mod 2^64 over active springs of the mix of (index, code << 30 xor
-    (face + 1)), code 1 for an obstacle spring, 2 for a self spring whose
-    vertex was in a pair (cast in that iteration), 0 for a kept one))."""
+    (face + 1)), code 1 for a sphere spring, 3 for a self spring whose vertex
+    was in a pair (cast in that iteration), 0 for a kept one))."""
     m = synth.small_finger(nx=20, ny=4, nz=4, n_ch=4, n_iters=6)
     X0 = synth.perturbed_positions(m, 0.3, seed=3, dtype=np.float32)
     sim = casim.Sim(m)
@@ -171,7 +171,7 @@ def test_signatures_deterministic_and_equal_to_their_definition():
     in_pair = set(sim.contacts()[0][:, 0].tolist())
     expect = 0
     for qi in np.nonzero(sp["active"])[0]:
-        code = 1 if sp["kind"][qi] == 1 else (2 if int(sp["verts"][qi]) in in_pair else 0)
+        code = 1 if sp["kind"][qi] == 1 else (3 if int(sp["verts"][qi]) in in_pair else 0)
         expect = (expect + _sig_mix(int(qi), ((code << 30) ^ (int(sp["face"][qi]) + 1)) & 0xFFFFFFFF)) \
             & ((1 << 64) - 1)
     assert sp["active"].sum() > 0

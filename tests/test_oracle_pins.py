@@ -550,3 +550,78 @@ def test_ray_cast_target_equals_brute_force_on_a_penetrating_finger():
         assert np.allclose([b1, b2], best[2:], atol=1e-9)
         checked += 1
     assert checked >= 5
+
+
+# ------------------------------------------------ tetrahedral obstacle (Eq. 4)
+def test_closest_points_array_rule_equals_scalar_rule():
+    from oracle import obstacle
+
+    rng = np.random.default_rng(31)
+    for _ in range(20):
+        q = rng.normal(size=(50, 3, 3))
+        p = rng.normal(size=3) * 1.5
+        x, b1, b2 = obstacle.closest_points(p, q[:, 0], q[:, 1], q[:, 2])
+        for k in range(q.shape[0]):
+            xs, s1, s2 = springs.closest_point_triangle(p, *q[k])
+            assert np.allclose(x[k], xs, atol=1e-12)
+            assert abs(b1[k] - s1) <= 1e-9 and abs(b2[k] - s2) <= 1e-9
+
+
+def test_box_obstacle_pairs_closest_point_target_and_release():
+    """Unit-cube obstacle (one voxel, 6 Kuhn tets): a generic point inside lies
+    in exactly one tet; the closest boundary point is the projection onto the
+    nearest cube face (closed form: distance min(x, 1-x, y, 1-y, z, 1-z)); the
+    target is that point moved eps outward; the release test flips between
+    0.5 eps and 2 eps outside."""
+    from oracle import obstacle
+
+    X, tets = synth.box_obstacle(1, 1, 1, 1.0, (0.0, 0.0, 0.0))
+    obs = obstacle.prepare(X, tets)
+    assert obs.faces.shape[0] == 12
+    rng = np.random.default_rng(5)
+    P = rng.uniform(0.02, 0.98, size=(40, 3))
+    outside = np.array([[1.5, 0.5, 0.5], [-0.1, 0.2, 0.3], [0.5, 0.5, 1.0 + 1e-9]])
+    Xr = np.concatenate([P, outside])
+    pr = obstacle.pairs(Xr, np.arange(Xr.shape[0]), obs)
+    counts = np.bincount(pr[:, 0], minlength=Xr.shape[0])
+    assert np.all(counts[:40] == 1) and np.all(counts[40:] == 0)
+    eps = 0.01
+    for p in P:
+        f, b1, b2, d2 = obstacle.closest_boundary_point(p, obs)
+        dist = np.array([p[0], 1 - p[0], p[1], 1 - p[1], p[2], 1 - p[2]])
+        j = int(np.argmin(dist))
+        assert math.isclose(math.sqrt(d2), dist[j], rel_tol=0, abs_tol=1e-12)
+        ax, side = j // 2, j % 2
+        foot = p.copy()
+        foot[ax] = float(side)
+        b, n = obstacle.face_point_and_normal(obs, f, b1, b2)
+        assert np.allclose(b, foot, atol=1e-12)
+        out = np.zeros(3)
+        out[ax] = 1.0 if side == 1 else -1.0
+        assert np.allclose(n, out, atol=1e-12)
+        assert np.allclose(obstacle.target(obs, f, b1, b2, eps), foot + eps * out, atol=1e-12)
+        assert obstacle.released(foot + 2 * eps * out, obs, f, b1, b2, eps)
+        assert not obstacle.released(foot + 0.5 * eps * out, obs, f, b1, b2, eps)
+
+
+def test_obstacle_spring_update_precedence_and_kinds():
+    """A vertex inside the box obstacle gets a mesh-obstacle spring; inside
+    both a sphere and the box, the smaller signed surface distance wins."""
+    from oracle import obstacle
+
+    X, tets = synth.box_obstacle(2, 2, 2, 0.5, (0.0, 0.0, 0.0))
+    obs = obstacle.prepare(X, tets)
+    Xr = np.array([[0.3, 0.45, 0.52], [0.47, 0.53, 0.05]])
+    q = np.arange(2)
+    pm = obstacle.pairs(Xr, q, obs)
+    assert sorted(set(pm[:, 0].tolist())) == [0, 1]
+    # sphere around vertex 1 only, reaching far inside: |x - c| - r = -0.25,
+    # while vertex 1 is 0.05 from the box bottom (signed distance -0.05)
+    sph = np.array([[0.47, 0.53, 0.05, 0.25]])
+    ps = collision.sphere_pairs(Xr, q, sph)
+    st = springs.update_springs(Xr, q, springs.SpringState.empty(2), np.zeros((0, 2), int), ps, sph,
+                                np.zeros((0, 3), int), np.zeros((2, 3)), 0.01, obs, pm)
+    assert st.kind[0] == springs.KIND_MESH_OBSTACLE and st.active[0]
+    assert st.kind[1] == springs.KIND_OBSTACLE and st.face[1] == 0
+    # vertex 0 is 0.3 from x = 0, 0.48 from z = 1 ... nearest face x = 0 at distance 0.3
+    assert np.allclose(st.target[0], [-0.01, 0.45, 0.52], atol=1e-12)
