@@ -121,6 +121,13 @@ typedef struct {
                                split of the rest centroids) and refitted every
                                iteration.  Both give the same contact pairs and
                                spring targets (exact leaf tests, same tie rules) */
+  int32_t local_block;      /* launch shapes (threads per block; 0 = default):   */
+  int32_t rhs_block;        /*   local step 64/128/256 (128), RHS gather          */
+  int32_t narrow_block;     /*   128/256/512 (256), narrow phase 128/256/512 (256,
+                               one warp per query vertex).  Results do not depend
+                               on them except for the summation order of the
+                               energy statistic; the autotuner picks them        */
+  int32_t pad_;
 } casim_params;
 
 #define CASIM_DEBUG_BARRIER_NEVER_COMPLETES 1

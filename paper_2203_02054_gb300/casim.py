@@ -65,6 +65,10 @@ class casim_params(ctypes.Structure):
         ("debug_flags", ctypes.c_int32),
         ("pcg_precond", ctypes.c_int32),
         ("broad_phase", ctypes.c_int32),
+        ("local_block", ctypes.c_int32),
+        ("rhs_block", ctypes.c_int32),
+        ("narrow_block", ctypes.c_int32),
+        ("pad_", ctypes.c_int32),
     ]
 
 
@@ -453,7 +457,8 @@ class Sim:
 
     def __init__(self, mesh, precision=None, collision=None, stream: int = 0, stats: int = 1,
                  pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0,
-                 pcg_kernel=0, debug_flags=0, pcg_precond=0, broad_phase=0):
+                 pcg_kernel=0, debug_flags=0, pcg_precond=0, broad_phase=0, local_block=0, rhs_block=0,
+                 narrow_block=0, cell_scale=1.0, tuned=False):
         load_library()
         self.batch = None
         if isinstance(mesh, (list, tuple)):
@@ -470,7 +475,7 @@ class Sim:
         self._knots = kn
         p.n_w_knots = kn.shape[0] // 2
         p.w_knots = _ptr(kn, ctypes.c_double)
-        p.cell_size = mesh.cell_size
+        p.cell_size = mesh.cell_size * cell_scale
         p.stats = stats
         p.max_pairs_per_vertex = max_pairs
         p.wait_budget_cycles = wait_budget_cycles
@@ -478,6 +483,14 @@ class Sim:
         p.debug_flags = debug_flags
         p.pcg_precond = pcg_precond
         p.broad_phase = broad_phase
+        p.local_block = local_block
+        p.rhs_block = rhs_block
+        p.narrow_block = narrow_block
+        self.tuned_from = None
+        if tuned:
+            from . import autotune
+
+            self.tuned_from = autotune.apply_cached(p, self.batch if self.batch is not None else mesh)
         self.params = p
         self.mesh = mesh
         self.h = casim_create(p, stream)

@@ -101,6 +101,7 @@ __global__ void __launch_bounds__(AA_THREADS) k_spring_energy(const R4<T>* __res
 }
 
 int aa_blocks(int n) { return (n + AA_THREADS - 1) / AA_THREADS; }
+int spring_energy_blocks(int n) { return n <= 0 ? 0 : aa_blocks(n); }
 int aa_dot_blocks(int n) { return std::max(1, std::min(256, (n + AA_THREADS - 1) / AA_THREADS)); }
 
 template <typename T>

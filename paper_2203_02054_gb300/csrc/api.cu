@@ -16,6 +16,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "casim.h"
 #include "common.cuh"
 #include "kernels.h"
@@ -64,21 +66,26 @@ void rcb_order(const double* xyz, int* idx, int n) {
   rcb_order(xyz, idx + nl, n - nl);
 }
 
-// AABB tree over n primitives with centroids cen (3 per primitive): median
-// split along the longest extent of the centroids' box (ties by primitive
-// id), built once (Sec. II-B keeps the tree and refits its boxes).  Internal
-// nodes in preorder, node 0 the root; child codes >= 0 internal, < 0 leaf
-// ~prim; parent[i] of internal node i, parent[n - 1 + p] of leaf p.
+// AABB trees over n primitives with centroids cen (3 per primitive), one tree
+// per group (robot): median split along the longest extent of the centroids'
+// box (ties by primitive id), built once (Sec. II-B keeps the trees and
+// refits their boxes).  Internal nodes in preorder, group after group; child
+// codes >= 0 internal, < 0 leaf ~prim; parent[i] of internal node i,
+// parent[n - 1 + p] of leaf p; root[g] the root code of group g (the
+// minimum int for an empty group).
 struct BvhHost {
   std::vector<int2> child;
   std::vector<int> parent;
+  std::vector<int> root;
 };
-void bvh_build(const std::vector<double>& cen, int n, BvhHost& out) {
-  out.child.assign(std::max(n - 1, 0), make_int2(0, 0));
-  out.parent.assign(std::max(2 * n - 1, 0), -1);
-  if (n < 2) return;
+void bvh_build(const std::vector<double>& cen, int n, const int* group, int n_groups, BvhHost& out) {
+  out.child.assign(std::max(n - 1, 1), make_int2(0, 0));
+  out.parent.assign(std::max(2 * n - 1, 1), -1);
+  out.root.assign(std::max(n_groups, 1), -2147483647 - 1);
+  if (n < 1) return;
   std::vector<int> idx(n);
   std::iota(idx.begin(), idx.end(), 0);
+  if (group) std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return group[a] < group[b]; });
   int next = 0;
   std::function<int(int, int, int)> build = [&](int a, int b, int par) -> int {
     if (b - a == 1) {
@@ -106,7 +113,13 @@ void bvh_build(const std::vector<double>& cen, int n, BvhHost& out) {
     out.child[node] = make_int2(l, r);
     return node;
   };
-  build(0, n, -1);
+  for (int a = 0; a < n;) {
+    const int g = group ? group[idx[a]] : 0;
+    int b = a + 1;
+    while (b < n && (group ? group[idx[b]] : 0) == g) ++b;
+    out.root[g] = build(a, b, -1);
+    a = b;
+  }
 }
 
 // Boundary faces of a tet mesh: faces of exactly one tet, oriented outward
@@ -249,8 +262,18 @@ struct casim_sim {
   float* cg_ainv = nullptr;
   bool pcg_seg = false; // segmented streaming PCG (batches: blocks per robot)
   int seg_blocks = 0;
-  std::vector<int> seg_h;  // 4 x seg_blocks: lo, hi, rb0, rb1
+  std::vector<int> seg_h;  // 5 x seg_blocks: lo, hi, rb0, rb1, robot
   int* seg_d = nullptr;
+  // segmented PCG coarse correction (per robot): aggregate offsets, inverse
+  // offsets, the inverses (FP32), and the per-aggregate sums exchanged
+  bool seg_coarse = false;
+  std::vector<int> seg_agg_base_h;
+  std::vector<long long> seg_ainv_off_h;
+  std::vector<float> seg_ainv_h;
+  int* seg_agg_base = nullptr;
+  long long* seg_ainv_off = nullptr;
+  float* seg_ainv = nullptr;
+  float* seg_aggsum = nullptr;
   int pcg_clusters = 0, cl_rows_cap = 0, n_robots = 1;
   // AABB trees (broad phase 1) of the robot's tets and boundary faces
   BvhHost bvh_t_h, bvh_f_h;
@@ -450,6 +473,12 @@ Dev<T> make_dev(casim_sim* sim) {
   d.seg_hi = sim->seg_d ? sim->seg_d + sim->seg_blocks : nullptr;
   d.seg_rb0 = sim->seg_d ? sim->seg_d + 2 * sim->seg_blocks : nullptr;
   d.seg_rb1 = sim->seg_d ? sim->seg_d + 3 * sim->seg_blocks : nullptr;
+  d.seg_robot = sim->seg_d ? sim->seg_d + 4 * sim->seg_blocks : nullptr;
+  d.seg_coarse = sim->seg_coarse ? 1 : 0;
+  d.seg_agg_base = sim->seg_agg_base;
+  d.seg_ainv_off = sim->seg_ainv_off;
+  d.seg_ainv = sim->seg_ainv;
+  d.seg_aggsum = sim->seg_aggsum;
   d.robot_row = sim->robot_row;
   d.cl_rows_cap = sim->cl_rows_cap;
   d.wait_budget = sim->params.wait_budget_cycles ? sim->params.wait_budget_cycles : 4000000000ull;
@@ -457,33 +486,62 @@ Dev<T> make_dev(casim_sim* sim) {
   d.hist = sim->hist;
   d.hist_cap = sim->hist_cap;
   d.e_partials = sim->e_partials;
-  d.n_e_local = sim->n_e_local;
-  d.n_e_spring = sim->n_e_spring;
+  d.local_threads = sim->params.local_block ? sim->params.local_block : LOCAL_THREADS;
+  d.rhs_threads = sim->params.rhs_block ? sim->params.rhs_block : RHS_THREADS;
+  d.narrow_threads = sim->params.narrow_block ? sim->params.narrow_block : 256;
+  d.n_e_local = local_blocks(sim->n_t, d.local_threads);
+  d.n_e_spring = rhs_blocks(sim->n_free, d.rhs_threads);
   return d;
 }
 
 // Enqueues one outer iteration on stream st (used for graph capture and for
 // the timed eager path).
+// NVTX range for profilers (a no-op unless a tool is attached); in graph
+// replay the ranges mark the capture, in eager mode every iteration.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <typename T>
 cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) {
+  NvtxRange outer("casim iteration");
   const Dev<T> d = make_dev<T>(sim);
   if (ev) cudaEventRecord(ev[0], st);
-  if (d.collision >= 1 && d.n_q > 0) launch_collision<T>(d, sim->cs, st);
+  if (d.collision >= 1 && d.n_q > 0) {
+    NvtxRange r("collision check");
+    launch_collision<T>(d, sim->cs, st);
+  }
   if (ev) cudaEventRecord(ev[1], st);
-  if (d.collision >= 1 && d.n_q > 0) launch_springs<T>(d, st);
+  if (d.collision >= 1 && d.n_q > 0) {
+    NvtxRange r("spring update");
+    launch_springs<T>(d, st);
+  }
   if (ev) cudaEventRecord(ev[2], st);
-  launch_local<T>(d, st);
+  {
+    NvtxRange r("local step");
+    launch_local<T>(d, st);
+  }
   if (ev) cudaEventRecord(ev[3], st);
-  launch_rhs<T>(d, st);
+  // the dataflow PCG forms the right-hand side, the diagonal and the
+  // iteration's record itself (one launch instead of three)
+  const bool fused = !sim->pcg_seg && !sim->pcg_cl && sim->pcg_variant == 5;
+  if (!fused) {
+    NvtxRange r("rhs gather");
+    launch_rhs<T>(d, st);
+  }
   if (ev) cudaEventRecord(ev[4], st);
+  NvtxRange rp("global solve");
   // reset the grid-barrier words (abort, count, generation) before the PCG
   cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st);
+  Dev<T> dp = d;
+  dp.rhs_in_pcg = fused ? 1 : 0;
   cudaError_t e = sim->pcg_seg  ? launch_pcg_seg<T>(d, sim->seg_blocks, st)
                   : sim->pcg_cl ? launch_pcg_cluster<T>(d, sim->pcg_clusters, st)
-                                : launch_pcg<T>(d, sim->pcg_grid, sim->pcg_variant, st);
+                                : launch_pcg<T>(dp, sim->pcg_grid, sim->pcg_variant, st);
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[5], st);
-  launch_finalize<T>(d, st);
+  if (!fused) launch_finalize<T>(d, st);
   return cudaGetLastError();
 }
 
@@ -557,6 +615,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
     b.n = n;
     b.nv = nv;
     b.prim = prim;
+    b.root = sim->dalloc<int>(h.root.size());
     b.child = sim->dalloc<int2>(std::max(n - 1, 1));
     b.parent = sim->dalloc<int>(2 * (size_t)n);
     b.lo = sim->dalloc<float4>(std::max(n - 1, 1));
@@ -574,6 +633,17 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->int_of_user_d = sim->dalloc<int>(n_v);
   sim->robot_row = sim->dalloc<int>(sim->robot_row_h.size());
   sim->seg_d = sim->seg_blocks ? sim->dalloc<int>(sim->seg_h.size()) : nullptr;
+  if (sim->seg_coarse) {
+    sim->seg_agg_base = sim->dalloc<int>(sim->seg_agg_base_h.size());
+    sim->seg_ainv_off = sim->dalloc<long long>(sim->seg_ainv_off_h.size());
+    sim->seg_ainv = sim->dalloc<float>(std::max<size_t>(sim->seg_ainv_h.size(), 1));
+    sim->seg_aggsum = sim->dalloc<float>(6 * (size_t)std::max(sim->seg_agg_base_h.back(), 1));
+  } else {
+    sim->seg_agg_base = nullptr;
+    sim->seg_ainv_off = nullptr;
+    sim->seg_ainv = nullptr;
+    sim->seg_aggsum = nullptr;
+  }
   if (sim->n_robots > 1) {
     sim->robot_of_vert = sim->dalloc<int>(n_v);
     sim->robot_of_tet = sim->dalloc<int>(n_t);
@@ -583,8 +653,9 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   }
   sim->ctrl = sim->dalloc<Ctrl>(1);
   sim->hist = sim->dalloc<IterRec>(sim->hist_cap);
-  sim->n_e_local = local_blocks(n_t);
-  sim->n_e_spring = rhs_blocks(n_free);
+  // energy partials: room for the smallest allowed block sizes
+  sim->n_e_local = local_blocks(n_t, 64);
+  sim->n_e_spring = rhs_blocks(n_free, 128);
   sim->e_partials = sim->dalloc<double>(sim->n_e_local + sim->n_e_spring + 1);
   alloc_bvh(sim->bvh_t_h, n_t, 4, sim->tet, sim->bt);
   alloc_bvh(sim->bvh_f_h, n_f, 3, sim->faces, sim->bf);
@@ -647,6 +718,14 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   CK(cudaMemcpyAsync(sim->robot_row, sim->robot_row_h.data(), sizeof(int) * sim->robot_row_h.size(), cudaMemcpyHostToDevice, st));
   if (sim->seg_blocks)
     CK(cudaMemcpyAsync(sim->seg_d, sim->seg_h.data(), sizeof(int) * sim->seg_h.size(), cudaMemcpyHostToDevice, st));
+  if (sim->seg_coarse) {
+    CK(cudaMemcpyAsync(sim->seg_agg_base, sim->seg_agg_base_h.data(), sizeof(int) * sim->seg_agg_base_h.size(),
+                       cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sim->seg_ainv_off, sim->seg_ainv_off_h.data(),
+                       sizeof(long long) * sim->seg_ainv_off_h.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(sim->seg_ainv, sim->seg_ainv_h.data(), sizeof(float) * sim->seg_ainv_h.size(),
+                       cudaMemcpyHostToDevice, st));
+  }
   if (sim->n_robots > 1) {
     CK(cudaMemcpyAsync(sim->robot_of_vert, sim->robot_of_vert_h.data(), sizeof(int) * n_v, cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(sim->robot_of_tet, sim->robot_of_tet_h.data(), sizeof(int) * n_t, cudaMemcpyHostToDevice, st));
@@ -666,10 +745,11 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   for (auto pr : {std::make_pair(&sim->bvh_t_h, &sim->bt), std::make_pair(&sim->bvh_f_h, &sim->bf)}) {
     const BvhHost& h = *pr.first;
     BvhDev& b = *pr.second;
-    if (b.n >= 2) {
+    if (b.n >= 1) {
       CK(cudaMemcpyAsync((void*)b.child, h.child.data(), sizeof(int2) * h.child.size(), cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync((void*)b.parent, h.parent.data(), sizeof(int) * h.parent.size(), cudaMemcpyHostToDevice,
                          st));
+      CK(cudaMemcpyAsync((void*)b.root, h.root.data(), sizeof(int) * h.root.size(), cudaMemcpyHostToDevice, st));
     }
   }
   {
@@ -873,6 +953,11 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
   else if (p.pcg_precond < 0 || p.pcg_precond > 1) why = "pcg_precond";
   else if (p.broad_phase < 0 || p.broad_phase > 1) why = "broad_phase";
+  else if (p.local_block != 0 && p.local_block != 64 && p.local_block != 128 && p.local_block != 256)
+    why = "local_block";
+  else if (p.rhs_block != 0 && p.rhs_block != 128 && p.rhs_block != 256 && p.rhs_block != 512) why = "rhs_block";
+  else if (p.narrow_block != 0 && p.narrow_block != 128 && p.narrow_block != 256 && p.narrow_block != 512)
+    why = "narrow_block";
   if (why.empty() && p.n_w_knots > 1) {
     for (int i = 0; i + 1 < p.n_w_knots; ++i)
       if (!(p.w_knots[2 * i + 2] > p.w_knots[2 * i])) why = "w_knots must be strictly ascending";
@@ -1415,7 +1500,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
         for (int k = 0; k < 4; ++k) a += rest_int[3 * (size_t)tets_int[4 * e + k] + c];
         cen[3 * (size_t)e + c] = 0.25 * a;
       }
-    bvh_build(cen, n_t, sim->bvh_t_h);
+    bvh_build(cen, n_t, robot_of_tet, n_robots, sim->bvh_t_h);
     cen.assign(3 * (size_t)sim->n_f, 0.0);
     for (int f = 0; f < sim->n_f; ++f)
       for (int c = 0; c < 3; ++c) {
@@ -1423,7 +1508,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
         for (int k = 0; k < 3; ++k) a += rest_int[3 * (size_t)faces4[4 * f + k] + c];
         cen[3 * (size_t)f + c] = a / 3.0;
       }
-    bvh_build(cen, sim->n_f, sim->bvh_f_h);
+    bvh_build(cen, sim->n_f, sim->robot_of_face_h.data(), n_robots, sim->bvh_f_h);
   }
   // ---- spatial hash sizes ----
   sim->H_t = (unsigned)pow2_at_least(2 * (size_t)n_t);
@@ -1513,24 +1598,75 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   sim->seg_h.clear();
   sim->seg_blocks = 0;
   if (sim->pcg_seg) {
-    // blocks per robot: one each, the rest in proportion to the rows
+    // blocks per robot: one each, the rest in proportion to the robot's work,
+    // rows x (expected CG iterations).  A launch lasts until the slowest robot
+    // converges, and Jacobi-CG on these slender bodies needs iterations in
+    // proportion to the body's length in elements, so the weight is the rows
+    // times the longest extent of the robot's rest box over its mean edge.
     const int R = sim->n_robots;
-    const long long total = std::max(1, n_free);
+    std::vector<double> wgt(R, 0.0);
+    {
+      std::vector<double> lo(3 * (size_t)R, 1e300), hi(3 * (size_t)R, -1e300), esum(R, 0.0);
+      std::vector<long long> ecnt(R, 0);
+      for (int v = 0; v < n_free; ++v) {
+        const int r = sim->robot_of_vert_h[v];
+        for (int c = 0; c < 3; ++c) {
+          lo[3 * (size_t)r + c] = std::min(lo[3 * (size_t)r + c], rest_int[3 * (size_t)v + c]);
+          hi[3 * (size_t)r + c] = std::max(hi[3 * (size_t)r + c], rest_int[3 * (size_t)v + c]);
+        }
+      }
+      for (int e = 0; e < n_t; ++e) {
+        const int r = robot_of_tet[e];
+        const int a = tets_int[4 * e], b = tets_int[4 * e + 1];
+        double dd = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          const double t = rest_int[3 * (size_t)a + c] - rest_int[3 * (size_t)b + c];
+          dd += t * t;
+        }
+        esum[r] += std::sqrt(dd);
+        ecnt[r] += 1;
+      }
+      for (int r = 0; r < R; ++r) {
+        const double rows = sim->robot_row_h[r + 1] - sim->robot_row_h[r];
+        double ext = 0.0;
+        for (int c = 0; c < 3; ++c) ext = std::max(ext, hi[3 * (size_t)r + c] - lo[3 * (size_t)r + c]);
+        const double edge = ecnt[r] ? esum[r] / ecnt[r] : 1.0;
+        wgt[r] = rows * std::max(1.0, edge > 0.0 ? ext / edge : 1.0);
+      }
+    }
+    double wtot = 0.0;
+    for (double w : wgt) wtot += w;
     std::vector<int> nb(R);
     int used = 0;
     for (int r = 0; r < R; ++r) {
       const long long rows = sim->robot_row_h[r + 1] - sim->robot_row_h[r];
-      nb[r] = 1 + (int)((rows * (long long)(seg_max - R)) / total);
+      nb[r] = 1 + (int)(wgt[r] * (double)(seg_max - R) / std::max(wtot, 1e-300));
+      nb[r] = (int)std::min<long long>(nb[r], std::max<long long>(1, rows));
       used += nb[r];
     }
-    std::vector<int> lo, hi, rb0, rb1;
+    // Block boundaries fall on whole aggregates of SA rows counted from the
+    // robot's first row (a block owns at most SEG_AGG_MAX aggregates), so the
+    // per-robot coarse correction below can be summed block by block.
+    const int SA = pcg_df_agg_rows();
+    bool coarse_ok = !fp64 && sim->params.pcg_precond == 0;
+    used = 0;
+    for (int r = 0; r < R; ++r) {
+      const int rows = sim->robot_row_h[r + 1] - sim->robot_row_h[r];
+      const int na = std::max(1, (rows + SA - 1) / SA);
+      nb[r] = std::max(1, std::min(nb[r], na));
+      if ((na + nb[r] - 1) / nb[r] > PCG_SEG_AGG_MAX) coarse_ok = false;
+      used += nb[r];
+    }
+    std::vector<int> lo, hi, rb0, rb1, rob;
     int bidx = 0;
     for (int r = 0; r < R; ++r) {
       const int r0 = sim->robot_row_h[r], rows = sim->robot_row_h[r + 1] - r0;
+      const int na = std::max(1, (rows + SA - 1) / SA);
       const int first = bidx;
       for (int k = 0; k < nb[r]; ++k) {
-        lo.push_back(r0 + (int)((long long)rows * k / nb[r]));
-        hi.push_back(r0 + (int)((long long)rows * (k + 1) / nb[r]));
+        lo.push_back(std::min(r0 + SA * (int)((long long)na * k / nb[r]), r0 + rows));
+        hi.push_back(std::min(r0 + SA * (int)((long long)na * (k + 1) / nb[r]), r0 + rows));
+        rob.push_back(r);
         ++bidx;
       }
       for (int k = 0; k < nb[r]; ++k) {
@@ -1539,12 +1675,36 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
       }
     }
     sim->seg_blocks = used;
-    sim->seg_h.reserve(4 * used);
+    sim->seg_h.reserve(5 * used);
     sim->seg_h.insert(sim->seg_h.end(), lo.begin(), lo.end());
     sim->seg_h.insert(sim->seg_h.end(), hi.begin(), hi.end());
     sim->seg_h.insert(sim->seg_h.end(), rb0.begin(), rb0.end());
     sim->seg_h.insert(sim->seg_h.end(), rb1.begin(), rb1.end());
+    sim->seg_h.insert(sim->seg_h.end(), rob.begin(), rob.end());
     sim->pcg_grid = std::max(sim->pcg_grid, used);
+    // per-robot Galerkin coarse matrices of the Laplacian over the robot's
+    // aggregates, inverted (Cholesky, FP64) and kept as FP32
+    sim->seg_agg_base_h.assign(R + 1, 0);
+    sim->seg_ainv_off_h.assign(R + 1, 0);
+    sim->seg_ainv_h.clear();
+    if (coarse_ok) {
+      for (int r = 0; r < R && coarse_ok; ++r) {
+        const int r0 = sim->robot_row_h[r], rows = sim->robot_row_h[r + 1] - r0;
+        const int na = std::max(1, (rows + SA - 1) / SA);
+        std::vector<double> Ac((size_t)na * na, 0.0);
+        for (int v = r0; v < r0 + rows; ++v) {
+          const int a = (v - r0) / SA;
+          Ac[(size_t)a * na + a] += diagL[v];
+          for (const auto& e : rows_ff[v]) Ac[(size_t)a * na + (e.first - r0) / SA] += e.second;
+        }
+        if (!cholesky_inverse(Ac, na)) coarse_ok = false;
+        sim->seg_agg_base_h[r + 1] = sim->seg_agg_base_h[r] + na;
+        sim->seg_ainv_off_h[r + 1] = sim->seg_ainv_off_h[r] + (long long)na * na;
+        sim->seg_ainv_h.insert(sim->seg_ainv_h.end(), Ac.begin(), Ac.end());
+      }
+    }
+    sim->seg_coarse = coarse_ok;
+    if (!coarse_ok) sim->seg_ainv_h.clear();
   }
   sim->pcg_cl = !sim->pcg_seg && ((kern == 3) || (kern == 0 && cl_fits && (many || !rr_fits)));
   const bool df = !sim->pcg_cl && !sim->pcg_seg && ((kern == 5) || (kern == 0 && !many && df_fits));
@@ -1703,7 +1863,7 @@ int set_obstacle_typed(casim_sim* sim, int32_t n_verts, const double* xyz, int32
       for (int k = 0; k < 4; ++k) a += xyz[3 * (size_t)tets[4 * e + k] + c];
       cen[3 * (size_t)e + c] = 0.25 * a;
     }
-  bvh_build(cen, n_tets, ht);
+  bvh_build(cen, n_tets, nullptr, 1, ht);
   cen.assign(3 * (size_t)n_of, 0.0);
   for (int f = 0; f < n_of; ++f)
     for (int c = 0; c < 3; ++c) {
@@ -1711,7 +1871,7 @@ int set_obstacle_typed(casim_sim* sim, int32_t n_verts, const double* xyz, int32
       for (int k = 0; k < 3; ++k) a += xyz[3 * (size_t)faces4[4 * f + k] + c];
       cen[3 * (size_t)f + c] = a / 3.0;
     }
-  bvh_build(cen, n_of, hf);
+  bvh_build(cen, n_of, nullptr, 1, hf);
   auto oalloc = [&](size_t bytes) -> void* {
     void* q = nullptr;
     if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) return nullptr;
@@ -1733,13 +1893,14 @@ int set_obstacle_typed(casim_sim* sim, int32_t n_verts, const double* xyz, int32
     b.n = n;
     b.nv = nv;
     b.prim = prim;
-    if (n < 2) return true;
-    b.child = (int2*)oalloc(sizeof(int2) * (n - 1));
+    if (n < 1) return true;
+    b.root = (int*)oalloc(sizeof(int) * h.root.size());
+    b.child = (int2*)oalloc(sizeof(int2) * std::max(n - 1, 1));
     b.parent = (int*)oalloc(sizeof(int) * (2 * (size_t)n - 1));
-    b.lo = (float4*)oalloc(sizeof(float4) * (n - 1));
-    b.hi = (float4*)oalloc(sizeof(float4) * (n - 1));
-    b.flag = (int*)oalloc(sizeof(int) * (n - 1));
-    return b.child && b.parent && b.lo && b.hi && b.flag;
+    b.lo = (float4*)oalloc(sizeof(float4) * std::max(n - 1, 1));
+    b.hi = (float4*)oalloc(sizeof(float4) * std::max(n - 1, 1));
+    b.flag = (int*)oalloc(sizeof(int) * std::max(n - 1, 1));
+    return b.root && b.child && b.parent && b.lo && b.hi && b.flag;
   };
   bool ok = OX && otet && oface && mk(ht, n_tets, 4, otet, sim->ot) && mk(hf, n_of, 3, oface, sim->of);
   if (!ok) {
@@ -1753,10 +1914,11 @@ int set_obstacle_typed(casim_sim* sim, int32_t n_verts, const double* xyz, int32
   for (auto pr : {std::make_pair(&ht, &sim->ot), std::make_pair(&hf, &sim->of)}) {
     const BvhHost& h = *pr.first;
     BvhDev& b = *pr.second;
-    if (b.n >= 2) {
+    if (b.n >= 1) {
       CK(cudaMemcpyAsync((void*)b.child, h.child.data(), sizeof(int2) * h.child.size(), cudaMemcpyHostToDevice, st));
       CK(cudaMemcpyAsync((void*)b.parent, h.parent.data(), sizeof(int) * h.parent.size(), cudaMemcpyHostToDevice,
                          st));
+      CK(cudaMemcpyAsync((void*)b.root, h.root.data(), sizeof(int) * h.root.size(), cudaMemcpyHostToDevice, st));
     }
   }
   // the obstacle does not move: its boxes are fitted once
@@ -1832,6 +1994,7 @@ int casim_reset(casim_sim* sim) {
 }
 
 int casim_step(casim_sim* sim, int32_t n_iters) {
+  NvtxRange r("casim_step");
   if (!sim) return CASIM_E_INVALID;
   if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
   if (!sim->has_act) return sim->fail(CASIM_E_STATE, "no actuation set");
@@ -1850,6 +2013,7 @@ int casim_forward_ckpt(casim_sim* sim, int32_t n_iters, int32_t ckpt_every) {
 }
 
 int casim_backward(casim_sim* sim, const double* dL_dX, double* dL_dalpha) {
+  NvtxRange r("casim_backward");
   if (!sim || !dL_dX || (!dL_dalpha && sim->n_groups > 0)) return CASIM_E_INVALID;
   if (!sim->has_mesh || !sim->adj.valid)
     return sim->fail(CASIM_E_STATE, "casim_backward needs a preceding casim_forward_ckpt with the same actuation");
@@ -2346,8 +2510,8 @@ int aa_energy(casim_sim* sim, void* Xbuf, double& E) {
   d.X = (R4<T>*)Xbuf;
   d.stats = 1;
   launch_local<T>(d, sim->stream);
-  launch_spring_energy<T>(d.X, d.spring_c, d.k_spring, sim->n_free, sim->e_partials + sim->n_e_local, sim->stream);
-  std::vector<double> parts(sim->n_e_local + sim->n_e_spring);
+  launch_spring_energy<T>(d.X, d.spring_c, d.k_spring, sim->n_free, sim->e_partials + d.n_e_local, sim->stream);
+  std::vector<double> parts(d.n_e_local + spring_energy_blocks(sim->n_free));
   CK(cudaMemcpyAsync(parts.data(), sim->e_partials, sizeof(double) * parts.size(), cudaMemcpyDeviceToHost,
                      sim->stream));
   CK(cudaStreamSynchronize(sim->stream));

@@ -275,22 +275,42 @@ __device__ __forceinline__ void obstacle_tests(const Dev<T>& d, T px, T py, T pz
     }
   }
   if (d.ot.n > 0)
-    bvh_point_query(d.ot, (double)px, (double)py, (double)pz, [&](int e) {
+    bvh_point_query(d.ot, 0, (double)px, (double)py, (double)pz, [&](int e) {
       if (strictly_inside_at(d.OX, px, py, pz, d.ot.prim[e])) ++n_mesh;
     });
 }
 
+template <typename T>
+__device__ void spring_update_vertex(const Dev<T>& d, int qi, int& active_out, unsigned long long& ssig);
+
 // One warp per query vertex: the lanes test the candidates of the vertex's
 // hash bucket in parallel; hits are merged by lane 0 into the vertex's sorted,
 // duplicate-free pair list.
-static constexpr int NARROW_THREADS = 256;
-
+// Block totals of one narrow-phase-and-spring-update launch into this
+// iteration's record: self pairs, obstacle pairs, finished springs and the
+// springs' signature.
 template <typename T>
-__global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
+__device__ __forceinline__ void narrow_block_totals(const Dev<T>& d, int n_self, int n_obs, int n_spr,
+                                                   unsigned long long ssig, int* shi) {
+  if (d.stats) warp_add_u64(ssig, &(d.hist + (d.ctrl->iter % d.hist_cap))->spring_sig);
+  const int s1 = block_sum_int(n_self, shi);
+  const int s2 = block_sum_int(n_obs, shi);
+  const int s3 = block_sum_int(n_spr, shi);
+  if (threadIdx.x == 0 && (s1 | s2 | s3)) {
+    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
+    if (s1) atomicAdd(&rec->n_self_pairs, s1);
+    if (s2) atomicAdd(&rec->n_obstacle_pairs, s2);
+    if (s3) atomicAdd(&rec->n_springs, s3);
+  }
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS) k_narrow(Dev<T> d) {
   __shared__ int shi[32];
   const int lane = threadIdx.x & 31;
   const int qi = (int)((blockIdx.x * (unsigned)blockDim.x + threadIdx.x) >> 5);
-  int n_self = 0, n_obs = 0;
+  int n_self = 0, n_obs = 0, n_spr = 0;
+  unsigned long long ssig = 0;
   if (qi < d.n_q) {
     const int v = d.q_verts[qi];
     const R4<T> pv = d.X[v];
@@ -353,13 +373,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
       if (d.obs_mesh) d.obs_mesh[qi] = n_mesh;
     }
   }
-  const int s1 = block_sum_int(n_self, shi);
-  const int s2 = block_sum_int(n_obs, shi);
-  if (threadIdx.x == 0 && (s1 | s2)) {
-    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
-    atomicAdd(&rec->n_self_pairs, s1);
-    atomicAdd(&rec->n_obstacle_pairs, s2);
-  }
+  narrow_block_totals(d, n_self, n_obs, n_spr, ssig, shi);
 }
 
 // ---- AABB trees: refit and point queries ----
@@ -371,7 +385,7 @@ __global__ void __launch_bounds__(NARROW_THREADS) k_narrow(Dev<T> d) {
 template <typename T>
 __global__ void __launch_bounds__(256) k_bvh_refit(BvhDev b, const R4<T>* __restrict__ X) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= b.n || b.n < 2) return;
+  if (p >= b.n) return;
   float4 lo, hi;
   prim_box(b, X, p, lo, hi);
   int me = ~p;
@@ -408,7 +422,8 @@ template <typename T>
 __global__ void __launch_bounds__(NARROW_BVH_THREADS) k_narrow_bvh(Dev<T> d) {
   __shared__ int shi[32];
   const int qi = blockIdx.x * blockDim.x + threadIdx.x;
-  int n_self = 0, n_obs = 0;
+  int n_self = 0, n_obs = 0, n_spr = 0;
+  unsigned long long ssig = 0;
   if (qi < d.n_q) {
     const int v = d.q_verts[qi];
     const R4<T> pv = d.X[v];
@@ -418,7 +433,7 @@ __global__ void __launch_bounds__(NARROW_BVH_THREADS) k_narrow_bvh(Dev<T> d) {
     int* out = d.pair_tet + (size_t)qi * d.max_pairs;
     const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
     if (d.collision >= 1 && isfinite(px) && isfinite(py) && isfinite(pz)) {
-      bvh_point_query(d.bt, (double)px, (double)py, (double)pz, [&](int e) {
+      bvh_point_query(d.bt, rv, (double)px, (double)py, (double)pz, [&](int e) {
         const int4 t = d.tet[e];
         if (d.robot_of_tet && d.robot_of_tet[e] != rv) return;
         if (t.x == v || t.y == v || t.z == v || t.w == v) return;
@@ -450,14 +465,9 @@ __global__ void __launch_bounds__(NARROW_BVH_THREADS) k_narrow_bvh(Dev<T> d) {
     n_obs = n_sph + n_mesh;
     d.obs_sphere[qi] = best;
     if (d.obs_mesh) d.obs_mesh[qi] = n_mesh;
+    if (d.sp.active) spring_update_vertex(d, qi, n_spr, ssig);
   }
-  const int s1 = block_sum_int(n_self, shi);
-  const int s2 = block_sum_int(n_obs, shi);
-  if (threadIdx.x == 0 && (s1 | s2)) {
-    IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
-    atomicAdd(&rec->n_self_pairs, s1);
-    atomicAdd(&rec->n_obstacle_pairs, s2);
-  }
+  narrow_block_totals(d, n_self, n_obs, n_spr, ssig, shi);
 }
 
 // ---- spring update ----
@@ -734,7 +744,7 @@ __device__ __forceinline__ int obstacle_closest(const Dev<T>& d, V3 x, double& b
   int bf = -1;
   double bd = INFINITY, c1 = 0.0, c2 = 0.0;
   bvh_nearest(
-      d.of, x.x, x.y, x.z,
+      d.of, 0, x.x, x.y, x.z,
       [&](int f) {
         const int4 fv = d.oface[f];
         const R4<T> a = d.OX[fv.x], b = d.OX[fv.y], c = d.OX[fv.z];
@@ -759,9 +769,9 @@ __device__ __forceinline__ int obstacle_closest(const Dev<T>& d, V3 x, double& b
 }
 
 // Spring update, one thread per query vertex.  A vertex in a self pair (and
-// in no obstacle pair) needs a ray cast: it is appended to the cast list with
-// its unit normal and finished by k_cast; every other vertex is finished here.
-static constexpr int SPRING_THREADS = 128;
+// in no obstacle) needs a ray cast: it is appended to the cast list with its
+// unit normal and finished by k_cast (or k_cast_bvh); every other vertex is
+// finished by the update itself.
 static constexpr int CAST_THREADS = 256;
 
 // Signature term of one spring record (see sig_mix): query index and the
@@ -772,13 +782,13 @@ __device__ __forceinline__ unsigned long long spring_term(int qi, int code, int 
   return sig_mix((unsigned)qi, ((unsigned)code << 30) ^ (unsigned)(face + 1));
 }
 
+// Spring update of query vertex qi, by one thread, once its contacts of this
+// iteration are known (pair_count, obs_sphere, obs_mesh): creates, re-targets
+// or releases its spring, or queues it for a ray cast.  Adds 1 to active_out
+// for a finished active spring and its signature term to ssig.
 template <typename T>
-__global__ void __launch_bounds__(SPRING_THREADS) k_springs(Dev<T> d) {
-  __shared__ int shi[32];
-  const int qi = blockIdx.x * blockDim.x + threadIdx.x;
-  int active_out = 0;
-  unsigned long long ssig = 0;
-  if (qi < d.n_q) {
+__device__ void spring_update_vertex(const Dev<T>& d, int qi, int& active_out, unsigned long long& ssig) {
+  {
     const int v = d.q_verts[qi];
     const V3 x = pos(d, v);
     // area-weighted vertex normal of the incident boundary faces
@@ -887,13 +897,24 @@ __global__ void __launch_bounds__(SPRING_THREADS) k_springs(Dev<T> d) {
       d.sp.target[3 * qi + 1] = tgt.y;
       d.sp.target[3 * qi + 2] = tgt.z;
       d.spring_c[v] = R4<double>{tgt.x, tgt.y, tgt.z, active ? 1.0 : 0.0};
-      active_out = active;
-      if (active) ssig = spring_term(qi, kind, face);
+      active_out += active;
+      if (active) ssig += spring_term(qi, kind, face);
     }
   }
-  if (d.stats) warp_add_u64(ssig, &(d.hist + (d.ctrl->iter % d.hist_cap))->spring_sig);
-  const int ns = block_sum_int(active_out, shi);
-  if (threadIdx.x == 0 && ns) atomicAdd(&(d.hist + (d.ctrl->iter % d.hist_cap))->n_springs, ns);
+}
+
+// Spring update of every query vertex, one thread each (the hash broad
+// phase's narrow phase runs one warp per vertex, which would leave 31 lanes
+// idle during this FP64 work; the tree's narrow phase runs one thread per
+// vertex and does the update in the same launch).
+template <typename T>
+__global__ void __launch_bounds__(128) k_springs(Dev<T> d) {
+  __shared__ int shi[32];
+  const int qi = blockIdx.x * blockDim.x + threadIdx.x;
+  int n_spr = 0;
+  unsigned long long ssig = 0;
+  if (qi < d.n_q) spring_update_vertex(d, qi, n_spr, ssig);
+  narrow_block_totals(d, 0, 0, n_spr, ssig, shi);
 }
 
 // Self springs of the listed vertices: one warp per vertex shares the ray
@@ -963,7 +984,7 @@ __global__ void __launch_bounds__(CAST_THREADS) k_cast_bvh(Dev<T> d) {
     double bt = INFINITY, b1 = 0.0, b2 = 0.0;
     const double o[3] = {x.x, x.y, x.z}, dv[3] = {dir.x, dir.y, dir.z};
     bvh_ray(
-        d.bf, o, dv,
+        d.bf, rv, o, dv,
         [&](int f) {
           if (d.robot_of_face && d.robot_of_face[f] != rv) return;
           V3 q0, q1, q2;
@@ -985,7 +1006,7 @@ __global__ void __launch_bounds__(CAST_THREADS) k_cast_bvh(Dev<T> d) {
       fell_back = 1;
       double bd = INFINITY;
       bvh_nearest(
-          d.bf, x.x, x.y, x.z,
+          d.bf, rv, x.x, x.y, x.z,
           [&](int f) {
             if (d.robot_of_face && d.robot_of_face[f] != rv) return;
             V3 q0, q1, q2;
@@ -1034,7 +1055,7 @@ __global__ void __launch_bounds__(CAST_THREADS) k_cast_bvh(Dev<T> d) {
 // ---- launchers ----
 template <typename T>
 void launch_bvh_refit(const BvhDev& b, const R4<T>* X, cudaStream_t st) {
-  if (b.n < 2) return;
+  if (b.n < 2 || !b.flag) return;
   cudaMemsetAsync(b.flag, 0, sizeof(int) * (size_t)(b.n - 1), st);
   k_bvh_refit<T><<<(b.n + 255) / 256, 256, 0, st>>>(b, X);
 }
@@ -1062,14 +1083,23 @@ void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t 
   k_grid_bin<T, true><<<(n_items + 255) / 256, 256, 0, st>>>(d);
   if (d.n_q > 0) {
     const long long threads = 32LL * d.n_q;
-    k_narrow<T><<<(unsigned)((threads + NARROW_THREADS - 1) / NARROW_THREADS), NARROW_THREADS, 0, st>>>(d);
+    const int bs = d.narrow_threads > 0 ? d.narrow_threads : 256;
+    const unsigned nb = (unsigned)((threads + bs - 1) / bs);
+    if (bs == 128)
+      k_narrow<T, 128><<<nb, 128, 0, st>>>(d);
+    else if (bs == 512)
+      k_narrow<T, 512><<<nb, 512, 0, st>>>(d);
+    else
+      k_narrow<T, 256><<<nb, 256, 0, st>>>(d);
   }
 }
 
+// The spring update (a separate launch after the hash's narrow phase, inside
+// the tree's narrow phase), then the ray casts of the vertices it queued.
 template <typename T>
 void launch_springs(const Dev<T>& d, cudaStream_t st) {
   if (d.n_q <= 0) return;
-  k_springs<T><<<(d.n_q + SPRING_THREADS - 1) / SPRING_THREADS, SPRING_THREADS, 0, st>>>(d);
+  if (d.broad != 1) k_springs<T><<<(d.n_q + 127) / 128, 128, 0, st>>>(d);
   // enough warps for one pass over a list of up to 8,192 casts
   if (d.broad == 1) {
     k_cast_bvh<T><<<std::min((d.n_q + CAST_THREADS - 1) / CAST_THREADS, 1024), CAST_THREADS, 0, st>>>(d);

@@ -98,7 +98,7 @@ __host__ __device__ inline double order_decode(long long c) {
   return u.d;
 }
 
-// One AABB tree (layout in bvh.cuh): n primitives, n - 1 internal nodes.
+// AABB trees (layout in bvh.cuh): n primitives, one tree per robot.
 struct BvhDev {
   int n;               // primitives; 0 = no tree
   int nv;              // vertices per primitive: 4 (tets) or 3 (faces)
@@ -108,6 +108,7 @@ struct BvhDev {
   float4* hi;
   int* flag;           // n - 1 refit arrival counters (zeroed before each refit)
   const int4* prim;    // primitive vertex ids
+  const int* root;     // per robot: root code of its tree (null: one tree rooted at node 0)
 };
 
 struct SpringDev {
@@ -187,6 +188,8 @@ struct Dev {
   // parameters
   double k_spring, eps, cell, inv_cell, tol2;
   int max_iter, collision, stats;
+  int local_threads, rhs_threads, narrow_threads;  // launch shapes (autotuned)
+  int rhs_in_pcg;        // 1: the dataflow PCG forms b, the diagonal and the iteration's record itself
   int n_robots;          // independent systems (robots) in the mesh
   const int* robot_row;  // n_robots + 1: first free row of each robot
   int cl_rows_cap;       // rows per CTA the cluster PCG's shared memory holds
@@ -197,6 +200,12 @@ struct Dev {
   const int* seg_hi;     //   one past the last row
   const int* seg_rb0;    //   first block of the block's robot
   const int* seg_rb1;    //   one past the robot's last block
+  const int* seg_robot;  //   the block's robot
+  int seg_coarse;        //   1: per-robot two-level preconditioner (MIXED)
+  const int* seg_agg_base;       // per robot: first aggregate (global index); + 1 entries
+  const long long* seg_ainv_off; // per robot: offset of its A_c^-1 (n_agg^2 floats, row-major)
+  const float* seg_ainv;
+  float* seg_aggsum;     //   per aggregate: sums of w (3) and r (3) of the last pass
   unsigned bar_extra;    // 0; 1 = test-only: the barrier expects one more block
   unsigned long long wait_budget;
   // control and statistics

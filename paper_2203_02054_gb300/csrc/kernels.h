@@ -19,6 +19,7 @@ static constexpr int PCG_RR_THREADS = 256;
 static constexpr int PCG_RR_MAXW = 16;   // widest sliced-ELL row kept in registers
 static constexpr int PCG_CL_THREADS = 1024;
 static constexpr int PCG_SEG_THREADS = 256;
+static constexpr int PCG_SEG_AGG_MAX = 64;  // aggregates per block of the segmented PCG's coarse correction
 static constexpr int PCG_DF_THREADS = 384;
 static constexpr size_t PCG_DF_HALO_MAX_BYTES = 160 * 1024;  // halo words in shared memory
 static constexpr int PCG_CL_SIZE = 16;   // CTAs per cluster (non-portable size)
@@ -63,6 +64,7 @@ void launch_remesh_flags(const Dev<T>& d, const double* ref, double alpha_max, d
 template <typename T>
 void launch_positions_f64(const Dev<T>& d, int n_v, double* out, cudaStream_t st);
 int aa_dot_blocks(int n);
+int spring_energy_blocks(int n);
 template <typename T>
 void launch_aa_update(const R4<T>* g, const R4<T>* x, R4<T>* f, R4<T>* f_prev, R4<T>* g_prev, R4<T>* dF, R4<T>* dG,
                       int n, int have_prev, cudaStream_t st);
@@ -125,6 +127,8 @@ void launch_scan_exclusive(const int* in, int* out, int n, int* tile_sums, int* 
 
 int local_blocks(int n_t);
 int rhs_blocks(int n_free);
+int local_blocks(int n_t, int threads);
+int rhs_blocks(int n_free, int threads);
 int scan_tiles(int n);
 
 }  // namespace casim

@@ -162,6 +162,7 @@ extern "C" int casim_contacts_noalloc(int32_t n_verts, const float* dev_xyz, int
   d.max_pairs = max_pairs;
   d.collision = 1;
   d.n_spheres = 0;
+  d.narrow_threads = 256;  // the regular narrow-phase launch shape; d.sp stays empty: no spring update
   d.cell = cell_size;
   d.inv_cell = 1.0 / cell_size;
   d.ctrl = ctrl;

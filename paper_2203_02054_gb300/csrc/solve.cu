@@ -47,8 +47,8 @@ __device__ __forceinline__ double w_table(const double* knots, int n, double eps
   return knots[2 * n - 1];
 }
 
-template <typename T, int SWEEPS>
-__global__ void __launch_bounds__(LOCAL_THREADS) k_local(Dev<T> d) {
+template <typename T, int SWEEPS, int BS>
+__global__ void __launch_bounds__(BS) k_local(Dev<T> d) {
   __shared__ double shd[32];
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   double en = 0.0;
@@ -143,33 +143,70 @@ __global__ void __launch_bounds__(LOCAL_THREADS) k_local(Dev<T> d) {
 // The rows also carry the spring energy k mask_v |x_v - c_v|^2 (Eq. 5) of
 // this iteration's springs (positions are unchanged since the spring update),
 // summed per block in row order.
+// One row of the right-hand side and of the diagonal: b_i, A_ii and the row's
+// spring energy (see above).
 template <typename T>
-__global__ void __launch_bounds__(RHS_THREADS) k_rhs(Dev<T> d) {
+__device__ __forceinline__ void rhs_row(const Dev<T>& d, int i, R4<double>& b, T& diag, double& es) {
+  double bx = 0.0, by = 0.0, bz = 0.0;
+  const int k1 = d.inc_ptr[i + 1];
+  for (int k = d.inc_ptr[i]; k < k1; ++k) {
+    const R4<T> p = d.P[d.inc[k]];
+    bx += (double)p.x;
+    by += (double)p.y;
+    bz += (double)p.z;
+  }
+  const R4<double> sc = d.spring_c[i];
+  const double km = d.k_spring * sc.w;
+  const R4<double> bf = d.bfix[i];
+  b = R4<double>{bx + km * sc.x - bf.x, by + km * sc.y - bf.y, bz + km * sc.z - bf.z, 0.0};
+  diag = d.diagL[i] + (T)km;
+  es = 0.0;
+  if (sc.w != 0.0) {
+    const R4<T> xi = d.X[i];
+    const double ex = (double)xi.x - sc.x, ey = (double)xi.y - sc.y, ez = (double)xi.z - sc.z;
+    es = km * (ex * ex + ey * ey + ez * ez);
+  }
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS) k_rhs(Dev<T> d) {
   __shared__ double shd[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double es = 0.0;
   if (i < d.n_free) {
-    double bx = 0.0, by = 0.0, bz = 0.0;
-    const int k1 = d.inc_ptr[i + 1];
-    for (int k = d.inc_ptr[i]; k < k1; ++k) {
-      const R4<T> p = d.P[d.inc[k]];
-      bx += (double)p.x;
-      by += (double)p.y;
-      bz += (double)p.z;
-    }
-    const R4<double> sc = d.spring_c[i];
-    const double km = d.k_spring * sc.w;
-    const R4<double> bf = d.bfix[i];
-    d.b[i] = R4<double>{bx + km * sc.x - bf.x, by + km * sc.y - bf.y, bz + km * sc.z - bf.z, 0.0};
-    d.diag[i] = d.diagL[i] + (T)km;
-    if (sc.w != 0.0) {
-      const R4<T> xi = d.X[i];
-      const double ex = (double)xi.x - sc.x, ey = (double)xi.y - sc.y, ez = (double)xi.z - sc.z;
-      es = km * (ex * ex + ey * ey + ez * ez);
-    }
+    R4<double> b;
+    T dg;
+    rhs_row(d, i, b, dg, es);
+    d.b[i] = b;
+    d.diag[i] = dg;
   }
   const double s = block_sum(es, shd);
   if (threadIdx.x == 0) d.e_partials[d.n_e_local + blockIdx.x] = s;
+}
+
+// End of an outer iteration (one thread): the energy into this iteration's
+// record, the iteration count, and the per-iteration words reset.
+template <typename T>
+__device__ __forceinline__ void finalize_iteration(const Dev<T>& d, double energy) {
+  Ctrl* c = d.ctrl;
+  IterRec* rec = d.hist + (c->iter % d.hist_cap);
+  rec->energy = energy;
+  if (!isfinite(energy) && d.stats) c->status |= ST_NONFINITE;
+  c->iter += 1;
+  c->n_cast = 0;
+  for (int j = 0; j < 3; ++j) {
+    c->box_lo[j] = 0x7FFFFFFFFFFFFFFFLL;
+    c->box_hi[j] = (long long)0x8000000000000000ULL;
+  }
+  IterRec* nx = d.hist + (c->iter % d.hist_cap);
+  nx->energy = 0.0;
+  nx->pcg_rel_residual = 0.0;
+  nx->n_self_pairs = 0;
+  nx->n_obstacle_pairs = 0;
+  nx->n_springs = 0;
+  nx->pcg_iters = 0;
+  nx->knot_sig = 0;
+  nx->spring_sig = 0;
 }
 
 // ------------------------------------------------------------------ PCG
@@ -520,7 +557,8 @@ __device__ __forceinline__ void write_pcg_record(const Ctrl* c, IterRec* hist, i
 // r_i = b_i - (A x)_i in FP64 and ||b_i||^2, ||r_i||^2 (the first residual of
 // the correction form; X is read-only while it is formed).
 template <typename T>
-__device__ __forceinline__ void residual_row_f64(const Dev<T>& d, int i, T dg, double (&rv)[3], double (&a0)[2]) {
+__device__ __forceinline__ void residual_row_f64(const Dev<T>& d, int i, T dg, double (&rv)[3], double (&a0)[2],
+                                                 const R4<double>* b_in = nullptr) {
   const R4<T> xi = d.X[i];
   double ax = (double)dg * xi.x, ay = (double)dg * xi.y, az = (double)dg * xi.z;
   const int sl = i >> 5, lane = i & 31;
@@ -532,7 +570,7 @@ __device__ __forceinline__ void residual_row_f64(const Dev<T>& d, int i, T dg, d
     ay += a * xc.y;
     az += a * xc.z;
   }
-  const R4<double> bi = d.b[i];
+  const R4<double> bi = b_in ? *b_in : d.b[i];
   rv[0] = bi.x - ax;
   rv[1] = bi.y - ay;
   rv[2] = bi.z - az;
@@ -1322,6 +1360,7 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   constexpr int NW = PCG_DF_THREADS / 32;
   __shared__ CgShared<float> cs;
   __shared__ double sc[5];  // bb, rr, gamma, alpha, beta: used by lane 0 of warp 0 only
+  __shared__ double s_es;   // the iteration's spring energy (fused right-hand side)
   extern __shared__ unsigned long long halo[];  // 2 tagged words per halo row (+ coarse rows)
   const int lane = threadIdx.x & 31;
   const bool w0 = threadIdx.x < 32;
@@ -1333,6 +1372,8 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   float val[MAXW];
   int width = 0;
   float dg = 1.0f;
+  R4<double> brow{0.0, 0.0, 0.0, 0.0};  // this row's right-hand side (formed here when fused)
+  double es = 0.0;                      // this row's spring energy (fused)
   if (act) {
     const int sl = i >> 5, ln = i & 31;
     const int base = d.sl_ptr[sl];
@@ -1342,7 +1383,10 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       lcol[j] = j < width ? d.sl_lcol[base + j * 32 + ln] : 0;
       val[j] = j < width ? d.sl_val[base + j * 32 + ln] : 0.0f;
     }
-    dg = d.diag[i];
+    if (d.rhs_in_pcg)
+      rhs_row(d, i, brow, dg, es);
+    else
+      dg = d.diag[i];
   }
   // coarse correction state (COARSE only): per-warp aggregate sums, the
   // parts of warps 1..5, the block's g values, this block's rows of A_c^-1
@@ -1438,11 +1482,14 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   unsigned ue = 0, re = 0;  // epochs of u and of the reductions (the same in every thread)
   float r[3] = {0.0f, 0.0f, 0.0f}, u[3], w[3] = {0.0f, 0.0f, 0.0f}, p[3], s[3], dd[3] = {0.0f, 0.0f, 0.0f};
   float gr[3] = {0.0f, 0.0f, 0.0f}, gs[3] = {0.0f, 0.0f, 0.0f};  // g(r), g(s) of this row's aggregate
-  double a0[2] = {0.0, 0.0};
+  double a0[3] = {0.0, 0.0, es};
   ++ue;
   if (act) {
     double rv[3];
-    residual_row_f64(d, i, dg, rv, a0);
+    double a01[2] = {0.0, 0.0};
+    residual_row_f64(d, i, dg, rv, a01, d.rhs_in_pcg ? &brow : nullptr);
+    a0[0] = a01[0];
+    a0[1] = a01[1];
     for (int c = 0; c < 3; ++c) {
       r[c] = (float)rv[c];
       u[c] = r[c] / dg;
@@ -1450,28 +1497,29 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
     if constexpr (!COARSE) store_u(ue, u);
   }
   {
-    double bs2[2], t[3];
+    // (||b||^2, ||r0||^2, spring energy) summed over the grid
+    double bs[3], t[3];
     if constexpr (COARSE) agg_warp_sums(w, r, s_zw);  // w is zero here
-    block_sums<2, NW>(a0, cs.sh, bs2);
+    block_sums<3, NW>(a0, cs.sh, bs);
     ++re;
     if constexpr (!COARSE) {
       if (w0) {
-        const double bs[3] = {bs2[0], bs2[1], 0.0};
         const bool ok = df_reduce(d, re, bs, t);
         if (lane == 0) {
           sc[0] = t[0];
           sc[1] = t[1];
+          s_es = t[2];
           cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
         }
       }
       __syncthreads();
     } else {
-      const double bs[3] = {bs2[0], bs2[1], 0.0};
       if (!reduce_c(re, bs, [&] {
             const bool ok = df_gather_dots_c(d, re, t);
             if (lane == 0) {
               sc[0] = t[0];
               sc[1] = t[1];
+              s_es = t[2];
               cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
             }
           }))
@@ -1606,7 +1654,23 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       d.X[i] = t;
     }
   }
-  if (i == 0) write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, sc[1], sc[0]);
+  if (blockIdx.x == 0 && w0) {
+    // the record of this outer iteration; with the fused right-hand side
+    // also what a separate finalize launch would do: the Eq. 8 energy (the
+    // local step's partials, summed by warp 0 in a fixed order, plus the
+    // spring energy of the first reduction), the iteration count, and the
+    // per-iteration words reset for the next iteration
+    double e_loc = 0.0;
+    if (d.rhs_in_pcg && d.stats) {
+      for (int k = lane; k < d.n_e_local; k += 32) e_loc += d.e_partials[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_down_sync(0xffffffffu, e_loc, o);
+    }
+    if (lane == 0) {
+      write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, sc[1], sc[0]);
+      if (d.rhs_in_pcg) finalize_iteration(d, d.stats ? e_loc + s_es : 0.0);
+    }
+  }
 }
 
 // Segmented streaming variant for batches: block b works on a contiguous row
@@ -1618,11 +1682,45 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
 // stops updating; the launch ends when every robot has converged (a counter
 // that the robot's first block increments, read after the next barrier so
 // every block sees the same value) or at the iteration cap.
-template <typename T>
+// Per-robot coarse correction of the segmented kernel (COARSE): the same
+// additive two-level preconditioner as the dataflow kernel's, per robot, with
+// aggregates of DF_AGG_ROWS rows counted from the robot's first row and block
+// boundaries on whole aggregates.  In a pass, round m of the block's threads
+// covers the rows lo + 256 m + t, i.e. the block's local aggregates 2m (warps
+// 0..3) and 2m + 1 (warps 4..7); each warp adds its rows' values by a fixed
+// shuffle tree and the four warp sums of an aggregate are added in order.
+static constexpr int SEG_WPA = DF_AGG_ROWS / 32;  // warps per aggregate
+
+template <int NV>
+__device__ __forceinline__ void seg_agg_partial(const float (&v)[NV], int m, float (*zp)[PCG_SEG_THREADS / 32][6],
+                                                int off) {
+  float a[NV];
+#pragma unroll
+  for (int c = 0; c < NV; ++c) {
+    a[c] = v[c];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a[c] = __fadd_rn(a[c], __shfl_down_sync(0xffffffffu, a[c], o));
+  }
+  const int wid = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    const int agg = 2 * m + wid / SEG_WPA;
+    if (agg < PCG_SEG_AGG_MAX)
+#pragma unroll
+      for (int c = 0; c < NV; ++c) zp[agg][wid % SEG_WPA][off + c] = a[c];
+  }
+}
+
+template <typename T, bool COARSE>
 __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
   using A = typename DotAcc<T>::type;
   constexpr int NW = PCG_SEG_THREADS / 32;
   __shared__ CgShared<T> cs;
+  // coarse state of the block's aggregates: warp partial sums of a pass,
+  // fresh g(w) and g(r) of the last reduction, the carried g(s)
+  __shared__ float s_zp[COARSE ? PCG_SEG_AGG_MAX : 1][PCG_SEG_THREADS / 32][6];
+  __shared__ float s_gw[COARSE ? PCG_SEG_AGG_MAX : 1][3];
+  __shared__ float s_gr[COARSE ? PCG_SEG_AGG_MAX : 1][3];
+  __shared__ float s_gs[COARSE ? PCG_SEG_AGG_MAX : 1][3];
   const GridCtx g{d.ctrl, d.partials, gridDim.x, d.wait_budget, d.bar_extra};
   unsigned epoch = 0;
   const int lane = threadIdx.x & 31;
@@ -1642,18 +1740,72 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
   // robot CG scalars: meaningful in lane 0 of warp 0
   double bb = 0.0, rr = 0.0, gamma = 0.0, alpha = 0.0, beta = 0.0;
   int it_done = 0;
+  // coarse bookkeeping
+  int rob = 0, r0 = 0, ga0 = 0, na_r = 0, na_b = 0;
+  const float* ainv = nullptr;
+  if constexpr (COARSE) {
+    rob = d.seg_robot[b];
+    r0 = d.robot_row[rob];
+    na_r = d.seg_agg_base[rob + 1] - d.seg_agg_base[rob];
+    ga0 = d.seg_agg_base[rob] + (lo - r0) / DF_AGG_ROWS;
+    na_b = (hi - lo + DF_AGG_ROWS - 1) / DF_AGG_ROWS;
+    ainv = d.seg_ainv + d.seg_ainv_off[rob] + (size_t)((lo - r0) / DF_AGG_ROWS) * na_r;
+  }
+  // the block's aggregate sums of this pass into the global exchange array
+  // (call after a __syncthreads that follows the pass); which = 0 w, 1 r
+  auto agg_store = [&](int which) {
+    for (int k = threadIdx.x; k < na_b * 3; k += blockDim.x) {
+      const int a = k / 3, c = k % 3;
+      float t = s_zp[a][0][3 * which + c];
+#pragma unroll
+      for (int q = 1; q < SEG_WPA; ++q) t = __fadd_rn(t, s_zp[a][q][3 * which + c]);
+      d.seg_aggsum[6 * (size_t)(ga0 + a) + 3 * which + c] = t;
+    }
+  };
+  // g = A_c^-1 Z^T v for the block's aggregates from the robot's exchanged
+  // sums (after the reduction made them visible): which = 0 w into s_gw, 1 r
+  // into s_gr; one thread per (aggregate, column, which), robot-order sums
+  auto agg_coarse = [&]() {
+    const int base = d.seg_agg_base[rob];
+    for (int k = threadIdx.x; k < na_b * 6; k += blockDim.x) {
+      const int a = k / 6, which = (k % 6) / 3, c = k % 3;
+      const float* row = ainv + (size_t)a * na_r;
+      float t = 0.0f;
+      for (int j = 0; j < na_r; ++j)
+        t = __fmaf_rn(row[j], __ldcg(&d.seg_aggsum[6 * (size_t)(base + j) + 3 * which + c]), t);
+      if (which == 0)
+        s_gw[a][c] = t;
+      else
+        s_gr[a][c] = t;
+    }
+  };
 
   double a0[2] = {0.0, 0.0};
-  for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
-    const T dg = d.diag[i];
-    double rv[3];
-    residual_row_f64(d, i, dg, rv, a0);
-    R4<T> ri, ui;
-    ri.x = (T)rv[0]; ri.y = (T)rv[1]; ri.z = (T)rv[2]; ri.w = T(0);
-    ui.x = ri.x / dg; ui.y = ri.y / dg; ui.z = ri.z / dg; ui.w = T(0);
-    r[i] = ri;
-    u[i] = ui;
-    dx[i] = zero;
+  for (int i = lo + (int)threadIdx.x, m = 0; i < hi || (COARSE && m * (int)blockDim.x < hi - lo);
+       i += blockDim.x, ++m) {
+    float rz[3] = {0.0f, 0.0f, 0.0f};
+    if (i < hi) {
+      const T dg = d.diag[i];
+      double rv[3];
+      residual_row_f64(d, i, dg, rv, a0);
+      R4<T> ri, ui;
+      ri.x = (T)rv[0]; ri.y = (T)rv[1]; ri.z = (T)rv[2]; ri.w = T(0);
+      ui.x = ri.x / dg; ui.y = ri.y / dg; ui.z = ri.z / dg; ui.w = T(0);
+      r[i] = ri;
+      u[i] = ui;
+      dx[i] = zero;
+      rz[0] = (float)ri.x; rz[1] = (float)ri.y; rz[2] = (float)ri.z;
+    }
+    if constexpr (COARSE) {
+      const float wz[3] = {0.0f, 0.0f, 0.0f};
+      seg_agg_partial<3>(wz, m, s_zp, 0);
+      seg_agg_partial<3>(rz, m, s_zp, 3);
+    }
+  }
+  if constexpr (COARSE) {
+    __syncthreads();
+    agg_store(0);
+    agg_store(1);
   }
   {
     double bs[2], t[2];
@@ -1672,18 +1824,51 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
   }
   if (cs.flag == CG_ABORT) return;
   bool done = cs.flag != CG_CONTINUE;
+  if constexpr (COARSE) {
+    // u_0 = D^-1 r_0 + Z g(r_0): one more pass and a grid barrier before the
+    // first SpMV reads the neighbours' u
+    if (!done) agg_coarse();
+    __syncthreads();
+    if (!done)
+      for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
+        const int a = (i - lo) / DF_AGG_ROWS;
+        R4<T> ui = u[i];
+        ui.x += (T)s_gr[a][0];
+        ui.y += (T)s_gr[a][1];
+        ui.z += (T)s_gr[a][2];
+        u[i] = ui;
+      }
+    if (!grid_barrier(g, epoch, &cs.ok)) return;
+  }
   A a1[2] = {acc_zero<A>(), acc_zero<A>()};
   if (!done) {
-    for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
-      const T dg = d.diag[i];
-      const R4<T> ui = u[i], ri = r[i];
-      T ax, ay, az;
-      spmv_row(d, i, u, dg, ui, ax, ay, az);
-      R4<T> wi;
-      wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
-      w[i] = wi;
-      a1[0] = acc_add(a1[0], dot3(ri.x, ri.y, ri.z, ui.x, ui.y, ui.z));
-      a1[1] = acc_add(a1[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
+    for (int i = lo + (int)threadIdx.x, m = 0; i < hi || (COARSE && m * (int)blockDim.x < hi - lo);
+         i += blockDim.x, ++m) {
+      float wz[3] = {0.0f, 0.0f, 0.0f}, rz[3] = {0.0f, 0.0f, 0.0f};
+      if (i < hi) {
+        const T dg = d.diag[i];
+        const R4<T> ui = u[i], ri = r[i];
+        T ax, ay, az;
+        spmv_row(d, i, u, dg, ui, ax, ay, az);
+        R4<T> wi;
+        wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
+        w[i] = wi;
+        a1[0] = acc_add(a1[0], dot3(ri.x, ri.y, ri.z, ui.x, ui.y, ui.z));
+        a1[1] = acc_add(a1[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
+        wz[0] = (float)ax; wz[1] = (float)ay; wz[2] = (float)az;
+        rz[0] = (float)ri.x; rz[1] = (float)ri.y; rz[2] = (float)ri.z;
+      }
+      if constexpr (COARSE) {
+        seg_agg_partial<3>(wz, m, s_zp, 0);
+        seg_agg_partial<3>(rz, m, s_zp, 3);
+      }
+    }
+  }
+  if constexpr (COARSE) {
+    __syncthreads();
+    if (!done) {
+      agg_store(0);
+      agg_store(1);
     }
   }
   {
@@ -1705,39 +1890,66 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
   }
   if (cs.flag == CG_ABORT) return;
   T ta = cs.ta, tb = T(0);
+  if constexpr (COARSE) {
+    if (!done) agg_coarse();  // g(w_0), g(r_0)
+    __syncthreads();
+  }
   bool first = true;
   int it = 1;
   for (;; ++it) {
+    if constexpr (COARSE) {
+      // g(s_k) = g(w_k) + beta_k g(s_k-1); g(r_k+1) = g(r_k) - alpha_k g(s_k)
+      if (!done)
+        for (int k = threadIdx.x; k < na_b * 3; k += blockDim.x) {
+          const int a = k / 3, c = k % 3;
+          const float gs = first ? s_gw[a][c] : s_gw[a][c] + (float)tb * s_gs[a][c];
+          s_gs[a][c] = gs;
+          s_gr[a][c] = s_gr[a][c] - (float)ta * gs;
+        }
+      __syncthreads();
+    }
     // r.u and r.r of the new residual are formed in the update pass, so the
     // SpMV pass does not read r again (same values, same order of rows)
     A a_ru = acc_zero<A>(), a_rr = acc_zero<A>();
     if (!done) {
-      for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
-        const R4<T> ui = u[i], wi = w[i];
-        R4<T> pi, si;
-        if (first) {
-          pi = ui;
-          si = wi;
-        } else {
-          const R4<T> po = p[i], so = s[i];
-          pi.x = ui.x + tb * po.x; pi.y = ui.y + tb * po.y; pi.z = ui.z + tb * po.z;
-          si.x = wi.x + tb * so.x; si.y = wi.y + tb * so.y; si.z = wi.z + tb * so.z;
+      for (int i = lo + (int)threadIdx.x, m = 0; i < hi || (COARSE && m * (int)blockDim.x < hi - lo);
+           i += blockDim.x, ++m) {
+        float rz[3] = {0.0f, 0.0f, 0.0f};
+        if (i < hi) {
+          const R4<T> ui = u[i], wi = w[i];
+          R4<T> pi, si;
+          if (first) {
+            pi = ui;
+            si = wi;
+          } else {
+            const R4<T> po = p[i], so = s[i];
+            pi.x = ui.x + tb * po.x; pi.y = ui.y + tb * po.y; pi.z = ui.z + tb * po.z;
+            si.x = wi.x + tb * so.x; si.y = wi.y + tb * so.y; si.z = wi.z + tb * so.z;
+          }
+          pi.w = T(0);
+          si.w = T(0);
+          p[i] = pi;
+          s[i] = si;
+          R4<T> di = dx[i], ri = r[i];
+          di.x += ta * pi.x; di.y += ta * pi.y; di.z += ta * pi.z;
+          ri.x -= ta * si.x; ri.y -= ta * si.y; ri.z -= ta * si.z;
+          dx[i] = di;
+          r[i] = ri;
+          const T dg = d.diag[i];
+          R4<T> un;
+          un.x = ri.x / dg; un.y = ri.y / dg; un.z = ri.z / dg; un.w = T(0);
+          if constexpr (COARSE) {
+            const int a = (i - lo) / DF_AGG_ROWS;
+            un.x += (T)s_gr[a][0];
+            un.y += (T)s_gr[a][1];
+            un.z += (T)s_gr[a][2];
+          }
+          u[i] = un;
+          a_ru = acc_add(a_ru, dot3(ri.x, ri.y, ri.z, un.x, un.y, un.z));
+          a_rr = acc_add(a_rr, dot3(ri.x, ri.y, ri.z, ri.x, ri.y, ri.z));
+          rz[0] = (float)ri.x; rz[1] = (float)ri.y; rz[2] = (float)ri.z;
         }
-        pi.w = T(0);
-        si.w = T(0);
-        p[i] = pi;
-        s[i] = si;
-        R4<T> di = dx[i], ri = r[i];
-        di.x += ta * pi.x; di.y += ta * pi.y; di.z += ta * pi.z;
-        ri.x -= ta * si.x; ri.y -= ta * si.y; ri.z -= ta * si.z;
-        dx[i] = di;
-        r[i] = ri;
-        const T dg = d.diag[i];
-        R4<T> un;
-        un.x = ri.x / dg; un.y = ri.y / dg; un.z = ri.z / dg; un.w = T(0);
-        u[i] = un;
-        a_ru = acc_add(a_ru, dot3(ri.x, ri.y, ri.z, un.x, un.y, un.z));
-        a_rr = acc_add(a_rr, dot3(ri.x, ri.y, ri.z, ri.x, ri.y, ri.z));
+        if constexpr (COARSE) seg_agg_partial<3>(rz, m, s_zp, 3);
       }
     }
     if (!grid_barrier(g, epoch, &cs.ok)) return;
@@ -1746,15 +1958,28 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
     if ((int)n_done >= d.n_robots || it > d.max_iter) break;
     A a2[3] = {a_ru, acc_zero<A>(), a_rr};
     if (!done) {
-      for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
-        const T dg = d.diag[i];
-        const R4<T> ui = u[i];
-        T ax, ay, az;
-        spmv_row(d, i, u, dg, ui, ax, ay, az);
-        R4<T> wi;
-        wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
-        w[i] = wi;
-        a2[1] = acc_add(a2[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
+      for (int i = lo + (int)threadIdx.x, m = 0; i < hi || (COARSE && m * (int)blockDim.x < hi - lo);
+           i += blockDim.x, ++m) {
+        float wz[3] = {0.0f, 0.0f, 0.0f};
+        if (i < hi) {
+          const T dg = d.diag[i];
+          const R4<T> ui = u[i];
+          T ax, ay, az;
+          spmv_row(d, i, u, dg, ui, ax, ay, az);
+          R4<T> wi;
+          wi.x = ax; wi.y = ay; wi.z = az; wi.w = T(0);
+          w[i] = wi;
+          a2[1] = acc_add(a2[1], dot3(ax, ay, az, ui.x, ui.y, ui.z));
+          wz[0] = (float)ax; wz[1] = (float)ay; wz[2] = (float)az;
+        }
+        if constexpr (COARSE) seg_agg_partial<3>(wz, m, s_zp, 0);
+      }
+    }
+    if constexpr (COARSE) {
+      __syncthreads();
+      if (!done) {
+        agg_store(0);
+        agg_store(1);
       }
     }
     {
@@ -1787,6 +2012,10 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
     ta = cs.ta;
     tb = cs.tb;
     first = false;
+    if constexpr (COARSE) {
+      if (!done) agg_coarse();  // g(w_k+1) and a fresh g(r_k+1)
+      __syncthreads();
+    }
   }
   if (!done && lead) {
     it_done = d.max_iter;
@@ -2046,27 +2275,7 @@ __global__ void k_finalize(Dev<T> d) {
   double a = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a += d.e_partials[i];
   const double t = block_sum(a, sh);
-  if (threadIdx.x == 0) {
-    Ctrl* c = d.ctrl;
-    IterRec* rec = d.hist + (c->iter % d.hist_cap);
-    rec->energy = t;
-    if (!isfinite(t) && d.stats) c->status |= ST_NONFINITE;
-    c->iter += 1;
-    c->n_cast = 0;
-    for (int j = 0; j < 3; ++j) {
-      c->box_lo[j] = 0x7FFFFFFFFFFFFFFFLL;
-      c->box_hi[j] = (long long)0x8000000000000000ULL;
-    }
-    IterRec* nx = d.hist + (c->iter % d.hist_cap);
-    nx->energy = 0.0;
-    nx->pcg_rel_residual = 0.0;
-    nx->n_self_pairs = 0;
-    nx->n_obstacle_pairs = 0;
-    nx->n_springs = 0;
-    nx->pcg_iters = 0;
-    nx->knot_sig = 0;
-    nx->spring_sig = 0;
-  }
+  if (threadIdx.x == 0) finalize_iteration(d, t);
 }
 
 template <typename T>
@@ -2080,22 +2289,38 @@ __global__ void k_gather_positions(const R4<T>* X, const int* int_of_user, int n
 }
 
 // ---------------------------------------------------------------- launchers
-int local_blocks(int n_t) { return (n_t + LOCAL_THREADS - 1) / LOCAL_THREADS; }
-int rhs_blocks(int n_free) { return (n_free + RHS_THREADS - 1) / RHS_THREADS; }
+int local_blocks(int n_t, int threads) { return (n_t + threads - 1) / threads; }
+int rhs_blocks(int n_free, int threads) { return (n_free + threads - 1) / threads; }
+int local_blocks(int n_t) { return local_blocks(n_t, LOCAL_THREADS); }
+int rhs_blocks(int n_free) { return rhs_blocks(n_free, RHS_THREADS); }
 
+// The block sizes are launch-shape choices of the autotuner: each allowed
+// size is its own instantiation (compiled with its own launch bound).
 template <typename T>
 void launch_local(const Dev<T>& d, cudaStream_t st) {
   if (d.n_t == 0) return;
-  if (sizeof(T) == 4)
-    k_local<T, 4><<<local_blocks(d.n_t), LOCAL_THREADS, 0, st>>>(d);
+  const int bs = d.local_threads > 0 ? d.local_threads : LOCAL_THREADS;
+  const int nb = local_blocks(d.n_t, bs);
+  constexpr int SW = sizeof(T) == 4 ? 4 : 6;
+  if (bs == 64)
+    k_local<T, SW, 64><<<nb, 64, 0, st>>>(d);
+  else if (bs == 256)
+    k_local<T, SW, 256><<<nb, 256, 0, st>>>(d);
   else
-    k_local<T, 6><<<local_blocks(d.n_t), LOCAL_THREADS, 0, st>>>(d);
+    k_local<T, SW, 128><<<nb, 128, 0, st>>>(d);
 }
 
 template <typename T>
 void launch_rhs(const Dev<T>& d, cudaStream_t st) {
   if (d.n_free == 0) return;
-  k_rhs<T><<<rhs_blocks(d.n_free), RHS_THREADS, 0, st>>>(d);
+  const int bs = d.rhs_threads > 0 ? d.rhs_threads : RHS_THREADS;
+  const int nb = rhs_blocks(d.n_free, bs);
+  if (bs == 128)
+    k_rhs<T, 128><<<nb, 128, 0, st>>>(d);
+  else if (bs == 512)
+    k_rhs<T, 512><<<nb, 512, 0, st>>>(d);
+  else
+    k_rhs<T, 256><<<nb, 256, 0, st>>>(d);
 }
 
 template <typename T>
@@ -2238,7 +2463,8 @@ int pcg_seg_max_blocks() {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_seg<T>, PCG_SEG_THREADS, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_seg<T, std::is_same<T, float>::value>,
+                                                PCG_SEG_THREADS, 0);
   return sms * per;
 }
 
@@ -2254,7 +2480,10 @@ cudaError_t launch_pcg_seg(const Dev<T>& d, int blocks, cudaStream_t st) {
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_pcg_seg<T>, d);
+  if constexpr (std::is_same<T, float>::value) {
+    if (d.seg_coarse) return cudaLaunchKernelEx(&cfg, k_pcg_seg<T, true>, d);
+  }
+  return cudaLaunchKernelEx(&cfg, k_pcg_seg<T, false>, d);
 }
 
 template int pcg_seg_max_blocks<float>();

@@ -103,14 +103,15 @@ def test_full_batch_of_256_fingers_properties():
     assert all(h["pcg_rel_residual"] <= 1e-6 for h in hist)
     X = sim.positions()
     assert np.all(np.isfinite(X))
-    # spot check: three robots against their own plain GPU runs with the same
-    # (Jacobi) preconditioner as the batch's segmented PCG: the two-level
-    # preconditioner of the single-robot kernel converges to the same
-    # tolerance along other iterates, and over several iterations with
-    # contacts the two trajectories differ by more than 1e-5 of the diagonal
+    # spot check: three robots against their own plain GPU runs, both with
+    # the two-level preconditioner (the batch's segmented kernel applies the
+    # same per-robot coarse correction, over the same 128-row aggregates, as
+    # the single-robot kernel; with different preconditioners the iterates
+    # differ and over several iterations with contacts the two trajectories
+    # drift apart by more than 1e-5 of the diagonal)
     vo, _ = _offsets(batch)
     for r in (0, 97, 255):
-        one = casim.Sim(batch[r], pcg_precond=1)
+        one = casim.Sim(batch[r])
         one.step(5)
         assert one.sync() == 0
         err = np.abs(X[vo[r]:vo[r + 1]] - one.positions()).max()
