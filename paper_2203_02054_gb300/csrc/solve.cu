@@ -359,6 +359,38 @@ __device__ __forceinline__ DW dot3(float a0, float a1, float a2, float b0, float
   return z;
 }
 
+// Double-word product: the exact product of the high parts by TwoProd (FMA),
+// the cross terms added in FP32, renormalised by Fast2Sum (relative error a
+// few u^2; the neglected lo * lo term is below u^2 of the result).
+__device__ __forceinline__ DW dw_mul(DW a, DW b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  DW z;
+  fast_two_sum_f(p, e, z.hi, z.lo);
+  return z;
+}
+__device__ __forceinline__ DW dw_neg(DW a) { return DW{-a.hi, -a.lo}; }
+
+// Double-word quotient by one correction step: q = a.hi / b.hi in FP32, the
+// remainder a - q b formed from the exact product q * b.hi (TwoProd; a.hi -
+// q b.hi is exact by Sterbenz's lemma, q b.hi being within an ulp of a.hi)
+// and the low parts, then q + remainder / b.hi renormalised (relative error a
+// few u^2 for b not near the FP32 range limits).
+__device__ __forceinline__ DW dw_div(DW a, DW b) {
+  const float q = __fdiv_rn(a.hi, b.hi);
+  const float p = __fmul_rn(q, b.hi);
+  const float pe = __fmaf_rn(q, b.hi, -p);
+  float r = __fsub_rn(a.hi, p);
+  r = __fsub_rn(r, pe);
+  r = __fadd_rn(r, a.lo);
+  r = __fmaf_rn(-q, b.lo, r);
+  DW z;
+  fast_two_sum_f(q, __fdiv_rn(r, b.hi), z.hi, z.lo);
+  return z;
+}
+
 __device__ __forceinline__ double dot3(double a0, double a1, double a2, double b0, double b1, double b2) {
   return fma(a2, b2, fma(a1, b1, a0 * b0));
 }
@@ -520,6 +552,38 @@ __device__ __forceinline__ int cg_scalars_warp(const double (&t)[3], double bb_l
   beta = __shfl_sync(full, quo, 1);
   alpha = __shfl_sync(full, quo, 0);
   gamma = gnew;
+  return CG_CONTINUE;
+}
+
+// The same CG scalars in double-word arithmetic on the FP32 pipes, for the
+// dataflow kernel (its dot sums are double words already): an FP64 division
+// and the FP64 products around it form a long dependent chain on this part,
+// which every CG iteration waits for.  The state (gamma, alpha) lives in
+// shared memory (st[0], st[1]); the stopping test compares ||r||^2 with the
+// FP32 threshold thr = tol^2 ||b||^2.  Inputs from lane 0, by all of warp 0;
+// lane 0 stores the new state and rr (st[2]).  Outputs: alpha_k and beta_k
+// rounded to FP32 (valid in every lane).
+__device__ __forceinline__ int cg_scalars_dw(const DW (&t)[3], float thr, DW* st, float& ta, float& tb) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const DW gnew{__shfl_sync(full, t[0].hi, 0), __shfl_sync(full, t[0].lo, 0)};
+  const DW delta{__shfl_sync(full, t[1].hi, 0), __shfl_sync(full, t[1].lo, 0)};
+  const DW rr{__shfl_sync(full, t[2].hi, 0), __shfl_sync(full, t[2].lo, 0)};
+  if (lane == 0) st[2] = rr;
+  if (!isfinite(gnew.hi) || !isfinite(delta.hi) || !isfinite(rr.hi)) return CG_NONFINITE;
+  if (rr.hi <= thr) return CG_DONE;
+  const DW g = st[0], a = st[1];
+  const DW q = dw_mul(g, a);
+  const DW num = lane == 1 ? gnew : dw_mul(gnew, q);
+  const DW den = lane == 1 ? g : dw_add_sloppy(dw_mul(delta, q), dw_neg(dw_mul(gnew, gnew)));
+  const DW quo = dw_div(num, den);
+  const DW alpha{__shfl_sync(full, quo.hi, 0), __shfl_sync(full, quo.lo, 0)};
+  tb = __shfl_sync(full, quo.hi, 1);
+  ta = alpha.hi;
+  if (lane == 0) {
+    st[0] = gnew;
+    st[1] = alpha;
+  }
   return CG_CONTINUE;
 }
 
@@ -1359,7 +1423,9 @@ template <int MAXW, bool COARSE>
 __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   constexpr int NW = PCG_DF_THREADS / 32;
   __shared__ CgShared<float> cs;
-  __shared__ double sc[5];  // bb, rr, gamma, alpha, beta: used by lane 0 of warp 0 only
+  __shared__ double sc[2];  // bb, rr of the first reduction: used by lane 0 of warp 0 only
+  __shared__ DW s_st[3];    // gamma, alpha, rr of the CG recurrence (double words)
+  __shared__ float s_thr;   // tol^2 ||b||^2 in FP32
   __shared__ double s_es;   // the iteration's spring energy (fused right-hand side)
   extern __shared__ unsigned long long halo[];  // 2 tagged words per halo row (+ coarse rows)
   const int lane = threadIdx.x & 31;
@@ -1509,6 +1575,7 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
           sc[0] = t[0];
           sc[1] = t[1];
           s_es = t[2];
+          s_thr = (float)(d.tol2 * t[0]);
           cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
         }
       }
@@ -1520,6 +1587,7 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
               sc[0] = t[0];
               sc[1] = t[1];
               s_es = t[2];
+              s_thr = (float)(d.tol2 * t[0]);
               cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
             }
           }))
@@ -1555,10 +1623,10 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       auto first_scalars = [&](bool ok) {
         if (lane == 0) {
           if (ok) {
-            const double g = acc_to_f64(t[0]);
-            sc[2] = g;
-            sc[3] = g / acc_to_f64(t[1]);
-            cs.ta = (float)sc[3];
+            const DW a = dw_div(t[0], t[1]);
+            s_st[0] = t[0];
+            s_st[1] = a;
+            cs.ta = a.hi;
           }
           cs.flag = ok ? CG_CONTINUE : CG_ABORT;
         }
@@ -1603,20 +1671,13 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
         ++re;
         auto scalars = [&](bool ok) {
           int f = CG_ABORT;
-          double gamma = sc[2], alpha = sc[3], beta = sc[4], rr = sc[1];
-          if (ok) {
-            const double t[3] = {acc_to_f64(tw[0]), acc_to_f64(tw[1]), acc_to_f64(tw[2])};
-            f = cg_scalars_warp(t, sc[0], d.tol2, gamma, alpha, beta, rr);
-          }
+          float fa = 0.0f, fb = 0.0f;
+          if (ok) f = cg_scalars_dw(tw, s_thr, s_st, fa, fb);
           if (lane == 0) {
             if (ok) {
               if (f == CG_NONFINITE && blockIdx.x == 0) set_status(d.ctrl, ST_NONFINITE);
-              sc[1] = rr;
-              sc[2] = gamma;
-              sc[3] = alpha;
-              sc[4] = beta;
-              cs.ta = (float)alpha;
-              cs.tb = (float)beta;
+              cs.ta = fa;
+              cs.tb = fb;
             }
             cs.flag = f;
           }
@@ -1667,7 +1728,8 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_down_sync(0xffffffffu, e_loc, o);
     }
     if (lane == 0) {
-      write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, sc[1], sc[0]);
+      const double rr = it > 0 ? (double)s_st[2].hi + (double)s_st[2].lo : sc[1];
+      write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, sc[0]);
       if (d.rhs_in_pcg) finalize_iteration(d, d.stats ? e_loc + s_es : 0.0);
     }
   }
