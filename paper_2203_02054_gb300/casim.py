@@ -457,7 +457,7 @@ class Sim:
 
     def __init__(self, mesh, precision=None, collision=None, stream: int = 0, stats: int = 1,
                  pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0,
-                 pcg_kernel=0, debug_flags=0, pcg_precond=0, broad_phase=0, local_block=0, rhs_block=0,
+                 pcg_kernel=0, debug_flags=0, pcg_precond=0, broad_phase=None, local_block=0, rhs_block=0,
                  narrow_block=0, cell_scale=1.0, tuned=False):
         load_library()
         self.batch = None
@@ -482,7 +482,8 @@ class Sim:
         p.pcg_kernel = pcg_kernel
         p.debug_flags = debug_flags
         p.pcg_precond = pcg_precond
-        p.broad_phase = broad_phase
+        if broad_phase is not None:
+            p.broad_phase = broad_phase
         p.local_block = local_block
         p.rhs_block = rhs_block
         p.narrow_block = narrow_block

@@ -587,7 +587,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->partials = sim->dalloc<double>(2 * 4 * (size_t)std::max(sim->pcg_grid, 1));
   if (sim->pcg_variant == 5) {
     sim->df_u = sim->dalloc<unsigned long long>(4 * (size_t)std::max(n_free, 1));
-    sim->df_p = sim->dalloc<unsigned long long>(2 * 16 * ((size_t)sim->pcg_grid + 1));
+    sim->df_p = sim->dalloc<unsigned long long>((size_t)PCG_DF_REPLICAS * 2 * 16 * ((size_t)sim->pcg_grid + 1));
     if (sim->n_agg > 0) sim->cg_ainv = sim->dalloc<float>((size_t)sim->n_agg * sim->n_agg);
     sim->halo_ptr = sim->dalloc<int>(sim->halo_ptr_h.size());
     sim->halo_rows = sim->dalloc<int>(std::max<size_t>(sim->halo_rows_h.size(), 1));

@@ -21,6 +21,7 @@ static constexpr int PCG_CL_THREADS = 1024;
 static constexpr int PCG_SEG_THREADS = 256;
 static constexpr int PCG_SEG_AGG_MAX = 64;  // aggregates per block of the segmented PCG's coarse correction
 static constexpr int PCG_DF_THREADS = 384;
+static constexpr int PCG_DF_REPLICAS = 4;  // copies of the dataflow PCG's reduction slots
 static constexpr size_t PCG_DF_HALO_MAX_BYTES = 160 * 1024;  // halo words in shared memory
 static constexpr int PCG_CL_SIZE = 16;   // CTAs per cluster (non-portable size)
 

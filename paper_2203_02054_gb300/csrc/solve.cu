@@ -1244,22 +1244,36 @@ __device__ __forceinline__ void agg_warp_sums(const float (&w)[3], const float (
     for (int c = 0; c < 6; ++c) sz[threadIdx.x >> 5][c] = a[c];
 }
 
-// Warp 0: lane 0 stores the block's sums bs and its aggregates' sums (warps
-// 4k..4k+3 of aggregate k, added in order) as one slot of epoch e, arrives on
-// the grid counter and waits for the round to complete.  Returns false
+// The slots are stored in PCG_DF_REPLICAS copies and block b reads copy
+// b % PCG_DF_REPLICAS: every block reads every slot once per round, and
+// spreading those reads over copies at different addresses (different L2
+// slices) shortens the queue of reads of one slot.
+__device__ __forceinline__ unsigned long long* df_slots(const Dev<float>& d, unsigned e, int copy) {
+  const size_t nb = gridDim.x;
+  return d.df_p + ((size_t)copy * 2 + (e & 1u)) * DF_SLOT_C * (nb + 1);
+}
+__device__ __forceinline__ double shfl0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+__device__ __forceinline__ DW shfl0(DW v) {
+  return DW{__shfl_sync(0xffffffffu, v.hi, 0), __shfl_sync(0xffffffffu, v.lo, 0)};
+}
+
+// Warp 0: lanes 0..PCG_DF_REPLICAS-1 store the block's sums bs (valid in
+// lane 0) and its aggregates' sums (warps 4k..4k+3 of aggregate k, added in
+// order) as one slot of epoch e, one copy each; lane 0 then arrives on the
+// grid counter and waits for the round to complete.  Returns false
 // (warp-uniform) when the wait gave up or another block aborted.
 template <typename S>
-__device__ __forceinline__ bool df_publish_c(const Dev<float>& d, unsigned e, const S (&bs)[3],
+__device__ __forceinline__ bool df_publish_c(const Dev<float>& d, unsigned e, const S (&bs_l0)[3],
                                              const float (*sz)[6]) {
   const int lane = threadIdx.x & 31;
   const int nb = gridDim.x;
-  unsigned long long* buf = d.df_p + (size_t)(e & 1u) * DF_SLOT_C * (size_t)nb;
   const unsigned long long tag = df_tag(e);
   int arrived = 1;
-  if (lane == 0) {
+  const S bs[3] = {shfl0(bs_l0[0]), shfl0(bs_l0[1]), shfl0(bs_l0[2])};
+  if (lane < PCG_DF_REPLICAS) {
     unsigned long long w[4];
     df_pack(tag, bs, w);
-    unsigned long long* slot = buf + DF_SLOT_C * (size_t)blockIdx.x;
+    unsigned long long* slot = df_slots(d, e, lane) + DF_SLOT_C * (size_t)blockIdx.x;
     st_v2_relaxed(slot, w[0], w[1]);
     st_v2_relaxed(slot + 2, w[2], w[3]);
     constexpr int WPA = DF_AGG_ROWS / 32;
@@ -1279,6 +1293,9 @@ __device__ __forceinline__ bool df_publish_c(const Dev<float>& d, unsigned e, co
       df_pack_u(tag, z[3], z[4], z[5], a, b);
       st_v2_relaxed(slot + 6 + 4 * k, a, b);
     }
+  }
+  __syncwarp();
+  if (lane == 0) {
     const unsigned add = blockIdx.x == 0 ? (0x80000000u - ((unsigned)nb - 1u + d.bar_extra)) : 1u;
     atomicAdd(&d.ctrl->bar_count, add);
     const unsigned want = (e & 1u) << 31;
@@ -1300,7 +1317,7 @@ template <typename S>
 __device__ __forceinline__ bool df_gather_dots_c(const Dev<float>& d, unsigned e, S (&tot)[3]) {
   const int lane = threadIdx.x & 31;
   const int nb = gridDim.x;
-  const unsigned long long* buf = d.df_p + (size_t)(e & 1u) * DF_SLOT_C * (size_t)nb;
+  const unsigned long long* buf = df_slots(d, e, blockIdx.x % PCG_DF_REPLICAS);
   const unsigned long long tag = df_tag(e);
   unsigned long long w[DF_MAXQ][4];
 #pragma unroll
@@ -1368,7 +1385,7 @@ __device__ __forceinline__ void df_gather_coarse(const Dev<float>& d, unsigned e
 #pragma unroll
     for (int cc = 0; cc < 6; ++cc) c[i][cc] = 0.0f;
   if (t < nb) {
-    const unsigned long long* slot = d.df_p + (size_t)(e & 1u) * DF_SLOT_C * (size_t)nb + DF_SLOT_C * (size_t)t + 4;
+    const unsigned long long* slot = df_slots(d, e, blockIdx.x % PCG_DF_REPLICAS) + DF_SLOT_C * (size_t)t + 4;
     const unsigned long long tag = df_tag(e);
     unsigned long long w[4 * DF_AGG];
 #pragma unroll
@@ -1479,30 +1496,36 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   // thread of the block: the block copies its halo rows of epoch e into
   // shared memory (re-reading rows whose words are not yet current), then
   // each active row multiplies from shared memory.
+  // Each halo row is unpacked once, into a float4 in place of its two words,
+  // so the multiply reads one 16-byte shared-memory word per entry.
+  float4* const halo4 = reinterpret_cast<float4*>(halo);
   auto spmv = [&](unsigned e, const float (&self)[3], float (&ax)[3]) {
     const unsigned long long* buf = d.df_u + (size_t)(e & 1u) * ustride;
     const unsigned long long tag = df_tag(e);
-    bool stale = false;
+    unsigned stale = 0;  // bit q: this thread's row threadIdx.x + q * PCG_DF_THREADS is not yet current
 #pragma unroll 4
-    for (int k = threadIdx.x; k < nh; k += PCG_DF_THREADS) {
+    for (int k = threadIdx.x, q = 0; k < nh; k += PCG_DF_THREADS, ++q) {
       unsigned long long w0, w1;
       ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
-      halo[2 * k] = w0;
-      halo[2 * k + 1] = w1;
-      stale |= !(df_has(w0, tag) && df_has(w1, tag));
+      if (df_has(w0, tag) && df_has(w1, tag)) {
+        float vx, vy, vz;
+        df_unpack_u(w0, w1, vx, vy, vz);
+        halo4[k] = make_float4(vx, vy, vz, 0.0f);
+      } else {
+        stale |= 1u << q;
+      }
     }
     if (stale) {
       DfWait wt;
-      for (int k = threadIdx.x; k < nh; k += PCG_DF_THREADS) {
+      for (int k = threadIdx.x, q = 0; k < nh; k += PCG_DF_THREADS, ++q) {
+        if (!(stale & (1u << q))) continue;
         unsigned long long w0, w1;
-        w0 = halo[2 * k];
-        w1 = halo[2 * k + 1];
-        while (!(df_has(w0, tag) && df_has(w1, tag))) {
-          if (!wt.again(d.ctrl, d.wait_budget)) break;
+        do {
           ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
-        }
-        halo[2 * k] = w0;
-        halo[2 * k + 1] = w1;
+        } while (!(df_has(w0, tag) && df_has(w1, tag)) && wt.again(d.ctrl, d.wait_budget));
+        float vx, vy, vz;
+        df_unpack_u(w0, w1, vx, vy, vz);
+        halo4[k] = make_float4(vx, vy, vz, 0.0f);
       }
       // a wait that gave up leaves the abort word raised: the next reduction
       // cannot complete, so every block leaves at its next reduction
@@ -1515,11 +1538,10 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
 #pragma unroll
       for (int j = 0; j < MAXW; ++j) {
         if (j < width) {
-          float vx, vy, vz;
-          df_unpack_u(halo[2 * lcol[j]], halo[2 * lcol[j] + 1], vx, vy, vz);
-          ax[0] += val[j] * vx;
-          ax[1] += val[j] * vy;
-          ax[2] += val[j] * vz;
+          const float4 v = halo4[lcol[j]];
+          ax[0] += val[j] * v.x;
+          ax[1] += val[j] * v.y;
+          ax[2] += val[j] * v.z;
         }
       }
     }
@@ -2439,7 +2461,8 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st) 
       // epoch-tagged words start from zero in every launch
       cudaError_t e = cudaMemsetAsync(d.df_u, 0, sizeof(unsigned long long) * 4 * (size_t)d.n_free, st);
       if (e == cudaSuccess)
-        e = cudaMemsetAsync(d.df_p, 0, sizeof(unsigned long long) * 2 * DF_SLOT_C * (size_t)(grid + 1), st);
+        e = cudaMemsetAsync(d.df_p, 0,
+                            sizeof(unsigned long long) * PCG_DF_REPLICAS * 2 * DF_SLOT_C * (size_t)(grid + 1), st);
       if (e != cudaSuccess) return e;
       cfg.dynamicSmemBytes = 16 * (size_t)d.halo_max;
       if (d.n_agg > 0) {

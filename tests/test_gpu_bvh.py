@@ -142,3 +142,39 @@ def test_tree_equals_hash_on_gripper_trajectory():
         got = outs[1]["pairs"][np.isin(outs[1]["pairs"][:, 0], sample)]
         assert expect.shape[0] > 10 and np.array_equal(got, expect), k
     run.close()
+
+
+def _stacked_tets(n_over):
+    """Tet 0 has one free vertex near the origin; tets 1..n_over are fixed,
+    slightly differently scaled copies of the unit corner tet, shifted so
+    that each strictly contains the free vertex."""
+    rest = [[0.001, 0.0013, 0.0017], [0.6, 0.0, 0.0], [0.0, 0.6, 0.0], [0.0, 0.0, 0.6]]
+    tets = [[0, 1, 2, 3]]
+    for k in range(1, n_over + 1):
+        s = 1.0 + 0.01 * k
+        base = len(rest)
+        for c in ([0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]):
+            rest.append([s * (c[0] - 0.2), s * (c[1] - 0.2), s * (c[2] - 0.2)])
+        tets.append([base, base + 1, base + 2, base + 3])
+    rest = np.array(rest, np.float64)
+    fixed = np.ones(rest.shape[0], np.uint8)
+    fixed[0] = 0
+    return synth.Mesh(name="stacked", rest=rest, tets=np.array(tets, np.int32),
+                      group=np.full(len(tets), -1, np.int32), fixed=fixed, alpha=np.zeros(0), n_iters=1)
+
+
+@pytest.mark.parametrize("max_pairs", [8, 16])
+def test_truncated_pair_list_keeps_the_smallest_tets(max_pairs):
+    """A vertex strictly inside 20 tets: both broad phases keep the max_pairs
+    smallest tet ids of the brute-force pair set and raise the truncation
+    warning."""
+    m = _stacked_tets(20)
+    expect = collision.self_pairs(m.rest, m.tets, np.array([0]))
+    assert expect.shape[0] == 20
+    for broad in (0, 1):
+        sim = casim.Sim(m, broad_phase=broad, max_pairs=max_pairs)
+        sim.step(1)
+        assert sim.sync() in (casim.CASIM_W_PCG_MAXIT, casim.CASIM_W_PAIRS_TRUNCATED), broad
+        assert sim.stats().status_bits & 16, broad  # a pair list was truncated
+        assert np.array_equal(sim.contacts()[0], expect[:max_pairs]), broad
+        sim.close()
