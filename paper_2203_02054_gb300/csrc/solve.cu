@@ -372,6 +372,34 @@ __device__ __forceinline__ DW dw_mul(DW a, DW b) {
   return z;
 }
 __device__ __forceinline__ DW dw_neg(DW a) { return DW{-a.hi, -a.lo}; }
+// s += x for an FP32 x: the high parts by TwoSum, its error into the low part
+// (renormalised once at the end by dw_norm).
+__device__ __forceinline__ void dw_acc(DW& s, float x) {
+  float h, e;
+  two_sum_f(s.hi, x, h, e);
+  s.hi = h;
+  s.lo = __fadd_rn(s.lo, e);
+}
+// s += a b, the product exact by TwoProd (FMA)
+__device__ __forceinline__ void dw_acc_prod(DW& s, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float pe = __fmaf_rn(a, b, -p);
+  float h, e;
+  two_sum_f(s.hi, p, h, e);
+  s.hi = h;
+  s.lo = __fadd_rn(s.lo, __fadd_rn(e, pe));
+}
+__device__ __forceinline__ DW dw_norm(DW s) {
+  DW z;
+  fast_two_sum_f(s.hi, s.lo, z.hi, z.lo);
+  return z;
+}
+// an FP64 value as a double word (hi = its FP32 rounding, lo = the rest rounded)
+__device__ __forceinline__ DW dw_from(double x) {
+  const float h = (float)x;
+  return DW{h, (float)(x - (double)h)};
+}
+
 
 // Double-word quotient by one correction step: q = a.hi / b.hi in FP32, the
 // remainder a - q b formed from the exact product q * b.hi (TwoProd; a.hi -
@@ -640,6 +668,70 @@ __device__ __forceinline__ void residual_row_f64(const Dev<T>& d, int i, T dg, d
   rv[2] = bi.z - az;
   a0[0] += bi.x * bi.x + bi.y * bi.y + bi.z * bi.z;
   a0[1] += rv[0] * rv[0] + rv[1] * rv[1] + rv[2] * rv[2];
+}
+
+// Right-hand side, diagonal and first residual of row i for FP32 positions,
+// in double-word arithmetic on the FP32 pipes (FP64 arithmetic is scarce on
+// this part, and these rows lie on every block's path to the first
+// reduction): b_i = sum of the row's P_e columns (FP32 values added by
+// TwoSum) + k mask_i c_i - bfix_i (the last two in FP64, only where nonzero),
+// A_ii = diagL_i + k mask_i, r_i = b_i - (A x)_i with the products exact
+// (TwoProd), and the row's ||b_i||^2, ||r_i||^2 and spring energy as double
+// words.  val holds the row's off-diagonal values (sliced ELL, `width`
+// entries); about 48 significant bits throughout, far beyond what the FP32
+// CG needs from its right-hand side.
+template <int MAXW>
+__device__ __forceinline__ void rhs_residual_row_dw(const Dev<float>& d, int i, const float (&val)[MAXW], int width,
+                                                    float& dg, float (&r)[3], DW (&a0)[3]) {
+  DW b[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+  const int k1 = d.inc_ptr[i + 1];
+#pragma unroll 4
+  for (int k = d.inc_ptr[i]; k < k1; ++k) {
+    const R4<float> p = d.P[d.inc[k]];
+    dw_acc(b[0], p.x);
+    dw_acc(b[1], p.y);
+    dw_acc(b[2], p.z);
+  }
+  const R4<double> sc = d.spring_c[i];
+  const double km = d.k_spring * sc.w;
+  const R4<double> bf = d.bfix[i];
+  const R4<float> xi = d.X[i];
+  dg = d.diagL[i] + (float)km;
+  DW es{0.0f, 0.0f};
+  if (km != 0.0) {
+    const double cv[3] = {sc.x, sc.y, sc.z};
+    for (int c = 0; c < 3; ++c) b[c] = dw_add_sloppy(dw_norm(b[c]), dw_from(km * cv[c]));
+    const double ex = (double)xi.x - sc.x, ey = (double)xi.y - sc.y, ez = (double)xi.z - sc.z;
+    es = dw_from(km * (ex * ex + ey * ey + ez * ez));
+  }
+  if (bf.x != 0.0 || bf.y != 0.0 || bf.z != 0.0) {
+    const double fv[3] = {bf.x, bf.y, bf.z};
+    for (int c = 0; c < 3; ++c) b[c] = dw_add_sloppy(dw_norm(b[c]), dw_neg(dw_from(fv[c])));
+  }
+  DW ax[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+  dw_acc_prod(ax[0], dg, xi.x);
+  dw_acc_prod(ax[1], dg, xi.y);
+  dw_acc_prod(ax[2], dg, xi.z);
+  const int sl = i >> 5, ln = i & 31;
+  const int base = d.sl_ptr[sl];
+#pragma unroll
+  for (int j = 0; j < MAXW; ++j) {
+    if (j < width) {
+      const R4<float> xc = d.X[d.sl_col[base + j * 32 + ln]];
+      dw_acc_prod(ax[0], val[j], xc.x);
+      dw_acc_prod(ax[1], val[j], xc.y);
+      dw_acc_prod(ax[2], val[j], xc.z);
+    }
+  }
+  DW rw[3];
+  for (int c = 0; c < 3; ++c) {
+    b[c] = dw_norm(b[c]);
+    rw[c] = dw_add_sloppy(b[c], dw_neg(dw_norm(ax[c])));
+    r[c] = rw[c].hi;
+  }
+  a0[0] = dot3(b[0].hi, b[1].hi, b[2].hi, b[0].hi, b[1].hi, b[2].hi);
+  a0[1] = dot3(rw[0].hi, rw[1].hi, rw[2].hi, rw[0].hi, rw[1].hi, rw[2].hi);
+  a0[2] = es;
 }
 
 // Streaming variant: any number of rows per thread (grid-stride); vectors in
@@ -1455,8 +1547,6 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   float val[MAXW];
   int width = 0;
   float dg = 1.0f;
-  R4<double> brow{0.0, 0.0, 0.0, 0.0};  // this row's right-hand side (formed here when fused)
-  double es = 0.0;                      // this row's spring energy (fused)
   if (act) {
     const int sl = i >> 5, ln = i & 31;
     const int base = d.sl_ptr[sl];
@@ -1466,10 +1556,6 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       lcol[j] = j < width ? d.sl_lcol[base + j * 32 + ln] : 0;
       val[j] = j < width ? d.sl_val[base + j * 32 + ln] : 0.0f;
     }
-    if (d.rhs_in_pcg)
-      rhs_row(d, i, brow, dg, es);
-    else
-      dg = d.diag[i];
   }
   // coarse correction state (COARSE only): per-warp aggregate sums, the
   // parts of warps 1..5, the block's g values, this block's rows of A_c^-1
@@ -1570,49 +1656,44 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   unsigned ue = 0, re = 0;  // epochs of u and of the reductions (the same in every thread)
   float r[3] = {0.0f, 0.0f, 0.0f}, u[3], w[3] = {0.0f, 0.0f, 0.0f}, p[3], s[3], dd[3] = {0.0f, 0.0f, 0.0f};
   float gr[3] = {0.0f, 0.0f, 0.0f}, gs[3] = {0.0f, 0.0f, 0.0f};  // g(r), g(s) of this row's aggregate
-  double a0[3] = {0.0, 0.0, es};
+  DW a0[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
   ++ue;
   if (act) {
-    double rv[3];
-    double a01[2] = {0.0, 0.0};
-    residual_row_f64(d, i, dg, rv, a01, d.rhs_in_pcg ? &brow : nullptr);
-    a0[0] = a01[0];
-    a0[1] = a01[1];
-    for (int c = 0; c < 3; ++c) {
-      r[c] = (float)rv[c];
-      u[c] = r[c] / dg;
+    if (d.rhs_in_pcg) {
+      rhs_residual_row_dw(d, i, val, width, dg, r, a0);
+    } else {
+      dg = d.diag[i];
+      double rv[3];
+      double a01[2] = {0.0, 0.0};
+      residual_row_f64(d, i, dg, rv, a01);
+      a0[0] = dw_from(a01[0]);
+      a0[1] = dw_from(a01[1]);
+      for (int c = 0; c < 3; ++c) r[c] = (float)rv[c];
     }
+    for (int c = 0; c < 3; ++c) u[c] = r[c] / dg;
     if constexpr (!COARSE) store_u(ue, u);
   }
   {
     // (||b||^2, ||r0||^2, spring energy) summed over the grid
-    double bs[3], t[3];
+    DW bs[3], t[3];
     if constexpr (COARSE) agg_warp_sums(w, r, s_zw);  // w is zero here
-    block_sums<3, NW>(a0, cs.sh, bs);
+    block_sums_dw<3, NW>(a0, cs.sh, bs);
     ++re;
-    if constexpr (!COARSE) {
-      if (w0) {
-        const bool ok = df_reduce(d, re, bs, t);
-        if (lane == 0) {
-          sc[0] = t[0];
-          sc[1] = t[1];
-          s_es = t[2];
-          s_thr = (float)(d.tol2 * t[0]);
-          cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
-        }
+    auto first = [&](bool ok) {
+      if (lane == 0) {
+        const double bb = acc_to_f64(t[0]), rr = acc_to_f64(t[1]);
+        sc[0] = bb;
+        sc[1] = rr;
+        s_es = acc_to_f64(t[2]);
+        s_thr = (float)(d.tol2 * bb);
+        cs.flag = !ok ? CG_ABORT : ((bb > 0.0 && rr > d.tol2 * bb) ? CG_CONTINUE : CG_DONE);
       }
+    };
+    if constexpr (!COARSE) {
+      if (w0) first(df_reduce(d, re, bs, t));
       __syncthreads();
     } else {
-      if (!reduce_c(re, bs, [&] {
-            const bool ok = df_gather_dots_c(d, re, t);
-            if (lane == 0) {
-              sc[0] = t[0];
-              sc[1] = t[1];
-              s_es = t[2];
-              s_thr = (float)(d.tol2 * t[0]);
-              cs.flag = !ok ? CG_ABORT : ((t[0] > 0.0 && t[1] > d.tol2 * t[0]) ? CG_CONTINUE : CG_DONE);
-            }
-          }))
+      if (!reduce_c(re, bs, [&] { first(df_gather_dots_c(d, re, t)); }))
         return;
       for (int c = 0; c < 3; ++c) gr[c] = s_g[1][ia][c];
     }
@@ -1737,22 +1818,20 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
       d.X[i] = t;
     }
   }
-  if (blockIdx.x == 0 && w0) {
+  if (blockIdx.x == 0) {
     // the record of this outer iteration; with the fused right-hand side
     // also what a separate finalize launch would do: the Eq. 8 energy (the
-    // local step's partials, summed by warp 0 in a fixed order, plus the
-    // spring energy of the first reduction), the iteration count, and the
+    // local step's partials, summed by the whole block in a fixed order, plus
+    // the spring energy of the first reduction), the iteration count, and the
     // per-iteration words reset for the next iteration
-    double e_loc = 0.0;
-    if (d.rhs_in_pcg && d.stats) {
-      for (int k = lane; k < d.n_e_local; k += 32) e_loc += d.e_partials[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) e_loc += __shfl_down_sync(0xffffffffu, e_loc, o);
-    }
-    if (lane == 0) {
+    double el[1] = {0.0}, e_loc[1];
+    if (d.rhs_in_pcg && d.stats)
+      for (int k = threadIdx.x; k < d.n_e_local; k += PCG_DF_THREADS) el[0] += d.e_partials[k];
+    block_sums<1, NW>(el, cs.sh, e_loc);
+    if (threadIdx.x == 0) {
       const double rr = it > 0 ? (double)s_st[2].hi + (double)s_st[2].lo : sc[1];
       write_pcg_record(d.ctrl, d.hist, d.hist_cap, d.ctrl, it, rr, sc[0]);
-      if (d.rhs_in_pcg) finalize_iteration(d, d.stats ? e_loc + s_es : 0.0);
+      if (d.rhs_in_pcg) finalize_iteration(d, d.stats ? e_loc[0] + s_es : 0.0);
     }
   }
 }
