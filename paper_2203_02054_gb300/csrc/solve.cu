@@ -22,268 +22,6 @@
 
 namespace casim {
 
-// ---------------------------------------------------------------- local step
-template <typename T>
-__device__ __forceinline__ T cbrt_t(T x);
-template <>
-__device__ __forceinline__ float cbrt_t<float>(float x) { return cbrtf(x); }
-template <>
-__device__ __forceinline__ double cbrt_t<double>(double x) { return cbrt(x); }
-
-__device__ __forceinline__ double w_table(const double* knots, int n, double eps, int& seg) {
-  // piecewise linear through (eps_i, w_i), clamped at both ends; seg = the
-  // interval used (0 below the first knot, i + 1 for [eps_i, eps_i+1), n above)
-  seg = 0;
-  if (eps <= knots[0]) return knots[1];
-  for (int i = 0; i + 1 < n; ++i) {
-    const double x0 = knots[2 * i], x1 = knots[2 * i + 2];
-    if (eps < x1) {
-      const double y0 = knots[2 * i + 1], y1 = knots[2 * i + 3];
-      seg = i + 1;
-      return y0 + (eps - x0) * (y1 - y0) / (x1 - x0);
-    }
-  }
-  seg = n;
-  return knots[2 * n - 1];
-}
-
-template <typename T, int SWEEPS, int BS>
-__global__ void __launch_bounds__(BS) k_local(Dev<T> d) {
-  __shared__ double shd[32];
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  double en = 0.0;
-  unsigned long long ksig = 0;
-  if (e < d.n_t) {
-    const int4 t = d.tet[e];
-    const R4<T> x0 = d.X[t.x], x1 = d.X[t.y], x2 = d.X[t.z], x3 = d.X[t.w];
-    // centered deformed shape X_c = V^d N, formed from differences to x0
-    T Xc[3][4];
-    {
-      const T r1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
-      const T r2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
-      const T r3[3] = {x3.x - x0.x, x3.y - x0.y, x3.z - x0.z};
-      for (int i = 0; i < 3; ++i) {
-        const T m = (r1[i] + r2[i] + r3[i]) * T(0.25);
-        Xc[i][0] = -m;
-        Xc[i][1] = r1[i] - m;
-        Xc[i][2] = r2[i] - m;
-        Xc[i][3] = r3[i] - m;
-      }
-    }
-    const R4<T> tx = d.Tc[3 * (size_t)e], ty = d.Tc[3 * (size_t)e + 1], tz = d.Tc[3 * (size_t)e + 2];
-    const T Tm[3][4] = {{tx.x, tx.y, tx.z, tx.w}, {ty.x, ty.y, ty.z, ty.w}, {tz.x, tz.y, tz.z, tz.w}};
-    T D[3][3];
-    for (int i = 0; i < 3; ++i)
-      for (int j = 0; j < 3; ++j)
-        D[i][j] = Xc[i][0] * Tm[j][0] + Xc[i][1] * Tm[j][1] + Xc[i][2] * Tm[j][2] + Xc[i][3] * Tm[j][3];
-    T R[3][3], tr;
-    kabsch_rotation<T, SWEEPS>(D, R, tr);
-    T RT[3][4];
-    for (int i = 0; i < 3; ++i)
-      for (int k = 0; k < 4; ++k) RT[i][k] = R[i][0] * Tm[0][k] + R[i][1] * Tm[1][k] + R[i][2] * Tm[2][k];
-    const R4<T> info = d.tinfo[e];
-    const T omega = info.x, vol0 = info.y, tt = info.z;
-    const int g = (int)info.w;
-    T P[3][4];
-    if (g >= 0) {
-      // chamber element: every target vertex is the rest vertex scaled by cbrt(alpha_g)
-      const T s = d.cbrt_alpha[g];
-      for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 4; ++k) P[i][k] = s * RT[i][k];
-    } else {
-      // body element: blend with w = R_omega(eps), then volume scaling (Eq. 6, Eq. 7)
-      T mis = T(0);
-      for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 4; ++k) {
-          const T q = Xc[i][k] - RT[i][k];
-          mis += q * q;
-        }
-      const double strain = sqrt((double)mis / (double)tt);
-      int seg;
-      const T w = (T)w_table(d.knots, d.n_knots, strain, seg);
-      if (d.stats) ksig = sig_mix((unsigned)e, (unsigned)seg);
-      T B[3][4];
-      for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 4; ++k) B[i][k] = (T(1) - w) * Xc[i][k] + w * RT[i][k];
-      const T a0 = B[0][1] - B[0][0], a1 = B[1][1] - B[1][0], a2 = B[2][1] - B[2][0];
-      const T b0 = B[0][2] - B[0][0], b1 = B[1][2] - B[1][0], b2 = B[2][2] - B[2][0];
-      const T c0 = B[0][3] - B[0][0], c1 = B[1][3] - B[1][0], c2 = B[2][3] - B[2][0];
-      const T volB = (a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0)) / T(6);
-      const T s = (volB > T(1e-3) * vol0) ? cbrt_t<T>(vol0 / volB) : T(1);
-      for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 4; ++k) P[i][k] = s * B[i][k];
-    }
-    if (d.stats) {
-      double acc = 0.0;
-      for (int i = 0; i < 3; ++i)
-        for (int k = 0; k < 4; ++k) {
-          const double q = (double)Xc[i][k] - (double)P[i][k];
-          acc += q * q;
-        }
-      en = (double)omega * acc;
-    }
-    R4<T>* out = d.P + 4 * (size_t)e;
-    for (int k = 0; k < 4; ++k) {
-      R4<T> c;
-      c.x = omega * P[0][k];
-      c.y = omega * P[1][k];
-      c.z = omega * P[2][k];
-      c.w = T(0);
-      out[k] = c;
-    }
-  }
-  if (d.stats) warp_add_u64(ksig, &(d.hist + (d.ctrl->iter % d.hist_cap))->knot_sig);
-  const double s = block_sum(en, shd);
-  if (threadIdx.x == 0) d.e_partials[blockIdx.x] = s;
-}
-
-// ------------------------------------------------------------ RHS gather
-// b_v = sum over incident (e, slot) of w_e P_e[:, slot] + k mask_v c_v - bfix_v,
-// accumulated in FP64 (the products of the FP32 targets need no rounding).
-// The rows also carry the spring energy k mask_v |x_v - c_v|^2 (Eq. 5) of
-// this iteration's springs (positions are unchanged since the spring update),
-// summed per block in row order.
-// One row of the right-hand side and of the diagonal: b_i, A_ii and the row's
-// spring energy (see above).
-template <typename T>
-__device__ __forceinline__ void rhs_row(const Dev<T>& d, int i, R4<double>& b, T& diag, double& es) {
-  double bx = 0.0, by = 0.0, bz = 0.0;
-  const int k1 = d.inc_ptr[i + 1];
-  for (int k = d.inc_ptr[i]; k < k1; ++k) {
-    const R4<T> p = d.P[d.inc[k]];
-    bx += (double)p.x;
-    by += (double)p.y;
-    bz += (double)p.z;
-  }
-  const R4<double> sc = d.spring_c[i];
-  const double km = d.k_spring * sc.w;
-  const R4<double> bf = d.bfix[i];
-  b = R4<double>{bx + km * sc.x - bf.x, by + km * sc.y - bf.y, bz + km * sc.z - bf.z, 0.0};
-  diag = d.diagL[i] + (T)km;
-  es = 0.0;
-  if (sc.w != 0.0) {
-    const R4<T> xi = d.X[i];
-    const double ex = (double)xi.x - sc.x, ey = (double)xi.y - sc.y, ez = (double)xi.z - sc.z;
-    es = km * (ex * ex + ey * ey + ez * ez);
-  }
-}
-
-template <typename T, int BS>
-__global__ void __launch_bounds__(BS) k_rhs(Dev<T> d) {
-  __shared__ double shd[32];
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double es = 0.0;
-  if (i < d.n_free) {
-    R4<double> b;
-    T dg;
-    rhs_row(d, i, b, dg, es);
-    d.b[i] = b;
-    d.diag[i] = dg;
-  }
-  const double s = block_sum(es, shd);
-  if (threadIdx.x == 0) d.e_partials[d.n_e_local + blockIdx.x] = s;
-}
-
-// End of an outer iteration (one thread): the energy into this iteration's
-// record, the iteration count, and the per-iteration words reset.
-template <typename T>
-__device__ __forceinline__ void finalize_iteration(const Dev<T>& d, double energy) {
-  Ctrl* c = d.ctrl;
-  IterRec* rec = d.hist + (c->iter % d.hist_cap);
-  rec->energy = energy;
-  if (!isfinite(energy) && d.stats) c->status |= ST_NONFINITE;
-  c->iter += 1;
-  c->n_cast = 0;
-  for (int j = 0; j < 3; ++j) {
-    c->box_lo[j] = 0x7FFFFFFFFFFFFFFFLL;
-    c->box_hi[j] = (long long)0x8000000000000000ULL;
-  }
-  IterRec* nx = d.hist + (c->iter % d.hist_cap);
-  nx->energy = 0.0;
-  nx->pcg_rel_residual = 0.0;
-  nx->n_self_pairs = 0;
-  nx->n_obstacle_pairs = 0;
-  nx->n_springs = 0;
-  nx->pcg_iters = 0;
-  nx->knot_sig = 0;
-  nx->spring_sig = 0;
-}
-
-// ------------------------------------------------------------------ PCG
-//
-// The PCG kernels solve for the correction d of the warm start x:
-//   r0 = b - A x  in FP64 (FP32 products are exact in FP64),
-//   A d = r0      by Jacobi-preconditioned CG in the working precision,
-//   x <- x + d    once at the end,
-// so that the rounding of the working precision applies to the small
-// correction, not to the positions (one step of mixed-precision iterative
-// refinement per outer iteration).  The stopping test ||r|| <= tol ||b|| is the
-// same as for the plain system.
-//
-// Per CG iteration there are two grid barriers: one publishes the new
-// preconditioned residual u for the neighbours' SpMV, one completes the
-// reduction of (r.u, w.u, r.r).
-//
-// Grid barrier: one arrival counter whose top bit flips once per round.
-// Block 0 adds 0x80000000 - (nblocks - 1) and every other block adds 1, so a
-// full round adds exactly 0x80000000: the low bits return to their value and
-// the top bit changes, which every block waits for (no reset, one atomic per
-// block).  Every wait is bounded by a clock budget, after which the kernel
-// records ST_TIMEOUT, raises the abort word and returns.
-//
-// Reductions: each block forms its sums (below), lane 0 of warp 0 stores them
-// as the block's partials and arrives; after the barrier warp 0 alone adds the
-// partials in block order (deterministic), computes the CG scalars once for
-// the block and hands them to the other warps through shared memory.  Partials
-// are stored value-major, partials[(parity * 4 + k) * nblocks + block], in two
-// buffers chosen by the barrier count's parity.
-struct GridCtx {
-  Ctrl* ctrl;
-  double* partials;
-  unsigned nblocks;
-  unsigned long long budget;
-  unsigned extra;  // test-only: arrivals expected beyond the grid (never come)
-};
-
-// One thread of the block arrives and waits for the round to complete.
-// Returns 0 when the wait gave up (timeout) or another block aborted.
-__device__ __forceinline__ int arrive_and_wait(const GridCtx& g) {
-  const unsigned add = blockIdx.x == 0 ? (0x80000000u - (g.nblocks - 1u + g.extra)) : 1u;
-  __threadfence();
-  const unsigned old = atomicAdd(&g.ctrl->bar_count, add);
-  volatile unsigned* vc = &g.ctrl->bar_count;
-  int ok = 1;
-  if (((old ^ *vc) & 0x80000000u) == 0) {
-    const long long t0 = clock64();
-    unsigned spins = 0;
-    while (((old ^ *vc) & 0x80000000u) == 0) {
-      if ((++spins & 63u) == 0) {
-        if (*(volatile int*)&g.ctrl->abort) {
-          ok = 0;
-          break;
-        }
-        if ((unsigned long long)(clock64() - t0) > g.budget) {
-          atomicExch(&g.ctrl->abort, 1);
-          atomicOr(&g.ctrl->status, ST_TIMEOUT);
-          ok = 0;
-          break;
-        }
-      }
-    }
-  }
-  __threadfence();
-  return ok;
-}
-
-// Plain grid barrier (makes every block's prior global writes visible).
-__device__ __forceinline__ bool grid_barrier(const GridCtx& g, unsigned& epoch, int* shf) {
-  ++epoch;
-  __syncthreads();
-  if (threadIdx.x == 0) *shf = arrive_and_wait(g);
-  __syncthreads();
-  return *shf != 0;
-}
-
 // ---- FP64-grade dot products
 // The CG dot products are accumulated to FP64 accuracy.  FP64 arithmetic is
 // slow on this part (a dependent FP64 add takes about 64 cycles and an SM
@@ -439,17 +177,6 @@ __device__ __forceinline__ DW acc_zero<DW>() { return DW{0.0f, 0.0f}; }
 template <>
 __device__ __forceinline__ double acc_zero<double>() { return 0.0; }
 
-// per-thread accumulator of the CG dot products for vectors of type T
-template <typename T>
-struct DotAcc;
-template <>
-struct DotAcc<float> {
-  using type = DW;
-};
-template <>
-struct DotAcc<double> {
-  using type = double;
-};
 
 // Block sums of NV per-thread values by fixed shuffle trees (within each warp,
 // then over the NW warp sums, padded with zeros to a power of two); the FP64
@@ -512,6 +239,329 @@ __device__ __forceinline__ void block_sums_dw(DW (&v)[NV], double* sh, DW (&bs)[
     }
   }
 }
+
+// ---------------------------------------------------------------- local step
+template <typename T>
+__device__ __forceinline__ T cbrt_t(T x);
+template <>
+__device__ __forceinline__ float cbrt_t<float>(float x) { return cbrtf(x); }
+template <>
+__device__ __forceinline__ double cbrt_t<double>(double x) { return cbrt(x); }
+
+__device__ __forceinline__ double w_table(const double* knots, int n, double eps, int& seg) {
+  // piecewise linear through (eps_i, w_i), clamped at both ends; seg = the
+  // interval used (0 below the first knot, i + 1 for [eps_i, eps_i+1), n above)
+  seg = 0;
+  if (eps <= knots[0]) return knots[1];
+  for (int i = 0; i + 1 < n; ++i) {
+    const double x0 = knots[2 * i], x1 = knots[2 * i + 2];
+    if (eps < x1) {
+      const double y0 = knots[2 * i + 1], y1 = knots[2 * i + 3];
+      seg = i + 1;
+      return y0 + (eps - x0) * (y1 - y0) / (x1 - x0);
+    }
+  }
+  seg = n;
+  return knots[2 * n - 1];
+}
+
+// The same table in FP32 (knots rounded to FP32), for FP32 positions.
+__device__ __forceinline__ float w_table_f(const float* knots, int n, float eps, int& seg) {
+  seg = 0;
+  if (eps <= knots[0]) return knots[1];
+  for (int i = 0; i + 1 < n; ++i) {
+    const float x0 = knots[2 * i], x1 = knots[2 * i + 2];
+    if (eps < x1) {
+      const float y0 = knots[2 * i + 1], y1 = knots[2 * i + 3];
+      seg = i + 1;
+      return y0 + (eps - x0) * (y1 - y0) / (x1 - x0);
+    }
+  }
+  seg = n;
+  return knots[2 * n - 1];
+}
+
+// One thread per tet.  For FP32 positions the strain, w(eps) and the energy
+// statistic stay on the FP32 pipes (FP32 strain and table, energy in double
+// words); FP64 positions use FP64 throughout.
+template <typename T, int SWEEPS, int BS>
+__global__ void __launch_bounds__(BS) k_local(Dev<T> d) {
+  constexpr bool F32 = std::is_same<T, float>::value;
+  __shared__ double shd[32];
+  __shared__ float s_kn[F32 ? 128 : 1];  // the knot table in FP32 (at most 64 knots)
+  if constexpr (F32) {
+    for (int k = threadIdx.x; k < 2 * d.n_knots; k += BS) s_kn[k] = (float)d.knots[k];
+    __syncthreads();
+  }
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  double en = 0.0;
+  DW en_w{0.0f, 0.0f};
+  unsigned long long ksig = 0;
+  if (e < d.n_t) {
+    const int4 t = d.tet[e];
+    const R4<T> x0 = d.X[t.x], x1 = d.X[t.y], x2 = d.X[t.z], x3 = d.X[t.w];
+    // centered deformed shape X_c = V^d N, formed from differences to x0
+    T Xc[3][4];
+    {
+      const T r1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
+      const T r2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
+      const T r3[3] = {x3.x - x0.x, x3.y - x0.y, x3.z - x0.z};
+      for (int i = 0; i < 3; ++i) {
+        const T m = (r1[i] + r2[i] + r3[i]) * T(0.25);
+        Xc[i][0] = -m;
+        Xc[i][1] = r1[i] - m;
+        Xc[i][2] = r2[i] - m;
+        Xc[i][3] = r3[i] - m;
+      }
+    }
+    const R4<T> tx = d.Tc[3 * (size_t)e], ty = d.Tc[3 * (size_t)e + 1], tz = d.Tc[3 * (size_t)e + 2];
+    const T Tm[3][4] = {{tx.x, tx.y, tx.z, tx.w}, {ty.x, ty.y, ty.z, ty.w}, {tz.x, tz.y, tz.z, tz.w}};
+    T D[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        D[i][j] = Xc[i][0] * Tm[j][0] + Xc[i][1] * Tm[j][1] + Xc[i][2] * Tm[j][2] + Xc[i][3] * Tm[j][3];
+    T R[3][3], tr;
+    kabsch_rotation<T, SWEEPS>(D, R, tr);
+    T RT[3][4];
+    for (int i = 0; i < 3; ++i)
+      for (int k = 0; k < 4; ++k) RT[i][k] = R[i][0] * Tm[0][k] + R[i][1] * Tm[1][k] + R[i][2] * Tm[2][k];
+    const R4<T> info = d.tinfo[e];
+    const T omega = info.x, vol0 = info.y, tt = info.z;
+    const int g = (int)info.w;
+    T P[3][4];
+    if (g >= 0) {
+      // chamber element: every target vertex is the rest vertex scaled by cbrt(alpha_g)
+      const T s = d.cbrt_alpha[g];
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) P[i][k] = s * RT[i][k];
+    } else {
+      // body element: blend with w = R_omega(eps), then volume scaling (Eq. 6, Eq. 7)
+      T mis = T(0);
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) {
+          const T q = Xc[i][k] - RT[i][k];
+          mis += q * q;
+        }
+      int seg;
+      T w;
+      if constexpr (F32) {
+        w = w_table_f(s_kn, d.n_knots, sqrtf(mis / tt), seg);
+      } else {
+        w = w_table(d.knots, d.n_knots, sqrt(mis / tt), seg);
+      }
+      if (d.stats) ksig = sig_mix((unsigned)e, (unsigned)seg);
+      T B[3][4];
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) B[i][k] = (T(1) - w) * Xc[i][k] + w * RT[i][k];
+      const T a0 = B[0][1] - B[0][0], a1 = B[1][1] - B[1][0], a2 = B[2][1] - B[2][0];
+      const T b0 = B[0][2] - B[0][0], b1 = B[1][2] - B[1][0], b2 = B[2][2] - B[2][0];
+      const T c0 = B[0][3] - B[0][0], c1 = B[1][3] - B[1][0], c2 = B[2][3] - B[2][0];
+      const T volB = (a0 * (b1 * c2 - b2 * c1) - a1 * (b0 * c2 - b2 * c0) + a2 * (b0 * c1 - b1 * c0)) / T(6);
+      const T s = (volB > T(1e-3) * vol0) ? cbrt_t<T>(vol0 / volB) : T(1);
+      for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 4; ++k) P[i][k] = s * B[i][k];
+    }
+    if (d.stats) {
+      if constexpr (F32) {
+        // sum of (Xc - P)^2 with each difference exact as a double word
+        DW acc{0.0f, 0.0f};
+        for (int i = 0; i < 3; ++i)
+          for (int k = 0; k < 4; ++k) {
+            float qh, ql;
+            two_sum_f(Xc[i][k], -P[i][k], qh, ql);
+            dw_acc_prod(acc, qh, qh);
+            acc.lo = __fmaf_rn(__fmul_rn(2.0f, qh), ql, acc.lo);
+          }
+        en_w = dw_mul(DW{omega, 0.0f}, dw_norm(acc));
+      } else {
+        double acc = 0.0;
+        for (int i = 0; i < 3; ++i)
+          for (int k = 0; k < 4; ++k) {
+            const double q = (double)Xc[i][k] - (double)P[i][k];
+            acc += q * q;
+          }
+        en = (double)omega * acc;
+      }
+    }
+    R4<T>* out = d.P + 4 * (size_t)e;
+    for (int k = 0; k < 4; ++k) {
+      R4<T> c;
+      c.x = omega * P[0][k];
+      c.y = omega * P[1][k];
+      c.z = omega * P[2][k];
+      c.w = T(0);
+      out[k] = c;
+    }
+  }
+  if (d.stats) warp_add_u64(ksig, &(d.hist + (d.ctrl->iter % d.hist_cap))->knot_sig);
+  if constexpr (F32) {
+    DW v[1] = {en_w}, bs[1];
+    block_sums_dw<1, BS / 32>(v, shd, bs);
+    if (threadIdx.x == 0) d.e_partials[blockIdx.x] = acc_to_f64(bs[0]);
+  } else {
+    const double s = block_sum(en, shd);
+    if (threadIdx.x == 0) d.e_partials[blockIdx.x] = s;
+  }
+}
+
+// ------------------------------------------------------------ RHS gather
+// b_v = sum over incident (e, slot) of w_e P_e[:, slot] + k mask_v c_v - bfix_v,
+// accumulated in FP64 (the products of the FP32 targets need no rounding).
+// The rows also carry the spring energy k mask_v |x_v - c_v|^2 (Eq. 5) of
+// this iteration's springs (positions are unchanged since the spring update),
+// summed per block in row order.
+// One row of the right-hand side and of the diagonal: b_i, A_ii and the row's
+// spring energy (see above).
+template <typename T>
+__device__ __forceinline__ void rhs_row(const Dev<T>& d, int i, R4<double>& b, T& diag, double& es) {
+  double bx = 0.0, by = 0.0, bz = 0.0;
+  const int k1 = d.inc_ptr[i + 1];
+  for (int k = d.inc_ptr[i]; k < k1; ++k) {
+    const R4<T> p = d.P[d.inc[k]];
+    bx += (double)p.x;
+    by += (double)p.y;
+    bz += (double)p.z;
+  }
+  const R4<double> sc = d.spring_c[i];
+  const double km = d.k_spring * sc.w;
+  const R4<double> bf = d.bfix[i];
+  b = R4<double>{bx + km * sc.x - bf.x, by + km * sc.y - bf.y, bz + km * sc.z - bf.z, 0.0};
+  diag = d.diagL[i] + (T)km;
+  es = 0.0;
+  if (sc.w != 0.0) {
+    const R4<T> xi = d.X[i];
+    const double ex = (double)xi.x - sc.x, ey = (double)xi.y - sc.y, ez = (double)xi.z - sc.z;
+    es = km * (ex * ex + ey * ey + ez * ez);
+  }
+}
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS) k_rhs(Dev<T> d) {
+  __shared__ double shd[32];
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double es = 0.0;
+  if (i < d.n_free) {
+    R4<double> b;
+    T dg;
+    rhs_row(d, i, b, dg, es);
+    d.b[i] = b;
+    d.diag[i] = dg;
+  }
+  const double s = block_sum(es, shd);
+  if (threadIdx.x == 0) d.e_partials[d.n_e_local + blockIdx.x] = s;
+}
+
+// End of an outer iteration (one thread): the energy into this iteration's
+// record, the iteration count, and the per-iteration words reset.
+template <typename T>
+__device__ __forceinline__ void finalize_iteration(const Dev<T>& d, double energy) {
+  Ctrl* c = d.ctrl;
+  IterRec* rec = d.hist + (c->iter % d.hist_cap);
+  rec->energy = energy;
+  if (!isfinite(energy) && d.stats) c->status |= ST_NONFINITE;
+  c->iter += 1;
+  c->n_cast = 0;
+  for (int j = 0; j < 3; ++j) {
+    c->box_lo[j] = 0x7FFFFFFFFFFFFFFFLL;
+    c->box_hi[j] = (long long)0x8000000000000000ULL;
+  }
+  IterRec* nx = d.hist + (c->iter % d.hist_cap);
+  nx->energy = 0.0;
+  nx->pcg_rel_residual = 0.0;
+  nx->n_self_pairs = 0;
+  nx->n_obstacle_pairs = 0;
+  nx->n_springs = 0;
+  nx->pcg_iters = 0;
+  nx->knot_sig = 0;
+  nx->spring_sig = 0;
+}
+
+// ------------------------------------------------------------------ PCG
+//
+// The PCG kernels solve for the correction d of the warm start x:
+//   r0 = b - A x  in FP64 (FP32 products are exact in FP64),
+//   A d = r0      by Jacobi-preconditioned CG in the working precision,
+//   x <- x + d    once at the end,
+// so that the rounding of the working precision applies to the small
+// correction, not to the positions (one step of mixed-precision iterative
+// refinement per outer iteration).  The stopping test ||r|| <= tol ||b|| is the
+// same as for the plain system.
+//
+// Per CG iteration there are two grid barriers: one publishes the new
+// preconditioned residual u for the neighbours' SpMV, one completes the
+// reduction of (r.u, w.u, r.r).
+//
+// Grid barrier: one arrival counter whose top bit flips once per round.
+// Block 0 adds 0x80000000 - (nblocks - 1) and every other block adds 1, so a
+// full round adds exactly 0x80000000: the low bits return to their value and
+// the top bit changes, which every block waits for (no reset, one atomic per
+// block).  Every wait is bounded by a clock budget, after which the kernel
+// records ST_TIMEOUT, raises the abort word and returns.
+//
+// Reductions: each block forms its sums (below), lane 0 of warp 0 stores them
+// as the block's partials and arrives; after the barrier warp 0 alone adds the
+// partials in block order (deterministic), computes the CG scalars once for
+// the block and hands them to the other warps through shared memory.  Partials
+// are stored value-major, partials[(parity * 4 + k) * nblocks + block], in two
+// buffers chosen by the barrier count's parity.
+struct GridCtx {
+  Ctrl* ctrl;
+  double* partials;
+  unsigned nblocks;
+  unsigned long long budget;
+  unsigned extra;  // test-only: arrivals expected beyond the grid (never come)
+};
+
+// One thread of the block arrives and waits for the round to complete.
+// Returns 0 when the wait gave up (timeout) or another block aborted.
+__device__ __forceinline__ int arrive_and_wait(const GridCtx& g) {
+  const unsigned add = blockIdx.x == 0 ? (0x80000000u - (g.nblocks - 1u + g.extra)) : 1u;
+  __threadfence();
+  const unsigned old = atomicAdd(&g.ctrl->bar_count, add);
+  volatile unsigned* vc = &g.ctrl->bar_count;
+  int ok = 1;
+  if (((old ^ *vc) & 0x80000000u) == 0) {
+    const long long t0 = clock64();
+    unsigned spins = 0;
+    while (((old ^ *vc) & 0x80000000u) == 0) {
+      if ((++spins & 63u) == 0) {
+        if (*(volatile int*)&g.ctrl->abort) {
+          ok = 0;
+          break;
+        }
+        if ((unsigned long long)(clock64() - t0) > g.budget) {
+          atomicExch(&g.ctrl->abort, 1);
+          atomicOr(&g.ctrl->status, ST_TIMEOUT);
+          ok = 0;
+          break;
+        }
+      }
+    }
+  }
+  __threadfence();
+  return ok;
+}
+
+// Plain grid barrier (makes every block's prior global writes visible).
+__device__ __forceinline__ bool grid_barrier(const GridCtx& g, unsigned& epoch, int* shf) {
+  ++epoch;
+  __syncthreads();
+  if (threadIdx.x == 0) *shf = arrive_and_wait(g);
+  __syncthreads();
+  return *shf != 0;
+}
+
+// per-thread accumulator of the CG dot products for vectors of type T
+template <typename T>
+struct DotAcc;
+template <>
+struct DotAcc<float> {
+  using type = DW;
+};
+template <>
+struct DotAcc<double> {
+  using type = double;
+};
 
 // Called by all of warp 0 after block_sums.  Lane 0 stores the block's sums
 // as its partials, arrives and waits; the warp then adds the partials of
