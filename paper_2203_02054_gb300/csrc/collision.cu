@@ -232,10 +232,23 @@ __device__ __forceinline__ T max4(T a, T b, T c, T e) {
 template <typename T>
 __device__ __forceinline__ bool strictly_inside_at(const R4<T>* X, T px, T py, T pz, int4 t) {
   const R4<T> a = X[t.x], b = X[t.y], c = X[t.z], e = X[t.w];
-  if (px < min4(a.x, b.x, c.x, e.x) || px > max4(a.x, b.x, c.x, e.x)) return false;
-  if (py < min4(a.y, b.y, c.y, e.y) || py > max4(a.y, b.y, c.y, e.y)) return false;
-  if (pz < min4(a.z, b.z, c.z, e.z) || pz > max4(a.z, b.z, c.z, e.z)) return false;
-  // p strictly inside iff each sub-tet with one vertex replaced by p is positive
+  // A point strictly inside a tet lies strictly inside its box: the tet
+  // reaches its extreme coordinates only on its boundary.  The open box test
+  // is exact and rejects the many points on a box face (vertices of
+  // axis-aligned meshes), whose orientation signs would be exact zeros.
+  if (!(px > min4(a.x, b.x, c.x, e.x) && px < max4(a.x, b.x, c.x, e.x))) return false;
+  if (!(py > min4(a.y, b.y, c.y, e.y) && py < max4(a.y, b.y, c.y, e.y))) return false;
+  if (!(pz > min4(a.z, b.z, c.z, e.z) && pz < max4(a.z, b.z, c.z, e.z))) return false;
+  // p strictly inside iff each sub-tet with one vertex replaced by p is
+  // positive; for FP32 positions every sign first gets the FP32 filter, so a
+  // certified negative sign ends the test before any FP64 or exact work
+  if constexpr (std::is_same<T, float>::value) {
+    const int s0 = orient_filter_f(px, py, pz, b.x, b.y, b.z, c.x, c.y, c.z, e.x, e.y, e.z);
+    const int s1 = orient_filter_f(a.x, a.y, a.z, px, py, pz, c.x, c.y, c.z, e.x, e.y, e.z);
+    const int s2 = orient_filter_f(a.x, a.y, a.z, b.x, b.y, b.z, px, py, pz, e.x, e.y, e.z);
+    const int s3 = orient_filter_f(a.x, a.y, a.z, b.x, b.y, b.z, c.x, c.y, c.z, px, py, pz);
+    if (s0 < 0 || s1 < 0 || s2 < 0 || s3 < 0) return false;
+  }
   if (orient_t(px, py, pz, b.x, b.y, b.z, c.x, c.y, c.z, e.x, e.y, e.z) <= 0) return false;
   if (orient_t(a.x, a.y, a.z, px, py, pz, c.x, c.y, c.z, e.x, e.y, e.z) <= 0) return false;
   if (orient_t(a.x, a.y, a.z, b.x, b.y, b.z, px, py, pz, e.x, e.y, e.z) <= 0) return false;
@@ -607,32 +620,43 @@ __device__ int ray_cast_warp(const Dev<T>& d, int v, int rv, V3 o, V3 dir, doubl
   int best_f = -1;
   double best_t = 0.0;
   rb1 = rb2 = 0.0;
-  int cell[3] = {cell_coord(o.x, d.inv_cell), cell_coord(o.y, d.inv_cell), cell_coord(o.z, d.inv_cell)};
-  const double dv[3] = {dir.x, dir.y, dir.z};
-  const double ov[3] = {o.x, o.y, o.z};
-  int step[3];
-  double tmax[3], tdel[3];
-  for (int a = 0; a < 3; ++a) {
-    if (dv[a] > 0.0) {
-      step[a] = 1;
-      tmax[a] = ((cell[a] + 1) * d.cell - ov[a]) / dv[a];
-      tdel[a] = d.cell / dv[a];
-    } else if (dv[a] < 0.0) {
-      step[a] = -1;
-      tmax[a] = (cell[a] * d.cell - ov[a]) / dv[a];
-      tdel[a] = -d.cell / dv[a];
-    } else {
-      step[a] = 0;
-      tmax[a] = INFINITY;
-      tdel[a] = INFINITY;
+  // DDA set-up: lane a < 3 forms axis a's start cell, step, first boundary
+  // parameter and increment, and its bound on the ray parameter from the
+  // bounding box of this iteration's items (the ray can meet no face beyond
+  // it); the warp shares them by shuffles, so the FP64 divisions run once per
+  // axis, not once per lane.  tbox is the minimum over the axes.
+  int cell[3], step[3];
+  double tmax[3], tdel[3], tbox;
+  {
+    const int a = lane < 3 ? lane : 0;
+    const double dva = a == 0 ? dir.x : a == 1 ? dir.y : dir.z;
+    const double ova = a == 0 ? o.x : a == 1 ? o.y : o.z;
+    int c_a = 0, st_a = 0;
+    double tm_a = INFINITY, td_a = INFINITY, tb_a = INFINITY;
+    if (lane < 3) {
+      c_a = cell_coord(ova, d.inv_cell);
+      const double blo = order_decode(d.ctrl->box_lo[a]) - d.cell, bhi = order_decode(d.ctrl->box_hi[a]) + d.cell;
+      if (dva > 0.0) {
+        st_a = 1;
+        tm_a = ((c_a + 1) * d.cell - ova) / dva;
+        td_a = d.cell / dva;
+        tb_a = (bhi - ova) / dva;
+      } else if (dva < 0.0) {
+        st_a = -1;
+        tm_a = (c_a * d.cell - ova) / dva;
+        td_a = -d.cell / dva;
+        tb_a = (blo - ova) / dva;
+      }
     }
-  }
-  // the ray can meet no face beyond the bounding box of this iteration's items
-  double tbox = INFINITY;
-  for (int a = 0; a < 3; ++a) {
-    const double blo = order_decode(d.ctrl->box_lo[a]) - d.cell, bhi = order_decode(d.ctrl->box_hi[a]) + d.cell;
-    if (dv[a] > 0.0) tbox = fmin(tbox, (bhi - ov[a]) / dv[a]);
-    else if (dv[a] < 0.0) tbox = fmin(tbox, (blo - ov[a]) / dv[a]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cell[k] = __shfl_sync(0xffffffffu, c_a, k);
+      step[k] = __shfl_sync(0xffffffffu, st_a, k);
+      tmax[k] = __shfl_sync(0xffffffffu, tm_a, k);
+      tdel[k] = __shfl_sync(0xffffffffu, td_a, k);
+    }
+    tbox = fmin(fmin(__shfl_sync(0xffffffffu, tb_a, 0), __shfl_sync(0xffffffffu, tb_a, 1)),
+                __shfl_sync(0xffffffffu, tb_a, 2));
   }
   for (int it = 0; it < MAX_DDA_STEPS; ++it) {
     const unsigned h = d.H_t + (hash_cell(cell[0], cell[1], cell[2], rv) & (d.H_f - 1u));

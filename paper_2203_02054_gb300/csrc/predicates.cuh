@@ -131,6 +131,29 @@ __device__ __forceinline__ int orient_sign(double ax, double ay, double az, doub
   return orient_exact(ax, ay, az, bx, by, bz, cx, cy, cz, dx, dy, dz);
 }
 
+// The FP32 stage alone: +1 or -1 when the FP32 filter certifies the sign, 0
+// when it does not (the sign may still be anything, zero included).
+__device__ __forceinline__ int orient_filter_f(float ax, float ay, float az, float bx, float by, float bz,
+                                               float cx, float cy, float cz, float dx, float dy, float dz) {
+  const float ux = __fsub_rn(bx, ax), uy = __fsub_rn(by, ay), uz = __fsub_rn(bz, az);
+  const float vx = __fsub_rn(cx, ax), vy = __fsub_rn(cy, ay), vz = __fsub_rn(cz, az);
+  const float wx = __fsub_rn(dx, ax), wy = __fsub_rn(dy, ay), wz = __fsub_rn(dz, az);
+  const float m1 = __fmul_rn(vy, wz), m2 = __fmul_rn(vz, wy);
+  const float m3 = __fmul_rn(wy, uz), m4 = __fmul_rn(wz, uy);
+  const float m5 = __fmul_rn(uy, vz), m6 = __fmul_rn(uz, vy);
+  const float det = __fadd_rn(__fadd_rn(__fmul_rn(ux, __fsub_rn(m1, m2)), __fmul_rn(vx, __fsub_rn(m3, m4))),
+                              __fmul_rn(wx, __fsub_rn(m5, m6)));
+  const float perm = __fadd_rn(__fadd_rn(__fmul_rn(__fadd_rn(fabsf(m1), fabsf(m2)), fabsf(ux)),
+                                         __fmul_rn(__fadd_rn(fabsf(m3), fabsf(m4)), fabsf(vx))),
+                               __fmul_rn(__fadd_rn(fabsf(m5), fabsf(m6)), fabsf(wx)));
+  const float bound = __fmul_rn(0x1.c0000ep-22f, perm);  // (7 + 56 e) e, e = 2^-24
+  if (perm >= 0x1p-60f) {
+    if (det > bound) return 1;
+    if (-det > bound) return -1;
+  }
+  return 0;
+}
+
 // Filtered exact orientation sign for float inputs.  The FP32 stage is
 // Shewchuk's error analysis with e = 2^-24: |det| > (7 + 56 e) e * permanent
 // certifies the sign.  That analysis assumes no underflow, so a permanent
