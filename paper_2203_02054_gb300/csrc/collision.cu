@@ -36,9 +36,10 @@ __device__ __forceinline__ void load3(const R4<T>* X, int v, double& x, double& 
   z = (double)a.z;
 }
 
-// Bounding box of item i: tets are items [0, n_t), boundary faces [n_t, n_t + n_f).
+// Bounding box of item i: tets are items [0, n_t), boundary faces [n_t, n_t + n_f),
+// in the positions' own precision.
 template <typename T>
-__device__ __forceinline__ bool item_box(const Dev<T>& d, int i, double lo[3], double hi[3]) {
+__device__ __forceinline__ bool item_box_t(const Dev<T>& d, int i, T lo[3], T hi[3]) {
   int vs[4];
   int nv;
   if (i < d.n_t) {
@@ -64,10 +65,21 @@ __device__ __forceinline__ bool item_box(const Dev<T>& d, int i, double lo[3], d
     }
   }
   for (int j = 0; j < 3; ++j) {
-    lo[j] = (double)l[j];
-    hi[j] = (double)h[j];
+    lo[j] = l[j];
+    hi[j] = h[j];
   }
   return ok;
+}
+
+// Cell coordinate in FP32 for FP32 positions, used for the tets and for the
+// narrow phase's point lookups only: it is monotone in x, so the cells of a
+// tet's box corners bound the cell of every point in the box, the property
+// the point-in-tet search needs.  The boundary faces keep FP64 cells
+// (cell_coord), the model of the ray walk and of the shell search.
+__device__ __forceinline__ int cell_coord_f(float x, float inv_cell) {
+  float c = floorf(x * inv_cell);
+  c = fminf(fmaxf(c, -1.0e6f), 1.0e6f);
+  return (int)c;
 }
 
 // Block-reduced bounding box of the item boxes (count pass only).
@@ -103,18 +115,31 @@ template <typename T, bool FILL>
 __global__ void __launch_bounds__(256) k_grid_bin(Dev<T> d) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int n = d.n_t + d.n_f;
-  double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-  const bool ok = i < n && item_box(d, i, lo, hi);
-  if (!FILL) reduce_box(d.ctrl, ok, lo, hi);
+  T lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+  const bool ok = i < n && item_box_t(d, i, lo, hi);
+  if (!FILL) {
+    const double lod[3] = {(double)lo[0], (double)lo[1], (double)lo[2]};
+    const double hid[3] = {(double)hi[0], (double)hi[1], (double)hi[2]};
+    reduce_box(d.ctrl, ok, lod, hid);
+  }
   if (i >= n) return;
   if (!ok) {
     if (!FILL) set_status(d.ctrl, ST_NONFINITE);
     return;
   }
   int c0[3], c1[3];
-  for (int j = 0; j < 3; ++j) {
-    c0[j] = cell_coord(lo[j], d.inv_cell);
-    c1[j] = cell_coord(hi[j], d.inv_cell);
+  const bool is_tet = i < d.n_t;
+  if (std::is_same<T, float>::value && is_tet) {
+    const float inv_f = (float)d.inv_cell;
+    for (int j = 0; j < 3; ++j) {
+      c0[j] = cell_coord_f((float)lo[j], inv_f);
+      c1[j] = cell_coord_f((float)hi[j], inv_f);
+    }
+  } else {
+    for (int j = 0; j < 3; ++j) {
+      c0[j] = cell_coord((double)lo[j], d.inv_cell);
+      c1[j] = cell_coord((double)hi[j], d.inv_cell);
+    }
   }
   const long long ncell =
       (long long)(c1[0] - c0[0] + 1) * (c1[1] - c0[1] + 1) * (c1[2] - c0[2] + 1);
@@ -122,7 +147,6 @@ __global__ void __launch_bounds__(256) k_grid_bin(Dev<T> d) {
     if (!FILL) set_status(d.ctrl, ST_OVERFLOW);
     return;
   }
-  const bool is_tet = i < d.n_t;
   const unsigned base = is_tet ? 0u : d.H_t;
   const unsigned mask = (is_tet ? d.H_t : d.H_f) - 1u;
   const int robot = is_tet ? (d.robot_of_tet ? d.robot_of_tet[i] : 0) : (d.robot_of_face ? d.robot_of_face[i - d.n_t] : 0);
@@ -333,10 +357,18 @@ __global__ void __launch_bounds__(BS) k_narrow(Dev<T> d) {
     int* out = d.pair_tet + (size_t)qi * d.max_pairs;
     const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
     if (d.collision >= 1 && isfinite(px) && isfinite(py) && isfinite(pz)) {
-      const unsigned h =
-          hash_cell(cell_coord((double)px, d.inv_cell), cell_coord((double)py, d.inv_cell),
-                    cell_coord((double)pz, d.inv_cell), rv) &
-          (d.H_t - 1u);
+      int cp[3];
+      if constexpr (std::is_same<T, float>::value) {
+        const float inv_f = (float)d.inv_cell;
+        cp[0] = cell_coord_f(px, inv_f);
+        cp[1] = cell_coord_f(py, inv_f);
+        cp[2] = cell_coord_f(pz, inv_f);
+      } else {
+        cp[0] = cell_coord((double)px, d.inv_cell);
+        cp[1] = cell_coord((double)py, d.inv_cell);
+        cp[2] = cell_coord((double)pz, d.inv_cell);
+      }
+      const unsigned h = hash_cell(cp[0], cp[1], cp[2], rv) & (d.H_t - 1u);
       const int b0 = d.cell_start[h];
       const int b1 = min(d.cell_start[h + 1], d.cap_items);
       for (int base = b0; base < b1; base += 32) {

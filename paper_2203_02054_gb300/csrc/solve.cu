@@ -1725,7 +1725,7 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   }
   {
     // (||b||^2, ||r0||^2, spring energy) summed over the grid
-    DW bs[3], t[3];
+    DW bs[3], t[3] = {};
     if constexpr (COARSE) agg_warp_sums(w, r, s_zw);  // w is zero here
     block_sums_dw<3, NW>(a0, cs.sh, bs);
     ++re;
