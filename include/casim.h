@@ -127,7 +127,10 @@ typedef struct {
                                one warp per query vertex).  Results do not depend
                                on them except for the summation order of the
                                energy statistic; the autotuner picks them        */
-  int32_t pad_;
+  int32_t pcg_block;        /* rows (threads) per block of the dataflow PCG (5): 0
+                               auto = 288 (9 warps; aggregates of 96 rows) when the
+                               system fits one such block per SM, else 384
+                               (aggregates of 128); 288 or 384 forces it          */
 } casim_params;
 
 #define CASIM_DEBUG_BARRIER_NEVER_COMPLETES 1

@@ -8,7 +8,8 @@ dimensions are
 * the global-step kernel and its preconditioner (``pcg_kernel``,
   ``pcg_precond``: for one robot the dataflow kernel with the two-level or the
   Jacobi preconditioner, the register-resident and the streaming kernels; for
-  a batch the segmented and the cluster kernels),
+  a batch the segmented and the cluster kernels) and the dataflow kernel's
+  rows per block (``pcg_block``),
 * the collision broad phase (``broad_phase``: spatial hash or AABB trees) and
   the hash cell edge (``cell_scale`` times the voxel edge),
 * the thread-block sizes of the local step, the RHS gather and the narrow
@@ -37,9 +38,10 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE_PATH = os.path.join(HERE, "tuned.json")
 
-PARAM_KEYS = ("pcg_kernel", "pcg_precond", "broad_phase", "cell_scale", "local_block", "rhs_block", "narrow_block")
-DEFAULTS = dict(pcg_kernel=0, pcg_precond=0, broad_phase=0, cell_scale=1.0, local_block=0, rhs_block=0,
-                narrow_block=0)
+PARAM_KEYS = ("pcg_kernel", "pcg_precond", "pcg_block", "broad_phase", "cell_scale", "local_block", "rhs_block",
+              "narrow_block")
+DEFAULTS = dict(pcg_kernel=0, pcg_precond=0, pcg_block=0, broad_phase=0, cell_scale=1.0, local_block=0,
+                rhs_block=0, narrow_block=0)
 
 
 def gpu_name() -> str:
@@ -69,6 +71,8 @@ def dimensions(mesh) -> List[List[Dict]]:
         if first.precision == synth.PRECISION_MIXED:
             pcg.insert(1, dict(pcg_kernel=0, pcg_precond=1))
     dims = [pcg]
+    if not batch and first.precision == synth.PRECISION_MIXED:
+        dims.append([dict(pcg_block=b) for b in (0, 288, 384)])
     if first.collision >= 1:
         # the hash's cell edge first, then the tree against the tuned hash
         dims.append([dict(cell_scale=c) for c in (1.0, 0.75, 1.5, 2.0)])
@@ -177,8 +181,8 @@ def apply_cached(params, mesh, path: str = CACHE_PATH) -> Optional[Dict]:
     if not rec:
         return None
     p = rec["params"]
-    for k in ("pcg_kernel", "pcg_precond", "broad_phase", "local_block", "rhs_block", "narrow_block"):
-        setattr(params, k, int(p[k]))
+    for k in ("pcg_kernel", "pcg_precond", "pcg_block", "broad_phase", "local_block", "rhs_block", "narrow_block"):
+        setattr(params, k, int(p.get(k, 0)))
     params.cell_size = params.cell_size * float(p["cell_scale"])
     return dict(p)
 

@@ -68,7 +68,7 @@ class casim_params(ctypes.Structure):
         ("local_block", ctypes.c_int32),
         ("rhs_block", ctypes.c_int32),
         ("narrow_block", ctypes.c_int32),
-        ("pad_", ctypes.c_int32),
+        ("pcg_block", ctypes.c_int32),
     ]
 
 
@@ -458,7 +458,7 @@ class Sim:
     def __init__(self, mesh, precision=None, collision=None, stream: int = 0, stats: int = 1,
                  pcg_tol=None, pcg_max_iter=1000, knots=None, max_pairs=8, wait_budget_cycles=0,
                  pcg_kernel=0, debug_flags=0, pcg_precond=0, broad_phase=None, local_block=0, rhs_block=0,
-                 narrow_block=0, cell_scale=1.0, tuned=False):
+                 narrow_block=0, cell_scale=1.0, tuned=False, pcg_block=0):
         load_library()
         self.batch = None
         if isinstance(mesh, (list, tuple)):
@@ -487,6 +487,7 @@ class Sim:
         p.local_block = local_block
         p.rhs_block = rhs_block
         p.narrow_block = narrow_block
+        p.pcg_block = pcg_block
         self.tuned_from = None
         if tuned:
             from . import autotune

@@ -40,11 +40,10 @@ size_t pow2_at_least(size_t n) {
 
 // Recursive coordinate bisection of the vertices idx[0..n) by their rest
 // positions: split along the longest extent of the set's bounding box so that
-// the first part holds a multiple of RCB_LEAF vertices (about half), order
+// the first part holds a multiple of `leaf` vertices (about half), order
 // each part recursively; ties by vertex id, so the order is deterministic.
-constexpr int RCB_LEAF = 128;
-void rcb_order(const double* xyz, int* idx, int n) {
-  if (n <= RCB_LEAF) {
+void rcb_order(const double* xyz, int* idx, int n, int leaf) {
+  if (n <= leaf) {
     std::sort(idx, idx + n);
     return;
   }
@@ -57,13 +56,13 @@ void rcb_order(const double* xyz, int* idx, int n) {
   int ax = 0;
   for (int c = 1; c < 3; ++c)
     if (hi[c] - lo[c] > hi[ax] - lo[ax]) ax = c;
-  const int nl = RCB_LEAF * ((n + 2 * RCB_LEAF - 1) / (2 * RCB_LEAF));
+  const int nl = leaf * ((n + 2 * leaf - 1) / (2 * leaf));
   std::nth_element(idx, idx + nl, idx + n, [&](int a, int b) {
     const double xa = xyz[3 * (size_t)a + ax], xb = xyz[3 * (size_t)b + ax];
     return xa < xb || (xa == xb && a < b);
   });
-  rcb_order(xyz, idx, nl);
-  rcb_order(xyz, idx + nl, n - nl);
+  rcb_order(xyz, idx, nl, leaf);
+  rcb_order(xyz, idx + nl, n - nl, leaf);
 }
 
 // AABB trees over n primitives with centroids cen (3 per primitive), one tree
@@ -257,6 +256,7 @@ struct casim_sim {
   int *halo_ptr = nullptr, *halo_rows = nullptr, *sl_lcol = nullptr;  // dataflow PCG: block halos
   std::vector<int> halo_ptr_h, halo_rows_h, sl_lcol_h;
   int halo_max = 0;
+  int df_rows = 384;  // rows per block of the dataflow PCG
   std::vector<float> cg_ainv_h;  // dataflow PCG coarse correction: A_c^-1, row-major
   int n_agg = 0;
   float* cg_ainv = nullptr;
@@ -425,6 +425,7 @@ Dev<T> make_dev(casim_sim* sim) {
   d.halo_rows = sim->halo_rows;
   d.sl_lcol = sim->sl_lcol;
   d.halo_max = sim->halo_max;
+  d.df_rows = sim->df_rows;
   d.cg_ainv = sim->cg_ainv;
   d.n_agg = sim->n_agg;
   d.q_verts = sim->q_verts_d;
@@ -953,6 +954,7 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
   else if (p.pcg_precond < 0 || p.pcg_precond > 1) why = "pcg_precond";
   else if (p.broad_phase < 0 || p.broad_phase > 1) why = "broad_phase";
+  else if (p.pcg_block != 0 && p.pcg_block != 288 && p.pcg_block != 384) why = "pcg_block";
   else if (p.local_block != 0 && p.local_block != 64 && p.local_block != 128 && p.local_block != 256)
     why = "local_block";
   else if (p.rhs_block != 0 && p.rhs_block != 128 && p.rhs_block != 256 && p.rhs_block != 512) why = "rhs_block";
@@ -1318,12 +1320,22 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   sim->user_of_int.assign(n_v, -1);
   int nf = 0;
   {
+    // rows per block of the dataflow PCG (single robot, MIXED): 288 (9 warps,
+    // more blocks, fewer rows each) when the system fits 152 such blocks,
+    // else 384; the bisection leaves are its aggregates (a third of a block)
+    int n_free_all = 0;
+    for (int v = 0; v < n_v; ++v) n_free_all += !fixed[v];
+    const int pb = sim->params.pcg_block;
+    sim->df_rows = (pb == PCG_DF_THREADS || (pb == 0 && n_free_all > pcg_df_max_rows(PCG_DF_ROWS_SMALL)))
+                       ? PCG_DF_THREADS
+                       : PCG_DF_ROWS_SMALL;
+    const int leaf = n_robots == 1 ? sim->df_rows / 3 : 128;
     std::vector<std::vector<int>> per_robot(n_robots);
     for (int v = 0; v < n_v; ++v)
       if (!fixed[v]) per_robot[std::max(0, robot_of_vert_user[v])].push_back(v);
     for (int r = 0; r < n_robots; ++r) {
       std::vector<int>& L = per_robot[r];
-      rcb_order(rest_xyz, L.data(), (int)L.size());
+      rcb_order(rest_xyz, L.data(), (int)L.size(), leaf);
       for (int v : L) sim->int_of_user[v] = nf++;
     }
   }
@@ -1521,17 +1533,18 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   const int rr_rows = fp64 ? pcg_rr_max_rows<double>() : pcg_rr_max_rows<float>();
   const bool rr_fits = max_width <= PCG_RR_MAXW && n_free <= rr_rows;
   // dataflow PCG (FP32 vectors only): one row per thread, one block per SM.
-  // Block b owns rows [b R, (b + 1) R), R = PCG_DF_THREADS (whole slices); its
+  // Block b owns rows [b R, (b + 1) R), R = df_rows (whole slices); its
   // halo is the sorted list of distinct columns its rows read, and every
   // sliced-ELL entry also gets its column's index in that list.
-  bool df_fits = !fp64 && max_width <= PCG_RR_MAXW && n_free <= pcg_df_max_rows();
+  const int R_df = sim->df_rows;
+  bool df_fits = !fp64 && max_width <= PCG_RR_MAXW && n_free <= pcg_df_max_rows(R_df);
   sim->halo_ptr_h.clear();
   sim->halo_rows_h.clear();
   sim->sl_lcol_h.clear();
   sim->halo_max = 0;
   if (df_fits) {
-    const int spb = PCG_DF_THREADS / 32;
-    const int nbk = (n_free + PCG_DF_THREADS - 1) / PCG_DF_THREADS;
+    const int spb = R_df / 32;
+    const int nbk = (n_free + R_df - 1) / R_df;
     sim->halo_ptr_h.assign(nbk + 1, 0);
     sim->sl_lcol_h.assign(sl_col.size(), 0);
     std::vector<int> cols;
@@ -1559,7 +1572,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   sim->n_agg = 0;
   sim->cg_ainv_h.clear();
   if (df_fits && n_robots == 1 && sim->params.pcg_precond == 0) {
-    const int R = pcg_df_agg_rows();
+    const int R = R_df / 3;
     const int na = (n_free + R - 1) / R;
     std::vector<double> Ac((size_t)na * na, 0.0);
     for (int v = 0; v < n_free; ++v) {
@@ -1572,7 +1585,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
       sim->cg_ainv_h.assign(Ac.begin(), Ac.end());
     }
   }
-  if (df_fits && !pcg_df_prepare(16 * sim->halo_max + (int)sizeof(float) * 3 * sim->n_agg)) df_fits = false;
+  if (df_fits && !pcg_df_prepare(R_df, 16 * sim->halo_max + (int)sizeof(float) * 3 * sim->n_agg)) df_fits = false;
   // cluster PCG: every robot's rows must fit the cluster's shared memory
   int max_robot_rows = 0;
   for (int r = 0; r < sim->n_robots; ++r)
@@ -1647,7 +1660,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
     // Block boundaries fall on whole aggregates of SA rows counted from the
     // robot's first row (a block owns at most SEG_AGG_MAX aggregates), so the
     // per-robot coarse correction below can be summed block by block.
-    const int SA = pcg_df_agg_rows();
+    const int SA = 128;  // the segmented kernel's aggregate rows
     bool coarse_ok = !fp64 && sim->params.pcg_precond == 0;
     used = 0;
     for (int r = 0; r < R; ++r) {
@@ -1715,7 +1728,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   if (sim->pcg_seg) {
     // partials buffer is sized by pcg_grid (already >= seg_blocks)
   } else if (sim->pcg_variant == 5) {
-    sim->pcg_grid = std::max(1, (n_free + PCG_DF_THREADS - 1) / PCG_DF_THREADS);
+    sim->pcg_grid = std::max(1, (n_free + R_df - 1) / R_df);
   } else if (sim->pcg_rr) {
     sim->pcg_grid = std::max(1, (n_free + PCG_RR_THREADS - 1) / PCG_RR_THREADS);
   } else {

@@ -155,6 +155,7 @@ struct Dev {
   const int* halo_rows;  //   distinct rows each block's SpMV reads (sorted per block)
   const int* sl_lcol;    //   per sliced-ELL entry: the column's index in its block's halo
   int halo_max;          //   longest halo (rows)
+  int df_rows;           //   rows (threads) per block: 288 or 384
   const float* cg_ainv;  // dataflow PCG coarse correction: A_c^-1 (n_agg x n_agg, row-major)
   int n_agg;             //   aggregates of 128 consecutive free rows; 0 = Jacobi only
   // collision

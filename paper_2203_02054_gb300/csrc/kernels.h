@@ -20,7 +20,8 @@ static constexpr int PCG_RR_MAXW = 16;   // widest sliced-ELL row kept in regist
 static constexpr int PCG_CL_THREADS = 1024;
 static constexpr int PCG_SEG_THREADS = 256;
 static constexpr int PCG_SEG_AGG_MAX = 64;  // aggregates per block of the segmented PCG's coarse correction
-static constexpr int PCG_DF_THREADS = 384;
+static constexpr int PCG_DF_THREADS = 384;     // rows (threads) per block of the dataflow PCG
+static constexpr int PCG_DF_ROWS_SMALL = 288;  // the same with 9 warps, for systems that fit 152 such blocks
 static constexpr int PCG_DF_REPLICAS = 4;  // copies of the dataflow PCG's reduction slots
 static constexpr size_t PCG_DF_HALO_MAX_BYTES = 160 * 1024;  // halo words in shared memory
 static constexpr int PCG_CL_SIZE = 16;   // CTAs per cluster (non-portable size)
@@ -39,9 +40,8 @@ template <typename T>
 cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st);
 template <typename T>
 int pcg_rr_max_rows();
-int pcg_df_max_rows();
-bool pcg_df_prepare(int smem_bytes);
-int pcg_df_agg_rows();
+int pcg_df_max_rows(int rows);
+bool pcg_df_prepare(int rows, int smem_bytes);
 template <typename T>
 int pcg_seg_max_blocks();
 template <typename T>

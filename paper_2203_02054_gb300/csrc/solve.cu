@@ -1355,7 +1355,7 @@ __device__ __forceinline__ bool df_reduce(const Dev<float>& d, unsigned e, const
 
 // ---- two-level preconditioner of the dataflow kernel ----------------------
 // M^-1 = D^-1 + Z A_c^-1 Z^T: Jacobi plus an additive coarse correction over
-// aggregates of DF_AGG_ROWS consecutive rows (compact pieces of the body: the
+// aggregates of ROWS / 3 consecutive rows (compact pieces of the body: the
 // free rows are numbered by recursive coordinate bisection), Z the 0/1
 // aggregation matrix and A_c = Z^T L Z the Galerkin coarse matrix of the
 // spring-free Laplacian (both SPD, so M is SPD: A + k diag(mask) >= L only
@@ -1368,9 +1368,9 @@ __device__ __forceinline__ bool df_reduce(const Dev<float>& d, unsigned e, const
 // publishes in the reduction it already makes, so g(r_k) and g(w_k) are
 // formed fresh from that round's sums (only g(s) is carried, like s itself),
 // and the coarse correction costs no extra grid-wide wait.
-static constexpr int DF_AGG_ROWS = 128;
-static constexpr int DF_AGG = PCG_DF_THREADS / DF_AGG_ROWS;  // aggregates per block
-static constexpr int DF_SLOT_C = 4 + 4 * DF_AGG;             // slot words with the aggregate sums
+static constexpr int DF_AGG = 3;                 // aggregates per block (of ROWS / 3 rows each)
+static constexpr int DF_SLOT_C = 4 + 4 * DF_AGG;  // slot words with the aggregate sums
+static constexpr int SEG_AGG_ROWS = 128;         // aggregate rows of the segmented batch kernel
 
 // All threads: per-warp sums of w and r over the warp's rows (fixed shuffle
 // trees), stored by lane 0 in sz[warp]; call before block_sums*, whose
@@ -1404,7 +1404,7 @@ __device__ __forceinline__ DW shfl0(DW v) {
 // order) as one slot of epoch e, one copy each; lane 0 then arrives on the
 // grid counter and waits for the round to complete.  Returns false
 // (warp-uniform) when the wait gave up or another block aborted.
-template <typename S>
+template <int WPA, typename S>
 __device__ __forceinline__ bool df_publish_c(const Dev<float>& d, unsigned e, const S (&bs_l0)[3],
                                              const float (*sz)[6]) {
   const int lane = threadIdx.x & 31;
@@ -1418,7 +1418,6 @@ __device__ __forceinline__ bool df_publish_c(const Dev<float>& d, unsigned e, co
     unsigned long long* slot = df_slots(d, e, lane) + DF_SLOT_C * (size_t)blockIdx.x;
     st_v2_relaxed(slot, w[0], w[1]);
     st_v2_relaxed(slot + 2, w[2], w[3]);
-    constexpr int WPA = DF_AGG_ROWS / 32;
 #pragma unroll
     for (int k = 0; k < DF_AGG; ++k) {
       float z[6];
@@ -1578,9 +1577,11 @@ __device__ __forceinline__ void df_gather_coarse(const Dev<float>& d, unsigned e
   }
 }
 
-template <int MAXW, bool COARSE>
-__global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
-  constexpr int NW = PCG_DF_THREADS / 32;
+template <int MAXW, bool COARSE, int ROWS>
+__global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
+  constexpr int NW = ROWS / 32;
+  constexpr int AGG_ROWS = ROWS / DF_AGG;
+  static_assert(AGG_ROWS % 32 == 0, "aggregates of whole warps");
   __shared__ CgShared<float> cs;
   __shared__ double sc[2];  // bb, rr of the first reduction: used by lane 0 of warp 0 only
   __shared__ DW s_st[3];    // gamma, alpha, rr of the CG recurrence (double words)
@@ -1614,9 +1615,9 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   __shared__ float s_g[2][DF_AGG][3];  // g(w), g(r) of the block's aggregates
   __shared__ int s_ok;
   float* ainv = reinterpret_cast<float*>(halo + 2 * (size_t)d.halo_max);
-  const int ia = (int)threadIdx.x / DF_AGG_ROWS;  // this row's aggregate within the block
+  const int ia = (int)threadIdx.x / AGG_ROWS;  // this row's aggregate within the block
   if constexpr (COARSE) {
-    for (int k = threadIdx.x; k < DF_AGG * d.n_agg; k += PCG_DF_THREADS) {
+    for (int k = threadIdx.x; k < DF_AGG * d.n_agg; k += ROWS) {
       const int r = k / d.n_agg, j = k - r * d.n_agg;
       const int a = DF_AGG * (int)blockIdx.x + r;
       ainv[k] = a < d.n_agg ? d.cg_ainv[(size_t)a * d.n_agg + j] : 0.0f;
@@ -1638,9 +1639,9 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   auto spmv = [&](unsigned e, const float (&self)[3], float (&ax)[3]) {
     const unsigned long long* buf = d.df_u + (size_t)(e & 1u) * ustride;
     const unsigned long long tag = df_tag(e);
-    unsigned stale = 0;  // bit q: this thread's row threadIdx.x + q * PCG_DF_THREADS is not yet current
+    unsigned long long stale = 0;  // bit q: this thread's row threadIdx.x + q * ROWS is not yet current
 #pragma unroll 4
-    for (int k = threadIdx.x, q = 0; k < nh; k += PCG_DF_THREADS, ++q) {
+    for (int k = threadIdx.x, q = 0; k < nh; k += ROWS, ++q) {
       unsigned long long w0, w1;
       ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
       if (df_has(w0, tag) && df_has(w1, tag)) {
@@ -1648,13 +1649,13 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
         df_unpack_u(w0, w1, vx, vy, vz);
         halo4[k] = make_float4(vx, vy, vz, 0.0f);
       } else {
-        stale |= 1u << q;
+        stale |= 1ull << q;
       }
     }
     if (stale) {
       DfWait wt;
-      for (int k = threadIdx.x, q = 0; k < nh; k += PCG_DF_THREADS, ++q) {
-        if (!(stale & (1u << q))) continue;
+      for (int k = threadIdx.x, q = 0; k < nh; k += ROWS, ++q) {
+        if (!(stale & (1ull << q))) continue;
         unsigned long long w0, w1;
         do {
           ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
@@ -1691,7 +1692,7 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
   // completed.
   auto reduce_c = [&](unsigned e, const auto (&bs)[3], auto dots) -> bool {
     if (w0) {
-      const bool ok = df_publish_c(d, e, bs, s_zw);
+      const bool ok = df_publish_c<AGG_ROWS / 32>(d, e, bs, s_zw);
       if (lane == 0) s_ok = ok;
     }
     __syncthreads();
@@ -1876,7 +1877,7 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
     // per-iteration words reset for the next iteration
     double el[1] = {0.0}, e_loc[1];
     if (d.rhs_in_pcg && d.stats)
-      for (int k = threadIdx.x; k < d.n_e_local; k += PCG_DF_THREADS) el[0] += d.e_partials[k];
+      for (int k = threadIdx.x; k < d.n_e_local; k += ROWS) el[0] += d.e_partials[k];
     block_sums<1, NW>(el, cs.sh, e_loc);
     if (threadIdx.x == 0) {
       const double rr = it > 0 ? (double)s_st[2].hi + (double)s_st[2].lo : sc[1];
@@ -1897,12 +1898,12 @@ __global__ void __launch_bounds__(PCG_DF_THREADS, 1) k_pcg_df(Dev<float> d) {
 // every block sees the same value) or at the iteration cap.
 // Per-robot coarse correction of the segmented kernel (COARSE): the same
 // additive two-level preconditioner as the dataflow kernel's, per robot, with
-// aggregates of DF_AGG_ROWS rows counted from the robot's first row and block
+// aggregates of SEG_AGG_ROWS rows counted from the robot's first row and block
 // boundaries on whole aggregates.  In a pass, round m of the block's threads
 // covers the rows lo + 256 m + t, i.e. the block's local aggregates 2m (warps
 // 0..3) and 2m + 1 (warps 4..7); each warp adds its rows' values by a fixed
 // shuffle tree and the four warp sums of an aggregate are added in order.
-static constexpr int SEG_WPA = DF_AGG_ROWS / 32;  // warps per aggregate
+static constexpr int SEG_WPA = SEG_AGG_ROWS / 32;  // warps per aggregate
 
 template <int NV>
 __device__ __forceinline__ void seg_agg_partial(const float (&v)[NV], int m, float (*zp)[PCG_SEG_THREADS / 32][6],
@@ -1960,9 +1961,9 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
     rob = d.seg_robot[b];
     r0 = d.robot_row[rob];
     na_r = d.seg_agg_base[rob + 1] - d.seg_agg_base[rob];
-    ga0 = d.seg_agg_base[rob] + (lo - r0) / DF_AGG_ROWS;
-    na_b = (hi - lo + DF_AGG_ROWS - 1) / DF_AGG_ROWS;
-    ainv = d.seg_ainv + d.seg_ainv_off[rob] + (size_t)((lo - r0) / DF_AGG_ROWS) * na_r;
+    ga0 = d.seg_agg_base[rob] + (lo - r0) / SEG_AGG_ROWS;
+    na_b = (hi - lo + SEG_AGG_ROWS - 1) / SEG_AGG_ROWS;
+    ainv = d.seg_ainv + d.seg_ainv_off[rob] + (size_t)((lo - r0) / SEG_AGG_ROWS) * na_r;
   }
   // the block's aggregate sums of this pass into the global exchange array
   // (call after a __syncthreads that follows the pass); which = 0 w, 1 r
@@ -2044,7 +2045,7 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
     __syncthreads();
     if (!done)
       for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
-        const int a = (i - lo) / DF_AGG_ROWS;
+        const int a = (i - lo) / SEG_AGG_ROWS;
         R4<T> ui = u[i];
         ui.x += (T)s_gr[a][0];
         ui.y += (T)s_gr[a][1];
@@ -2152,7 +2153,7 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
           R4<T> un;
           un.x = ri.x / dg; un.y = ri.y / dg; un.z = ri.z / dg; un.w = T(0);
           if constexpr (COARSE) {
-            const int a = (i - lo) / DF_AGG_ROWS;
+            const int a = (i - lo) / SEG_AGG_ROWS;
             un.x += (T)s_gr[a][0];
             un.y += (T)s_gr[a][1];
             un.z += (T)s_gr[a][2];
@@ -2554,22 +2555,28 @@ int pcg_rr_max_rows() {
   return sms * per * PCG_RR_THREADS;
 }
 
-bool pcg_df_prepare(int smem_bytes) {
-  return cudaFuncSetAttribute(k_pcg_df<PCG_RR_MAXW, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+template <int ROWS>
+static bool pcg_df_prepare_rows(int smem_bytes) {
+  return cudaFuncSetAttribute(k_pcg_df<PCG_RR_MAXW, false, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               smem_bytes) == cudaSuccess &&
-         cudaFuncSetAttribute(k_pcg_df<PCG_RR_MAXW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+         cudaFuncSetAttribute(k_pcg_df<PCG_RR_MAXW, true, ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               smem_bytes) == cudaSuccess;
 }
+bool pcg_df_prepare(int rows, int smem_bytes) {
+  return rows == PCG_DF_ROWS_SMALL ? pcg_df_prepare_rows<PCG_DF_ROWS_SMALL>(smem_bytes)
+                                   : pcg_df_prepare_rows<PCG_DF_THREADS>(smem_bytes);
+}
 
-int pcg_df_agg_rows() { return DF_AGG_ROWS; }
-
-int pcg_df_max_rows() {
+int pcg_df_max_rows(int rows) {
   int dev = 0, sms = 0, per = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_df<PCG_RR_MAXW, true>, PCG_DF_THREADS, 0);
+  if (rows == PCG_DF_ROWS_SMALL)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_df<PCG_RR_MAXW, true, PCG_DF_ROWS_SMALL>, rows, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg_df<PCG_RR_MAXW, true, PCG_DF_THREADS>, rows, 0);
   const int blocks = std::min(sms * per, 32 * DF_MAXQ);
-  return blocks * PCG_DF_THREADS;
+  return blocks * rows;
 }
 
 template <typename T>
@@ -2577,7 +2584,7 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st) 
   if (d.n_free == 0) return cudaSuccess;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(variant == 5 ? PCG_DF_THREADS : variant == 2 ? PCG_RR_THREADS : PCG_THREADS);
+  cfg.blockDim = dim3(variant == 5 ? d.df_rows : variant == 2 ? PCG_RR_THREADS : PCG_THREADS);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
@@ -2594,11 +2601,14 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st) 
                             sizeof(unsigned long long) * PCG_DF_REPLICAS * 2 * DF_SLOT_C * (size_t)(grid + 1), st);
       if (e != cudaSuccess) return e;
       cfg.dynamicSmemBytes = 16 * (size_t)d.halo_max;
+      const bool small = d.df_rows == PCG_DF_ROWS_SMALL;
       if (d.n_agg > 0) {
         cfg.dynamicSmemBytes += sizeof(float) * DF_AGG * (size_t)d.n_agg;
-        return cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW, true>, d);
+        return small ? cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW, true, PCG_DF_ROWS_SMALL>, d)
+                     : cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW, true, PCG_DF_THREADS>, d);
       }
-      return cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW, false>, d);
+      return small ? cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW, false, PCG_DF_ROWS_SMALL>, d)
+                   : cudaLaunchKernelEx(&cfg, k_pcg_df<PCG_RR_MAXW, false, PCG_DF_THREADS>, d);
     } else {
       return cudaErrorInvalidValue;
     }
