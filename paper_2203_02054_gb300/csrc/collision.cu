@@ -82,7 +82,7 @@ __device__ __forceinline__ int cell_coord_f(float x, float inv_cell) {
   return (int)c;
 }
 
-// Block-reduced bounding box of the item boxes (count pass only).
+// Block-reduced bounding box of the valid item boxes (count pass only).
 __device__ __forceinline__ void reduce_box(Ctrl* c, bool valid, const double lo[3], const double hi[3]) {
   __shared__ long long s_lo[3][8], s_hi[3][8];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -118,9 +118,15 @@ __global__ void __launch_bounds__(256) k_grid_bin(Dev<T> d) {
   T lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
   const bool ok = i < n && item_box_t(d, i, lo, hi);
   if (!FILL) {
-    const double lod[3] = {(double)lo[0], (double)lo[1], (double)lo[2]};
-    const double hid[3] = {(double)hi[0], (double)hi[1], (double)hi[2]};
-    reduce_box(d.ctrl, ok, lod, hid);
+    // the box of the boundary faces bounds the ray walks (no face lies beyond it)
+    const bool face = ok && i >= d.n_t;
+    double lod[3] = {0.0, 0.0, 0.0}, hid[3] = {0.0, 0.0, 0.0};
+    if (face)
+      for (int j = 0; j < 3; ++j) {
+        lod[j] = (double)lo[j];
+        hid[j] = (double)hi[j];
+      }
+    reduce_box(d.ctrl, face, lod, hid);
   }
   if (i >= n) return;
   if (!ok) {
@@ -654,8 +660,8 @@ __device__ int ray_cast_warp(const Dev<T>& d, int v, int rv, V3 o, V3 dir, doubl
   rb1 = rb2 = 0.0;
   // DDA set-up: lane a < 3 forms axis a's start cell, step, first boundary
   // parameter and increment, and its bound on the ray parameter from the
-  // bounding box of this iteration's items (the ray can meet no face beyond
-  // it); the warp shares them by shuffles, so the FP64 divisions run once per
+  // bounding box of this iteration's boundary faces (the ray can meet no face
+  // beyond it); the warp shares them by shuffles, so the FP64 divisions run once per
   // axis, not once per lane.  tbox is the minimum over the axes.
   int cell[3], step[3];
   double tmax[3], tdel[3], tbox;
@@ -847,16 +853,21 @@ __device__ void spring_update_vertex(const Dev<T>& d, int qi, int& active_out, u
   {
     const int v = d.q_verts[qi];
     const V3 x = pos(d, v);
-    // area-weighted vertex normal of the incident boundary faces
-    V3 n = {0.0, 0.0, 0.0};
-    for (int k = d.qf_ptr[qi]; k < d.qf_ptr[qi + 1]; ++k) {
-      V3 q0, q1, q2;
-      int4 fv;
-      face_verts(d, d.qf[k], q0, q1, q2, fv);
-      n = add(n, cross(sub(q1, q0), sub(q2, q0)));
-    }
-    const double nl = norm(n);
-    n = nl > 0.0 ? scl(1.0 / nl, n) : V3{0.0, 0.0, 0.0};
+    // area-weighted unit vertex normal of the incident boundary faces, formed
+    // only where it is used (a queued ray cast, a sphere spring whose vertex
+    // sits at the centre): most vertices have no contact, and this FP64
+    // work is the costliest part of the update
+    auto normal = [&]() {
+      V3 n = {0.0, 0.0, 0.0};
+      for (int k = d.qf_ptr[qi]; k < d.qf_ptr[qi + 1]; ++k) {
+        V3 q0, q1, q2;
+        int4 fv;
+        face_verts(d, d.qf[k], q0, q1, q2, fv);
+        n = add(n, cross(sub(q1, q0), sub(q2, q0)));
+      }
+      const double nl = norm(n);
+      return nl > 0.0 ? scl(1.0 / nl, n) : V3{0.0, 0.0, 0.0};
+    };
     int active = d.sp.active[qi];
     int kind = d.sp.kind[qi];
     int face = d.sp.face[qi];
@@ -884,7 +895,7 @@ __device__ void spring_update_vertex(const Dev<T>& d, int qi, int& active_out, u
       const double r = d.spheres[4 * js + 3];
       V3 u = sub(x, c);
       const double nu = norm(u);
-      u = nu == 0.0 ? scl(-1.0, n) : scl(1.0 / nu, u);
+      u = nu == 0.0 ? scl(-1.0, normal()) : scl(1.0 / nu, u);
       active = 1;
       kind = 1;
       face = js;
@@ -903,6 +914,7 @@ __device__ void spring_update_vertex(const Dev<T>& d, int qi, int& active_out, u
       deferred = true;
       const int slot = atomicAdd(&d.ctrl->n_cast, 1);  // < n_q: each vertex enters once
       d.cast_list[slot] = qi;
+      const V3 n = normal();
       d.cast_nrm[3 * qi] = n.x;
       d.cast_nrm[3 * qi + 1] = n.y;
       d.cast_nrm[3 * qi + 2] = n.z;
@@ -915,7 +927,7 @@ __device__ void spring_update_vertex(const Dev<T>& d, int qi, int& active_out, u
         if (nu - r > eps) {
           active = 0;
         } else {
-          u = nu == 0.0 ? scl(-1.0, n) : scl(1.0 / nu, u);
+          u = nu == 0.0 ? scl(-1.0, normal()) : scl(1.0 / nu, u);
           tgt = add(c, scl(r + eps, u));
         }
       } else if (kind == 2) {

@@ -104,14 +104,15 @@ def test_full_batch_of_256_fingers_properties():
     X = sim.positions()
     assert np.all(np.isfinite(X))
     # spot check: three robots against their own plain GPU runs, both with
-    # the two-level preconditioner (the batch's segmented kernel applies the
-    # same per-robot coarse correction, over the same 128-row aggregates, as
-    # the single-robot kernel; with different preconditioners the iterates
-    # differ and over several iterations with contacts the two trajectories
-    # drift apart by more than 1e-5 of the diagonal)
+    # the two-level preconditioner over the same 128-row aggregates (the
+    # batch's segmented kernel applies the same per-robot coarse correction
+    # as the single-robot kernel with 384-row blocks; with different
+    # preconditioners the iterates differ and over several iterations with
+    # contacts the two trajectories drift apart by more than 1e-5 of the
+    # diagonal)
     vo, _ = _offsets(batch)
     for r in (0, 97, 255):
-        one = casim.Sim(batch[r])
+        one = casim.Sim(batch[r], pcg_block=384)
         one.step(5)
         assert one.sync() == 0
         err = np.abs(X[vo[r]:vo[r + 1]] - one.positions()).max()
