@@ -33,11 +33,11 @@ namespace casim {
 //   TwoSum (Knuth) and Fast2Sum (Dekker),
 //   the compensated dot product Dot2 of Ogita, Rump and Oishi (2005), kept
 //   unrounded as a double word,
-//   the accurate double-word addition of Joldes, Muller and Popescu (2017),
-//   relative error at most 3u^2 (u = 2^-24) per addition.
+//   the double-word addition of Joldes, Muller and Popescu (2017) in its
+//   11-operation form (below), relative error a few u^2 (u = 2^-24).
 // Every operation is an explicitly rounded intrinsic, so the compiler can
-// neither contract nor reassociate them.  A block's double-word sum is
-// converted to FP64 once and the block partials are summed in FP64.
+// neither contract nor reassociate them.  Block partials are summed in block
+// order (FP64 in the barrier kernels, double words in the dataflow kernel).
 struct DW {
   float hi, lo;
 };
@@ -52,18 +52,6 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
 __device__ __forceinline__ void fast_two_sum_f(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
-__device__ __forceinline__ DW dw_add(DW x, DW y) {
-  float sh, sl, th, tl, vh, vl;
-  two_sum_f(x.hi, y.hi, sh, sl);
-  two_sum_f(x.lo, y.lo, th, tl);
-  const float c = __fadd_rn(sl, th);
-  fast_two_sum_f(sh, c, vh, vl);
-  const float w = __fadd_rn(tl, vl);
-  DW z;
-  fast_two_sum_f(vh, w, z.hi, z.lo);
-  return z;
 }
 
 // Sloppy double-word addition (Joldes, Muller, Popescu 2017, Algorithm 5):
@@ -161,7 +149,7 @@ __device__ __forceinline__ double dot3(double a0, double a1, double a2, double b
   return fma(a2, b2, fma(a1, b1, a0 * b0));
 }
 
-__device__ __forceinline__ DW acc_add(DW a, DW b) { return dw_add(a, b); }
+__device__ __forceinline__ DW acc_add(DW a, DW b) { return dw_add_sloppy(a, b); }
 __device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
 __device__ __forceinline__ DW shfl_down(DW v, int o) {
   return DW{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
@@ -1597,7 +1585,7 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
   int lcol[MAXW];  // columns as indices into the block's halo
   float val[MAXW];
   int width = 0;
-  float dg = 1.0f;
+  float dg = 1.0f, idg = 1.0f;  // the row's diagonal and its reciprocal (the Jacobi part of the preconditioner)
   if (act) {
     const int sl = i >> 5, ln = i & 31;
     const int base = d.sl_ptr[sl];
@@ -1721,7 +1709,8 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
       a0[1] = dw_from(a01[1]);
       for (int c = 0; c < 3; ++c) r[c] = (float)rv[c];
     }
-    for (int c = 0; c < 3; ++c) u[c] = r[c] / dg;
+    idg = 1.0f / dg;
+    for (int c = 0; c < 3; ++c) u[c] = r[c] * idg;
     if constexpr (!COARSE) store_u(ue, u);
   }
   {
@@ -1755,7 +1744,7 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
     DW a1[2] = {acc_zero<DW>(), acc_zero<DW>()};
     if constexpr (COARSE) {
       if (act) {
-        for (int c = 0; c < 3; ++c) u[c] = r[c] / dg + gr[c];
+        for (int c = 0; c < 3; ++c) u[c] = r[c] * idg + gr[c];
         store_u(ue, u);
       }
     }
@@ -1806,7 +1795,7 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
         for (int c = 0; c < 3; ++c) {
           dd[c] += ta * p[c];
           r[c] -= ta * s[c];
-          u[c] = r[c] / dg;
+          u[c] = r[c] * idg;
           if constexpr (COARSE) u[c] += gr[c];
         }
         store_u(ue, u);
@@ -2004,7 +1993,8 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
       residual_row_f64(d, i, dg, rv, a0);
       R4<T> ri, ui;
       ri.x = (T)rv[0]; ri.y = (T)rv[1]; ri.z = (T)rv[2]; ri.w = T(0);
-      ui.x = ri.x / dg; ui.y = ri.y / dg; ui.z = ri.z / dg; ui.w = T(0);
+      const T idg = T(1) / dg;
+      ui.x = ri.x * idg; ui.y = ri.y * idg; ui.z = ri.z * idg; ui.w = T(0);
       r[i] = ri;
       u[i] = ui;
       dx[i] = zero;
@@ -2149,9 +2139,9 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
           ri.x -= ta * si.x; ri.y -= ta * si.y; ri.z -= ta * si.z;
           dx[i] = di;
           r[i] = ri;
-          const T dg = d.diag[i];
+          const T idg = T(1) / d.diag[i];
           R4<T> un;
-          un.x = ri.x / dg; un.y = ri.y / dg; un.z = ri.z / dg; un.w = T(0);
+          un.x = ri.x * idg; un.y = ri.y * idg; un.z = ri.z * idg; un.w = T(0);
           if constexpr (COARSE) {
             const int a = (i - lo) / SEG_AGG_ROWS;
             un.x += (T)s_gr[a][0];
