@@ -423,20 +423,70 @@ __device__ __forceinline__ void rhs_row(const Dev<T>& d, int i, R4<double>& b, T
   }
 }
 
+// The same row for FP32 positions with the FP32 terms added as double words
+// (TwoSum) and the FP64 spring and fixed-vertex terms only on the rows that
+// have them; the spring energy as a double word.
+__device__ __forceinline__ void rhs_row_dw(const Dev<float>& d, int i, R4<double>& b, float& diag, DW& es) {
+  DW bx{0.0f, 0.0f}, by{0.0f, 0.0f}, bz{0.0f, 0.0f};
+  const int k1 = d.inc_ptr[i + 1];
+#pragma unroll 4
+  for (int k = d.inc_ptr[i]; k < k1; ++k) {
+    const R4<float> p = d.P[d.inc[k]];
+    dw_acc(bx, p.x);
+    dw_acc(by, p.y);
+    dw_acc(bz, p.z);
+  }
+  bx = dw_norm(bx);
+  by = dw_norm(by);
+  bz = dw_norm(bz);
+  b = R4<double>{(double)bx.hi + (double)bx.lo, (double)by.hi + (double)by.lo, (double)bz.hi + (double)bz.lo, 0.0};
+  const R4<double> sc = d.spring_c[i];
+  const double km = d.k_spring * sc.w;
+  const R4<double> bf = d.bfix[i];
+  diag = d.diagL[i] + (float)km;
+  es = DW{0.0f, 0.0f};
+  if (km != 0.0) {
+    b.x += km * sc.x;
+    b.y += km * sc.y;
+    b.z += km * sc.z;
+    const R4<float> xi = d.X[i];
+    const double ex = (double)xi.x - sc.x, ey = (double)xi.y - sc.y, ez = (double)xi.z - sc.z;
+    es = dw_from(km * (ex * ex + ey * ey + ez * ez));
+  }
+  if (bf.x != 0.0 || bf.y != 0.0 || bf.z != 0.0) {
+    b.x -= bf.x;
+    b.y -= bf.y;
+    b.z -= bf.z;
+  }
+}
+
 template <typename T, int BS>
 __global__ void __launch_bounds__(BS) k_rhs(Dev<T> d) {
   __shared__ double shd[32];
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double es = 0.0;
-  if (i < d.n_free) {
-    R4<double> b;
-    T dg;
-    rhs_row(d, i, b, dg, es);
-    d.b[i] = b;
-    d.diag[i] = dg;
+  if constexpr (std::is_same<T, float>::value) {
+    DW es[1] = {{0.0f, 0.0f}}, bs[1];
+    if (i < d.n_free) {
+      R4<double> b;
+      float dg;
+      rhs_row_dw(d, i, b, dg, es[0]);
+      d.b[i] = b;
+      d.diag[i] = dg;
+    }
+    block_sums_dw<1, BS / 32>(es, shd, bs);
+    if (threadIdx.x == 0) d.e_partials[d.n_e_local + blockIdx.x] = acc_to_f64(bs[0]);
+  } else {
+    double es = 0.0;
+    if (i < d.n_free) {
+      R4<double> b;
+      T dg;
+      rhs_row(d, i, b, dg, es);
+      d.b[i] = b;
+      d.diag[i] = dg;
+    }
+    const double s = block_sum(es, shd);
+    if (threadIdx.x == 0) d.e_partials[d.n_e_local + blockIdx.x] = s;
   }
-  const double s = block_sum(es, shd);
-  if (threadIdx.x == 0) d.e_partials[d.n_e_local + blockIdx.x] = s;
 }
 
 // End of an outer iteration (one thread): the energy into this iteration's
@@ -2475,10 +2525,24 @@ template <typename T>
 __global__ void k_finalize(Dev<T> d) {
   __shared__ double sh[32];
   const int n = d.n_e_local + d.n_e_spring;
-  // fixed-order sum: thread-strided then a fixed tree
-  double a = 0.0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a += d.e_partials[i];
-  const double t = block_sum(a, sh);
+  // fixed-order sum: eight interleaved thread-strided chains (so that the
+  // loads overlap), added in a fixed order, then a fixed tree
+  constexpr int K = 8;
+  double a[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) a[k] = 0.0;
+  const int step = (int)blockDim.x * K;
+  for (int i0 = threadIdx.x; i0 < n; i0 += step) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int i = i0 + k * (int)blockDim.x;
+      if (i < n) a[k] += d.e_partials[i];
+    }
+  }
+  double at = 0.0;
+#pragma unroll
+  for (int k = 0; k < K; ++k) at += a[k];
+  const double t = block_sum(at, sh);
   if (threadIdx.x == 0) finalize_iteration(d, t);
 }
 
@@ -2609,7 +2673,7 @@ cudaError_t launch_pcg(const Dev<T>& d, int grid, int variant, cudaStream_t st) 
 
 template <typename T>
 void launch_finalize(const Dev<T>& d, cudaStream_t st) {
-  k_finalize<T><<<1, 256, 0, st>>>(d);
+  k_finalize<T><<<1, 1024, 0, st>>>(d);
 }
 
 template <typename T>
