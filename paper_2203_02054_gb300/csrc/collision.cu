@@ -608,6 +608,12 @@ __device__ void face_verts(const Dev<T>& d, int f, V3& q0, V3& q1, V3& q2, int4&
 // Warp argmin of (key, face id) over the lanes (face id < 0: no candidate);
 // every lane ends with the minimum and its barycentrics.  The order is total,
 // so the result does not depend on which lane held which face.
+// Keys are non-negative doubles (ray parameters t > 0, squared distances), so
+// their bit patterns order like their values and the comparisons run on the
+// integer pipes: every lane of the warp takes part, and FP64 instructions
+// with 32 active lanes are what the narrow FP64 pipe of this part is slowest
+// at.
+__device__ __forceinline__ unsigned long long key_bits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ void warp_argmin(int& f, double& key, double& b1, double& b2) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
@@ -615,7 +621,8 @@ __device__ __forceinline__ void warp_argmin(int& f, double& key, double& b1, dou
     const double ok = __shfl_xor_sync(0xffffffffu, key, o);
     const double o1 = __shfl_xor_sync(0xffffffffu, b1, o);
     const double o2 = __shfl_xor_sync(0xffffffffu, b2, o);
-    if (of >= 0 && (f < 0 || ok < key || (ok == key && of < f))) {
+    const unsigned long long kb = key_bits(key), okb = key_bits(ok);
+    if (of >= 0 && (f < 0 || okb < kb || (okb == kb && of < f))) {
       f = of;
       key = ok;
       b1 = o1;
@@ -657,6 +664,7 @@ __device__ int ray_cast_warp(const Dev<T>& d, int v, int rv, V3 o, V3 dir, doubl
   fell_back = 0;
   int best_f = -1;
   double best_t = 0.0;
+  unsigned long long best_lim = 0;  // bits of best_t (1 + 1e-9)
   rb1 = rb2 = 0.0;
   // DDA set-up: lane a < 3 forms axis a's start cell, step, first boundary
   // parameter and increment, and its bound on the ray parameter from the
@@ -685,6 +693,12 @@ __device__ int ray_cast_warp(const Dev<T>& d, int v, int rv, V3 o, V3 dir, doubl
         td_a = -d.cell / dva;
         tb_a = (blo - ova) / dva;
       }
+      // ray parameters of the walk are compared by their bit patterns below,
+      // so they are made non-negative: a start within rounding of a cell face
+      // can give -0.0 or a tiny negative first boundary (either way the walk
+      // first steps across it), and the walk starts inside the faces' box
+      tm_a = tm_a > 0.0 ? tm_a : 0.0;
+      tb_a = tb_a > 0.0 ? tb_a : 0.0;
     }
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
@@ -720,17 +734,19 @@ __device__ int ray_cast_warp(const Dev<T>& d, int v, int rv, V3 o, V3 dir, doubl
     }
     if (__any_sync(0xffffffffu, lf >= 0)) {
       warp_argmin(lf, lt, l1, l2);
-      if (best_f < 0 || lt < best_t || (lt == best_t && lf < best_f)) {
+      if (best_f < 0 || key_bits(lt) < key_bits(best_t) || (lt == best_t && lf < best_f)) {
         best_f = lf;
         best_t = lt;
         rb1 = l1;
         rb2 = l2;
+        best_lim = key_bits(best_t * (1.0 + 1e-9));
       }
     }
-    const double texit = fmin(tmax[0], fmin(tmax[1], tmax[2]));
-    if (best_f >= 0 && best_t * (1.0 + 1e-9) < texit) return best_f;
-    if (!(texit < INFINITY) || texit > tbox) break;
-    const int a = (tmax[0] <= tmax[1] && tmax[0] <= tmax[2]) ? 0 : (tmax[1] <= tmax[2] ? 1 : 2);
+    const unsigned long long m0 = key_bits(tmax[0]), m1 = key_bits(tmax[1]), m2 = key_bits(tmax[2]);
+    const unsigned long long texit = m0 < m1 ? (m0 < m2 ? m0 : m2) : (m1 < m2 ? m1 : m2);
+    if (best_f >= 0 && best_lim < texit) return best_f;
+    if (texit >= key_bits(INFINITY) || texit > key_bits(tbox)) break;
+    const int a = (m0 <= m1 && m0 <= m2) ? 0 : (m1 <= m2 ? 1 : 2);
     cell[a] += step[a];
     tmax[a] += tdel[a];
   }
