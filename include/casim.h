@@ -51,6 +51,8 @@ extern "C" {
 #define CASIM_E_NONFINITE (-6) /* NaN or Inf met on the device                   */
 #define CASIM_E_TIMEOUT (-7)   /* a device-side wait ran out of its budget       */
 #define CASIM_E_OVERFLOW (-8)  /* a device work list exceeded its capacity       */
+#define CASIM_E_BOUNDS (-9)    /* a checked build met an out-of-range gather
+                                  index (see casim_build_checked)                */
 #define CASIM_W_PCG_MAXIT 1    /* PCG stopped at its iteration cap (warning)     */
 #define CASIM_W_PAIRS_TRUNCATED 2 /* a vertex lay in more tets than
                                      max_pairs_per_vertex; its pair list (not its
@@ -108,10 +110,13 @@ typedef struct {
                                has (the cluster kernel uses the hardware cluster
                                barrier), so every wait runs out of
                                wait_budget_cycles and the step ends with
-                               CASIM_E_TIMEOUT                                  */
+                               CASIM_E_TIMEOUT; CASIM_DEBUG_CORRUPT_INCIDENCE
+                               (checked builds only, else CASIM_E_INVALID) plants
+                               an out-of-range gather index                      */
   int32_t pcg_precond;      /* preconditioner of the dataflow kernel (5): 0 auto =
                                two-level (Jacobi plus an additive coarse
-                               correction over aggregates of 128 rows, Galerkin
+                               correction over aggregates of a third of a block,
+                               Galerkin
                                coarse matrix of the Laplacian, its inverse formed
                                at upload); 1 Jacobi only.  Other kernels use
                                Jacobi                                            */
@@ -134,6 +139,10 @@ typedef struct {
 } casim_params;
 
 #define CASIM_DEBUG_BARRIER_NEVER_COMPLETES 1
+/* test-only, accepted by checked builds only: the upload writes one entry of
+   the vertex-to-tet incidence list out of range on the device, so the right-
+   hand-side gather meets it and the step ends with CASIM_E_BOUNDS           */
+#define CASIM_DEBUG_CORRUPT_INCIDENCE 2
 
 /* Per-iteration record (Eq. 8 energy at X_i with the targets of iteration i). */
 typedef struct {
@@ -166,7 +175,9 @@ typedef struct {
                                since the mesh upload: 1 non-finite value, 2 wait
                                timeout, 4 PCG iteration cap, 8 hash / pair
                                overflow, 16 a vertex's pair list truncated at
-                               params.max_pairs_per_vertex                          */
+                               params.max_pairs_per_vertex, 32 an out-of-range
+                               input id, 64 an out-of-range gather index
+                               (checked builds)                                      */
   int32_t pad;
 } casim_stats;
 
@@ -475,6 +486,15 @@ void casim_destroy(casim_sim* sim);
    handle (casim_create, casim_contacts_noalloc).  Valid until the next call
    on the handle (or the next handle-free call on the thread). */
 const char* casim_last_error(const casim_sim* sim);
+
+/* 1 when the library was built with -DCASIM_CHECKED (libcasim_checked.so):
+   every gather index of the hot kernels (tet and face vertices, hash items,
+   incidence entries, matrix columns, PCG halo rows and columns, cast list) is
+   checked on the device, and an index outside its array sets a status bit
+   and reads element 0 instead, so the step ends with CASIM_E_BOUNDS rather
+   than an out-of-range access.  It stands in for a memory checker.  0
+   otherwise.  No error. */
+int casim_build_checked(void);
 
 #ifdef __cplusplus
 }

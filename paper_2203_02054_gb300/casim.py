@@ -19,6 +19,9 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcasim.so")
+# the same library with every gather index of the hot kernels bounds-checked
+# on the device (built alongside it; see casim_build_checked)
+LIB_CHECKED_PATH = os.path.join(HERE, "libcasim_checked.so")
 
 CASIM_OK = 0
 CASIM_E_INVALID = -1
@@ -29,12 +32,14 @@ CASIM_E_CAPACITY = -5
 CASIM_E_NONFINITE = -6
 CASIM_E_TIMEOUT = -7
 CASIM_E_OVERFLOW = -8
+CASIM_E_BOUNDS = -9
 CASIM_W_PCG_MAXIT = 1
 CASIM_W_PAIRS_TRUNCATED = 2
 
 CASIM_FP64 = 0
 CASIM_MIXED = 1
 CASIM_DEBUG_BARRIER_NEVER_COMPLETES = 1
+CASIM_DEBUG_CORRUPT_INCIDENCE = 2
 
 EXPORTS = [
     "casim_default_params", "casim_create", "casim_upload_mesh", "casim_upload_batch", "casim_set_actuation",
@@ -43,7 +48,7 @@ EXPORTS = [
     "casim_get_contacts", "casim_get_springs", "casim_set_springs", "casim_get_targets",
     "casim_get_history", "casim_get_stats", "casim_save_state", "casim_load_state",
     "casim_get_sizes", "casim_get_phase_times", "casim_contacts_noalloc", "casim_remesh_flags",
-    "casim_progressive", "casim_step_anderson", "casim_destroy", "casim_last_error",
+    "casim_progressive", "casim_step_anderson", "casim_destroy", "casim_last_error", "casim_build_checked",
 ]
 
 
@@ -186,6 +191,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                     ctypes.c_double, ctypes.c_double, ctypes.POINTER(casim_outer_record), _I32]
     L.casim_step_anderson.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(casim_aa_record), _I32]
     L.casim_destroy.argtypes = [_P]
+    L.casim_build_checked.argtypes = []
     L.casim_destroy.restype = None
     L.casim_last_error.argtypes = [_P]
     L.casim_last_error.restype = ctypes.c_char_p

@@ -689,7 +689,18 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   CK(cudaMemcpyAsync(sim->tinfo, info.data(), sizeof(R4<T>) * n_t, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->knots_d, sim->knots.data(), sizeof(double) * sim->knots.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->inc_ptr, inc_ptr.data(), sizeof(int) * inc_ptr.size(), cudaMemcpyHostToDevice, st));
-  if (!inc.empty()) CK(cudaMemcpyAsync(sim->inc, inc.data(), sizeof(int) * inc.size(), cudaMemcpyHostToDevice, st));
+  if (!inc.empty()) {
+    if (sim->params.debug_flags & CASIM_DEBUG_CORRUPT_INCIDENCE) {
+      // test-only (checked builds): one incidence entry out of range on the
+      // device, which the checked gathers must catch
+      std::vector<int> bad(inc);
+      bad[0] = 4 * n_t + 7;
+      CK(cudaMemcpyAsync(sim->inc, bad.data(), sizeof(int) * bad.size(), cudaMemcpyHostToDevice, st));
+      CK(cudaStreamSynchronize(st));
+    } else {
+      CK(cudaMemcpyAsync(sim->inc, inc.data(), sizeof(int) * inc.size(), cudaMemcpyHostToDevice, st));
+    }
+  }
   if (!dl.empty()) CK(cudaMemcpyAsync(sim->diagL, dl.data(), sizeof(T) * dl.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->sl_ptr, sl_ptr.data(), sizeof(int) * sl_ptr.size(), cudaMemcpyHostToDevice, st));
   if (!sl_col.empty()) {
@@ -914,6 +925,14 @@ struct Triplet {
 
 }  // namespace
 
+// 1 in builds with -DCASIM_CHECKED (every gather index of the hot kernels
+// bounds-checked on the device, failures reported as CASIM_E_BOUNDS)
+#ifdef CASIM_CHECKED
+static constexpr int kCheckedBuild = 1;
+#else
+static constexpr int kCheckedBuild = 0;
+#endif
+
 extern "C" {
 
 void casim_default_params(casim_params* p) {
@@ -951,7 +970,8 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   else if (!(p.cell_size > 0.0) || !std::isfinite(p.cell_size)) why = "cell_size";
   else if (p.max_pairs_per_vertex < 1 || p.max_pairs_per_vertex > 16) why = "max_pairs_per_vertex";
   else if (p.pcg_kernel < 0 || p.pcg_kernel > 5) why = "pcg_kernel";
-  else if (p.debug_flags & ~CASIM_DEBUG_BARRIER_NEVER_COMPLETES) why = "debug_flags";
+  else if (p.debug_flags & ~(CASIM_DEBUG_BARRIER_NEVER_COMPLETES | (kCheckedBuild ? CASIM_DEBUG_CORRUPT_INCIDENCE : 0)))
+    why = "debug_flags";
   else if (p.pcg_precond < 0 || p.pcg_precond > 1) why = "pcg_precond";
   else if (p.broad_phase < 0 || p.broad_phase > 1) why = "broad_phase";
   else if (p.pcg_block != 0 && p.pcg_block != 288 && p.pcg_block != 384) why = "pcg_block";
@@ -2043,7 +2063,8 @@ int casim_sync(casim_sim* sim) {
   CK(cudaMemset(&sim->ctrl->status, 0, sizeof(int)));
   sim->status_bits |= st;
   int rc = CASIM_OK;
-  if (st & ST_TIMEOUT) rc = CASIM_E_TIMEOUT;
+  if (st & ST_BOUNDS) rc = CASIM_E_BOUNDS;
+  else if (st & ST_TIMEOUT) rc = CASIM_E_TIMEOUT;
   else if (st & ST_NONFINITE) rc = CASIM_E_NONFINITE;
   else if (st & ST_OVERFLOW) rc = CASIM_E_OVERFLOW;
   else if (st & ST_PCG_MAXIT) rc = CASIM_W_PCG_MAXIT;
@@ -2678,6 +2699,8 @@ void casim_destroy(casim_sim* sim) {
   if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
   delete sim;
 }
+
+int casim_build_checked(void) { return kCheckedBuild; }
 
 const char* casim_last_error(const casim_sim* sim) {
   if (!sim) return g_create_error.c_str();

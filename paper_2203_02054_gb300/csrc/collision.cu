@@ -43,11 +43,11 @@ __device__ __forceinline__ bool item_box_t(const Dev<T>& d, int i, T lo[3], T hi
   int vs[4];
   int nv;
   if (i < d.n_t) {
-    const int4 t = d.tet[i];
+    const int4 t = chk_idx4(d.ctrl, d.tet[i], d.n_v);
     vs[0] = t.x; vs[1] = t.y; vs[2] = t.z; vs[3] = t.w;
     nv = 4;
   } else {
-    const int4 f = d.faces[i - d.n_t];
+    const int4 f = chk_face(d.ctrl, d.faces[i - d.n_t], d.n_v);
     vs[0] = f.x; vs[1] = f.y; vs[2] = f.z;
     nv = 3;
   }
@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(BS) k_narrow(Dev<T> d) {
         int e = -1;
         bool hit = false;
         if (k < b1) {
-          e = d.items[k];
-          const int4 t = d.tet[e];
+          e = chk_idx(d.ctrl, d.items[k], d.n_t);
+          const int4 t = chk_idx4(d.ctrl, d.tet[e], d.n_v);
           const bool same_robot = !d.robot_of_tet || d.robot_of_tet[e] == rv;
           if (same_robot && t.x != v && t.y != v && t.z != v && t.w != v) hit = strictly_inside(d, px, py, pz, t);
         }
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(NARROW_BVH_THREADS) k_narrow_bvh(Dev<T> d) {
     const int rv = d.robot_of_vert ? d.robot_of_vert[v] : 0;
     if (d.collision >= 1 && isfinite(px) && isfinite(py) && isfinite(pz)) {
       bvh_point_query(d.bt, rv, (double)px, (double)py, (double)pz, [&](int e) {
-        const int4 t = d.tet[e];
+        const int4 t = chk_idx4(d.ctrl, d.tet[e], d.n_v);
         if (d.robot_of_tet && d.robot_of_tet[e] != rv) return;
         if (t.x == v || t.y == v || t.z == v || t.w == v) return;
         if (!strictly_inside(d, px, py, pz, t)) return;
@@ -599,7 +599,7 @@ __device__ __forceinline__ V3 closest_tri(V3 p, V3 q0, V3 q1, V3 q2, double& b1,
 
 template <typename T>
 __device__ void face_verts(const Dev<T>& d, int f, V3& q0, V3& q1, V3& q2, int4& fv) {
-  fv = d.faces[f];
+  fv = chk_face(d.ctrl, d.faces[chk_idx(d.ctrl, f, d.n_f)], d.n_v);
   q0 = pos(d, fv.x);
   q1 = pos(d, fv.y);
   q2 = pos(d, fv.z);
@@ -1012,7 +1012,7 @@ __global__ void __launch_bounds__(CAST_THREADS) k_cast(Dev<T> d) {
   const int n_cast = d.ctrl->n_cast;
   int active_out = 0;
   for (int j = (int)((blockIdx.x * (unsigned)CAST_THREADS + threadIdx.x) >> 5); j < n_cast; j += n_warps) {
-    const int qi = d.cast_list[j];
+    const int qi = chk_idx(d.ctrl, d.cast_list[j], d.n_q);
     const int v = d.q_verts[qi];
     const V3 x = pos(d, v);
     const V3 n = {d.cast_nrm[3 * qi], d.cast_nrm[3 * qi + 1], d.cast_nrm[3 * qi + 2]};
@@ -1059,7 +1059,7 @@ __global__ void __launch_bounds__(CAST_THREADS) k_cast_bvh(Dev<T> d) {
   const int n_cast = d.ctrl->n_cast;
   int active_out = 0;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n_cast; j += gridDim.x * blockDim.x) {
-    const int qi = d.cast_list[j];
+    const int qi = chk_idx(d.ctrl, d.cast_list[j], d.n_q);
     const int v = d.q_verts[qi];
     const V3 x = pos(d, v);
     const V3 dir = {-d.cast_nrm[3 * qi], -d.cast_nrm[3 * qi + 1], -d.cast_nrm[3 * qi + 2]};

@@ -34,6 +34,7 @@ enum : int {
   ST_OVERFLOW = 8,
   ST_PAIRS_TRUNC = 16,   // a vertex had more self pairs than max_pairs_per_vertex
   ST_BAD_INPUT = 32,     // an input id out of range (checked on the device before use)
+  ST_BOUNDS = 64,        // a gather index out of range (builds with -DCASIM_CHECKED only)
 };
 
 struct IterRec {
@@ -241,6 +242,29 @@ __device__ inline bool finite4(const R4<T>& a) {
 }
 
 __device__ inline void set_status(Ctrl* c, int bits) { atomicOr(&c->status, bits); }
+
+// Gather index check.  In builds with -DCASIM_CHECKED (the stand-in for a
+// memory checker, which this pool does not offer) an index outside [0, n)
+// sets ST_BOUNDS and is replaced by 0, so the access stays inside its array
+// and the step ends with CASIM_E_BOUNDS; other builds use the index as is.
+#ifdef CASIM_CHECKED
+__device__ __forceinline__ int chk_idx(Ctrl* c, int i, int n) {
+  if ((unsigned)i >= (unsigned)n) {
+    atomicOr(&c->status, ST_BOUNDS);
+    return 0;
+  }
+  return i;
+}
+#else
+__device__ __forceinline__ int chk_idx(Ctrl*, int i, int) { return i; }
+#endif
+__device__ __forceinline__ int4 chk_idx4(Ctrl* c, int4 t, int n) {
+  return make_int4(chk_idx(c, t.x, n), chk_idx(c, t.y, n), chk_idx(c, t.z, n), chk_idx(c, t.w, n));
+}
+// a boundary face (x, y, z vertices, w its tet): the three vertex indices
+__device__ __forceinline__ int4 chk_face(Ctrl* c, int4 f, int n_v) {
+  return make_int4(chk_idx(c, f.x, n_v), chk_idx(c, f.y, n_v), chk_idx(c, f.z, n_v), f.w);
+}
 
 // Block-wide sum of one double (blockDim.x a multiple of 32, <= 1024); the
 // result is valid in thread 0.  Fixed reduction order -> deterministic.

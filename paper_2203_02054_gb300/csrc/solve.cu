@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(BS) k_local(Dev<T> d) {
   DW en_w{0.0f, 0.0f};
   unsigned long long ksig = 0;
   if (e < d.n_t) {
-    const int4 t = d.tet[e];
+    const int4 t = chk_idx4(d.ctrl, d.tet[e], d.n_v);
     const R4<T> x0 = d.X[t.x], x1 = d.X[t.y], x2 = d.X[t.z], x3 = d.X[t.w];
     // centered deformed shape X_c = V^d N, formed from differences to x0
     T Xc[3][4];
@@ -405,7 +405,7 @@ __device__ __forceinline__ void rhs_row(const Dev<T>& d, int i, R4<double>& b, T
   double bx = 0.0, by = 0.0, bz = 0.0;
   const int k1 = d.inc_ptr[i + 1];
   for (int k = d.inc_ptr[i]; k < k1; ++k) {
-    const R4<T> p = d.P[d.inc[k]];
+    const R4<T> p = d.P[chk_idx(d.ctrl, d.inc[k], 4 * d.n_t)];
     bx += (double)p.x;
     by += (double)p.y;
     bz += (double)p.z;
@@ -431,7 +431,7 @@ __device__ __forceinline__ void rhs_row_dw(const Dev<float>& d, int i, R4<double
   const int k1 = d.inc_ptr[i + 1];
 #pragma unroll 4
   for (int k = d.inc_ptr[i]; k < k1; ++k) {
-    const R4<float> p = d.P[d.inc[k]];
+    const R4<float> p = d.P[chk_idx(d.ctrl, d.inc[k], 4 * d.n_t)];
     dw_acc(bx, p.x);
     dw_acc(by, p.y);
     dw_acc(bz, p.z);
@@ -745,7 +745,7 @@ __device__ __forceinline__ void residual_row_f64(const Dev<T>& d, int i, T dg, d
   const int k1 = d.sl_ptr[sl + 1];
   for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
     const double a = (double)d.sl_val[k];
-    const R4<T> xc = d.X[d.sl_col[k]];
+    const R4<T> xc = d.X[chk_idx(d.ctrl, d.sl_col[k], d.n_v)];
     ax += a * xc.x;
     ay += a * xc.y;
     az += a * xc.z;
@@ -775,7 +775,7 @@ __device__ __forceinline__ void rhs_residual_row_dw(const Dev<float>& d, int i, 
   const int k1 = d.inc_ptr[i + 1];
 #pragma unroll 4
   for (int k = d.inc_ptr[i]; k < k1; ++k) {
-    const R4<float> p = d.P[d.inc[k]];
+    const R4<float> p = d.P[chk_idx(d.ctrl, d.inc[k], 4 * d.n_t)];
     dw_acc(b[0], p.x);
     dw_acc(b[1], p.y);
     dw_acc(b[2], p.z);
@@ -805,7 +805,7 @@ __device__ __forceinline__ void rhs_residual_row_dw(const Dev<float>& d, int i, 
 #pragma unroll
   for (int j = 0; j < MAXW; ++j) {
     if (j < width) {
-      const R4<float> xc = d.X[d.sl_col[base + j * 32 + ln]];
+      const R4<float> xc = d.X[chk_idx(d.ctrl, d.sl_col[base + j * 32 + ln], d.n_v)];
       dw_acc_prod(ax[0], val[j], xc.x);
       dw_acc_prod(ax[1], val[j], xc.y);
       dw_acc_prod(ax[2], val[j], xc.z);
@@ -833,7 +833,7 @@ __device__ __forceinline__ void spmv_row(const Dev<T>& d, int i, const R4<T>* __
   const int s = i >> 5, lane = i & 31;
   const int k1 = d.sl_ptr[s + 1];
   for (int k = d.sl_ptr[s] + lane; k < k1; k += 32) {
-    const int c = d.sl_col[k];
+    const int c = chk_idx(d.ctrl, d.sl_col[k], d.n_v);
     const T a = d.sl_val[k];
     const R4<T> x = ld_cg<T>(src + c);
     ax += a * x.x;
@@ -1642,7 +1642,7 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
     width = (d.sl_ptr[sl + 1] - base) >> 5;
 #pragma unroll
     for (int j = 0; j < MAXW; ++j) {
-      lcol[j] = j < width ? d.sl_lcol[base + j * 32 + ln] : 0;
+      lcol[j] = j < width ? chk_idx(d.ctrl, d.sl_lcol[base + j * 32 + ln], d.halo_max) : 0;
       val[j] = j < width ? d.sl_val[base + j * 32 + ln] : 0.0f;
     }
   }
@@ -1681,7 +1681,7 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
 #pragma unroll 4
     for (int k = threadIdx.x, q = 0; k < nh; k += ROWS, ++q) {
       unsigned long long w0, w1;
-      ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
+      ld_v2_relaxed_at(buf, chk_idx(d.ctrl, d.halo_rows[h0 + k], n), w0, w1);
       if (df_has(w0, tag) && df_has(w1, tag)) {
         float vx, vy, vz;
         df_unpack_u(w0, w1, vx, vy, vz);
@@ -1696,7 +1696,7 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
         if (!(stale & (1ull << q))) continue;
         unsigned long long w0, w1;
         do {
-          ld_v2_relaxed_at(buf, d.halo_rows[h0 + k], w0, w1);
+          ld_v2_relaxed_at(buf, chk_idx(d.ctrl, d.halo_rows[h0 + k], n), w0, w1);
         } while (!(df_has(w0, tag) && df_has(w1, tag)) && wt.again(d.ctrl, d.wait_budget));
         float vx, vy, vz;
         df_unpack_u(w0, w1, vx, vy, vz);

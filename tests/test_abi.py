@@ -43,3 +43,25 @@ def test_binding_loads_and_reports_create_errors(lib):
         casim.casim_create(p)
     assert ei.value.code == casim.CASIM_E_INVALID
     assert "precision" in casim.casim_last_error(None)
+
+
+def test_checked_build_reports_itself_and_exports_the_same_symbols(lib):
+    if not os.path.exists(casim.LIB_CHECKED_PATH):
+        casim_build.build()
+    chk = ctypes.CDLL(casim.LIB_CHECKED_PATH)
+    for name in _declared():
+        assert hasattr(chk, name), name
+    chk.casim_build_checked.restype = ctypes.c_int
+    lib.casim_build_checked.restype = ctypes.c_int
+    assert chk.casim_build_checked() == 1
+    assert lib.casim_build_checked() == 0
+
+
+def test_plain_build_refuses_the_checked_builds_fault_injection(lib):
+    casim.load_library()
+    p = casim.casim_default_params()
+    p.debug_flags = casim.CASIM_DEBUG_CORRUPT_INCIDENCE  # rejected on the host before any CUDA call
+    with pytest.raises(casim.CasimError) as ei:
+        casim.casim_create(p)
+    assert ei.value.code == casim.CASIM_E_INVALID
+    assert "debug_flags" in casim.casim_last_error(None)
