@@ -541,9 +541,10 @@ def main():
     units = float(m.n_tets) * n_iters * args.steps * world
     value, ms_max = aggregate(ms, float(m.n_tets) * n_iters * args.steps, pg, "cuda")
     stats = casim.casim_get_stats(sim.h)
-    # 2 hash binning + 3 scan + narrow phase + spring update + ray casts + local step + PCG; the dataflow PCG
-    # (kernel 5) forms the right-hand side and finalizes the iteration itself, the others need 2 launches more
-    kernels_per_iter = 10 if stats.pcg_kernel == 5 else 12
+    # 2 hash binning + 1 single-pass scan + narrow phase + spring update + ray casts + local step + PCG; the
+    # dataflow PCG (kernel 5) forms the right-hand side and finalizes the iteration itself, the others need 2
+    # launches more
+    kernels_per_iter = 8 if stats.pcg_kernel == 5 else 10
     gpu_launches = kernels_per_iter * n_iters * args.steps
     hist = casim.casim_get_history(sim.h, n_iters)
 

@@ -600,7 +600,14 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->faces = sim->dalloc<int4>(n_f);
   sim->spheres_d = sim->dalloc<double>(4 * 64);
   const size_t H = (size_t)sim->H_t + sim->H_f;
-  sim->cell_count = sim->dalloc<int>(H + 1);
+  // the count array is followed by the single-pass scan's status words and
+  // ticket (8-byte aligned), which its memset zeroes as well
+  sim->cell_count = sim->dalloc<int>(H + 1 + scan_lookback_extra_ints((int)H + 1));
+  {
+    const size_t off = ((H + 1 + 1) / 2) * 2;  // ints, rounded up to 8 bytes
+    sim->cs.tile_status = reinterpret_cast<unsigned long long*>(sim->cell_count + off);
+    sim->cs.ticket = reinterpret_cast<unsigned*>(sim->cs.tile_status + (scan_tiles((int)H + 1) + 1));
+  }
   sim->cell_start = sim->dalloc<int>(H + 1);
   sim->cell_cursor = sim->dalloc<int>(H);
   sim->items = sim->dalloc<int>(sim->cap_items);

@@ -238,6 +238,113 @@ __global__ void k_scan_add(int* out, const int* tile_sums, int n) {
   if (i < n) out[i] += tile_sums[i / SCAN_TILE];
 }
 
+// ---- single-pass exclusive scan with decoupled look-back -----------------
+// (Merrill and Garland 2016).  Each block takes a tile ticket (so every
+// smaller tile belongs to a block that is already running), scans its tile,
+// publishes the tile's sum as a status word (flag 1: the tile's own sum,
+// flag 2: the inclusive prefix up to and including the tile), and warp 0
+// walks back over the predecessors' words, 32 at a time, adding own sums
+// until it meets an inclusive prefix.  Waits for a predecessor's word are
+// bounded by the clock budget (then ST_TIMEOUT).  Integer sums, so the result
+// is the same as any other scan order.  The status words and the ticket are
+// zeroed with the count array before each use; the last tile resets nothing
+// and writes the total (with the capacity check).
+__device__ __forceinline__ unsigned long long scan_word(unsigned flag, int v) {
+  return ((unsigned long long)flag << 62) | (unsigned)v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_lookback(const int* __restrict__ in, int* __restrict__ out, int n,
+                                                                unsigned long long* status, unsigned* ticket,
+                                                                int* total_out, Ctrl* ctrl, int cap,
+                                                                unsigned long long budget) {
+  __shared__ int sh[SCAN_THREADS];
+  __shared__ int s_tile, s_prefix;
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(ticket, 1u);
+  __syncthreads();
+  const int tile = s_tile;
+  const int base = tile * SCAN_TILE + threadIdx.x * SCAN_PER_THREAD;
+  int v[SCAN_PER_THREAD];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  sh[threadIdx.x] = s;
+  __syncthreads();
+  for (int off = 1; off < SCAN_THREADS; off <<= 1) {
+    const int t = (threadIdx.x >= off) ? sh[threadIdx.x - off] : 0;
+    __syncthreads();
+    sh[threadIdx.x] += t;
+    __syncthreads();
+  }
+  const int agg = sh[SCAN_THREADS - 1];
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int prefix = 0;
+    if (tile == 0) {
+      if (lane == 0) st_relaxed_u64(status + tile, scan_word(2u, agg));
+    } else {
+      if (lane == 0) st_relaxed_u64(status + tile, scan_word(1u, agg));
+      long long t0 = 0;
+      unsigned polls = 0;
+      bool failed = false;
+      for (int j = tile - 1; j >= 0 && !failed; j -= 32) {
+        const int q = j - lane;  // predecessor this lane reads (nearest first)
+        unsigned long long w = q >= 0 ? ld_relaxed_u64(status + q) : scan_word(1u, 0);
+        // wait until every word of the window is published
+        while (__any_sync(0xffffffffu, (w >> 62) == 0ull)) {
+          if ((++polls & 31u) == 0) {
+            const long long now = clock64();
+            if (t0 == 0) t0 = now;
+            else if ((unsigned long long)(now - t0) > budget) {
+              failed = true;
+              break;
+            }
+          }
+          if ((w >> 62) == 0ull) w = ld_relaxed_u64(status + q);
+        }
+        if (failed) break;
+        const unsigned incl = __ballot_sync(0xffffffffu, (w >> 62) == 2ull);
+        const int stop = incl ? __ffs(incl) - 1 : 32;  // nearest inclusive prefix in the window
+        int part = (lane <= stop && q >= 0) ? (int)(unsigned)(w & 0xFFFFFFFFull) : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+        prefix += __shfl_sync(0xffffffffu, part, 0);
+        if (incl) break;
+      }
+      if (failed && lane == 0) atomicOr(&ctrl->status, ST_TIMEOUT);
+      if (lane == 0) st_relaxed_u64(status + tile, scan_word(2u, prefix + agg));
+    }
+    if (lane == 0) s_prefix = prefix;
+  }
+  __syncthreads();
+  int run = s_prefix + sh[threadIdx.x] - s;  // exclusive prefix of this thread
+#pragma unroll
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (tile == (int)gridDim.x - 1 && threadIdx.x == 0) {
+    const int tot = s_prefix + agg;
+    *total_out = tot;
+    if (ctrl) {
+      ctrl->n_items = tot;
+      if (tot > cap) atomicOr(&ctrl->status, ST_OVERFLOW);
+    }
+  }
+}
+
+int scan_lookback_extra_ints(int n) { return 2 + 2 * (scan_tiles(n) + 1) + 2; }
+
 // ---- narrow phase ----
 __device__ __forceinline__ int orient_t(float ax, float ay, float az, float bx, float by, float bz, float cx, float cy,
                                         float cz, float dx, float dy, float dz) {
@@ -1156,14 +1263,22 @@ void launch_collision(const Dev<T>& d, const CollisionScratch& cs, cudaStream_t 
   }
   const int n_items = d.n_t + d.n_f;
   const int H = (int)(d.H_t + d.H_f);
-  cudaMemsetAsync(d.cell_count, 0, sizeof(int) * (size_t)(H + 1), st);
+  // with the single-pass scan its status words and ticket follow the counts
+  // and are zeroed by the same memset
+  const size_t n_zero = (size_t)(H + 1) + (cs.tile_status ? (size_t)scan_lookback_extra_ints(H + 1) : 0);
+  cudaMemsetAsync(d.cell_count, 0, sizeof(int) * n_zero, st);
   cudaMemsetAsync(d.cell_cursor, 0, sizeof(int) * (size_t)H, st);
   k_grid_bin<T, false><<<(n_items + 255) / 256, 256, 0, st>>>(d);
   const int n_scan = H + 1;
   const int n_tiles = (n_scan + SCAN_TILE - 1) / SCAN_TILE;
-  k_scan_tiles<<<n_tiles, SCAN_THREADS, 0, st>>>(d.cell_count, d.cell_start, cs.tile_sums, n_scan);
-  k_scan_top<<<1, 1024, 0, st>>>(cs.tile_sums, n_tiles, cs.total, d.ctrl, d.cap_items);
-  k_scan_add<<<(n_scan + 255) / 256, 256, 0, st>>>(d.cell_start, cs.tile_sums, n_scan);
+  if (cs.tile_status) {
+    k_scan_lookback<<<n_tiles, SCAN_THREADS, 0, st>>>(d.cell_count, d.cell_start, n_scan, cs.tile_status, cs.ticket,
+                                                       cs.total, d.ctrl, d.cap_items, d.wait_budget);
+  } else {
+    k_scan_tiles<<<n_tiles, SCAN_THREADS, 0, st>>>(d.cell_count, d.cell_start, cs.tile_sums, n_scan);
+    k_scan_top<<<1, 1024, 0, st>>>(cs.tile_sums, n_tiles, cs.total, d.ctrl, d.cap_items);
+    k_scan_add<<<(n_scan + 255) / 256, 256, 0, st>>>(d.cell_start, cs.tile_sums, n_scan);
+  }
   k_grid_bin<T, true><<<(n_items + 255) / 256, 256, 0, st>>>(d);
   if (d.n_q > 0) {
     const long long threads = 32LL * d.n_q;

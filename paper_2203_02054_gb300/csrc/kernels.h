@@ -10,6 +10,11 @@ namespace casim {
 struct CollisionScratch {
   int* tile_sums;  // scan tiles of the hash count array
   int* total;      // total hash entries
+  // single-pass scan (null: the three-kernel scan): per-tile status words and
+  // the tile ticket, stored right after the hash count array so that its one
+  // memset zeroes them too
+  unsigned long long* tile_status;
+  unsigned* ticket;
 };
 
 static constexpr int LOCAL_THREADS = 128;
@@ -131,5 +136,7 @@ int rhs_blocks(int n_free);
 int local_blocks(int n_t, int threads);
 int rhs_blocks(int n_free, int threads);
 int scan_tiles(int n);
+// ints to allocate after an (n + 1)-int count array for the single-pass scan
+int scan_lookback_extra_ints(int n);
 
 }  // namespace casim
