@@ -319,7 +319,7 @@ def bench_batched(stream, plain_value, n_iters=100, n_seq=16):
 
     batch = synth.config4_batch(n_iters=n_iters)
     n_t = sum(m.n_tets for m in batch)
-    sim = casim.Sim(batch, stream=stream.cuda_stream, stats=0)
+    sim = casim.Sim(batch, stream=stream.cuda_stream, stats=0, tuned=True)
     kern = sim.stats().pcg_kernel
     step = lambda: (casim.casim_reset(sim.h), casim.casim_step(sim.h, n_iters))
     casim.casim_reset(sim.h)
@@ -328,6 +328,7 @@ def bench_batched(stream, plain_value, n_iters=100, n_seq=16):
     ms = _event_ms(stream, step)
     status = casim.casim_sync(sim.h)
     st = casim.casim_get_stats(sim.h)
+    tuned = sim.tuned_from
     sim.close()
     rng = np.random.default_rng(1004)
     sub = sorted(rng.choice(len(batch), n_seq, replace=False).tolist())
@@ -346,7 +347,8 @@ def bench_batched(stream, plain_value, n_iters=100, n_seq=16):
     return {"workload": "256 pneumatic fingers (20k x 4k x 4k voxels, k~U{1..4}, 4-10 chambers), "
                         "12,119,040 tets, self-collision per robot", "n_robots": len(batch), "n_tets": n_t,
             "n_iters": n_iters, "value": value, "unit": UNIT, "ms_per_step": ms, "device_status": status,
-            "pcg_kernel": kern, "k_pcg_max_mean": st.total_pcg_iters / max(1, st.iterations) / len(batch),
+            "pcg_kernel": kern, "tuned": tuned,
+            "k_pcg_max_mean": st.total_pcg_iters / max(1, st.iterations) / len(batch),
             "sequential": {"robots": n_seq, "value": seq_value, "how": "each robot alone, same GPU, scaled by tets"},
             "vs_sequential": value / seq_value, "vs_plain": value / plain_value}
 
@@ -461,7 +463,7 @@ def run_only_batched(n_iters: int) -> int:
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream(0)
     batch = synth.config4_batch(n_iters=n_iters)
-    sim = casim.Sim(batch, stream=stream.cuda_stream, stats=0)
+    sim = casim.Sim(batch, stream=stream.cuda_stream, stats=0, tuned=True)
     casim.casim_step(sim.h, 2)
     casim.casim_sync(sim.h)
     st0 = casim.casim_get_stats(sim.h)
@@ -502,7 +504,9 @@ def main():
     stream = torch.cuda.current_stream()
     m = synth.config3_gripper(n_iters=args.iters)
     n_iters = args.iters
-    sim = casim.Sim(m, stream=stream.cuda_stream, stats=0)
+    # the autotuner's cached winners for this GPU and workload shape, if any
+    # (paper_2203_02054_gb300/tuned.json): what a user of casim.Sim(tuned=True) runs
+    sim = casim.Sim(m, stream=stream.cuda_stream, stats=0, tuned=True)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
     def one_step():
@@ -568,7 +572,7 @@ def main():
     line = None
     if rank == 0:
         # ---- roofline of the dominant kernel: eager pass with phase events ----
-        prof = casim.Sim(m, stream=stream.cuda_stream, stats=2)
+        prof = casim.Sim(m, stream=stream.cuda_stream, stats=2, tuned=True)
         prof.step(n_iters)
         prof.sync()
         ph = casim.casim_get_phase_times(prof.h)
@@ -590,7 +594,7 @@ def main():
                        "precision": "MIXED (FP32 vectors/targets, FP64 dots, exact predicates)",
                        "l2": "flushed between timed steps (256 MiB write); one step's working set fits L2",
                        "parallelism": "replicas" if world > 1 else "single-gpu",
-                       "device_status": status},
+                       "tuned": sim.tuned_from, "device_status": status},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * 3 * m.n_verts + 8 * m.n_groups,
                     "d2h_bytes_per_step": 8 * 3 * m.n_verts},
             "gpu_launches": gpu_launches,
