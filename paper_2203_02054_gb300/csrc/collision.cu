@@ -83,15 +83,22 @@ __device__ __forceinline__ int cell_coord_f(float x, float inv_cell) {
 }
 
 // Block-reduced bounding box of the valid item boxes (count pass only).
+// Warps without a valid item skip the shuffles, and blocks without one skip
+// the atomics (only the boundary faces' blocks contribute).
 __device__ __forceinline__ void reduce_box(Ctrl* c, bool valid, const double lo[3], const double hi[3]) {
   __shared__ long long s_lo[3][8], s_hi[3][8];
+  constexpr long long kLo = 0x7FFFFFFFFFFFFFFFLL, kHi = (long long)0x8000000000000000ULL;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const bool any = __any_sync(0xffffffffu, valid);
   for (int j = 0; j < 3; ++j) {
-    long long a = valid ? order_code(lo[j]) : 0x7FFFFFFFFFFFFFFFLL;
-    long long b = valid ? order_code(hi[j]) : (long long)0x8000000000000000ULL;
-    for (int o = 16; o > 0; o >>= 1) {
-      a = min(a, __shfl_down_sync(0xffffffffu, a, o));
-      b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+    long long a = kLo, b = kHi;
+    if (any) {
+      a = valid ? order_code(lo[j]) : kLo;
+      b = valid ? order_code(hi[j]) : kHi;
+      for (int o = 16; o > 0; o >>= 1) {
+        a = min(a, __shfl_down_sync(0xffffffffu, a, o));
+        b = max(b, __shfl_down_sync(0xffffffffu, b, o));
+      }
     }
     if (lane == 0) {
       s_lo[j][wid] = a;
@@ -106,8 +113,8 @@ __device__ __forceinline__ void reduce_box(Ctrl* c, bool valid, const double lo[
       a = min(a, s_lo[j][w]);
       b = max(b, s_hi[j][w]);
     }
-    atomicMin(&c->box_lo[j], a);
-    atomicMax(&c->box_hi[j], b);
+    if (a != kLo) atomicMin(&c->box_lo[j], a);
+    if (b != kHi) atomicMax(&c->box_hi[j], b);
   }
 }
 
