@@ -420,6 +420,21 @@ __device__ __forceinline__ void obstacle_tests(const Dev<T>& d, T px, T py, T pz
   for (int j = 0; j < d.n_spheres; ++j) {
     const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
     const double r = d.spheres[4 * j + 3];
+    // FP32 reject first: a point farther than r from the centre along one axis
+    // is outside; the margins (1e-5 relative to the magnitudes involved) cover
+    // the FP32 rounding of the centre, the radius and the difference, so only
+    // points near the sphere reach the FP64 test (on this part an FP64
+    // instruction costs about as much in one lane as in thirty-two)
+    {
+      const float rf = (float)r;
+      const float cf[3] = {(float)cx, (float)cy, (float)cz};
+      const float pf[3] = {(float)px, (float)py, (float)pz};
+      bool far = false;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        far |= fabsf(pf[k] - cf[k]) > rf * 1.00001f + 1e-5f * (fabsf(cf[k]) + fabsf(pf[k]));
+      if (far) continue;
+    }
     const double dx = __dsub_rn((double)px, cx), dy = __dsub_rn((double)py, cy), dz = __dsub_rn((double)pz, cz);
     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     if (d2 < __dmul_rn(r, r)) {
