@@ -242,6 +242,7 @@ struct casim_sim {
   int* cast_list = nullptr;
   double* cast_nrm = nullptr;
   double *knots_d = nullptr, *spheres_d = nullptr, *partials = nullptr, *e_partials = nullptr;
+  float* spheres_fd = nullptr;
   SpringDev sp{};
   Ctrl* ctrl = nullptr;
   IterRec* hist = nullptr;
@@ -433,6 +434,7 @@ Dev<T> make_dev(casim_sim* sim) {
   d.qf = sim->qf;
   d.faces = sim->faces;
   d.spheres = sim->spheres_d;
+  d.spheres_f = sim->spheres_fd;
   d.H_t = sim->H_t;
   d.H_f = sim->H_f;
   d.cell_count = sim->cell_count;
@@ -493,6 +495,16 @@ Dev<T> make_dev(casim_sim* sim) {
   d.n_e_local = local_blocks(sim->n_t, d.local_threads);
   d.n_e_spring = rhs_blocks(sim->n_free, d.rhs_threads);
   return d;
+}
+
+// Copies the obstacle spheres to the device: the FP64 values the tests use and
+// their round-to-nearest FP32 images for the reject test that precedes them.
+cudaError_t upload_spheres(casim_sim* sim) {
+  const int n = sim->n_spheres;
+  std::vector<float> f(sim->spheres.begin(), sim->spheres.begin() + 4 * n);
+  cudaError_t e = cudaMemcpy(sim->spheres_d, sim->spheres.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(sim->spheres_fd, f.data(), sizeof(float) * 4 * n, cudaMemcpyHostToDevice);
+  return e;
 }
 
 // Enqueues one outer iteration on stream st (used for graph capture and for
@@ -599,6 +611,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->qf = sim->dalloc<int>(qf.size());
   sim->faces = sim->dalloc<int4>(n_f);
   sim->spheres_d = sim->dalloc<double>(4 * 64);
+  sim->spheres_fd = sim->dalloc<float>(4 * 64);
   const size_t H = (size_t)sim->H_t + sim->H_f;
   // the count array is followed by the single-pass scan's status words and
   // ticket (8-byte aligned), which its memset zeroes as well
@@ -1779,10 +1792,7 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
     sim->free_all();
     return rc;
   }
-  if (!sim->spheres.empty()) {
-    const int n = sim->n_spheres;
-    CK(cudaMemcpy(sim->spheres_d, sim->spheres.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice));
-  }
+  if (!sim->spheres.empty()) CK(upload_spheres(sim));
   sim->iters = 0;
   sim->status_bits = 0;
   sim->has_mesh = true;
@@ -1876,8 +1886,7 @@ int casim_set_spheres(casim_sim* sim, int32_t n, const double* cxyzr) {
     if (!(cxyzr[4 * i + 3] > 0.0)) return sim->fail(CASIM_E_INVALID, "sphere radius must be positive");
   sim->spheres.assign(cxyzr, cxyzr + 4 * n);
   sim->n_spheres = n;
-  if (sim->has_mesh && n > 0)
-    CK(cudaMemcpy(sim->spheres_d, sim->spheres.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice));
+  if (sim->has_mesh && n > 0) CK(upload_spheres(sim));
   sim->graph_dirty = true;
   return CASIM_OK;
 }

@@ -418,16 +418,14 @@ __device__ __forceinline__ void obstacle_tests(const Dev<T>& d, T px, T py, T pz
   if (d.collision < 2) return;
   double bestd = 0.0;
   for (int j = 0; j < d.n_spheres; ++j) {
-    const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
-    const double r = d.spheres[4 * j + 3];
     // FP32 reject first: a point farther than r from the centre along one axis
     // is outside; the margins (1e-5 relative to the magnitudes involved) cover
     // the FP32 rounding of the centre, the radius and the difference, so only
     // points near the sphere reach the FP64 test (on this part an FP64
     // instruction costs about as much in one lane as in thirty-two)
     {
-      const float rf = (float)r;
-      const float cf[3] = {(float)cx, (float)cy, (float)cz};
+      const float rf = d.spheres_f[4 * j + 3];
+      const float cf[3] = {d.spheres_f[4 * j], d.spheres_f[4 * j + 1], d.spheres_f[4 * j + 2]};
       const float pf[3] = {(float)px, (float)py, (float)pz};
       bool far = false;
 #pragma unroll
@@ -435,6 +433,8 @@ __device__ __forceinline__ void obstacle_tests(const Dev<T>& d, T px, T py, T pz
         far |= fabsf(pf[k] - cf[k]) > rf * 1.00001f + 1e-5f * (fabsf(cf[k]) + fabsf(pf[k]));
       if (far) continue;
     }
+    const double cx = d.spheres[4 * j], cy = d.spheres[4 * j + 1], cz = d.spheres[4 * j + 2];
+    const double r = d.spheres[4 * j + 3];
     const double dx = __dsub_rn((double)px, cx), dy = __dsub_rn((double)py, cy), dz = __dsub_rn((double)pz, cz);
     const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     if (d2 < __dmul_rn(r, r)) {
@@ -997,7 +997,6 @@ template <typename T>
 __device__ void spring_update_vertex(const Dev<T>& d, int qi, int& active_out, unsigned long long& ssig) {
   {
     const int v = d.q_verts[qi];
-    const V3 x = pos(d, v);
     // area-weighted unit vertex normal of the incident boundary faces, formed
     // only where it is used (a queued ray cast, a sphere spring whose vertex
     // sits at the centre): most vertices have no contact, and this FP64
@@ -1021,12 +1020,17 @@ __device__ void spring_update_vertex(const Dev<T>& d, int qi, int& active_out, u
     int js = d.obs_sphere[qi];
     const double eps = d.eps;
     bool deferred = false;
+    const bool in_mesh = d.obs_mesh && d.obs_mesh[qi] > 0;
+    // the position in FP64, read only by a vertex with an obstacle contact or
+    // a spring to re-target (the conversions are FP64 instructions)
+    V3 x = {0.0, 0.0, 0.0};
+    if (in_mesh || js >= 0 || active) x = pos(d, v);
     // inside the tetrahedral obstacle: its closest boundary point, unless a
     // containing sphere's surface is at least as near (signed distances
     // |x - c| - r and minus the distance to the obstacle's boundary)
     int mf = -1;
     double m1 = 0.0, m2 = 0.0;
-    if (d.obs_mesh && d.obs_mesh[qi] > 0) {
+    if (in_mesh) {
       double md2;
       mf = obstacle_closest(d, x, m1, m2, md2);
       if (js >= 0 && mf >= 0) {

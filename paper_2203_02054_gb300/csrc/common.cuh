@@ -165,6 +165,7 @@ struct Dev {
   const int* qf;         // face ids
   const int4* faces;     // n_f (v0, v1, v2, owning tet)
   const double* spheres; // 4 n_spheres
+  const float* spheres_f; // the same, rounded to FP32 (the reject test before the FP64 one)
   unsigned H_t, H_f;     // hash sizes (powers of two)
   int* cell_count;       // H_t + H_f (+1)
   int* cell_start;       // H_t + H_f + 1
