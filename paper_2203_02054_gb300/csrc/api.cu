@@ -212,6 +212,10 @@ struct casim_sim {
   std::vector<double> knots;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // graph capture only: the local step's branch, forked from and joined back
+  // into cap_stream
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
   int device = 0;
   bool has_mesh = false;
@@ -508,7 +512,12 @@ cudaError_t upload_spheres(casim_sim* sim) {
 }
 
 // Enqueues one outer iteration on stream st (used for graph capture and for
-// the timed eager path).
+// the timed eager path).  With a side stream (graph capture) the local step
+// runs on it, concurrently with the spring update and the ray casts: it
+// reads only the positions, which no collision kernel writes, and writes
+// only the projections P and its energy partials, which the collision
+// kernels do not read; the iteration's record takes both sides' terms by
+// integer atomics.  The global solve waits for both branches.
 // NVTX range for profilers (a no-op unless a tool is attached); in graph
 // replay the ranges mark the capture, in eager mode every iteration.
 struct NvtxRange {
@@ -517,7 +526,7 @@ struct NvtxRange {
 };
 
 template <typename T>
-cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) {
+cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev, cudaStream_t side = nullptr) {
   NvtxRange outer("casim iteration");
   const Dev<T> d = make_dev<T>(sim);
   if (ev) cudaEventRecord(ev[0], st);
@@ -526,12 +535,21 @@ cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev) 
     launch_collision<T>(d, sim->cs, st);
   }
   if (ev) cudaEventRecord(ev[1], st);
+  if (side) {
+    cudaEventRecord(sim->ev_fork, st);
+    cudaStreamWaitEvent(side, sim->ev_fork, 0);
+    NvtxRange r("local step");
+    launch_local<T>(d, side);
+    cudaEventRecord(sim->ev_join, side);
+  }
   if (d.collision >= 1 && d.n_q > 0) {
     NvtxRange r("spring update");
     launch_springs<T>(d, st);
   }
   if (ev) cudaEventRecord(ev[2], st);
-  {
+  if (side) {
+    cudaStreamWaitEvent(st, sim->ev_join, 0);
+  } else {
     NvtxRange r("local step");
     launch_local<T>(d, st);
   }
@@ -883,7 +901,7 @@ int capture_graph(casim_sim* sim) {
   }
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(sim->cap_stream, cudaStreamCaptureModeThreadLocal));
-  cudaError_t e = enqueue_iteration<T>(sim, sim->cap_stream, nullptr);
+  cudaError_t e = enqueue_iteration<T>(sim, sim->cap_stream, nullptr, sim->side_stream);
   cudaError_t e2 = cudaStreamEndCapture(sim->cap_stream, &g);
   if (e != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
@@ -1022,8 +1040,14 @@ int casim_create(const casim_params* params, void* cuda_stream, casim_sim** out)
   sim->params.n_w_knots = (int)sim->knots.size() / 2;
   sim->stream = static_cast<cudaStream_t>(cuda_stream);
   if (cudaGetDevice(&sim->device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaStreamCreateWithFlags(&sim->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&sim->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&sim->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&sim->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     g_create_error = "CUDA unavailable";
+    if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
+    if (sim->side_stream) cudaStreamDestroy(sim->side_stream);
+    if (sim->ev_fork) cudaEventDestroy(sim->ev_fork);
     delete sim;
     return CASIM_E_CUDA;
   }
@@ -2713,6 +2737,9 @@ void casim_destroy(casim_sim* sim) {
   cudaStreamSynchronize(sim->stream);
   sim->free_all();
   if (sim->cap_stream) cudaStreamDestroy(sim->cap_stream);
+  if (sim->side_stream) cudaStreamDestroy(sim->side_stream);
+  if (sim->ev_fork) cudaEventDestroy(sim->ev_fork);
+  if (sim->ev_join) cudaEventDestroy(sim->ev_join);
   delete sim;
 }
 
