@@ -259,7 +259,8 @@ struct casim_sim {
   int pcg_variant = 1;  // whole-grid kernel: 1 streaming, 2 register-resident, 5 dataflow
   unsigned long long *df_u = nullptr, *df_p = nullptr;  // dataflow PCG: epoch-tagged words
   int *halo_ptr = nullptr, *halo_rows = nullptr, *sl_lcol = nullptr;  // dataflow PCG: block halos
-  std::vector<int> halo_ptr_h, halo_rows_h, sl_lcol_h;
+  int *halo_own = nullptr, *halo_self = nullptr;
+  std::vector<int> halo_ptr_h, halo_rows_h, sl_lcol_h, halo_own_h, halo_self_h;
   int halo_max = 0;
   int df_rows = 384;  // rows per block of the dataflow PCG
   std::vector<float> cg_ainv_h;  // dataflow PCG coarse correction: A_c^-1, row-major
@@ -428,6 +429,8 @@ Dev<T> make_dev(casim_sim* sim) {
   d.df_p = sim->df_p;
   d.halo_ptr = sim->halo_ptr;
   d.halo_rows = sim->halo_rows;
+  d.halo_own = sim->halo_own;
+  d.halo_self = sim->halo_self;
   d.sl_lcol = sim->sl_lcol;
   d.halo_max = sim->halo_max;
   d.df_rows = sim->df_rows;
@@ -623,6 +626,8 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
     sim->halo_ptr = sim->dalloc<int>(sim->halo_ptr_h.size());
     sim->halo_rows = sim->dalloc<int>(std::max<size_t>(sim->halo_rows_h.size(), 1));
     sim->sl_lcol = sim->dalloc<int>(std::max<size_t>(sim->sl_lcol_h.size(), 1));
+    sim->halo_own = sim->dalloc<int>(std::max<size_t>(sim->halo_own_h.size(), 1));
+    sim->halo_self = sim->dalloc<int>(std::max<size_t>(sim->halo_self_h.size(), 1));
   }
   sim->q_verts_d = sim->dalloc<int>(n_q);
   sim->qf_ptr = sim->dalloc<int>(n_q + 1);
@@ -753,6 +758,12 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
                          cudaMemcpyHostToDevice, st));
     if (!sim->sl_lcol_h.empty())
       CK(cudaMemcpyAsync(sim->sl_lcol, sim->sl_lcol_h.data(), sizeof(int) * sim->sl_lcol_h.size(),
+                         cudaMemcpyHostToDevice, st));
+    if (!sim->halo_own_h.empty())
+      CK(cudaMemcpyAsync(sim->halo_own, sim->halo_own_h.data(), sizeof(int) * sim->halo_own_h.size(),
+                         cudaMemcpyHostToDevice, st));
+    if (!sim->halo_self_h.empty())
+      CK(cudaMemcpyAsync(sim->halo_self, sim->halo_self_h.data(), sizeof(int) * sim->halo_self_h.size(),
                          cudaMemcpyHostToDevice, st));
     if (sim->n_agg > 0)
       CK(cudaMemcpyAsync(sim->cg_ainv, sim->cg_ainv_h.data(), sizeof(float) * sim->cg_ainv_h.size(),
@@ -1598,34 +1609,52 @@ static int upload_robots(casim_sim* sim, int32_t n_verts, const double* rest_xyz
   const bool rr_fits = max_width <= PCG_RR_MAXW && n_free <= rr_rows;
   // dataflow PCG (FP32 vectors only): one row per thread, one block per SM.
   // Block b owns rows [b R, (b + 1) R), R = df_rows (whole slices); its
-  // halo is the sorted list of distinct columns its rows read, and every
-  // sliced-ELL entry also gets its column's index in that list.
+  // halo is the list of distinct columns its rows read, its own rows first
+  // (each row writes its value there itself, from its registers), then the
+  // other blocks' rows it loads, each part ascending; every sliced-ELL entry
+  // also gets its column's index in that list.
   const int R_df = sim->df_rows;
   bool df_fits = !fp64 && max_width <= PCG_RR_MAXW && n_free <= pcg_df_max_rows(R_df);
   sim->halo_ptr_h.clear();
   sim->halo_rows_h.clear();
   sim->sl_lcol_h.clear();
+  sim->halo_own_h.clear();
+  sim->halo_self_h.clear();
   sim->halo_max = 0;
   if (df_fits) {
     const int spb = R_df / 32;
     const int nbk = (n_free + R_df - 1) / R_df;
     sim->halo_ptr_h.assign(nbk + 1, 0);
+    sim->halo_own_h.assign(nbk, 0);
+    sim->halo_self_h.assign(n_free, -1);
     sim->sl_lcol_h.assign(sl_col.size(), 0);
-    std::vector<int> cols;
+    std::vector<int> cols, own, other;
     for (int b = 0; b < nbk; ++b) {
       const int s0 = b * spb, s1 = std::min(sim->n_slices, s0 + spb);
+      const int r0 = b * R_df, r1 = r0 + R_df;
       cols.clear();
       for (int s = s0; s < s1; ++s)
         for (int k = sl_ptr[s]; k < sl_ptr[s + 1]; ++k)
           if (32 * s + (k - sl_ptr[s]) % 32 < n_free) cols.push_back(sl_col[k]);
       std::sort(cols.begin(), cols.end());
       cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+      own.clear();
+      other.clear();
+      for (int c : cols) (c >= r0 && c < r1 ? own : other).push_back(c);
+      const int n_own = (int)own.size();
+      for (int j = 0; j < n_own; ++j) sim->halo_self_h[own[j]] = j;
       for (int s = s0; s < s1; ++s)
         for (int k = sl_ptr[s]; k < sl_ptr[s + 1]; ++k)
-          if (32 * s + (k - sl_ptr[s]) % 32 < n_free)
-            sim->sl_lcol_h[k] = (int)(std::lower_bound(cols.begin(), cols.end(), sl_col[k]) - cols.begin());
-      sim->halo_rows_h.insert(sim->halo_rows_h.end(), cols.begin(), cols.end());
+          if (32 * s + (k - sl_ptr[s]) % 32 < n_free) {
+            const int c = sl_col[k];
+            sim->sl_lcol_h[k] =
+                c >= r0 && c < r1 ? (int)(std::lower_bound(own.begin(), own.end(), c) - own.begin())
+                                  : n_own + (int)(std::lower_bound(other.begin(), other.end(), c) - other.begin());
+          }
+      sim->halo_rows_h.insert(sim->halo_rows_h.end(), own.begin(), own.end());
+      sim->halo_rows_h.insert(sim->halo_rows_h.end(), other.begin(), other.end());
       sim->halo_ptr_h[b + 1] = (int)sim->halo_rows_h.size();
+      sim->halo_own_h[b] = n_own;
       sim->halo_max = std::max(sim->halo_max, (int)cols.size());
     }
     if ((size_t)sim->halo_max * 16 > PCG_DF_HALO_MAX_BYTES) df_fits = false;

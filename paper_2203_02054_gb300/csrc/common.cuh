@@ -153,7 +153,10 @@ struct Dev {
   unsigned long long* df_u;  // dataflow PCG: 2 x n_free x 2 epoch-tagged words of u
   unsigned long long* df_p;  // dataflow PCG: 2 x (grid + 1) x 4 epoch-tagged partial words
   const int* halo_ptr;   // dataflow PCG: per block, start of its halo in halo_rows
-  const int* halo_rows;  //   distinct rows each block's SpMV reads (sorted per block)
+  const int* halo_rows;  //   distinct rows each block's SpMV reads: its own rows, then the
+                         //   others (each part ascending)
+  const int* halo_own;   //   per block, how many of its halo rows are its own
+  const int* halo_self;  //   per free row, its index in its block's halo (-1: not read)
   const int* sl_lcol;    //   per sliced-ELL entry: the column's index in its block's halo
   int halo_max;          //   longest halo (rows)
   int df_rows;           //   rows (threads) per block: 288 or 384

@@ -1667,19 +1667,23 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
     st_v2_relaxed(d.df_u + (size_t)(e & 1u) * ustride + 2 * (size_t)i, a, b);
   };
   const int h0 = d.halo_ptr[blockIdx.x], nh = d.halo_ptr[blockIdx.x + 1] - h0;
+  const int n_own = d.halo_own[blockIdx.x];  // the halo's first n_own rows are this block's
+  const int hself = act ? d.halo_self[i] : -1;
   // A u for this row from the neighbours' u of epoch e.  Called by every
-  // thread of the block: the block copies its halo rows of epoch e into
-  // shared memory (re-reading rows whose words are not yet current), then
-  // each active row multiplies from shared memory.
+  // thread of the block with its own u of epoch e: each row that the block
+  // reads writes its own value into the halo, the block copies the other
+  // blocks' rows of epoch e (re-reading rows whose words are not yet
+  // current), then each active row multiplies from shared memory.
   // Each halo row is unpacked once, into a float4 in place of its two words,
   // so the multiply reads one 16-byte shared-memory word per entry.
   float4* const halo4 = reinterpret_cast<float4*>(halo);
   auto spmv = [&](unsigned e, const float (&self)[3], float (&ax)[3]) {
     const unsigned long long* buf = d.df_u + (size_t)(e & 1u) * ustride;
     const unsigned long long tag = df_tag(e);
-    unsigned long long stale = 0;  // bit q: this thread's row threadIdx.x + q * ROWS is not yet current
+    unsigned long long stale = 0;  // bit q: this thread's row n_own + threadIdx.x + q * ROWS is not yet current
+    if (hself >= 0) halo4[chk_idx(d.ctrl, hself, d.halo_max)] = make_float4(self[0], self[1], self[2], 0.0f);
 #pragma unroll 4
-    for (int k = threadIdx.x, q = 0; k < nh; k += ROWS, ++q) {
+    for (int k = n_own + (int)threadIdx.x, q = 0; k < nh; k += ROWS, ++q) {
       unsigned long long w0, w1;
       ld_v2_relaxed_at(buf, chk_idx(d.ctrl, d.halo_rows[h0 + k], n), w0, w1);
       if (df_has(w0, tag) && df_has(w1, tag)) {
@@ -1692,7 +1696,7 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
     }
     if (stale) {
       DfWait wt;
-      for (int k = threadIdx.x, q = 0; k < nh; k += ROWS, ++q) {
+      for (int k = n_own + (int)threadIdx.x, q = 0; k < nh; k += ROWS, ++q) {
         if (!(stale & (1ull << q))) continue;
         unsigned long long w0, w1;
         do {
