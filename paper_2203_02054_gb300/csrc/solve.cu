@@ -154,6 +154,9 @@ __device__ __forceinline__ double acc_add(double a, double b) { return a + b; }
 __device__ __forceinline__ DW shfl_down(DW v, int o) {
   return DW{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
 }
+__device__ __forceinline__ DW shfl_xor(DW v, int o) {
+  return DW{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+}
 __device__ __forceinline__ double shfl_down(double v, int o) { return __shfl_down_sync(0xffffffffu, v, o); }
 __device__ __forceinline__ double acc_to_f64(DW a) { return (double)a.hi + (double)a.lo; }
 __device__ __forceinline__ double acc_to_f64(double a) { return a; }
@@ -201,21 +204,52 @@ __device__ __forceinline__ void block_sums(A (&v)[NV], double* sh, double (&bs)[
 // Block sums of NV per-thread double words by fixed shuffle trees of sloppy
 // double-word additions; the double-word result is valid in lane 0 of warp 0.
 // Contains one __syncthreads; sh holds at least 32 * NV doubles.
+// Warp sums of NV <= 4 double words by one butterfly that halves the values
+// each lane carries at every level (a warp reduce-scatter): lanes exchange
+// the half they give up at distance 16, then 8 (NV > 2), and every lane then
+// finishes its one value with the remaining levels.  The pairs added are
+// those of a shuffle-down tree over distances 16, 8, 4, 2, 1 (the sloppy
+// addition is commutative bit for bit: TwoSum's error term is exact), so each
+// sum equals that tree's, with 6 instead of 15 exchanges for NV = 3.  Value k
+// ends in lanes [k L, (k + 1) L), L = 32 / (NV rounded up to a power of two).
+template <int NV>
+__device__ __forceinline__ DW warp_sums_dw_rs(const DW (&v)[NV]) {
+  static_assert(NV >= 1 && NV <= 4, "one to four values");
+  const int lane = threadIdx.x & 31;
+  if constexpr (NV == 1) {
+    DW x = v[0];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x = dw_add_sloppy(x, shfl_xor(x, o));
+    return x;
+  } else if constexpr (NV == 2) {
+    const bool up = lane & 16;
+    DW x = dw_add_sloppy(up ? v[1] : v[0], shfl_xor(up ? v[0] : v[1], 16));
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) x = dw_add_sloppy(x, shfl_xor(x, o));
+    return x;
+  } else {
+    const DW z{0.0f, 0.0f};
+    const DW a2 = v[2], a3 = NV > 3 ? v[NV > 3 ? 3 : 0] : z;
+    const bool up = lane & 16;
+    const DW k0 = dw_add_sloppy(up ? a2 : v[0], shfl_xor(up ? v[0] : a2, 16));
+    const DW k1 = dw_add_sloppy(up ? a3 : v[1], shfl_xor(up ? v[1] : a3, 16));
+    const bool up8 = lane & 8;
+    DW x = dw_add_sloppy(up8 ? k1 : k0, shfl_xor(up8 ? k0 : k1, 8));
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) x = dw_add_sloppy(x, shfl_xor(x, o));
+    return x;
+  }
+}
+
 template <int NV, int NW>
 __device__ __forceinline__ void block_sums_dw(DW (&v)[NV], double* sh, DW (&bs)[NV]) {
   static_assert(NW >= 1 && NW <= 32, "at most 32 warps per block");
   constexpr int NW2 = NW <= 1 ? 1 : NW <= 2 ? 2 : NW <= 4 ? 4 : NW <= 8 ? 8 : NW <= 16 ? 16 : 32;
+  constexpr int L = NV == 1 ? 32 : NV == 2 ? 16 : 8;  // lanes per value after the butterfly
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   DW* sa = reinterpret_cast<DW*>(sh);
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v[k] = dw_add_sloppy(v[k], shfl_down(v[k], o));
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) sa[k * 32 + wid] = v[k];
-  }
+  const DW x = warp_sums_dw_rs<NV>(v);
+  if (lane % L == 0 && lane / L < NV) sa[(lane / L) * 32 + wid] = x;
   __syncthreads();
   if (wid == 0) {
 #pragma unroll
@@ -773,7 +807,7 @@ __device__ __forceinline__ void rhs_residual_row_dw(const Dev<float>& d, int i, 
                                                     float& dg, float (&r)[3], DW (&a0)[3]) {
   DW b[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
   const int k1 = d.inc_ptr[i + 1];
-#pragma unroll 4
+#pragma unroll 8
   for (int k = d.inc_ptr[i]; k < k1; ++k) {
     const R4<float> p = d.P[chk_idx(d.ctrl, d.inc[k], 4 * d.n_t)];
     dw_acc(b[0], p.x);
@@ -1414,14 +1448,25 @@ static constexpr int SEG_AGG_ROWS = 128;         // aggregate rows of the segmen
 // trees), stored by lane 0 in sz[warp]; call before block_sums*, whose
 // __syncthreads publishes them.
 __device__ __forceinline__ void agg_warp_sums(const float (&w)[3], const float (&r)[3], float (*sz)[6]) {
-  float a[6] = {w[0], w[1], w[2], r[0], r[1], r[2]};
+  // reduce-scatter butterfly over the six values (padded to eight): the
+  // lanes give up half their values at distances 16, 8 and 4 and finish the
+  // one left at 2 and 1; the pairs added, and so the sums, are those of a
+  // shuffle-down tree over distances 16, 8, 4, 2, 1 (9 exchanges instead of
+  // 30); value c ends in lanes 4c .. 4c + 3
+  const int lane = threadIdx.x & 31;
+  const float a[8] = {w[0], w[1], w[2], r[0], r[1], r[2], 0.0f, 0.0f};
+  float b[4], c2[2];
+  const bool u16 = lane & 16, u8 = lane & 8, u4 = lane & 4;
 #pragma unroll
-  for (int c = 0; c < 6; ++c)
+  for (int k = 0; k < 4; ++k)
+    b[k] = __fadd_rn(u16 ? a[4 + k] : a[k], __shfl_xor_sync(0xffffffffu, u16 ? a[k] : a[4 + k], 16));
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) a[c] = __fadd_rn(a[c], __shfl_down_sync(0xffffffffu, a[c], o));
-  if ((threadIdx.x & 31) == 0)
-#pragma unroll
-    for (int c = 0; c < 6; ++c) sz[threadIdx.x >> 5][c] = a[c];
+  for (int k = 0; k < 2; ++k)
+    c2[k] = __fadd_rn(u8 ? b[2 + k] : b[k], __shfl_xor_sync(0xffffffffu, u8 ? b[k] : b[2 + k], 8));
+  float x = __fadd_rn(u4 ? c2[1] : c2[0], __shfl_xor_sync(0xffffffffu, u4 ? c2[0] : c2[1], 4));
+  x = __fadd_rn(x, __shfl_xor_sync(0xffffffffu, x, 2));
+  x = __fadd_rn(x, __shfl_xor_sync(0xffffffffu, x, 1));
+  if ((lane & 3) == 0 && (lane >> 2) < 6) sz[threadIdx.x >> 5][lane >> 2] = x;
 }
 
 // The slots are stored in PCG_DF_REPLICAS copies and block b reads copy
