@@ -95,6 +95,30 @@ def test_gripper_full_run_properties():
     assert np.array_equal(outs[0], outs[1])
 
 
+def test_gripper_graph_branches_match_one_stream():
+    """The CUDA graph runs the local step on a branch beside the spring update
+    and the ray casts; eager launches on one stream (stats=2) run the same
+    kernels in sequence.  Every reduction has a fixed order, so any race
+    between the branches would show as a difference: positions, spring
+    records and every iteration's record must agree bit for bit."""
+    m = synth.config3_gripper()
+    n = 60
+    runs = []
+    for stats in (1, 2):
+        sim = casim.Sim(m, stats=stats)
+        sim.step(n)
+        assert sim.sync() == 0
+        runs.append((sim.positions(), sim.springs(), sim.history()))
+        sim.close()
+    (xa, sa, ha), (xb, sb, hb) = runs
+    assert np.array_equal(xa, xb)
+    for key in ("active", "kind", "face", "bary", "target"):
+        assert np.array_equal(sa[key], sb[key]), key
+    assert len(ha) == len(hb) == n
+    assert ha == hb
+    assert max(h["n_springs"] for h in ha) > 0
+
+
 def _oracle_springs(prep, rec):
     st = osprings.SpringState.empty(prep.query.shape[0])
     assert np.array_equal(rec["verts"], prep.query)
