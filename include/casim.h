@@ -256,12 +256,14 @@ int casim_set_obstacle_mesh(casim_sim* sim, int32_t n_verts, const double* xyz, 
                             const int32_t* tets);
 
 /* Overwrites all vertex positions (host, n_verts*3 doubles, caller order).
-   In MIXED mode the values are rounded to FP32. */
+   In MIXED mode the values are rounded to FP32.  Clears the last step: the
+   next global solve starts from these positions. */
 int casim_set_positions(casim_sim* sim, const double* xyz);
 
 /* Asynchronously restores the rest positions (or the positions of the last
-   casim_set_positions / casim_load_state call) and clears every spring, on the
-   stream, without host copies.  History and counters are kept. */
+   casim_set_positions / casim_load_state call) and clears every spring and
+   the last step, on the stream, without host copies.  History and counters
+   are kept. */
 int casim_reset(casim_sim* sim);
 
 /* Enqueues n_iters outer iterations on the stream (asynchronous).
@@ -341,8 +343,12 @@ int casim_get_history(casim_sim* sim, int32_t cap, casim_iter_record* out, int32
 
 int casim_get_stats(casim_sim* sim, casim_stats* out);
 
-/* Saves / restores positions and spring records (checkpoint / resume).
-   casim_save_state with buf == NULL stores the required size in *len. */
+/* Saves / restores positions and spring records (checkpoint / resume), and
+   the last outer iteration's step x_i - x_(i-1), from which the next global
+   solve of the single-robot MIXED path starts (so a resumed run repeats the
+   uninterrupted one bit for bit).  casim_save_state with buf == NULL stores
+   the required size in *len.  casim_load_state also accepts the earlier
+   layout without the step (the next solve then starts from x_i). */
 int casim_save_state(casim_sim* sim, void* buf, size_t* len);
 int casim_load_state(casim_sim* sim, const void* buf, size_t len);
 

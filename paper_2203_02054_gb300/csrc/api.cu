@@ -238,6 +238,7 @@ struct casim_sim {
   void *r = nullptr, *u = nullptr, *p = nullptr, *s = nullptr, *w = nullptr, *dx = nullptr, *spring_c = nullptr;
   void* pos_out = nullptr;
   void* X0 = nullptr;  // positions restored by casim_reset
+  void* xstep = nullptr;  // the last outer iteration's step per free row (dataflow PCG warm start)
   int4 *tet = nullptr, *faces = nullptr;
   int *inc_ptr = nullptr, *inc = nullptr, *sl_ptr = nullptr, *sl_col = nullptr;
   int *q_verts_d = nullptr, *qf_ptr = nullptr, *qf = nullptr;
@@ -504,6 +505,45 @@ Dev<T> make_dev(casim_sim* sim) {
   return d;
 }
 
+// Forgets the last outer iteration's step: the next solve starts from x_i.
+// Called wherever the positions are set other than by an outer iteration.
+cudaError_t clear_xstep(casim_sim* sim) {
+  if (!sim->xstep) return cudaSuccess;
+  return cudaMemsetAsync(sim->xstep, 0, 4 * sim->rs * (size_t)std::max(sim->n_free, 1), sim->stream);
+}
+
+// The last step in caller order (n_v*3 doubles; zero for fixed vertices and
+// where none is kept): out != NULL reads it from the device, else it is set
+// from in.
+template <typename T>
+int xstep_io(casim_sim* sim, double* out, const double* in) {
+  const int nf = sim->n_free;
+  if (!sim->xstep || nf == 0) {
+    if (out) std::fill(out, out + 3 * (size_t)sim->n_v, 0.0);
+    return CASIM_OK;
+  }
+  std::vector<R4<T>> h(nf);
+  if (out) {
+    CK(cudaStreamSynchronize(sim->stream));
+    CK(cudaMemcpy(h.data(), sim->xstep, sizeof(R4<T>) * nf, cudaMemcpyDeviceToHost));
+    std::fill(out, out + 3 * (size_t)sim->n_v, 0.0);
+    for (int i = 0; i < nf; ++i) {
+      const size_t uv = (size_t)sim->user_of_int[i];
+      out[3 * uv] = (double)h[i].x;
+      out[3 * uv + 1] = (double)h[i].y;
+      out[3 * uv + 2] = (double)h[i].z;
+    }
+  } else {
+    for (int i = 0; i < nf; ++i) {
+      const size_t uv = (size_t)sim->user_of_int[i];
+      h[i] = R4<T>{(T)in[3 * uv], (T)in[3 * uv + 1], (T)in[3 * uv + 2], T(0)};
+    }
+    CK(cudaMemcpyAsync(sim->xstep, h.data(), sizeof(R4<T>) * nf, cudaMemcpyHostToDevice, sim->stream));
+    CK(cudaStreamSynchronize(sim->stream));
+  }
+  return CASIM_OK;
+}
+
 // Copies the obstacle spheres to the device: the FP64 values the tests use and
 // their round-to-nearest FP32 images for the reject test that precedes them.
 cudaError_t upload_spheres(casim_sim* sim) {
@@ -570,7 +610,8 @@ cudaError_t enqueue_iteration(casim_sim* sim, cudaStream_t st, cudaEvent_t* ev, 
   cudaMemsetAsync(reinterpret_cast<char*>(sim->ctrl) + offsetof(Ctrl, abort), 0, 3 * sizeof(int), st);
   Dev<T> dp = d;
   dp.rhs_in_pcg = fused ? 1 : 0;
-  cudaError_t e = sim->pcg_seg  ? launch_pcg_seg<T>(d, sim->seg_blocks, st)
+  dp.xstep = (fused || sim->pcg_seg) ? (R4<T>*)sim->xstep : nullptr;
+  cudaError_t e = sim->pcg_seg  ? launch_pcg_seg<T>(dp, sim->seg_blocks, st)
                   : sim->pcg_cl ? launch_pcg_cluster<T>(d, sim->pcg_clusters, st)
                                 : launch_pcg<T>(dp, sim->pcg_grid, sim->pcg_variant, st);
   if (e != cudaSuccess) return e;
@@ -617,6 +658,10 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   sim->s = sim->dalloc<R4<T>>(n_free);
   sim->w = sim->dalloc<R4<T>>(n_free);
   sim->dx = sim->dalloc<R4<T>>(n_free);
+  // the step that the next solve starts from (MIXED; dataflow and batch PCG)
+  sim->xstep = std::is_same<T, float>::value && (sim->pcg_variant == 5 || sim->pcg_seg)
+                   ? sim->dalloc<R4<T>>(std::max(n_free, 1))
+                   : nullptr;
   sim->spring_c = sim->dalloc<R4<double>>(n_free);
   sim->partials = sim->dalloc<double>(2 * 4 * (size_t)std::max(sim->pcg_grid, 1));
   if (sim->pcg_variant == 5) {
@@ -727,6 +772,7 @@ int upload_typed(casim_sim* sim, const std::vector<double>& rest_int, const std:
   cudaStream_t st = sim->stream;
   CK(cudaMemcpyAsync(sim->X, Xh.data(), sizeof(R4<T>) * n_v, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->X0, Xh.data(), sizeof(R4<T>) * n_v, cudaMemcpyHostToDevice, st));
+  if (sim->xstep) CK(cudaMemsetAsync(sim->xstep, 0, sizeof(R4<T>) * std::max(n_free, 1), st));
   CK(cudaMemcpyAsync(sim->tet, th.data(), sizeof(int4) * n_t, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->Tc, Tch.data(), sizeof(R4<T>) * 3 * (size_t)n_t, cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(sim->tinfo, info.data(), sizeof(R4<T>) * n_t, cudaMemcpyHostToDevice, st));
@@ -858,6 +904,7 @@ int set_positions_typed(casim_sim* sim, const double* xyz) {
     for (int c = 0; c < 3; ++c) sim->X_fixed[3 * (size_t)(i - sim->n_free) + c] = (double)(&Xh[i].x)[c];
   CK(cudaMemcpyAsync(sim->X, Xh.data(), sizeof(R4<T>) * sim->n_v, cudaMemcpyHostToDevice, sim->stream));
   CK(cudaMemcpyAsync(sim->X0, Xh.data(), sizeof(R4<T>) * sim->n_v, cudaMemcpyHostToDevice, sim->stream));
+  CK(clear_xstep(sim));
   return upload_bfix<T>(sim);
 }
 
@@ -1170,9 +1217,15 @@ int forward_ckpt_typed(casim_sim* sim, int n_iters, int every) {
   for (int c = 0; c < n_ckpt; ++c) {
     CK((adj_copy_state<T>(sim, (R4<T>*)A.ckX + c * nv, A.ck_act + c * nq, A.ck_kind + c * nq, A.ck_face + c * nq,
                           A.ck_bary + c * 2 * nq, A.ck_tgt + c * 3 * nq, true)));
+    // every solve of the adjoint's forward pass starts from x_i, so that the
+    // map x_i -> x_(i+1) (and its recomputation in the backward pass) does
+    // not depend on where the checkpoints fall
     const int m = std::min(every, n_iters - done);
-    rc = step_typed<T>(sim, m);
-    if (rc) return rc;
+    for (int j = 0; j < m; ++j) {
+      CK(clear_xstep(sim));
+      rc = step_typed<T>(sim, 1);
+      if (rc) return rc;
+    }
     done += m;
   }
   CK((adj_copy_state<T>(sim, A.finX, A.fin_act, A.fin_kind, A.fin_face, A.fin_bary, A.fin_tgt, true)));
@@ -1215,6 +1268,7 @@ int backward_typed(casim_sim* sim, const double* dL_dX, double* dL_dalpha) {
     // recompute the segment, keeping X_i and the spring decisions of each iteration
     for (int j = 0; j < m; ++j) {
       CK(cudaMemcpyAsync((R4<T>*)A.segX + j * nv, sim->X, sizeof(R4<T>) * nv, cudaMemcpyDeviceToDevice, st));
+      CK(clear_xstep(sim));
       int rc = step_typed<T>(sim, 1);
       if (rc) return rc;
       if (sim->n_q) {
@@ -2086,6 +2140,7 @@ int casim_reset(casim_sim* sim) {
   if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
   const size_t nq = std::max(sim->n_q, 1);
   CK(cudaMemcpyAsync(sim->X, sim->X0, 4 * sim->rs * (size_t)sim->n_v, cudaMemcpyDeviceToDevice, sim->stream));
+  CK(clear_xstep(sim));
   CK(cudaMemsetAsync(sim->spring_c, 0, sizeof(R4<double>) * (size_t)std::max(sim->n_free, 1), sim->stream));
   CK(cudaMemsetAsync(sim->sp.active, 0, sizeof(int) * nq, sim->stream));
   CK(cudaMemsetAsync(sim->sp.kind, 0, sizeof(int) * nq, sim->stream));
@@ -2308,20 +2363,25 @@ int casim_get_stats(casim_sim* sim, casim_stats* out) {
 
 // Checkpoint layout: header (magic, version, precision, n_v, n_q), positions
 // (n_v*3 doubles, caller order), then per spring vertex active, kind, face
-// (int32), bary (2 doubles), target (3 doubles).
+// (int32), bary (2 doubles), target (3 doubles); version 2 appends the last
+// outer iteration's step x_i - x_(i-1) (n_v*3 doubles, caller order, zero
+// where the solver keeps none), from which the next solve starts.  Version 1
+// states load with a zero step.
 namespace {
 struct StateHeader {
   uint32_t magic, version;
   int32_t precision, n_v, n_q, pad;
 };
 const uint32_t kMagic = 0x4d495343u;  // "CSIM"
+
 }  // namespace
 
 int casim_save_state(casim_sim* sim, void* buf, size_t* len) {
   if (!sim || !len) return CASIM_E_INVALID;
   if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
   const size_t nq = sim->n_q;
-  const size_t need = sizeof(StateHeader) + sizeof(double) * 3 * sim->n_v + nq * (3 * sizeof(int32_t) + 5 * sizeof(double));
+  const size_t need =
+      sizeof(StateHeader) + 2 * sizeof(double) * 3 * sim->n_v + nq * (3 * sizeof(int32_t) + 5 * sizeof(double));
   if (!buf) {
     *len = need;
     return CASIM_OK;
@@ -2331,7 +2391,7 @@ int casim_save_state(casim_sim* sim, void* buf, size_t* len) {
     return sim->fail(CASIM_E_CAPACITY, "state buffer too small");
   }
   char* o = static_cast<char*>(buf);
-  StateHeader h{kMagic, 1u, sim->params.precision, sim->n_v, sim->n_q, 0};
+  StateHeader h{kMagic, 2u, sim->params.precision, sim->n_v, sim->n_q, 0};
   std::memcpy(o, &h, sizeof(h));
   o += sizeof(h);
   int rc = casim_get_positions(sim, reinterpret_cast<double*>(o), nullptr);
@@ -2352,6 +2412,11 @@ int casim_save_state(casim_sim* sim, void* buf, size_t* len) {
     std::memcpy(o + 28, &tgt[3 * q], 24);
     o += 52;
   }
+  std::vector<double> step(3 * (size_t)sim->n_v);
+  rc = sim->params.precision == CASIM_FP64 ? xstep_io<double>(sim, step.data(), nullptr)
+                                           : xstep_io<float>(sim, step.data(), nullptr);
+  if (rc) return rc;
+  std::memcpy(o, step.data(), sizeof(double) * step.size());
   *len = need;
   return CASIM_OK;
 }
@@ -2360,13 +2425,15 @@ int casim_load_state(casim_sim* sim, const void* buf, size_t len) {
   if (!sim || !buf) return CASIM_E_INVALID;
   if (!sim->has_mesh) return sim->fail(CASIM_E_STATE, "no mesh uploaded");
   const size_t nq = sim->n_q;
-  const size_t need = sizeof(StateHeader) + sizeof(double) * 3 * sim->n_v + nq * 52;
-  if (len < need) return sim->fail(CASIM_E_INVALID, "state buffer too short");
+  const size_t need1 = sizeof(StateHeader) + sizeof(double) * 3 * sim->n_v + nq * 52;
+  if (len < need1) return sim->fail(CASIM_E_INVALID, "state buffer too short");
   const char* o = static_cast<const char*>(buf);
   StateHeader h;
   std::memcpy(&h, o, sizeof(h));
-  if (h.magic != kMagic || h.version != 1u || h.n_v != sim->n_v || h.n_q != sim->n_q)
+  if (h.magic != kMagic || (h.version != 1u && h.version != 2u) || h.n_v != sim->n_v || h.n_q != sim->n_q)
     return sim->fail(CASIM_E_INVALID, "state does not match this mesh");
+  if (h.version == 2u && len < need1 + sizeof(double) * 3 * sim->n_v)
+    return sim->fail(CASIM_E_INVALID, "state buffer too short");
   o += sizeof(h);
   std::vector<double> X(3 * (size_t)sim->n_v);
   std::memcpy(X.data(), o, sizeof(double) * X.size());
@@ -2387,7 +2454,12 @@ int casim_load_state(casim_sim* sim, const void* buf, size_t len) {
     verts[q] = sim->user_of_int[sim->q_verts[q]];
     o += 52;
   }
-  return casim_set_springs(sim, (int64_t)nq, verts.data(), act.data(), kind.data(), face.data(), bary.data(), tgt.data());
+  rc = casim_set_springs(sim, (int64_t)nq, verts.data(), act.data(), kind.data(), face.data(), bary.data(), tgt.data());
+  if (rc || h.version < 2u) return rc;  // a version 1 state keeps the zero step set by casim_set_positions
+  std::vector<double> step(3 * (size_t)sim->n_v);
+  std::memcpy(step.data(), o, sizeof(double) * step.size());
+  return sim->params.precision == CASIM_FP64 ? xstep_io<double>(sim, nullptr, step.data())
+                                             : xstep_io<float>(sim, nullptr, step.data());
 }
 
 int casim_get_sizes(casim_sim* sim, int32_t* n_verts, int32_t* n_tets, int32_t* n_free, int32_t* n_boundary_faces,
@@ -2729,6 +2801,7 @@ int step_anderson_typed(casim_sim* sim, int n_iters, int m, casim_aa_record* rec
         r.proposed = 1;
         if (ea < ep) {
           CK(cudaMemcpyAsync(sim->X, A.xa, row * nf, cudaMemcpyDeviceToDevice, st));
+          CK(clear_xstep(sim));  // the accepted proposal is not the last solve's end point
           r.accepted = 1;
           ++accepted;
         }

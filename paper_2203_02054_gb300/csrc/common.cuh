@@ -149,6 +149,8 @@ struct Dev {
   R4<T>* s;
   R4<T>* w;
   R4<T>* dx;             // PCG correction (streaming kernel)
+  R4<T>* xstep;          // dataflow PCG of an outer iteration: x_i - x_(i-1) per free row; the solve starts
+                         //   from x_i + xstep instead of x_i (null: from x_i)
   double* partials;      // 2 x 4 x pcg grid
   unsigned long long* df_u;  // dataflow PCG: 2 x n_free x 2 epoch-tagged words of u
   unsigned long long* df_p;  // dataflow PCG: 2 x (grid + 1) x 4 epoch-tagged partial words

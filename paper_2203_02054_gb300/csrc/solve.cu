@@ -770,16 +770,35 @@ __device__ __forceinline__ void write_pcg_record(const Ctrl* c, IterRec* hist, i
 
 // r_i = b_i - (A x)_i in FP64 and ||b_i||^2, ||r_i||^2 (the first residual of
 // the correction form; X is read-only while it is formed).
+// The solve's starting point for free row i: x_i, plus the last outer
+// iteration's step x_i - x_(i-1) where one is kept (an outer iteration's
+// solve in MIXED mode; null otherwise).  The local-global iteration
+// approaches its fixed point along a slowly turning direction, so
+// x_i + (x_i - x_(i-1)) is a closer guess for x_(i+1) than x_i: the solve
+// still stops at the same relative residual, from a smaller first one.  The
+// same rounded sums in every row that reads it.
+template <typename T>
+__device__ __forceinline__ R4<T> warm_start(const Dev<T>& d, int i, R4<T> xi) {
+  if (d.xstep) {
+    const R4<T> s = d.xstep[i];
+    xi.x += s.x;
+    xi.y += s.y;
+    xi.z += s.z;
+  }
+  return xi;
+}
+
 template <typename T>
 __device__ __forceinline__ void residual_row_f64(const Dev<T>& d, int i, T dg, double (&rv)[3], double (&a0)[2],
                                                  const R4<double>* b_in = nullptr) {
-  const R4<T> xi = d.X[i];
+  const R4<T> xi = warm_start(d, i, d.X[i]);
   double ax = (double)dg * xi.x, ay = (double)dg * xi.y, az = (double)dg * xi.z;
   const int sl = i >> 5, lane = i & 31;
   const int k1 = d.sl_ptr[sl + 1];
   for (int k = d.sl_ptr[sl] + lane; k < k1; k += 32) {
     const double a = (double)d.sl_val[k];
-    const R4<T> xc = d.X[chk_idx(d.ctrl, d.sl_col[k], d.n_v)];
+    const int col = chk_idx(d.ctrl, d.sl_col[k], d.n_free);
+    const R4<T> xc = warm_start(d, col, d.X[col]);
     ax += a * xc.x;
     ay += a * xc.y;
     az += a * xc.z;
@@ -818,6 +837,7 @@ __device__ __forceinline__ void rhs_residual_row_dw(const Dev<float>& d, int i, 
   const double km = d.k_spring * sc.w;
   const R4<double> bf = d.bfix[i];
   const R4<float> xi = d.X[i];
+  const R4<float> xs = warm_start(d, i, xi);  // the solve's starting point
   dg = d.diagL[i] + (float)km;
   DW es{0.0f, 0.0f};
   if (km != 0.0) {
@@ -831,15 +851,16 @@ __device__ __forceinline__ void rhs_residual_row_dw(const Dev<float>& d, int i, 
     for (int c = 0; c < 3; ++c) b[c] = dw_add_sloppy(dw_norm(b[c]), dw_neg(dw_from(fv[c])));
   }
   DW ax[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
-  dw_acc_prod(ax[0], dg, xi.x);
-  dw_acc_prod(ax[1], dg, xi.y);
-  dw_acc_prod(ax[2], dg, xi.z);
+  dw_acc_prod(ax[0], dg, xs.x);
+  dw_acc_prod(ax[1], dg, xs.y);
+  dw_acc_prod(ax[2], dg, xs.z);
   const int sl = i >> 5, ln = i & 31;
   const int base = d.sl_ptr[sl];
 #pragma unroll
   for (int j = 0; j < MAXW; ++j) {
     if (j < width) {
-      const R4<float> xc = d.X[chk_idx(d.ctrl, d.sl_col[base + j * 32 + ln], d.n_v)];
+      const int col = chk_idx(d.ctrl, d.sl_col[base + j * 32 + ln], d.n_free);
+      const R4<float> xc = warm_start(d, col, d.X[col]);
       dw_acc_prod(ax[0], val[j], xc.x);
       dw_acc_prod(ax[1], val[j], xc.y);
       dw_acc_prod(ax[2], val[j], xc.z);
@@ -1952,9 +1973,13 @@ __global__ void __launch_bounds__(ROWS, 1) k_pcg_df(Dev<float> d) {
       if (i == 0) set_status(d.ctrl, ST_PCG_MAXIT);
     }
     if (act) {
-      R4<float> t = d.X[i];
+      // x_(i+1) = start + correction; the step x_(i+1) - x_i is kept for the
+      // next outer iteration's start
+      const R4<float> x0 = d.X[i];
+      R4<float> t = warm_start(d, i, x0);
       t.x += dd[0]; t.y += dd[1]; t.z += dd[2];
       d.X[i] = t;
+      if (d.xstep) d.xstep[i] = R4<float>{t.x - x0.x, t.y - x0.y, t.z - x0.z, 0.0f};
     }
   }
   if (blockIdx.x == 0) {
@@ -2325,10 +2350,13 @@ __global__ void __launch_bounds__(PCG_SEG_THREADS, 4) k_pcg_seg(Dev<T> d) {
     set_status(d.ctrl, ST_PCG_MAXIT);
   }
   for (int i = lo + (int)threadIdx.x; i < hi; i += blockDim.x) {
-    R4<T> xi = X[i];
+    // x_(i+1) = start + correction; the step is kept for the next start
+    const R4<T> x0 = X[i];
+    R4<T> xi = warm_start(d, i, x0);
     const R4<T> di = dx[i];
     xi.x += di.x; xi.y += di.y; xi.z += di.z;
     X[i] = xi;
+    if (d.xstep) d.xstep[i] = R4<T>{xi.x - x0.x, xi.y - x0.y, xi.z - x0.z, T(0)};
   }
   if (lead) {
     IterRec* rec = d.hist + (d.ctrl->iter % d.hist_cap);
