@@ -201,9 +201,6 @@ __device__ __forceinline__ void block_sums(A (&v)[NV], double* sh, double (&bs)[
   }
 }
 
-// Block sums of NV per-thread double words by fixed shuffle trees of sloppy
-// double-word additions; the double-word result is valid in lane 0 of warp 0.
-// Contains one __syncthreads; sh holds at least 32 * NV doubles.
 // Warp sums of NV <= 4 double words by one butterfly that halves the values
 // each lane carries at every level (a warp reduce-scatter): lanes exchange
 // the half they give up at distance 16, then 8 (NV > 2), and every lane then
@@ -241,6 +238,10 @@ __device__ __forceinline__ DW warp_sums_dw_rs(const DW (&v)[NV]) {
   }
 }
 
+// Block sums of NV per-thread double words by fixed trees of sloppy
+// double-word additions (the warp butterfly above, then warp 0 over the
+// warps' sums); the double-word result is valid in lane 0 of warp 0.
+// Contains one __syncthreads; sh holds at least 32 * NV doubles.
 template <int NV, int NW>
 __device__ __forceinline__ void block_sums_dw(DW (&v)[NV], double* sh, DW (&bs)[NV]) {
   static_assert(NW >= 1 && NW <= 32, "at most 32 warps per block");
@@ -768,8 +769,6 @@ __device__ __forceinline__ void write_pcg_record(const Ctrl* c, IterRec* hist, i
   rec->pcg_rel_residual = bb > 0.0 ? sqrt(rr / bb) : 0.0;
 }
 
-// r_i = b_i - (A x)_i in FP64 and ||b_i||^2, ||r_i||^2 (the first residual of
-// the correction form; X is read-only while it is formed).
 // The solve's starting point for free row i: x_i, plus the last outer
 // iteration's step x_i - x_(i-1) where one is kept (an outer iteration's
 // solve in MIXED mode; null otherwise).  The local-global iteration
@@ -788,6 +787,9 @@ __device__ __forceinline__ R4<T> warm_start(const Dev<T>& d, int i, R4<T> xi) {
   return xi;
 }
 
+// r_i = b_i - (A x)_i in FP64, x the solve's starting point, and ||b_i||^2,
+// ||r_i||^2 (the first residual of the correction form; X is read-only while
+// it is formed).
 template <typename T>
 __device__ __forceinline__ void residual_row_f64(const Dev<T>& d, int i, T dg, double (&rv)[3], double (&a0)[2],
                                                  const R4<double>* b_in = nullptr) {
