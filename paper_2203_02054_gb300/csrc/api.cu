@@ -238,7 +238,7 @@ struct casim_sim {
   void *r = nullptr, *u = nullptr, *p = nullptr, *s = nullptr, *w = nullptr, *dx = nullptr, *spring_c = nullptr;
   void* pos_out = nullptr;
   void* X0 = nullptr;  // positions restored by casim_reset
-  void* xstep = nullptr;  // the last outer iteration's step per free row (dataflow PCG warm start)
+  void* xstep = nullptr;  // the last outer iteration's step per free row (MIXED warm start of the dataflow and batch PCG)
   int4 *tet = nullptr, *faces = nullptr;
   int *inc_ptr = nullptr, *inc = nullptr, *sl_ptr = nullptr, *sl_col = nullptr;
   int *q_verts_d = nullptr, *qf_ptr = nullptr, *qf = nullptr;
